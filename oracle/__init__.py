@@ -1,0 +1,29 @@
+"""FP64 CPU oracle for one Hessian-free ray-Born frequency-set update.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously-correct
+reference that the CUDA library is checked against.  Only the tests, the
+smoke check and the CPU-baseline timing of ``bench.py`` may import it; the
+product path never does, and it shares no code with the CUDA library.
+
+It follows the paper's statement of the problem step by step, in double
+precision:
+
+* geometry.py - ring, pixels and support (Sec. 4 acquisition);
+* fields.py   - sound-speed derivative grids and bilinear sampling;
+* rays.py     - ray fans: Eikonal characteristics and dynamic ray tracing
+                (Eqs. 6-7), in the C file rb_oracle.c;
+* grid.py     - first-arrival gridding of the fans onto pixels;
+* green.py    - high-frequency 2-D Green's function (Eqs. 4-5) with
+                absorption and power-law dispersion;
+* link.py     - ray linking to receivers: the ray-model data p(c) of Eq. 8;
+* born.py     - Born forward operator, its adjoint and the Gauss-Newton
+                Hessian diagonal (the linearisation of Eqs. 9-10);
+* update.py   - data weighting (75 % receiver mask, 1 % outlier zeroing),
+                the diagonal one-step update and the frequency sweep.
+
+Parity status: every function is pinned by tests under tests/test_oracle_*.py
+against closed forms, library routines or brute force, except the sweep
+(update.sweep), whose end result has no printed value to match: parity
+unpinned against the paper; it is checked only as GPU-vs-oracle and by the
+smoke property that the update norm falls across frequency sets.
+"""

@@ -1,0 +1,99 @@
+"""Acquisition configurations (ring, grid, fan and frequency schedule).
+
+Three workloads, named for what they are:
+
+* ``tiny``      — 64-element ring of radius 50 mm, 64x64 grid at 1.6 mm,
+                  64 rays per emitter, 0.3/0.4/0.5 MHz as three sets of one.
+* ``breast256`` — 256-element ring of radius 110 mm, 256x256 grid at 0.9 mm,
+                  256 rays per emitter, 12 frequencies 0.3-1.0 MHz in 4 sets of 3.
+* ``breast512`` — same ring, 512x512 grid at 0.45 mm, 256 rays per emitter,
+                  20 frequencies 0.3-1.25 MHz in 5 sets of 4.
+
+The ring of 256 elements with an 11 cm radius, the 1480 m/s water speed and
+the low-to-high sweep over sets of consecutive frequencies are the paper's
+in-vitro acquisition (Sec. 4.1); the grid pitches and frequency counts are
+synthetic workload choices.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Tuple
+
+
+@dataclasses.dataclass(frozen=True)
+class Config:
+    name: str
+    n_elem: int            # ring elements; each is emitter and receiver
+    ring_radius: float     # [m]
+    nx: int
+    ny: int
+    h: float               # pixel pitch [m]
+    n_rays: int            # rays per emitter fan
+    freqs_hz: Tuple[float, ...]
+    sets: Tuple[Tuple[int, ...], ...]   # indices into freqs_hz, low -> high
+    power_y: float         # absorption power-law exponent
+    c_water: float = 1480.0
+    seed: int = 20251116
+    kind: str = "ellipses"  # phantom family: "ellipses" or "breast"
+
+    @property
+    def npix(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def ds(self) -> float:
+        """Ray step: half a pixel."""
+        return self.h / 2.0
+
+    @property
+    def max_steps(self) -> int:
+        return int(math.ceil(4.0 * self.ring_radius / self.ds))
+
+    @property
+    def support_margin(self) -> float:
+        return max(2e-3, 2.0 * self.h)
+
+    def set_freqs(self, j: int) -> List[float]:
+        return [self.freqs_hz[i] for i in self.sets[j]]
+
+
+def _sets(n: int, per: int) -> Tuple[Tuple[int, ...], ...]:
+    return tuple(tuple(range(k, k + per)) for k in range(0, n, per))
+
+
+def _linspace_hz(lo_mhz: float, hi_mhz: float, n: int) -> Tuple[float, ...]:
+    if n == 1:
+        return (lo_mhz * 1e6,)
+    return tuple((lo_mhz + (hi_mhz - lo_mhz) * k / (n - 1)) * 1e6 for k in range(n))
+
+
+def tiny(**kw) -> Config:
+    base = dict(name="tiny", n_elem=64, ring_radius=0.050, nx=64, ny=64, h=1.6e-3, n_rays=64,
+                freqs_hz=(0.3e6, 0.4e6, 0.5e6), sets=((0,), (1,), (2,)), power_y=1.0,
+                seed=20251116 + 0, kind="ellipses")
+    base.update(kw)
+    return Config(**base)
+
+
+def breast256(**kw) -> Config:
+    f = _linspace_hz(0.3, 1.0, 12)
+    base = dict(name="breast256", n_elem=256, ring_radius=0.110, nx=256, ny=256, h=0.9e-3, n_rays=256,
+                freqs_hz=f, sets=_sets(12, 3), power_y=1.1, seed=20251116 + 1, kind="breast")
+    base.update(kw)
+    return Config(**base)
+
+
+def breast512(**kw) -> Config:
+    f = _linspace_hz(0.3, 1.25, 20)
+    base = dict(name="breast512", n_elem=256, ring_radius=0.110, nx=512, ny=512, h=0.45e-3, n_rays=256,
+                freqs_hz=f, sets=_sets(20, 4), power_y=1.1, seed=20251116 + 2, kind="breast")
+    base.update(kw)
+    return Config(**base)
+
+
+CONFIGS = {"tiny": tiny, "breast256": breast256, "breast512": breast512}
+
+
+def config_by_name(name: str, **kw) -> Config:
+    return CONFIGS[name](**kw)

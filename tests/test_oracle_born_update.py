@@ -1,0 +1,142 @@
+"""Pins for the oracle's Born operators, data weights and one-step update (CPU only).
+
+* Adjoint identity <B m, S> = <m, B* S> to 1e-12 for complex m and data.
+* Brute force on small grids: B applied to every unit vector gives
+  w^2 G_e(x_j) G_r(x_j); the Hessian diagonal equals ||W^(1/2) B e_j||^2; the
+  gradient equals central finite differences of 1/2 ||W^(1/2)(B m + R)||^2.
+* One-step update on a single-pixel support with eps = 0 equals the
+  least-squares solution (numpy.linalg.lstsq) of that 1-unknown problem.
+* Outlier zeroing: invariants of a top-k selection and its tie rule.
+* Sweep smoke (no printed values exist to match): the update norm is finite
+  and the error to the true phantom falls on noise-free data.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import rbgen
+from oracle import born, geometry, green, grid, update
+
+
+def _small_problem(n_elem=12, n=10, seed=3):
+    rng = np.random.default_rng(seed)
+    G = (rng.standard_normal((n_elem, n * n)) + 1j * rng.standard_normal((n_elem, n * n))) * 1e-2
+    return rng, G
+
+
+def test_adjoint_identity_complex():
+    rng, G = _small_problem()
+    f = 0.4e6
+    m = rng.standard_normal(G.shape[1]) + 1j * rng.standard_normal(G.shape[1])
+    S = rng.standard_normal((12, 12)) + 1j * rng.standard_normal((12, 12))
+    lhs = np.vdot(born.born_forward(G, m, f), S)                  # <B m, S>
+    rhs = np.vdot(m, born.born_adjoint(G, S, f))                  # <m, B* S>
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_adjoint_identity_real_m_on_ray_tables():
+    cfg = rbgen.tiny()
+    g = geometry.from_config(cfg)
+    inp = rbgen.make_inputs(cfg)
+    tabs = grid.grid(g, inp.c_init, inp.alpha0)
+    G = green.green(g, tabs, inp.c_init, 0.4e6)
+    rng = np.random.default_rng(0)
+    m = rng.standard_normal(g.npix)
+    S = rng.standard_normal((g.n_elem, g.n_elem)) + 1j * rng.standard_normal((g.n_elem, g.n_elem))
+    lhs = np.real(np.vdot(born.born_forward(G, m, 0.4e6), S))
+    rhs = float(m @ np.real(born.born_adjoint(G, S, 0.4e6)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_brute_force_columns_hessian_and_gradient():
+    rng, G = _small_problem(n_elem=8, n=8)
+    f = 0.3e6
+    w = 2 * math.pi * f
+    npix = G.shape[1]
+    W = (rng.uniform(size=(8, 8)) > 0.3).astype(np.uint8)
+    R = rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8))
+    Bcols = []
+    for j in range(npix):
+        e = np.zeros(npix)
+        e[j] = 1.0
+        d = born.born_forward(G, e, f)
+        assert np.allclose(d, w * w * np.outer(G[:, j], G[:, j]), rtol=1e-13, atol=0)
+        Bcols.append(d)
+    H = born.hess_diag(G, W, f)
+    Hb = np.array([np.sum(W * np.abs(b) ** 2) for b in Bcols])
+    assert np.allclose(H, Hb, rtol=1e-12)
+    # gradient of F(m) = 1/2 sum W |R + B m|^2 at m = 0 by central differences
+    gr = np.real(born.born_adjoint(G, W * R, f))
+    F = lambda m: 0.5 * np.sum(W * np.abs(R + born.born_forward(G, m, f)) ** 2)
+    hstep = 1e-3 / (w * w * 1e-4)
+    for j in (0, 17, 40, 63):
+        e = np.zeros(npix)
+        e[j] = hstep
+        fd = (F(e) - F(-e)) / (2 * hstep)
+        assert abs(fd - gr[j]) <= 1e-7 * (abs(gr[j]) + 1e-30) + 1e-9 * np.max(np.abs(gr))
+
+
+def test_one_step_single_pixel_equals_least_squares():
+    cfg = rbgen.tiny()
+    # margin so large that the support holds the 4 central pixels only
+    g = geometry.from_config(cfg, support_margin=cfg.ring_radius - 1.2 * cfg.h)
+    sup = geometry.support_mask(g).ravel()
+    assert 1 <= sup.sum() <= 4
+    inp = rbgen.make_inputs(cfg)
+    rng = np.random.default_rng(5)
+    fr = [0.3e6, 0.35e6]
+    p_obs = 0.01 * (rng.standard_normal((2, g.n_elem, g.n_elem)) + 1j * rng.standard_normal((2, g.n_elem, g.n_elem)))
+    r = update.hf_update(g, inp.c_init, inp.alpha0, fr, p_obs, outlier_frac=0.0, eps_rel=0.0, step="diag")
+    # least squares for each support pixel alone: min_dm sum_w ||W^(1/2) (R_w + b_w dm)||^2
+    tabs = grid.grid(g, inp.c_init, inp.alpha0)
+    for j in np.flatnonzero(sup):
+        rows, rhs = [], []
+        for k, f in enumerate(fr):
+            G = green.green(g, tabs, inp.c_init, f)
+            b = (2 * math.pi * f) ** 2 * np.outer(G[:, j], G[:, j])
+            sw = np.sqrt(r.W[k].astype(float))
+            rows += [(sw * b).real.ravel(), (sw * b).imag.ravel()]
+            rhs += [-(sw * r.R[k]).real.ravel(), -(sw * r.R[k]).imag.ravel()]
+        A = np.concatenate(rows)[:, None]
+        y = np.concatenate(rhs)
+        dm_ls = np.linalg.lstsq(A, y, rcond=None)[0][0]
+        dm = r.dc.ravel()[j] * (-2 * g.h * g.h) / np.asarray(inp.c_init, float).ravel()[j] ** 3
+        # with several support pixels the diagonal step for pixel j is still that pixel's
+        # own least-squares solution (off-diagonal couplings are ignored by construction)
+        assert abs(dm - dm_ls) <= 1e-10 * abs(dm_ls)
+
+
+def test_outlier_selection_invariants_and_ties():
+    rng = np.random.default_rng(11)
+    base = rng.uniform(size=(3, 16, 16)) > 0.2
+    R = rng.standard_normal((3, 16, 16)) + 1j * rng.standard_normal((3, 16, 16))
+    W, n, k = update.outlier_weights(base, R, 0.05)
+    assert n == base.sum() and k == int(math.floor(0.05 * n))
+    zeroed = base & (W == 0)
+    assert zeroed.sum() == k
+    kept = base & (W == 1)
+    assert np.abs(R[zeroed]).min() >= np.abs(R[kept]).max()
+    # ties: equal magnitudes go by smallest flat index
+    R2 = np.ones((2, 4, 4), dtype=complex)
+    b2 = np.ones((2, 4, 4), dtype=bool)
+    W2, n2, k2 = update.outlier_weights(b2, R2, 0.1)
+    assert k2 == 3
+    assert list(np.flatnonzero(W2.ravel() == 0)) == [0, 1, 2]
+
+
+@pytest.mark.parametrize("step", ["exact", "diag"])
+def test_sweep_smoke_noise_free(step):
+    cfg = rbgen.tiny()
+    g = geometry.from_config(cfg)
+    inp = rbgen.make_inputs(cfg)
+    p = update.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, cfg.freqs_hz, level=0.0)
+    sup = geometry.support_mask(g)
+    e0 = np.sqrt(np.mean((inp.c_init.astype(float) - inp.c_true)[sup] ** 2))
+    r = update.hf_update(g, inp.c_init, inp.alpha0, [cfg.freqs_hz[0]], p[[0]], 0.0, 1e-3, step)
+    assert np.isfinite(r.dc_norm)
+    e1 = np.sqrt(np.mean((r.c_new - inp.c_true)[sup] ** 2))
+    corr = np.sum(r.dc[sup] * (inp.c_true - inp.c_init)[sup])
+    assert corr > 0          # the step points toward the truth
+    if step == "exact":
+        assert e1 < e0
