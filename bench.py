@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: ray-Born updates/s on the 256-element ring, 512x512 grid (breast phantom).
+
+One step = one ``rb_hf_update`` on one frequency set of 4 frequencies: field
+prep, fused ray fans + gridding, ray linking + residuals + data weights, Born
+adjoint + Hessian diagonal over the set, the step's line search (Born forward
+of the direction over the set) and the update of c.  Sets are taken in sweep
+order, c evolving; after the last set c is restored from a device copy
+(outside the timed kernels, inside the wall-clock bracket: a 1 MB copy).
+
+Prints one JSON line (see the keys below).  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import rbgen  # noqa: E402
+
+WORKLOAD = "breast512"
+METRIC = "ray-Born updates/s, 256-el ring 512² grid, mixed vs plain FP32; p50/p99 ms"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rb_clocks_{os.getpid()}.csv")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in rows])), "sm_max_mhz": rows[0]["smax"],
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def algorithmic_work(cfg, n_freq):
+    """Per-update algorithmic work of the stages (FLOP or bytes), documented in the design doc."""
+    ne, npix = cfg.n_elem, cfg.nx * cfg.ny
+    adj_flop = n_freq * (8.0 * ne * ne * npix + 2.0 * ne * ne * npix + 10.0 * ne * npix)
+    fwd_flop = n_freq * 8.0 * ne * ne * npix
+    table_bytes = ne * npix * 16.0
+    return dict(adjoint_flop=adj_flop, forward_flop=fwd_flop, trace_grid_bytes=table_bytes)
+
+
+def run_ours(args):
+    import torch
+    from paper_2511_16633_gb300 import rb
+    from paper_2511_16633_gb300.recon import synth_data
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = rb.RB_PREC_FP32 if args.prec == "fp32" else rb.RB_PREC_BF16X3
+
+    cfg = rbgen.breast512()
+    inp = rbgen.make_inputs(cfg)
+    geom = rb.geometry_from_config(cfg)
+    c0 = torch.as_tensor(inp.c_init, device=dev).contiguous()
+    a0 = torch.as_tensor(inp.alpha0, device=dev).contiguous()
+    ct = torch.as_tensor(inp.c_true, device=dev).contiguous()
+    p_obs = synth_data(geom, c0, ct, a0, list(cfg.freqs_hz), inp.noise_re, inp.noise_im, 0.01)
+    nsets = len(cfg.sets)
+    nf = max(len(s) for s in cfg.sets)
+    ws = rb.workspace(geom, nf, prec, dev)
+    c = c0.clone()
+    dc = torch.empty_like(c)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    nst = len(rb.STAGES)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)]
+    for e in evs:
+        e.record(stream)
+    ev_arr = rb.stage_event_array(evs)
+
+    def step(k, events=None):
+        j = k % nsets
+        if j == 0:
+            c.copy_(c0)
+        s = cfg.sets[j]
+        freqs = [cfg.freqs_hz[i] for i in s]
+        rb.rb_hf_update(geom, c, a0, freqs, p_obs[s[0]:s[-1] + 1], ws, 0.01, 1e-3, rb.RB_STEP_EXACT, prec, dc, diag,
+                        stream, events)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, per-step events + per-stage events
+    per_step = []
+    stage_ms = np.zeros(nst)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        step(args.warmup + k, ev_arr)
+        ends[k].record(stream)
+        # stage events are reused every step: read them back after this step completes
+        ends[k].synchronize()
+        for s_ in range(nst):
+            stage_ms[s_] += evs[2 * s_].elapsed_time(evs[2 * s_ + 1])
+    g1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    dev_ms = g0.elapsed_time(g1)
+    per_step = np.array([starts[k].elapsed_time(ends[k]) for k in range(args.steps)])
+    ms = float(np.sum(per_step))
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+    d = rb.decode_diag(diag)
+
+    # end to end: pinned host data in, c and diagnostics out, every step
+    host_p = torch.empty(p_obs.shape, dtype=p_obs.dtype, pin_memory=True)
+    host_p.copy_(p_obs.cpu())
+    host_c = torch.empty(c.shape, dtype=c.dtype, pin_memory=True)
+    host_diag = torch.empty(48, dtype=torch.uint8, pin_memory=True)
+    dev_p = torch.empty((nf,) + tuple(p_obs.shape[1:]), dtype=p_obs.dtype, device=dev)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for k in range(e2e_steps):
+        j = k % nsets
+        if j == 0:
+            c.copy_(c0)
+        s = cfg.sets[j]
+        dev_p[:len(s)].copy_(host_p[s[0]:s[-1] + 1], non_blocking=True)
+        rb.rb_hf_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], dev_p[:len(s)], ws, 0.01, 1e-3, rb.RB_STEP_EXACT,
+                        prec, dc, diag, stream)
+        host_c.copy_(c, non_blocking=True)
+        host_diag.copy_(diag, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    te = time.perf_counter() - te0
+    h2d = int(nf * p_obs.shape[1] * p_obs.shape[2] * 8)
+    d2h = int(c.numel() * 4 + 48)
+
+    peaks, peak_src = _peaks()
+    work = algorithmic_work(cfg, nf)
+    st = {name: stage_ms[i] / args.steps for i, name in enumerate(rb.STAGES)}
+    dominant = max(st, key=st.get)
+    clock_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s at max SM clock
+    if dominant == "adjoint":
+        ach = work["adjoint_flop"] / (st["adjoint"] / 1e3) / 1e12
+        roof = {"kernel": "adjoint+hessian (k_adjoint_simt)", "bound": "alu", "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    elif dominant == "forward":
+        ach = work["forward_flop"] / (st["forward"] / 1e3) / 1e12
+        roof = {"kernel": "born forward (k_forward_simt)", "bound": "alu", "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        ach = work["trace_grid_bytes"] / (st["trace_grid"] / 1e3) / 1e9
+        roof = {"kernel": "fused ray fans + gridding (k_trace)", "bound": "hbm", "achieved": ach,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peak_src}
+    launches_per_step = 23 if prec == rb.RB_PREC_FP32 else 23
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == rb.RB_PREC_FP32 else "bf16x3",
+        "data": "synthetic (seeded breast phantom; data from the library's own ray-Born forward model + 1% noise)",
+        "config": {"workload": WORKLOAD, "n_elem": cfg.n_elem, "grid": [cfg.nx, cfg.ny], "h_m": cfg.h,
+                   "n_rays": cfg.n_rays, "freqs_per_set": nf, "n_sets": nsets, "precision": args.prec,
+                   "step_mode": "exact", "l2": "working set (1.1 GB tables) larger than L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
+        "stage_ms": {k: round(v, 4) for k, v in st.items()},
+        "device_ms_total": dev_ms, "wall_s": wall,
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": e2e_steps / te, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "diag_last": {k: d[k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sample_fans=args.cpu_fans, sample_pix=args.cpu_pix)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(sample_fans=32, sample_pix=32768, seed=0):
+    """The FP64 oracle, as it stands, on a bounded sample of one breast512 update, scaled to updates/s.
+
+    Sample: (a) rays + gridding of `sample_fans` of the 256 fans (an element subset of the same ring
+    and grid, same work per fan), scaled by 256/sample_fans; (b) Green's functions, Born adjoint,
+    Hessian diagonal and Born forward at one frequency on `sample_pix` of the 262144 pixels, scaled by
+    the pixel ratio and the 4 frequencies of a set."""
+    from oracle import born, geometry, green, grid
+    cfg = rbgen.breast512()
+    inp = rbgen.make_inputs(cfg)
+    g = geometry.from_config(cfg)
+    gs = geometry.from_config(cfg, n_elem=sample_fans)
+    t0 = time.perf_counter()
+    grid.grid_pixels(gs, inp.c_init, inp.alpha0, np.arange(16))
+    t_rays = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    sup = np.flatnonzero(geometry.support_mask(g).ravel())
+    pix = np.sort(rng.choice(sup, sample_pix, replace=False))
+    # tables at the sampled pixels for all fans (not timed: it repeats the timed ray work above)
+    tabs = grid.grid_pixels(g, inp.c_init, inp.alpha0, pix)
+    f = cfg.freqs_hz[10]
+    S = rng.standard_normal((g.n_elem, g.n_elem)) + 1j * rng.standard_normal((g.n_elem, g.n_elem))
+    W = (rng.uniform(size=S.shape) > 0.25).astype(np.uint8)
+    t1 = time.perf_counter()
+    G = green.green(g, tabs, inp.c_init, f, pix=pix)
+    born.born_adjoint(G, W * S, f)
+    born.hess_diag(G, W, f)
+    born.born_forward(G, rng.standard_normal(pix.size), f)
+    t_born = time.perf_counter() - t1
+    nf = len(cfg.sets[0])
+    per_update = t_rays * (cfg.n_elem / sample_fans) + t_born * (g.npix / sample_pix) * nf
+    return {"value": 1.0 / per_update, "unit": "updates/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"rays+gridding of {sample_fans}/256 fans ({t_rays:.2f} s) and G+adjoint+Hessian+forward on "
+                      f"{sample_pix}/262144 pixels at 1 of 4 frequencies ({t_born:.2f} s), scaled to one update",
+            "seconds_per_update_est": per_update}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(sample_fans=args.cpu_fans, sample_pix=args.cpu_pix, seed=k)
+        if k >= args.warmup:
+            vals.append(cb["seconds_per_update_est"])
+    v = 1.0 / float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_elem": 256, "grid": [512, 512]},
+            "cpu_baseline": {"value": v, "unit": "updates/s", "cores": _cores(), "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--cpu-fans", type=int, default=32)
+    ap.add_argument("--cpu-pix", type=int, default=32768)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -58,5 +58,7 @@ def lib():
         L.orc_trace_endpoints.restype = ctypes.c_int
         L.orc_grid.argtypes = [ctypes.POINTER(OrcGeom), P, ctypes.c_int64, P]
         L.orc_grid.restype = ctypes.c_int
+        L.orc_grid_pixels.argtypes = [ctypes.POINTER(OrcGeom), P, ctypes.c_int64, P, ctypes.c_int64, P]
+        L.orc_grid_pixels.restype = ctypes.c_int
         _lib = L
     return _lib

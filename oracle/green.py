@@ -65,13 +65,14 @@ def gridded_traveltime(g: Geom, tables) -> np.ndarray:
 
 
 def green(g: Geom, tables, c: np.ndarray, f_hz: float, pix=None) -> np.ndarray:
-    """G[n_elem, npix] complex128 (or [n_elem, len(pix)] for a pixel subset); zero at holes."""
+    """G[n_elem, npix] complex128 from full tables; or, with pix, G[n_elem, len(pix)] at those flat
+    pixel indices from tables that hold exactly those pixels (grid.grid_pixels); zero at holes."""
     c = np.asarray(c, dtype=np.float64).ravel()
     xe, ye = element_positions(g)
     X, Y = pixel_centres(g)
     X, Y = X.ravel(), Y.ravel()
     sl = slice(None) if pix is None else np.asarray(pix)
     D = np.hypot(X[sl][None, :] - xe[:, None], Y[sl][None, :] - ye[:, None])
-    T = D / g.c_ref + tables.t_res[:, sl]
-    G = green_value(g, f_hz, T, tables.q[:, sl], tables.l[:, sl], tables.kappa[:, sl], c[sl][None, :])
-    return np.where(tables.hit[:, sl], G, 0.0)
+    T = D / g.c_ref + tables.t_res
+    G = green_value(g, f_hz, T, tables.q, tables.l, tables.kappa, c[sl][None, :])
+    return np.where(tables.hit, G, 0.0)

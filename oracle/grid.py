@@ -54,6 +54,21 @@ def grid(g: Geom, c: np.ndarray, alpha0: np.ndarray, F: np.ndarray | None = None
                   hit=out[..., 5] > 0.5, n_lost=int(nl))
 
 
+def grid_pixels(g: Geom, c: np.ndarray, alpha0: np.ndarray, pix: np.ndarray, F: np.ndarray | None = None) -> Tables:
+    """The same tables as grid(), kept only at the listed flat pixel indices ([n_elem, len(pix)])."""
+    if F is None:
+        F = fields(g, c, alpha0)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    sel = np.ascontiguousarray(pix, dtype=np.int64)
+    out = np.zeros((g.n_elem, sel.size, 6))
+    cg = _cgeom(g)
+    nl = _clib.lib().orc_grid_pixels(ctypes.byref(cg), _ptr(F), ctypes.c_int64(r2max(g)), _ptr(sel),
+                                     ctypes.c_int64(sel.size), _ptr(out))
+    return Tables(t_res=out[..., 0].copy(), q=out[..., 1].copy(), l=out[..., 2].copy(),
+                  kappa=out[..., 3].astype(np.int64), tri=out[..., 4].astype(np.int64),
+                  hit=out[..., 5] > 0.5, n_lost=int(nl))
+
+
 def triangles_of_fan(g: Geom, V: np.ndarray, nvert: np.ndarray):
     """Every triangle of one fan as arrays (ids, vertex records [n, 3, NV]), in id order.
     Used by tests to brute-force the first arrival."""

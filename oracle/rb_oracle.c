@@ -334,3 +334,28 @@ int orc_grid(const orc_geom* g, const double* F, int64_t r2max, double* OUT) {
     }
     return total;
 }
+
+/* All fans, but only the listed pixels are kept: OUT[n_elem][n_sel][NO]. */
+int orc_grid_pixels(const orc_geom* g, const double* F, int64_t r2max, const int64_t* sel, int64_t n_sel,
+                    double* OUT) {
+    const size_t stride = (size_t)(g->max_steps + 1) * NV;
+    const size_t npix = (size_t)g->nx * g->ny;
+    int total = 0;
+#pragma omp parallel reduction(+ : total)
+    {
+        double* V = (double*)malloc(stride * g->n_rays * sizeof(double));
+        int32_t* nvert = (int32_t*)malloc(sizeof(int32_t) * g->n_rays);
+        double* full = (double*)malloc(npix * NO * sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+        for (int t = 0; t < g->n_elem; ++t) {
+            total += orc_trace_fan(g, F, t, V, nvert);
+            grid_fan(g, t, V, nvert, r2max, full);
+            for (int64_t j = 0; j < n_sel; ++j)
+                memcpy(OUT + ((size_t)t * n_sel + j) * NO, full + (size_t)sel[j] * NO, NO * sizeof(double));
+        }
+        free(V);
+        free(nvert);
+        free(full);
+    }
+    return total;
+}

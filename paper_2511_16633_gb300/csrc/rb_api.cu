@@ -1,0 +1,345 @@
+// C-ABI entry points of librb: argument checks, workspace carving, launch order.
+#include <math.h>
+#include <string.h>
+
+#include "rb_internal.cuh"
+
+namespace {
+
+constexpr double K_A = 11.512925464970229;  // 100 ln(10) / 20: dB/cm -> Np/m
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool geom_ok(const rb_geometry* g) {
+    if (!g) return false;
+    if (g->n_elem < 2 || g->n_elem > 1024) return false;
+    if (g->nx < 3 || g->ny < 3 || g->nx > 4096 || g->ny > 4096) return false;
+    if (!(g->h > 0.0) || !(g->ring_radius > 0.0) || !(g->ds > 0.0)) return false;
+    if (g->n_rays < 2 || g->n_rays > 4096) return false;
+    if (g->max_steps < 1 || g->max_steps > (1 << 20)) return false;
+    if (!(g->support_margin >= 0.0) || !(g->support_margin < g->ring_radius)) return false;
+    if (!(g->c_ref > 0.0) || !(g->f_ref > 0.0) || !(g->power_y > 0.0) || !(g->power_y < 3.0)) return false;
+    // the ring must lie inside the grid
+    const double half = 0.5 * (double)((g->nx < g->ny ? g->nx : g->ny) - 1) * g->h;
+    if (!(g->ring_radius < half)) return false;
+    // triangle ids must fit the 24-bit field of the table tag
+    const double ids = 2.0 * (double)(g->n_rays - 1) * (double)(g->max_steps + 1);
+    if (ids >= 16777216.0) return false;
+    return true;
+}
+
+GeoDev make_geo(const rb_geometry* g, const double* elem_xy) {
+    GeoDev G;
+    G.n_elem = g->n_elem;
+    G.nx = g->nx;
+    G.ny = g->ny;
+    G.n_rays = g->n_rays;
+    G.max_steps = g->max_steps;
+    G.n_wpf = (g->n_rays - 1 + 30) / 31;
+    if (G.n_wpf < 1) G.n_wpf = 1;
+    G.npix = g->nx * g->ny;
+    G.h = (float)g->h;
+    G.inv_h = (float)(1.0 / g->h);
+    G.cxg = 0.5f * (float)(g->nx - 1);
+    G.cyg = 0.5f * (float)(g->ny - 1);
+    const DF hd = df_from_double(g->h);
+    G.h_hi = hd.hi;
+    G.h_lo = hd.lo;
+    G.ds = (float)g->ds;
+    G.R = (float)g->ring_radius;
+    G.R2 = (float)(g->ring_radius * g->ring_radius);
+    G.inv_cref = (float)(1.0 / g->c_ref);
+    G.c_ref = (float)g->c_ref;
+    G.j_floor = (float)(0.25 * g->h);
+    G.R_d = g->ring_radius;
+    G.ds_d = g->ds;
+    G.c_ref_d = g->c_ref;
+    G.h_d = g->h;
+    const double q = 2.0 * (g->ring_radius - g->support_margin) / g->h;
+    G.r2max = (long long)floor(q * q);
+    G.elem_xy = elem_xy;
+    return G;
+}
+
+// dispersion phase per unit alpha0 integral [rad]: causal power law relative to f_ref
+double dispersion_phase(double f, double y, double f_ref) {
+    const double w = 2.0 * M_PI * f, wr = 2.0 * M_PI * f_ref;
+    if (y == 1.0) return -(2.0 / M_PI) * w * log(w / wr) * K_A / (2.0 * M_PI * 1e6);
+    const double diff = pow(wr, y - 1.0) * expm1((y - 1.0) * log(w / wr));
+    return w * tan(0.5 * M_PI * y) * diff * K_A * pow(2.0 * M_PI * 1e6, -y);
+}
+
+FreqC make_freq(const rb_geometry* g, double f) {
+    FreqC F;
+    const double w = 2.0 * M_PI * f;
+    F.f_d = f;
+    F.f_hi = (float)f;
+    const DF kf = df_from_double(f / g->c_ref);
+    F.kf_hi = kf.hi;
+    F.kf_lo = kf.lo;
+    F.w_isqrt = (float)(1.0 / sqrt(w));
+    F.a_abs = (float)(K_A * pow(f / 1e6, g->power_y));
+    F.disp_cyc = (float)(dispersion_phase(f, g->power_y, g->f_ref) / (2.0 * M_PI));
+    F.w2 = (float)(w * w);
+    F.w4 = (float)(w * w * w * w);
+    return F;
+}
+
+bool make_freqs(const rb_geometry* g, const double* f, int n, FreqSet* F) {
+    if (!f || n < 1 || n > RB_MAX_FREQ) return false;
+    F->n = n;
+    for (int i = 0; i < n; ++i) {
+        if (!(f[i] > 0.0) || !isfinite(f[i])) return false;
+        F->f[i] = make_freq(g, f[i]);
+    }
+    return true;
+}
+
+struct Ws {
+    WsLayout L;
+    char* base;
+    template <class T> T* at(size_t off) const { return (T*)(base + off); }
+};
+
+rb_status check_ws(const rb_geometry* g, int n_freq, rb_precision prec, void* ws, size_t ws_bytes, Ws* W) {
+    if (!ws) return RB_ERR_WORKSPACE;
+    if (((uintptr_t)ws & 255) != 0) return RB_ERR_WORKSPACE;
+    const size_t need = rb_ws_layout(g, n_freq, prec, &W->L);
+    if (need == 0) return RB_ERR_SHAPE;
+    if (ws_bytes < need) return RB_ERR_WORKSPACE;
+    W->base = (char*)ws;
+    return RB_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+#define RB_CU(x)                                   \
+    do {                                           \
+        if ((x) != cudaSuccess) return RB_ERR_CUDA; \
+    } while (0)
+
+}  // namespace
+
+size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision /*prec*/, WsLayout* L) {
+    if (!geom_ok(g) || n_freq < 1 || n_freq > RB_MAX_FREQ) return 0;
+    const size_t ne = (size_t)g->n_elem, npix = (size_t)g->nx * g->ny;
+    const size_t ncell = (size_t)(g->nx - 1) * (g->ny - 1);
+    const size_t nf = (size_t)n_freq;
+    size_t o = 0;
+    L->counters = o; o = align256(o + CNT_N * 4 + DBL_N * 8);
+    L->elem_xy = o; o = align256(o + ne * 16);
+    L->cells = o; o = align256(o + ncell * 128);
+    L->tables = o; o = align256(o + ne * npix * sizeof(rb_cell));
+    L->ends = o; o = align256(o + ne * (size_t)g->n_rays * sizeof(rb_ray_end));
+    L->pray = o; o = align256(o + nf * ne * ne * 8);
+    L->linked = o; o = align256(o + ne * ne);
+    L->wts = o; o = align256(o + nf * ne * ne);
+    L->keys = o; o = align256(o + nf * ne * ne * 8);
+    L->gsum = o; o = align256(o + npix * 4);
+    L->hsum = o; o = align256(o + npix * 4);
+    L->pdir = o; o = align256(o + npix * 4);
+    L->part = o; o = align256(o + (size_t)(RB_MAX_FREQ + 2) * 256 * 8);
+    L->fwd = o; o = align256(o + (size_t)rb_fwd_chunks_for((int)npix) * ne * ne * 8);
+    L->total = o;
+    return o;
+}
+
+extern "C" {
+
+size_t rb_workspace_size(const rb_geometry* geom, int32_t n_freq, rb_precision prec) {
+    WsLayout L;
+    if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return 0;
+    return rb_ws_layout(geom, n_freq, prec, &L);
+}
+
+const char* rb_status_string(rb_status s) {
+    switch (s) {
+        case RB_OK: return "ok";
+        case RB_ERR_ARG: return "invalid argument";
+        case RB_ERR_SHAPE: return "unsupported sizes";
+        case RB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case RB_ERR_CUDA: return "CUDA launch or call failed";
+        case RB_ERR_LIMIT: return "device-side limit reached";
+        case RB_ERR_UNSUPPORTED: return "not supported by this build";
+    }
+    return "unknown status";
+}
+
+rb_status rb_trace_rays(const rb_geometry* geom, const float* c, const float* alpha0, rb_rays* out, void* ws,
+                        size_t ws_bytes, rb_stream stream) {
+    if (!geom || !c || !alpha0 || !out || !out->ends) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    const bool any = out->vx || out->vy || out->vt || out->vq || out->vl || out->vkappa;
+    const bool all = out->vx && out->vy && out->vt && out->vq && out->vl && out->vkappa;
+    if (any && !all) return RB_ERR_ARG;
+    Ws W;
+    rb_status st = check_ws(geom, 1, RB_PREC_FP32, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* exy = W.at<double>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    const GeoDev G = make_geo(geom, exy);
+    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, cnt, s));
+    return RB_OK;
+}
+
+rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* alpha0, rb_cell* tables,
+                        const double* freqs_hz, int32_t n_freq, float* g_out, void* ws, size_t ws_bytes,
+                        rb_stream stream) {
+    if (!geom || !c || !alpha0 || !tables) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    if (!aligned16(tables)) return RB_ERR_ARG;
+    FreqSet F;
+    F.n = 0;
+    if (g_out && !make_freqs(geom, freqs_hz, n_freq, &F)) return RB_ERR_ARG;
+    Ws W;
+    rb_status st = check_ws(geom, 1, RB_PREC_FP32, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* exy = W.at<double>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    const GeoDev G = make_geo(geom, exy);
+    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
+    RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, tables, cnt, s));
+    if (g_out) RB_CU(launch_green_out(G, tables, c, F, (float2*)g_out, s));
+    return RB_OK;
+}
+
+rb_status rb_ray_forward(const rb_geometry* geom, const float* c, const rb_ray_end* ends, const double* freqs_hz,
+                         int32_t n_freq, float* p_out, uint8_t* linked_out, rb_stream stream) {
+    if (!geom || !c || !ends || !p_out) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    FreqSet F;
+    if (!make_freqs(geom, freqs_hz, n_freq, &F)) return RB_ERR_ARG;
+    const GeoDev G = make_geo(geom, nullptr);
+    RB_CU(launch_link(G, c, ends, F, (float2*)p_out, linked_out, (cudaStream_t)stream));
+    return RB_OK;
+}
+
+rb_status rb_born_forward(const rb_geometry* geom, const rb_cell* tables, const float* c, double f_hz, const float* m,
+                          float* d_out, rb_precision prec, void* ws, size_t ws_bytes, rb_stream stream) {
+    if (!geom || !tables || !c || !m || !d_out) return RB_ERR_ARG;
+    if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    if (!(f_hz > 0.0) || !isfinite(f_hz)) return RB_ERR_ARG;
+    if (prec != RB_PREC_FP32) return RB_ERR_UNSUPPORTED;
+    Ws W;
+    rb_status st = check_ws(geom, 1, prec, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* exy = W.at<double>(W.L.elem_xy);
+    const GeoDev G = make_geo(geom, exy);
+    const FreqC F = make_freq(geom, f_hz);
+    const int nch = rb_fwd_chunks_for(G.npix);
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_forward_simt(G, tables, c, F, m, W.at<float2>(W.L.fwd), nch, s));
+    RB_CU(launch_forward_reduce(G, F, W.at<float2>(W.L.fwd), nch, (float2*)d_out, nullptr, nullptr, s));
+    return RB_OK;
+}
+
+rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const float* c, double f_hz,
+                          const float* resid, const uint8_t* w, float* g_out, float* hdiag_out, rb_precision prec,
+                          void* ws, size_t ws_bytes, rb_stream stream) {
+    if (!geom || !tables || !c || !resid || !w || !g_out) return RB_ERR_ARG;
+    if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    if (!(f_hz > 0.0) || !isfinite(f_hz)) return RB_ERR_ARG;
+    if (prec != RB_PREC_FP32) return RB_ERR_UNSUPPORTED;
+    Ws W;
+    rb_status st = check_ws(geom, 1, prec, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* exy = W.at<double>(W.L.elem_xy);
+    const GeoDev G = make_geo(geom, exy);
+    FreqSet F;
+    F.n = 1;
+    F.f[0] = make_freq(geom, f_hz);
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_adjoint_simt(G, tables, c, F, (const float2*)resid, w, (float2*)g_out, hdiag_out, nullptr, nullptr,
+                              nullptr, s));
+    return RB_OK;
+}
+
+rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alpha0, const double* freqs_hz,
+                       int32_t n_freq, const float* p_obs, const rb_update_params* params, rb_precision prec,
+                       float* dc_out, rb_diag* diag_out, void* ws, size_t ws_bytes, rb_stream stream) {
+    if (!geom || !c_inout || !alpha0 || !p_obs || !params) return RB_ERR_ARG;
+    if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    if (!(params->outlier_frac >= 0.0 && params->outlier_frac < 1.0)) return RB_ERR_ARG;
+    if (!(params->eps_rel >= 0.0) || !isfinite(params->eps_rel)) return RB_ERR_ARG;
+    if (params->step_mode != RB_STEP_EXACT && params->step_mode != RB_STEP_DIAG) return RB_ERR_ARG;
+    FreqSet F;
+    if (!make_freqs(geom, freqs_hz, n_freq, &F)) return RB_ERR_ARG;
+    if (prec != RB_PREC_FP32) return RB_ERR_UNSUPPORTED;
+    Ws W;
+    rb_status st = check_ws(geom, n_freq, prec, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* exy = W.at<double>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    double* dbl = (double*)(cnt + CNT_N);
+    const GeoDev G = make_geo(geom, exy);
+    const int ne2 = G.n_elem * G.n_elem;
+    float4* cells = W.at<float4>(W.L.cells);
+    rb_cell* tables = W.at<rb_cell>(W.L.tables);
+    rb_ray_end* ends = W.at<rb_ray_end>(W.L.ends);
+    float2* R = W.at<float2>(W.L.pray);
+    uint8_t* linked = W.at<uint8_t>(W.L.linked);
+    uint8_t* wts = W.at<uint8_t>(W.L.wts);
+    uint64_t* keys = W.at<uint64_t>(W.L.keys);
+    float* gsum = W.at<float>(W.L.gsum);
+    float* hsum = W.at<float>(W.L.hsum);
+    float* pdir = W.at<float>(W.L.pdir);
+    double* part = W.at<double>(W.L.part);
+    float2* fwd = W.at<float2>(W.L.fwd);
+    const int nch = rb_fwd_chunks_for(G.npix);
+    cudaEvent_t* ev = (cudaEvent_t*)params->stage_events;
+    auto mark = [&](int stage, int end) -> cudaError_t {
+        return ev ? cudaEventRecord(ev[2 * stage + end], s) : cudaSuccess;
+    };
+
+    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4 + DBL_N * 8, s));
+    RB_CU(mark(RB_STAGE_FIELDS, 0));
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_fields(G, c_inout, alpha0, cells, s));
+    RB_CU(mark(RB_STAGE_FIELDS, 1));
+    RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
+    RB_CU(mark(RB_STAGE_TRACE_GRID, 0));
+    RB_CU(launch_trace(G, cells, ends, nullptr, tables, cnt, s));
+    RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
+    RB_CU(mark(RB_STAGE_LINK, 0));
+    RB_CU(launch_link(G, c_inout, ends, F, R, linked, s));
+    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, s));
+    RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, cnt, s));
+    RB_CU(mark(RB_STAGE_LINK, 1));
+    RB_CU(mark(RB_STAGE_ADJOINT, 0));
+    RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));
+    RB_CU(mark(RB_STAGE_ADJOINT, 1));
+    RB_CU(mark(RB_STAGE_DIRECTION, 0));
+    RB_CU(launch_update(G, c_inout, gsum, hsum, pdir, dc_out, part, dbl, cnt, diag_out, params->eps_rel,
+                        params->step_mode, 0, s));
+    RB_CU(mark(RB_STAGE_DIRECTION, 1));
+    RB_CU(mark(RB_STAGE_FORWARD, 0));
+    if (params->step_mode == RB_STEP_EXACT) {
+        for (int w = 0; w < n_freq; ++w) {
+            RB_CU(launch_forward_simt(G, tables, c_inout, F.f[w], pdir, fwd, nch, s));
+            RB_CU(launch_forward_reduce(G, F.f[w], fwd, nch, nullptr, wts + (size_t)w * ne2, part + (size_t)w * 256, s));
+        }
+        RB_CU(launch_sum_partials(part, n_freq * 256, dbl, DBL_DEN, 1.0, 0, s));
+    }
+    RB_CU(mark(RB_STAGE_FORWARD, 1));
+    RB_CU(mark(RB_STAGE_APPLY, 0));
+    RB_CU(launch_update(G, c_inout, gsum, hsum, pdir, dc_out, part + (size_t)RB_MAX_FREQ * 256, dbl, cnt, diag_out,
+                        params->eps_rel, params->step_mode, 1, s));
+    RB_CU(mark(RB_STAGE_APPLY, 1));
+    return RB_OK;
+}
+
+}  // extern "C"

