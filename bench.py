@@ -118,7 +118,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     prec = rb.RB_PREC_FP32 if args.prec == "fp32" else rb.RB_PREC_BF16X3
 
-    cfg = rbgen.breast512()
+    cfg = rbgen.config_by_name(args.workload)
     inp = rbgen.make_inputs(cfg)
     geom = rb.geometry_from_config(cfg)
     c0 = torch.as_tensor(inp.c_init, device=dev).contiguous()
@@ -240,7 +240,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == rb.RB_PREC_FP32 else "bf16x3",
         "data": "synthetic (seeded breast phantom; data from the library's own ray-Born forward model + 1% noise)",
-        "config": {"workload": WORKLOAD, "n_elem": cfg.n_elem, "grid": [cfg.nx, cfg.ny], "h_m": cfg.h,
+        "config": {"workload": args.workload, "n_elem": cfg.n_elem, "grid": [cfg.nx, cfg.ny], "h_m": cfg.h,
                    "n_rays": cfg.n_rays, "freqs_per_set": nf, "n_sets": nsets, "precision": args.prec,
                    "step_mode": "exact", "l2": "working set (1.1 GB tables) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -253,7 +253,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "diag_last": {k: d[k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         line["cpu_baseline"] = cpu_baseline(sample_fans=args.cpu_fans, sample_pix=args.cpu_pix)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["breast512", "breast256", "tiny"],
+                    help="the timed workload is breast512; smaller ones are for profiling captures")
     ap.add_argument("--cpu-fans", type=int, default=32)
     ap.add_argument("--cpu-pix", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -50,7 +50,9 @@ def synth_data(geom, c0, c_true, alpha0, freqs: Sequence[float], noise_re=None, 
     c0d, ctd = c0.reshape(-1).double(), c_true.reshape(-1).double()
     m = torch.where(sup, -2.0 * geom.h * geom.h * (ctd - c0d) / c0d ** 3, torch.zeros_like(c0d)).float().contiguous()
     p = torch.empty((len(freqs), ne, ne), dtype=torch.complex64, device=dev)
-    rb.rb_ray_forward(geom, c0, ends, freqs, p)
+    for j0 in range(0, len(freqs), rb.RB_MAX_FREQ):
+        j1 = min(len(freqs), j0 + rb.RB_MAX_FREQ)
+        rb.rb_ray_forward(geom, c0, ends, list(freqs[j0:j1]), p[j0:j1])
     d = torch.empty((ne, ne), dtype=torch.complex64, device=dev)
     mask = receiver_mask(ne, dev)
     for j, f in enumerate(freqs):

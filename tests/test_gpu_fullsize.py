@@ -1,0 +1,164 @@
+"""GPU-vs-oracle parity at the benchmark sizes (needs a CUDA GPU).
+
+* 256x256 grid, 256-element ring: full tables and the Born adjoint / Hessian
+  diagonal against the oracle on every pixel.
+* 512x512 grid (the benchmarked workload, same launch configuration): every
+  ray endpoint against the oracle; tables, Born adjoint and Hessian diagonal
+  at a seeded sample of support pixels (the oracle grids every fan but keeps
+  only those pixels); one full rb_hf_update checked by properties that hold
+  at any size (counts, the outlier rule, the update norm, finiteness).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import rbgen
+from oracle import born as oborn
+from oracle import geometry as ogeom
+from oracle import green as ogreen
+from oracle import grid as ogrid
+from oracle import rays as orays
+from oracle.rays import VT, VTH, VX, VY
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_16633_gb300 import rb  # noqa: E402
+from paper_2511_16633_gb300.recon import synth_data  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rb.load()
+    return torch.device("cuda:0")
+
+
+def _t(a, dev):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _tables(geom, c, a0, dev):
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    tab = torch.empty((geom.n_elem, geom.nx * geom.ny, 4), dtype=torch.int32, device=dev)
+    rb.rb_green_grid(geom, _t(c, dev), _t(a0, dev), tab, ws)
+    return tab, ws
+
+
+def _random_data(n, seed):
+    rng = np.random.default_rng(seed)
+    R = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    W = (rng.uniform(size=(n, n)) > 0.25).astype(np.uint8)
+    return R, W
+
+
+def test_breast256_tables_and_adjoint(dev):
+    cfg = rbgen.breast256()
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    tab, ws = _tables(geom, inp.c_init, inp.alpha0, dev)
+    ot = ogrid.grid(g, inp.c_init, inp.alpha0)
+    d = rb.decode_tables(tab)
+    sup = ogeom.support_mask(g).ravel()
+    both = d["hit"] & ot.hit & sup[None, :]
+    same = both & (d["tri"] == ot.tri)
+    bad = (np.sum(d["hit"][:, sup] != ot.hit[:, sup]) + np.sum(both & ~same)) / (g.n_elem * sup.sum())
+    assert bad < 1e-3, bad
+    Ttot = ogreen.gridded_traveltime(g, ot)
+    assert np.max(np.abs(d["t_res"] - ot.t_res)[same] / Ttot[same]) <= 1e-6
+    R, W = _random_data(g.n_elem, 1)
+    f = cfg.freqs_hz[-1]
+    gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
+    hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+    rb.rb_born_adjoint(geom, tab, _t(inp.c_init, dev), f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev),
+                       gg, ws, hh)
+    Go = ogreen.green(g, ot, inp.c_init, f)
+    go = oborn.born_adjoint(Go, W * R.astype(np.complex128), f)
+    ho = oborn.hess_diag(Go, W, f)
+    assert rel_l2(gg.cpu().numpy(), go) <= 1e-4
+    assert rel_l2(hh.cpu().numpy(), ho) <= 1e-4
+
+
+@pytest.fixture(scope="module")
+def big(dev):
+    cfg = rbgen.breast512()
+    inp = rbgen.make_inputs(cfg)
+    return cfg, inp, ogeom.from_config(cfg), rb.geometry_from_config(cfg)
+
+
+def test_breast512_endpoints(dev, big):
+    cfg, inp, g, geom = big
+    E, nv, lost = orays.trace_endpoints(g, inp.c_init, inp.alpha0)
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    ends = torch.zeros((g.n_elem, g.n_rays, 56), dtype=torch.uint8, device=dev)
+    rb.rb_trace_rays(geom, _t(inp.c_init, dev), _t(inp.alpha0, dev), ends, ws)
+    G = rb.decode_ends(ends)
+    assert lost.sum() == 0 and np.all(G["n_vert"] > 0)
+    assert np.mean(G["n_vert"] == nv) >= 0.999
+    R = cfg.ring_radius
+    sinb = np.abs(np.cos(E[..., VTH]) * E[..., VX] + np.sin(E[..., VTH]) * E[..., VY]) / R
+    well = sinb >= 0.1
+    relT = np.abs(G["t"] - E[..., VT]) / E[..., VT]
+    dpos = np.hypot(G["x"] - E[..., VX], G["y"] - E[..., VY]) / R
+    assert np.max(relT[well]) <= 1e-6 and np.max(dpos[well]) <= 1e-6
+    bound = np.minimum(1e-6 / np.maximum(sinb, 1e-12), 1e-4)
+    assert np.all(relT <= np.maximum(bound, 1e-6))
+
+
+def test_breast512_sampled_tables_and_adjoint(dev, big):
+    cfg, inp, g, geom = big
+    rng = np.random.default_rng(12)
+    sup = np.flatnonzero(ogeom.support_mask(g).ravel())
+    pix = np.sort(rng.choice(sup, 3000, replace=False))
+    tab, ws = _tables(geom, inp.c_init, inp.alpha0, dev)
+    d = rb.decode_tables(tab)
+    ot = ogrid.grid_pixels(g, inp.c_init, inp.alpha0, pix)
+    dh, dt, dtri = d["hit"][:, pix], d["t_res"][:, pix], d["tri"][:, pix]
+    both = dh & ot.hit
+    same = both & (dtri == ot.tri)
+    bad = (np.sum(dh != ot.hit) + np.sum(both & ~same)) / dh.size
+    assert bad < 1e-3, bad
+    R, W = _random_data(g.n_elem, 2)
+    f = cfg.freqs_hz[-1]
+    gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
+    hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+    rb.rb_born_adjoint(geom, tab, _t(inp.c_init, dev), f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev),
+                       gg, ws, hh)
+    Go = ogreen.green(g, ot, inp.c_init, f, pix=pix)
+    go = oborn.born_adjoint(Go, W * R.astype(np.complex128), f)
+    ho = oborn.hess_diag(Go, W, f)
+    assert rel_l2(gg.cpu().numpy()[pix], go) <= 1e-4
+    assert rel_l2(hh.cpu().numpy()[pix], ho) <= 1e-4
+
+
+def test_breast512_update_properties(dev, big):
+    cfg, inp, g, geom = big
+    c0 = _t(inp.c_init, dev)
+    a0 = _t(inp.alpha0, dev)
+    p = synth_data(geom, c0, _t(inp.c_true, dev), a0, list(cfg.freqs_hz[:4]), inp.noise_re, inp.noise_im)
+    ws = rb.workspace(geom, 4, rb.RB_PREC_FP32, dev)
+    c = c0.clone()
+    dc = torch.empty_like(c)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    rb.rb_hf_update(geom, c, a0, list(cfg.freqs_hz[:4]), p, ws, dc_out=dc, diag_out=diag)
+    torch.cuda.synchronize()
+    dd = rb.decode_diag(diag)
+    dcn = dc.cpu().numpy().astype(np.float64)
+    sup = ogeom.support_mask(g)
+    assert np.all(np.isfinite(dcn))
+    assert np.all(dcn[~sup] == 0.0)
+    assert abs(dd["dc_norm"] - np.sqrt(np.sum(dcn[sup] ** 2))) <= 1e-4 * dd["dc_norm"]
+    assert dd["lost_rays"] == 0 and dd["cas_giveup"] == 0
+    min_sep = math.ceil(g.n_elem / 8)
+    assert dd["kept"] + 4 * dd["unlinked"] == 4 * g.n_elem * (g.n_elem - 2 * min_sep + 1)
+    assert dd["zeroed"] == math.floor(0.01 * dd["kept"])
+    assert dd["alpha"] > 0
+    # the step lowers the linearised objective: c moved by dc exactly
+    assert np.allclose(c.cpu().numpy(), inp.c_init + dc.cpu().numpy(), rtol=0, atol=1e-3)
