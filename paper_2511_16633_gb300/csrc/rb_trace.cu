@@ -149,15 +149,16 @@ __device__ __forceinline__ double exit_lambda(double ax, double ay, double bx, d
     return fmin(fmax(lam, 0.0), 1.0);
 }
 
-// Atomic "keep the smaller (tkey, tag)" on a 16-byte table record.
+// Atomic "keep the smaller (tkey, tag)" on a 16-byte table record.  The first
+// attempt assumes the record is still a hole (all bytes 0xff), which is the common
+// case, so no load precedes it; a failed attempt returns the current record.
 __device__ __forceinline__ void cell_min(rb_cell* dst, uint32_t tkey, uint32_t tag, float q, float l,
                                         uint32_t* giveup) {
     const unsigned long long nk = ((unsigned long long)tkey << 32) | tag;
     const unsigned long long nv = ((unsigned long long)__float_as_uint(l) << 32) | __float_as_uint(q);
-    unsigned long long ck, cv;
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(ck), "=l"(cv) : "l"(dst) : "memory");
+    unsigned long long ck = ~0ull, cv = ~0ull;
     int it = 0;
-    for (; it < 256 && nk < ck; ++it) {
+    for (; it < 256; ++it) {
         unsigned long long ok, ov;
         asm volatile(
             "{\n\t.reg .b128 d, cmp, val;\n\t"
@@ -168,48 +169,90 @@ __device__ __forceinline__ void cell_min(rb_cell* dst, uint32_t tkey, uint32_t t
             : "=l"(ok), "=l"(ov)
             : "l"(ck), "l"(cv), "l"(nk), "l"(nv), "l"(dst)
             : "memory");
-        if (ok == ck && ov == cv) break;
+        if (ok == ck && ov == cv) break;   // stored
         ck = ok;
         cv = ov;
+        if (!(nk < ck)) break;             // an earlier arrival (or tie winner) is already there
     }
     if (it == 256) atomicAdd(giveup, 1u);
 }
 
-__device__ __forceinline__ void raster_tri(const GeoDev& G, const Vtx& a, const Vtx& b, const Vtx& c, uint32_t tri_id,
-                                           rb_cell* __restrict__ tab, uint32_t* giveup) {
-    const float e1x = (b.xh - a.xh) + (b.xl - a.xl), e1y = (b.yh - a.yh) + (b.yl - a.yl);
-    const float e2x = (c.xh - a.xh) + (c.xl - a.xl), e2y = (c.yh - a.yh) + (c.yl - a.yl);
-    const float area = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
-    if (area == 0.f) return;
-    const float inv = 1.0f / area;
-    const float xmin = fminf(a.xh, fminf(b.xh, c.xh)), xmax = fmaxf(a.xh, fmaxf(b.xh, c.xh));
-    const float ymin = fminf(a.yh, fminf(b.yh, c.yh)), ymax = fmaxf(a.yh, fmaxf(b.yh, c.yh));
-    const int ix0 = max(0, (int)floorf(fmaf(xmin, G.inv_h, G.cxg)));
-    const int ix1 = min(G.nx - 1, (int)ceilf(fmaf(xmax, G.inv_h, G.cxg)));
-    const int iy0 = max(0, (int)floorf(fmaf(ymin, G.inv_h, G.cyg)));
-    const int iy1 = min(G.ny - 1, (int)ceilf(fmaf(ymax, G.inv_h, G.cyg)));
+// Rasterise one ray-tube quad: triangles T0 = (A0, B0, B1) (id base) and
+// T1 = (A0, B1, A1) (id base + 1), A = this ray, B = the next ray, 0/1 = steps k-1/k.
+// One pixel box (pixel centres inside the quad's bounding box) serves both
+// triangles; where both contain a pixel the smaller T_res (then T0) is kept.
+// Coordinates are taken relative to A0 from float-pair differences.
+__device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1,
+                                            uint32_t base, rb_cell* __restrict__ tab, uint32_t* giveup) {
+    const float b0x = (B0.xh - A0.xh) + (B0.xl - A0.xl), b0y = (B0.yh - A0.yh) + (B0.yl - A0.yl);
+    const float b1x = (B1.xh - A0.xh) + (B1.xl - A0.xl), b1y = (B1.yh - A0.yh) + (B1.yl - A0.yl);
+    const float a1x = (A1.xh - A0.xh) + (A1.xl - A0.xl), a1y = (A1.yh - A0.yh) + (A1.yl - A0.yl);
+    // twice the signed areas; exactly zero when two vertices coincide (frozen or shared vertices)
+    const float ar0 = __fsub_rn(__fmul_rn(b0x, b1y), __fmul_rn(b0y, b1x));
+    const float ar1 = __fsub_rn(__fmul_rn(b1x, a1y), __fmul_rn(b1y, a1x));
+    const bool t0 = ar0 != 0.f, t1 = ar1 != 0.f;
+    if (!t0 && !t1) return;
+    const float i0 = t0 ? 1.0f / ar0 : 0.f, i1 = t1 ? 1.0f / ar1 : 0.f;
+    // tight box of pixel centres (index space), with a 1e-3 px guard
+    const float ua = fmaf(A0.xh, G.inv_h, G.cxg) + A0.xl * G.inv_h;
+    const float va = fmaf(A0.yh, G.inv_h, G.cyg) + A0.yl * G.inv_h;
+    const float xmin = fminf(fminf(0.f, b0x), fminf(b1x, a1x)), xmax = fmaxf(fmaxf(0.f, b0x), fmaxf(b1x, a1x));
+    const float ymin = fminf(fminf(0.f, b0y), fminf(b1y, a1y)), ymax = fmaxf(fmaxf(0.f, b0y), fmaxf(b1y, a1y));
+    const int ix0 = max(0, (int)ceilf(fmaf(xmin, G.inv_h, ua) - 1e-3f));
+    const int ix1 = min(G.nx - 1, (int)floorf(fmaf(xmax, G.inv_h, ua) + 1e-3f));
+    const int iy0 = max(0, (int)ceilf(fmaf(ymin, G.inv_h, va) - 1e-3f));
+    const int iy1 = min(G.ny - 1, (int)floorf(fmaf(ymax, G.inv_h, va) + 1e-3f));
     const float tol = -1e-6f;
     for (int iy = iy0; iy <= iy1; ++iy) {
         const long long jy = 2LL * iy - (G.ny - 1);
         const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
-        const float dy = (Y.hi - a.yh) + (Y.lo - a.yl);
+        const float dy = (Y.hi - A0.yh) + (Y.lo - A0.yl);
         for (int ix = ix0; ix <= ix1; ++ix) {
             const long long jx = 2LL * ix - (G.nx - 1);
             if (jx * jx + jy * jy > G.r2max) continue;
             const DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
-            const float dx = (X.hi - a.xh) + (X.lo - a.xl);
-            const float wb = (dx * e2y - dy * e2x) * inv;
-            const float wc = (e1x * dy - e1y * dx) * inv;
-            const float wa = 1.f - wb - wc;
-            if (wa < tol || wb < tol || wc < tol) continue;
-            const float tr = wa * a.t + wb * b.t + wc * c.t;
-            const float q = wa * a.q + wb * b.q + wc * c.q;
-            const float l = wa * a.l + wb * b.l + wc * c.l;
-            int kap = a.k;
-            float wbest = wa;
-            if (wb > wbest) { kap = b.k; wbest = wb; }
-            if (wc > wbest) { kap = c.k; }
-            const uint32_t tag = (tri_id << 8) | (uint32_t)min(kap, 255);
+            const float dx = (X.hi - A0.xh) + (X.lo - A0.xl);
+            bool in0 = false, in1 = false;
+            float wb0 = 0.f, wc0 = 0.f, wa0 = 0.f, wb1 = 0.f, wc1 = 0.f, wa1 = 0.f;
+            if (t0) {
+                wb0 = (dx * b1y - dy * b1x) * i0;
+                wc0 = (b0x * dy - b0y * dx) * i0;
+                wa0 = 1.f - wb0 - wc0;
+                in0 = wa0 >= tol && wb0 >= tol && wc0 >= tol;
+            }
+            if (t1) {
+                wb1 = (dx * a1y - dy * a1x) * i1;
+                wc1 = (b1x * dy - b1y * dx) * i1;
+                wa1 = 1.f - wb1 - wc1;
+                in1 = wa1 >= tol && wb1 >= tol && wc1 >= tol;
+            }
+            if (!in0 && !in1) continue;
+            const float tr0 = in0 ? wa0 * A0.t + wb0 * B0.t + wc0 * B1.t : 0.f;
+            const float tr1 = in1 ? wa1 * A0.t + wb1 * B1.t + wc1 * A1.t : 0.f;
+            const bool use1 = in1 && (!in0 || tr1 < tr0);
+            float tr, q, l;
+            int kap;
+            uint32_t id;
+            if (!use1) {
+                tr = tr0;
+                q = wa0 * A0.q + wb0 * B0.q + wc0 * B1.q;
+                l = wa0 * A0.l + wb0 * B0.l + wc0 * B1.l;
+                kap = A0.k;
+                float wbest = wa0;
+                if (wb0 > wbest) { kap = B0.k; wbest = wb0; }
+                if (wc0 > wbest) kap = B1.k;
+                id = base;
+            } else {
+                tr = tr1;
+                q = wa1 * A0.q + wb1 * B1.q + wc1 * A1.q;
+                l = wa1 * A0.l + wb1 * B1.l + wc1 * A1.l;
+                kap = A0.k;
+                float wbest = wa1;
+                if (wb1 > wbest) { kap = B1.k; wbest = wb1; }
+                if (wc1 > wbest) kap = A1.k;
+                id = base + 1u;
+            }
+            const uint32_t tag = (id << 8) | (uint32_t)min(kap, 255);
             cell_min(tab + (size_t)iy * G.nx + ix, f2key(tr), tag, q, l, giveup);
         }
     }
@@ -375,8 +418,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
         nb_cur = shfl_down_vtx(cur);
         if (tab && tube) {
             const uint32_t base = ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u;
-            raster_tri(G, prev, nb_prev, nb_cur, base, tab, giveup);
-            raster_tri(G, prev, nb_cur, cur, base + 1u, tab, giveup);
+            raster_quad(G, prev, cur, nb_prev, nb_cur, base, tab, giveup);
         }
     }
 }
