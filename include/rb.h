@@ -227,6 +227,28 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
                        int32_t n_freq, const float* p_obs, const rb_update_params* params, rb_precision prec,
                        float* dc_out, rb_diag* diag_out, void* ws, size_t ws_bytes, rb_stream stream);
 
+/*
+ * Born forward operator without a workspace (the paper has no counterpart:
+ * this is a calling convention of the library).  For callers that cannot
+ * give the library device scratch memory, such as plugins of a host
+ * framework that passes in its own tensors but no allocator, or real-time
+ * loops that forbid device allocation once running.  Computes the same
+ * d[e][r] = w^2 sum_x G_e(x) G_r(x) m(x) as rb_born_forward (FP32), from
+ * tables, c and m into d_out[n_elem][n_elem] complex, and allocates nothing.
+ *
+ * Its scratch is one fixed device array of RB_NOALLOC_SCRATCH_BYTES inside
+ * the library, held on every device that loads the library until the process
+ * exits.  The first call on each device looks up the array's device address
+ * (make that first call before any stream capture).  All calls share the
+ * array: calls whose kernels overlap on the GPU race and must be serialised
+ * by the caller.  Sizes whose scratch does not fit (n_elem^2 * 8 bytes above
+ * RB_NOALLOC_SCRATCH_BYTES - 16 KiB) return RB_ERR_SHAPE; with the current
+ * size every n_elem <= 1024 fits.  Errors are returned as for rb_born_forward.
+ */
+#define RB_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u + 16u * 1024u)
+rb_status rb_born_forward_noalloc(const rb_geometry* geom, const rb_cell* tables, const float* c, double f_hz,
+                                  const float* m, float* d_out, rb_stream stream);
+
 /* Static description of a status code. */
 const char* rb_status_string(rb_status s);
 

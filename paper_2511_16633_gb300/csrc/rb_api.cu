@@ -120,6 +120,9 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
 
+GeoDev rb_make_geo(const rb_geometry* g, const double* elem_xy) { return make_geo(g, elem_xy); }
+FreqC rb_make_freq(const rb_geometry* g, double f_hz) { return make_freq(g, f_hz); }
+
 size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision /*prec*/, WsLayout* L) {
     if (!geom_ok(g) || n_freq < 1 || n_freq > RB_MAX_FREQ) return 0;
     const size_t ne = (size_t)g->n_elem, npix = (size_t)g->nx * g->ny;

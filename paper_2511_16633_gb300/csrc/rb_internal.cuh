@@ -170,6 +170,8 @@ struct WsLayout {
 };
 
 size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayout* L);
+GeoDev rb_make_geo(const rb_geometry* g, const double* elem_xy);
+FreqC rb_make_freq(const rb_geometry* g, double f_hz);
 
 // counters (uint32 slots)
 enum { CNT_LOST = 0, CNT_HOLES = 1, CNT_UNLINKED = 2, CNT_KEPT = 3, CNT_ZEROED = 4, CNT_CAS_GIVEUP = 5, CNT_N = 64 };

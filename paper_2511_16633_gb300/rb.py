@@ -22,7 +22,7 @@ RB_MAX_FREQ = 16
 RB_HOLE = 0xFFFFFFFF
 
 EXPORTS = ("rb_workspace_size", "rb_trace_rays", "rb_green_grid", "rb_ray_forward", "rb_born_forward",
-           "rb_born_adjoint", "rb_hf_update", "rb_status_string")
+           "rb_born_adjoint", "rb_hf_update", "rb_born_forward_noalloc", "rb_status_string")
 
 
 class RbError(RuntimeError):
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
     L.rb_born_adjoint.argtypes = [G, P, P, ctypes.c_double, P, P, P, P, ctypes.c_int, P, ctypes.c_size_t, P]
     L.rb_hf_update.argtypes = [G, P, P, P, ctypes.c_int32, P, ctypes.POINTER(rb_update_params), ctypes.c_int, P, P,
                                P, ctypes.c_size_t, P]
+    L.rb_born_forward_noalloc.argtypes = [G, P, P, ctypes.c_double, P, P, P]
     L.rb_status_string.argtypes = [ctypes.c_int]
     L.rb_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -179,6 +180,13 @@ def rb_born_forward(geom, tables, c, f_hz, m, d_out, ws, prec=RB_PREC_FP32, stre
     code = load().rb_born_forward(ctypes.byref(geom), _ptr(tables), _ptr(c), float(f_hz), _ptr(m), _ptr(d_out),
                                   int(prec), _ptr(ws), ws.numel(), _stream(stream))
     _check("rb_born_forward", code)
+
+
+def rb_born_forward_noalloc(geom, tables, c, f_hz, m, d_out, stream=None):
+    """Born forward without a workspace (scratch inside the library; see include/rb.h)."""
+    code = load().rb_born_forward_noalloc(ctypes.byref(geom), _ptr(tables), _ptr(c), float(f_hz), _ptr(m), _ptr(d_out),
+                                          _stream(stream))
+    _check("rb_born_forward_noalloc", code)
 
 
 def rb_born_adjoint(geom, tables, c, f_hz, resid, w, g_out, ws, hdiag_out=None, prec=RB_PREC_FP32, stream=None):
