@@ -113,6 +113,13 @@ rb_status check_ws(const rb_geometry* g, int n_freq, rb_precision prec, void* ws
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
+int tc_ctas() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    return n < RB_TC_MAX_CTAS ? n : RB_TC_MAX_CTAS;
+}
+
 #define RB_CU(x)                                   \
     do {                                           \
         if ((x) != cudaSuccess) return RB_ERR_CUDA; \
@@ -123,8 +130,9 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 GeoDev rb_make_geo(const rb_geometry* g, const double* elem_xy) { return make_geo(g, elem_xy); }
 FreqC rb_make_freq(const rb_geometry* g, double f_hz) { return make_freq(g, f_hz); }
 
-size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision /*prec*/, WsLayout* L) {
+size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayout* L) {
     if (!geom_ok(g) || n_freq < 1 || n_freq > RB_MAX_FREQ) return 0;
+    const bool tcp = prec == RB_PREC_BF16X3;
     const size_t ne = (size_t)g->n_elem, npix = (size_t)g->nx * g->ny;
     const size_t ncell = (size_t)(g->nx - 1) * (g->ny - 1);
     const size_t nf = (size_t)n_freq;
@@ -143,6 +151,8 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision /*prec*/, WsL
     L->pdir = o; o = align256(o + npix * 4);
     L->part = o; o = align256(o + (size_t)(RB_MAX_FREQ + 2) * 256 * 8);
     L->fwd = o; o = align256(o + (size_t)rb_fwd_chunks_for((int)npix) * ne * ne * 8);
+    L->tcimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_b_images_bytes(g->n_elem) : 0));
+    L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * 8 : 0));
     L->total = o;
     return o;
 }
@@ -253,19 +263,27 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
     if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return RB_ERR_ARG;
     if (!geom_ok(geom)) return RB_ERR_SHAPE;
     if (!(f_hz > 0.0) || !isfinite(f_hz)) return RB_ERR_ARG;
-    if (prec != RB_PREC_FP32) return RB_ERR_UNSUPPORTED;
+    if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
     Ws W;
     rb_status st = check_ws(geom, 1, prec, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     double* exy = W.at<double>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
     const GeoDev G = make_geo(geom, exy);
     FreqSet F;
     F.n = 1;
     F.f[0] = make_freq(geom, f_hz);
     RB_CU(launch_elem_positions(G, exy, s));
-    RB_CU(launch_adjoint_simt(G, tables, c, F, (const float2*)resid, w, (float2*)g_out, hdiag_out, nullptr, nullptr,
-                              nullptr, s));
+    if (prec == RB_PREC_BF16X3) {
+        RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
+        RB_CU(launch_prep_b(G.n_elem, (const float2*)resid, w, W.at<void>(W.L.tcimg), s));
+        RB_CU(launch_adjoint_tc(G, tables, c, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
+                                (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, s));
+    } else {
+        RB_CU(launch_adjoint_simt(G, tables, c, F, (const float2*)resid, w, (float2*)g_out, hdiag_out, nullptr,
+                                  nullptr, nullptr, s));
+    }
     return RB_OK;
 }
 
@@ -280,7 +298,7 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     if (params->step_mode != RB_STEP_EXACT && params->step_mode != RB_STEP_DIAG) return RB_ERR_ARG;
     FreqSet F;
     if (!make_freqs(geom, freqs_hz, n_freq, &F)) return RB_ERR_ARG;
-    if (prec != RB_PREC_FP32) return RB_ERR_UNSUPPORTED;
+    if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
     Ws W;
     rb_status st = check_ws(geom, n_freq, prec, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
@@ -323,7 +341,15 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, cnt, s));
     RB_CU(mark(RB_STAGE_LINK, 1));
     RB_CU(mark(RB_STAGE_ADJOINT, 0));
-    RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));
+    if (prec == RB_PREC_BF16X3) {
+        const size_t img = tc_b_images_bytes(G.n_elem);
+        for (int w = 0; w < n_freq; ++w)
+            RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
+        RB_CU(launch_adjoint_tc(G, tables, c_inout, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
+                                nullptr, nullptr, gsum, hsum, cnt, s));
+    } else {
+        RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));
+    }
     RB_CU(mark(RB_STAGE_ADJOINT, 1));
     RB_CU(mark(RB_STAGE_DIRECTION, 0));
     RB_CU(launch_update(G, c_inout, gsum, hsum, pdir, dc_out, part, dbl, cnt, diag_out, params->eps_rel,

@@ -166,15 +166,18 @@ struct WsLayout {
     size_t pdir;       // [npix] float
     size_t part;       // reduction partials: [n_part] double
     size_t fwd;        // forward partial sums: [n_chunks][n_elem][n_elem] float2
+    size_t tcimg;      // tensor-core path: bf16 B-operand images, [n_freq][image]
+    size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
     size_t total;
 };
 
+#define RB_TC_MAX_CTAS 160
 size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayout* L);
 GeoDev rb_make_geo(const rb_geometry* g, const double* elem_xy);
 FreqC rb_make_freq(const rb_geometry* g, double f_hz);
 
 // counters (uint32 slots)
-enum { CNT_LOST = 0, CNT_HOLES = 1, CNT_UNLINKED = 2, CNT_KEPT = 3, CNT_ZEROED = 4, CNT_CAS_GIVEUP = 5, CNT_N = 64 };
+enum { CNT_LOST = 0, CNT_HOLES = 1, CNT_UNLINKED = 2, CNT_KEPT = 3, CNT_ZEROED = 4, CNT_CAS_GIVEUP = 5, CNT_TC_TIMEOUT = 6, CNT_N = 64 };
 // double scalars after the uint32 block
 enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_HMEAN = 5, DBL_N = 64 };
 
@@ -201,6 +204,12 @@ cudaError_t launch_forward_simt(const GeoDev& G, const rb_cell* tables, const fl
 cudaError_t launch_forward_reduce(const GeoDev& G, const FreqC& F, const float2* partial, int n_chunks,
                                   float2* d_out, const uint8_t* w, double* den_part, cudaStream_t s);
 int rb_fwd_chunks_for(int npix);
+bool tc_adjoint_supported(int n_elem);
+size_t tc_b_images_bytes(int n_elem);
+cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, cudaStream_t s);
+cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
+                              const void* images, float2* gscr, int n_ctas, float2* g_out, float* h_out, float* gsum,
+                              float* hsum, uint32_t* counters, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);
 cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir,

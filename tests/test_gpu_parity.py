@@ -320,3 +320,54 @@ def test_outlier_selection_valid(dev):
     p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, freqs, inp.noise_re, inp.noise_im)
     ref, c_new, dc, d = _update_pair(cfg, inp, inp.c_init, freqs, p_obs, dev, step="diag")
     assert d["zeroed"] == math.floor(0.01 * d["kept"])
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision: tcgen05 BF16 x3 split products, FP32 accumulation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["tiny_init", "tiny_true"])
+def test_born_adjoint_bf16x3(dev, case):
+    cfg, inp, c = _case(case)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    tab, _ = gpu_tables(geom, c, inp.alpha0, dev)
+    ot = ogrid.grid(g, c, inp.alpha0)
+    rng = np.random.default_rng(4)
+    R = (rng.standard_normal((g.n_elem, g.n_elem)) + 1j * rng.standard_normal((g.n_elem, g.n_elem))).astype(np.complex64)
+    W = (rng.uniform(size=(g.n_elem, g.n_elem)) > 0.2).astype(np.uint8)
+    ws = rb.workspace(geom, 1, rb.RB_PREC_BF16X3, dev)
+    ct = _t(c, dev)
+    for f in (cfg.freqs_hz[0], cfg.freqs_hz[-1]):
+        Go = ogreen.green(g, ot, c, f)
+        gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
+        hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+        rb.rb_born_adjoint(geom, tab, ct, f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev), gg, ws, hh,
+                           prec=rb.RB_PREC_BF16X3)
+        go = oborn.born_adjoint(Go, W * R.astype(np.complex128), f)
+        ho = oborn.hess_diag(Go, W, f)
+        eg, eh = rel_l2(gg.cpu().numpy(), go), rel_l2(hh.cpu().numpy(), ho)
+        print(f"bf16x3 {case} f={f:.3g}: gradient rel L2 {eg:.3g}, Hessian diagonal rel L2 {eh:.3g}")
+        assert eg <= 1e-4, eg
+        assert eh <= 1e-4, eh
+
+
+def test_hf_update_bf16x3_tiny(dev):
+    cfg = rbgen.tiny()
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    freqs = [cfg.freqs_hz[1]]
+    p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, freqs, inp.noise_re, inp.noise_im)
+    ref = oupd.hf_update(g, inp.c_init, inp.alpha0, freqs, p_obs)
+    geom = rb.geometry_from_config(cfg)
+    c = _t(inp.c_init, dev)
+    dc = torch.empty_like(c)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    ws = rb.workspace(geom, 1, rb.RB_PREC_BF16X3, dev)
+    rb.rb_hf_update(geom, c, _t(inp.alpha0, dev), freqs, torch.as_tensor(p_obs.astype(np.complex64), device=dev), ws,
+                    prec=rb.RB_PREC_BF16X3, dc_out=dc, diag_out=diag)
+    torch.cuda.synchronize()
+    d = rb.decode_diag(diag)
+    assert d["cas_giveup"] == 0
+    err = np.sqrt(np.mean((dc.cpu().numpy() - ref.dc) ** 2))
+    assert err <= 0.05 * max(1.0, np.sqrt(np.mean(ref.dc ** 2))), err
+    assert abs(d["dc_norm"] - ref.dc_norm) <= 1e-3 * ref.dc_norm
