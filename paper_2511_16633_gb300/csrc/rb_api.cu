@@ -28,7 +28,7 @@ bool geom_ok(const rb_geometry* g) {
     return true;
 }
 
-GeoDev make_geo(const rb_geometry* g, const double* elem_xy) {
+GeoDev make_geo(const rb_geometry* g, const float4* elem_xy) {
     GeoDev G;
     G.n_elem = g->n_elem;
     G.nx = g->nx;
@@ -127,7 +127,7 @@ int tc_ctas() {
 
 }  // namespace
 
-GeoDev rb_make_geo(const rb_geometry* g, const double* elem_xy) { return make_geo(g, elem_xy); }
+GeoDev rb_make_geo(const rb_geometry* g, const float4* elem_xy) { return make_geo(g, elem_xy); }
 FreqC rb_make_freq(const rb_geometry* g, double f_hz) { return make_freq(g, f_hz); }
 
 size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayout* L) {
@@ -153,6 +153,8 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->fwd = o; o = align256(o + (size_t)rb_fwd_chunks_for((int)npix) * ne * ne * 8);
     L->tcimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_b_images_bytes(g->n_elem) : 0));
     L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * 8 : 0));
+    L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
+    L->gimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_gimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->total = o;
     return o;
 }
@@ -189,7 +191,7 @@ rb_status rb_trace_rays(const rb_geometry* geom, const float* c, const float* al
     rb_status st = check_ws(geom, 1, RB_PREC_FP32, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    double* exy = W.at<double>(W.L.elem_xy);
+    float4* exy = W.at<float4>(W.L.elem_xy);
     uint32_t* cnt = W.at<uint32_t>(W.L.counters);
     const GeoDev G = make_geo(geom, exy);
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
@@ -212,7 +214,7 @@ rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* al
     rb_status st = check_ws(geom, 1, RB_PREC_FP32, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    double* exy = W.at<double>(W.L.elem_xy);
+    float4* exy = W.at<float4>(W.L.elem_xy);
     uint32_t* cnt = W.at<uint32_t>(W.L.counters);
     const GeoDev G = make_geo(geom, exy);
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
@@ -241,18 +243,29 @@ rb_status rb_born_forward(const rb_geometry* geom, const rb_cell* tables, const 
     if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return RB_ERR_ARG;
     if (!geom_ok(geom)) return RB_ERR_SHAPE;
     if (!(f_hz > 0.0) || !isfinite(f_hz)) return RB_ERR_ARG;
-    if (prec != RB_PREC_FP32) return RB_ERR_UNSUPPORTED;
+    if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
     Ws W;
     rb_status st = check_ws(geom, 1, prec, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    double* exy = W.at<double>(W.L.elem_xy);
+    float4* exy = W.at<float4>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
     const GeoDev G = make_geo(geom, exy);
     const FreqC F = make_freq(geom, f_hz);
     const int nch = rb_fwd_chunks_for(G.npix);
     RB_CU(launch_elem_positions(G, exy, s));
-    RB_CU(launch_forward_simt(G, tables, c, F, m, W.at<float2>(W.L.fwd), nch, s));
-    RB_CU(launch_forward_reduce(G, F, W.at<float2>(W.L.fwd), nch, (float2*)d_out, nullptr, nullptr, s));
+    if (prec == RB_PREC_BF16X3) {
+        RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
+        FreqSet F1;
+        F1.n = 1;
+        F1.f[0] = F;
+        RB_CU(launch_gimage(G, tables, c, F1, W.at<void>(W.L.gimg), s));
+        RB_CU(launch_forward_tc(G, W.at<void>(W.L.gimg), F, m, W.at<float>(W.L.tcfwd), tc_ctas(), (float2*)d_out,
+                                nullptr, nullptr, cnt, s));
+    } else {
+        RB_CU(launch_forward_simt(G, tables, c, F, m, W.at<float2>(W.L.fwd), nch, s));
+        RB_CU(launch_forward_reduce(G, F, W.at<float2>(W.L.fwd), nch, (float2*)d_out, nullptr, nullptr, s));
+    }
     return RB_OK;
 }
 
@@ -268,7 +281,7 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
     rb_status st = check_ws(geom, 1, prec, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    double* exy = W.at<double>(W.L.elem_xy);
+    float4* exy = W.at<float4>(W.L.elem_xy);
     uint32_t* cnt = W.at<uint32_t>(W.L.counters);
     const GeoDev G = make_geo(geom, exy);
     FreqSet F;
@@ -279,7 +292,7 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
         RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
         RB_CU(launch_prep_b(G.n_elem, (const float2*)resid, w, W.at<void>(W.L.tcimg), s));
         RB_CU(launch_adjoint_tc(G, tables, c, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
-                                (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, s));
+                                (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, nullptr, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c, F, (const float2*)resid, w, (float2*)g_out, hdiag_out, nullptr,
                                   nullptr, nullptr, s));
@@ -303,7 +316,7 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     rb_status st = check_ws(geom, n_freq, prec, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    double* exy = W.at<double>(W.L.elem_xy);
+    float4* exy = W.at<float4>(W.L.elem_xy);
     uint32_t* cnt = W.at<uint32_t>(W.L.counters);
     double* dbl = (double*)(cnt + CNT_N);
     const GeoDev G = make_geo(geom, exy);
@@ -346,7 +359,8 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
         for (int w = 0; w < n_freq; ++w)
             RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
         RB_CU(launch_adjoint_tc(G, tables, c_inout, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
-                                nullptr, nullptr, gsum, hsum, cnt, s));
+                                nullptr, nullptr, gsum, hsum, cnt,
+                                params->step_mode == RB_STEP_EXACT ? W.at<void>(W.L.gimg) : nullptr, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));
     }
@@ -358,8 +372,15 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_FORWARD, 0));
     if (params->step_mode == RB_STEP_EXACT) {
         for (int w = 0; w < n_freq; ++w) {
-            RB_CU(launch_forward_simt(G, tables, c_inout, F.f[w], pdir, fwd, nch, s));
-            RB_CU(launch_forward_reduce(G, F.f[w], fwd, nch, nullptr, wts + (size_t)w * ne2, part + (size_t)w * 256, s));
+            if (prec == RB_PREC_BF16X3) {
+                RB_CU(launch_forward_tc(G, W.at<char>(W.L.gimg) + (size_t)w * tc_gimage_elems(G.n_elem, G.npix) * 2,
+                                        F.f[w], pdir, W.at<float>(W.L.tcfwd), tc_ctas(), nullptr,
+                                        wts + (size_t)w * ne2, part + (size_t)w * 256, cnt, s));
+            } else {
+                RB_CU(launch_forward_simt(G, tables, c_inout, F.f[w], pdir, fwd, nch, s));
+                RB_CU(launch_forward_reduce(G, F.f[w], fwd, nch, nullptr, wts + (size_t)w * ne2,
+                                            part + (size_t)w * 256, s));
+            }
         }
         RB_CU(launch_sum_partials(part, n_freq * 256, dbl, DBL_DEN, 1.0, 0, s));
     }

@@ -35,7 +35,8 @@ __device__ __forceinline__ void synth_tile(const GeoDev& G, const rb_cell* __res
             const rb_cell rec = tables[(size_t)t * G.npix + pix];
             const int ix = pix % G.nx, iy = pix / G.nx;
             if (rec.tkey != RB_HOLE) {
-                const DF ex = df_from_double(G.elem_xy[2 * t]), ey = df_from_double(G.elem_xy[2 * t + 1]);
+                DF ex, ey;
+                elem_pos(G, t, ex, ey);
                 const DF dist = pixel_elem_dist(G, ix, iy, ex, ey);
                 v = green_eval(rec, __ldg(c + pix), dist, F, G.j_floor);
             } else if (count_holes) {
@@ -217,7 +218,8 @@ __global__ void __launch_bounds__(FTHR) k_forward_simt(GeoDev G, const rb_cell* 
                 const rb_cell rec = tables[(size_t)t * G.npix + pix];
                 if (rec.tkey != RB_HOLE) {
                     const int ix = pix % G.nx, iy = pix / G.nx;
-                    const DF ex = df_from_double(G.elem_xy[2 * t]), ey = df_from_double(G.elem_xy[2 * t + 1]);
+                    DF ex, ey;
+                    elem_pos(G, t, ex, ey);
                     v = green_eval(rec, __ldg(c + pix), pixel_elem_dist(G, ix, iy, ex, ey), F, G.j_floor);
                     if (which == 0) {
                         const float mv = __ldg(m + pix);
@@ -300,7 +302,8 @@ __global__ void k_green_out(GeoDev G, const rb_cell* __restrict__ tables, const 
         const int t = (int)(j / G.npix), pix = (int)(j % G.npix);
         const rb_cell rec = tables[j];
         const int ix = pix % G.nx, iy = pix / G.nx;
-        const DF ex = df_from_double(G.elem_xy[2 * t]), ey = df_from_double(G.elem_xy[2 * t + 1]);
+        DF ex, ey;
+        elem_pos(G, t, ex, ey);
         const DF dist = pixel_elem_dist(G, ix, iy, ex, ey);
         const float cv = __ldg(c + pix);
         for (int w = 0; w < F.n; ++w) g[(size_t)w * total + j] = green_eval(rec, cv, dist, F.f[w], G.j_floor);

@@ -19,7 +19,7 @@
 namespace {
 
 constexpr int TP = 128;                 // pixels per tile = MMA M
-constexpr int NTHR = 128;               // threads per CTA: thread = pixel = TMEM lane
+constexpr int NTHR = 256;               // threads per CTA: two per pixel (pixel = TMEM lane)
 constexpr uint32_t kMaxTries = 1u << 22; // mbarrier polls before giving up (each poll suspends briefly)
 
 // ---------------------------------------------------------------------------
@@ -78,215 +78,337 @@ struct TcArgs {
     uint32_t* counters;
     int n_tiles;
     uint32_t tmem_cols;
+    __nv_bfloat16* gimg;       // optional: per-frequency G operand images for the forward (see gimage_seg)
+    size_t gimg_stride;        // bf16 elements per frequency
 };
 
-// cooperative 16-byte copy of `bytes` (multiple of 16) from global to shared
-__device__ __forceinline__ void copy_chunk(void* dst, const void* src, int bytes) {
-    const uint4* s = (const uint4*)src;
-    uint4* d = (uint4*)dst;
-    for (int i = threadIdx.x; i < bytes / 16; i += NTHR) d[i] = __ldg(s + i);
+// G operand image of the forward, per frequency: chunks of 32 pixels, each a hi
+// image then a lo image of 2n rows (r' = 2r + {0: Re, 1: Im}) x 32 pixels in the
+// core-matrix layout.  One call writes the 8-pixel segment starting at pixel
+// pix0 (a multiple of 8) for element r.
+__device__ __forceinline__ void gimage_seg(__nv_bfloat16* img, int n, int pix0, int r, const float2 (&g)[8]) {
+    const int chunk = pix0 >> 5, kg = (pix0 & 31) >> 3;
+    const size_t cimg = (size_t)2 * n * 32;
+    __nv_bfloat16* base = img + (size_t)chunk * 2 * cimg;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+        uint32_t wh[4], wl[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            tc::split_bf16(part == 0 ? g[2 * j].x : g[2 * j].y, h0, l0);
+            tc::split_bf16(part == 0 ? g[2 * j + 1].x : g[2 * j + 1].y, h1, l1);
+            wh[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            wl[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        const uint32_t off = tc::chunk_offset((uint32_t)(2 * r + part), 8u * kg) / 2;
+        *(uint4*)(base + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        *(uint4*)(base + cimg + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    }
+}
+
+// Standalone G images: G_r(x) for every element and pixel at each frequency.
+__global__ void k_gimage(GeoDev G, const rb_cell* __restrict__ tables, const float* __restrict__ c, FreqSet F,
+                         __nv_bfloat16* __restrict__ img, size_t stride) {
+    const int n = G.n_elem;
+    const int nseg = (G.npix + 7) / 8;
+    const long long total = (long long)n * nseg;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(u % n), seg = (int)(u / n);
+        DF ex, ey;
+        elem_pos(G, r, ex, ey);
+        rb_cell rec[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int pix = 8 * seg + j;
+            if (pix < G.npix) rec[j] = tables[(size_t)r * G.npix + pix];
+            else rec[j].tkey = RB_HOLE;
+        }
+        for (int w = 0; w < F.n; ++w) {
+            float2 g[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int pix = 8 * seg + j;
+                g[j] = make_float2(0.f, 0.f);
+                if (rec[j].tkey != RB_HOLE)
+                    g[j] = green_eval(rec[j], __ldg(c + pix), pixel_elem_dist(G, pix % G.nx, pix / G.nx, ex, ey), F.f[w],
+                                      G.j_floor);
+            }
+            gimage_seg(img + (size_t)w * stride, n, 8 * seg, r, g);
+        }
+    }
 }
 
 }  // namespace
 
 namespace {
 
-// Synthesise this thread's pixel row of one A chunk: G_r for r in [r0, r0 + 16),
-// (Re, -Im) split into bf16 hi/lo, stored in the core-matrix layout; exact values to gs.
-__device__ __forceinline__ void synth_a_chunk(const TcArgs& A, const FreqC& fc, int r0, int px, bool valid, int ix,
-                                              int iy, float c_px, float2* gs, unsigned char* sa_hi,
-                                              unsigned char* sa_lo) {
+// Thread (p, h) of a CTA: pixel p = tid % 128 (its TMEM lane), half h = tid / 128.
+// Pack 8 (Re, -Im) or 16 real values of one pixel row into the two core-matrix
+// K-groups 2h, 2h+1 of a 32-wide chunk, as bf16 hi and lo.
+__device__ __forceinline__ void store_rows(unsigned char* a_hi, unsigned char* a_lo, uint32_t p, uint32_t h,
+                                           const uint32_t (&whi)[8], const uint32_t (&wlo)[8]) {
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        const uint32_t off = tc::chunk_offset(p, 8u * (2u * h + g));
+        *(uint4*)(a_hi + off) = make_uint4(whi[4 * g], whi[4 * g + 1], whi[4 * g + 2], whi[4 * g + 3]);
+        *(uint4*)(a_lo + off) = make_uint4(wlo[4 * g], wlo[4 * g + 1], wlo[4 * g + 2], wlo[4 * g + 3]);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// U chunk: G_r(p) for r in [r0 + 8h, r0 + 8h + 8): exact values to gs, bf16 hi/lo of (Re, -Im) to A.
+__device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h, int px,
+                                        bool valid, int ix, int iy, float c_px, float2* gs, unsigned char* a_hi,
+                                        unsigned char* a_lo) {
     const GeoDev& G = A.G;
-    uint32_t whi[16], wlo[16];
-#pragma unroll 4
-    for (int j = 0; j < 16; ++j) {
-        const int r = r0 + j;
+    rb_cell rec[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int r = r0 + 8 * (int)h + j;
+        if (valid) rec[j] = A.tables[(size_t)r * G.npix + px];
+        else rec[j].tkey = RB_HOLE;
+    }
+    uint32_t whi[8], wlo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int r = r0 + 8 * (int)h + j;
         float2 g = make_float2(0.f, 0.f);
-        if (valid) {
-            const rb_cell rec = A.tables[(size_t)r * G.npix + px];
-            if (rec.tkey != RB_HOLE) {
-                const DF ex = df_from_double(G.elem_xy[2 * r]), ey = df_from_double(G.elem_xy[2 * r + 1]);
-                g = green_eval(rec, c_px, pixel_elem_dist(G, ix, iy, ex, ey), fc, G.j_floor);
-            }
+        if (rec[j].tkey != RB_HOLE) {
+            DF ex, ey;
+            elem_pos(G, r, ex, ey);
+            g = green_eval(rec[j], c_px, pixel_elem_dist(G, ix, iy, ex, ey), fc, G.j_floor);
         }
-        gs[(size_t)r * TP + threadIdx.x] = g;
+        gs[(size_t)r * TP + p] = g;
         __nv_bfloat16 h0, l0, h1, l1;
         tc::split_bf16(g.x, h0, l0);
         tc::split_bf16(-g.y, h1, l1);
-        whi[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        wlo[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        whi[j] = pack2(h0, h1);
+        wlo[j] = pack2(l0, l1);
     }
-    const uint32_t row = (uint32_t)threadIdx.x;
-#pragma unroll
-    for (int kg = 0; kg < 4; ++kg) {
-        const uint32_t off = tc::chunk_offset(row, 8u * kg);
-        *(uint4*)(sa_hi + off) = make_uint4(whi[4 * kg], whi[4 * kg + 1], whi[4 * kg + 2], whi[4 * kg + 3]);
-        *(uint4*)(sa_lo + off) = make_uint4(wlo[4 * kg], wlo[4 * kg + 1], wlo[4 * kg + 2], wlo[4 * kg + 3]);
-    }
+    store_rows(a_hi, a_lo, p, h, whi, wlo);
 }
 
-// |G_r(x)|^2 for r in [r0, r0 + 32) from the exact values, split into bf16 hi/lo.
-__device__ __forceinline__ void synth_a2_chunk(int r0, const float2* gs, unsigned char* sa_hi, unsigned char* sa_lo) {
-    uint32_t whi[16], wlo[16];
+// V chunk: |G_r(p)|^2 for r in [r0 + 16h, r0 + 16h + 16) from the exact values.
+__device__ __forceinline__ void synth_v(int r0, uint32_t p, uint32_t h, const float2* gs, unsigned char* a_hi,
+                                        unsigned char* a_lo) {
+    uint32_t whi[8], wlo[8];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const float2 g0 = gs[(size_t)(r0 + 2 * j) * TP + threadIdx.x];
-        const float2 g1 = gs[(size_t)(r0 + 2 * j + 1) * TP + threadIdx.x];
+    for (int j = 0; j < 8; ++j) {
+        const int r = r0 + 16 * (int)h + 2 * j;
+        const float2 g0 = gs[(size_t)r * TP + p], g1 = gs[(size_t)(r + 1) * TP + p];
         __nv_bfloat16 h0, l0, h1, l1;
         tc::split_bf16(g0.x * g0.x + g0.y * g0.y, h0, l0);
         tc::split_bf16(g1.x * g1.x + g1.y * g1.y, h1, l1);
-        whi[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        wlo[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        whi[j] = pack2(h0, h1);
+        wlo[j] = pack2(l0, l1);
     }
-    const uint32_t row = (uint32_t)threadIdx.x;
-#pragma unroll
-    for (int kg = 0; kg < 4; ++kg) {
-        const uint32_t off = tc::chunk_offset(row, 8u * kg);
-        *(uint4*)(sa_hi + off) = make_uint4(whi[4 * kg], whi[4 * kg + 1], whi[4 * kg + 2], whi[4 * kg + 3]);
-        *(uint4*)(sa_lo + off) = make_uint4(wlo[4 * kg], wlo[4 * kg + 1], wlo[4 * kg + 2], wlo[4 * kg + 3]);
-    }
+    store_rows(a_hi, a_lo, p, h, whi, wlo);
 }
 
-constexpr uint32_t OFF_AHI = 0, OFF_ALO = 8192, OFF_B = 16384;
+constexpr uint32_t STAGE = 80u * 1024u;        // A hi (8 KB) + A lo (8 KB) + B (64 KB)
+constexpr uint32_t OFF_ALO = 8192u, OFF_B = 16384u;
+
+// Pipeline state shared by all threads (uniform control flow).
+struct Pipe {
+    uint32_t bph[2], mph[2];
+    bool pend[2];
+    uint32_t q;
+};
 
 __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t s_mbar;
+    __shared__ uint64_t s_bfull[2], s_mdone[2];
     __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
+    __shared__ float s_red[3][TP];
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
     const int tid = threadIdx.x, warp = tid >> 5;
-    unsigned char* sa_hi = smem + OFF_AHI;
-    unsigned char* sa_lo = smem + OFF_ALO;
-    unsigned char* sb_hi = smem + OFF_B;
-    unsigned char* sb_lo = smem + OFF_B + (size_t)n2 * 64;
-    const uint32_t mbar = tc::smem_u32(&s_mbar);
-    if (tid == 0) tc::mbar_init(mbar, 1);
+    const uint32_t p = (uint32_t)(tid & (TP - 1)), h = (uint32_t)(tid / TP);
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(tc::smem_u32(&s_bfull[s]), 1);
+            tc::mbar_init(tc::smem_u32(&s_mdone[s]), 1);
+        }
+        s_err = 0;
+    }
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), A.tmem_cols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
     const int nbk = n2 > 256 ? 2 : 1;
     const int nb_u = n2 / nbk;
     const uint32_t id_u = tc::idesc_bf16_f32(128, (uint32_t)nb_u);
     const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)n);
     const size_t img_u = (size_t)n2 * 32, img_w = (size_t)n * 32;   // bf16 elements
     float2* gs = A.gscr + (size_t)blockIdx.x * n * TP;
-    uint32_t phase = 0;
+    Pipe P = {{0u, 0u}, {0u, 0u}, {false, false}, 0u};
     bool ok = true;
 
+    // wait until the MMAs that read stage s are done (all threads)
+    auto drain = [&](int s) {
+        if (P.pend[s]) {
+            const bool w = tc::mbar_wait(tc::smem_u32(&s_mdone[s]), P.mph[s], kMaxTries);
+            ok = ok && (__syncthreads_and(w ? 1 : 0) != 0);
+            P.mph[s] ^= 1u;
+            P.pend[s] = false;
+        }
+    };
+    // one K chunk: stage s gets B by a bulk copy and A from the producer lambda, then the MMAs
+    auto run_chunk = [&](const void* bsrc, uint32_t bbytes, auto&& produce, auto&& issue) {
+        const int s = (int)(P.q & 1u);
+        drain(s);
+        unsigned char* st = smem + s * STAGE;
+        if (tid == 0) tc::bulk_load(tc::smem_u32(st + OFF_B), bsrc, bbytes, tc::smem_u32(&s_bfull[s]));
+        produce(st, st + OFF_ALO);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            if (!tc::mbar_wait(tc::smem_u32(&s_bfull[s]), P.bph[s], kMaxTries)) s_err = 1;
+            tc::fence_after();
+            issue(tc::smem_u32(st), tc::smem_u32(st + OFF_ALO), tc::smem_u32(st + OFF_B));
+            tc::commit(tc::smem_u32(&s_mdone[s]));
+        }
+        P.bph[s] ^= 1u;
+        P.pend[s] = true;
+        ++P.q;
+    };
+
     for (int tile = blockIdx.x; tile < A.n_tiles && ok; tile += gridDim.x) {
-        const int px = tile * TP + tid;
+        const int px = tile * TP + (int)p;
         const bool valid = px < G.npix;
         const int ix = valid ? px % G.nx : 0, iy = valid ? px / G.nx : 0;
         const float c_px = valid ? __ldg(A.c + px) : 0.f;
         float acc_g = 0.f, acc_h = 0.f;
         for (int fw = 0; fw < A.F.n && ok; ++fw) {
-            const FreqC& fc = A.F.f[fw];
+            const FreqC fc = A.F.f[fw];
             const __nv_bfloat16* bu = A.bu + (size_t)fw * A.bu_stride;
             const __nv_bfloat16* bw = A.bw + (size_t)fw * A.bw_stride;
-            // ---- U = A B^T over K' = 2n, chunks of 32 ----
+            // ---- U over K' = 2n ----
             for (int kc = 0; kc < n2 / 32 && ok; ++kc) {
-                synth_a_chunk(A, fc, kc * 16, px, valid, ix, iy, c_px, gs, sa_hi, sa_lo);
-                copy_chunk(sb_hi, bu + (size_t)kc * 2 * img_u, n2 * 64);
-                copy_chunk(sb_lo, bu + (size_t)kc * 2 * img_u + img_u, n2 * 64);
-                tc::fence_proxy_async();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::fence_after();
-                    for (int ks = 0; ks < 2; ++ks) {
-                        const uint64_t ah = tc::sdesc(tc::smem_u32(sa_hi) + 256u * ks, 128, 512);
-                        const uint64_t al = tc::sdesc(tc::smem_u32(sa_lo) + 256u * ks, 128, 512);
-                        for (int nb = 0; nb < nbk; ++nb) {
-                            const uint32_t boff = (uint32_t)(nb * nb_u / 8) * 512u + 256u * ks;
-                            const uint64_t bh = tc::sdesc(tc::smem_u32(sb_hi) + boff, 128, 512);
-                            const uint64_t bl = tc::sdesc(tc::smem_u32(sb_lo) + boff, 128, 512);
-                            const uint32_t d = tmem + (uint32_t)(nb * nb_u);
-                            tc::mma_bf16(d, ah, bh, id_u, (kc > 0 || ks > 0) ? 1u : 0u);
-                            tc::mma_bf16(d, ah, bl, id_u, 1u);
-                            tc::mma_bf16(d, al, bh, id_u, 1u);
+                run_chunk(
+                    bu + (size_t)kc * 2 * img_u, (uint32_t)(2 * n2 * 64),
+                    [&](unsigned char* ahi, unsigned char* alo) {
+                        synth_u(A, fc, kc * 16, p, h, px, valid, ix, iy, c_px, gs, ahi, alo);
+                    },
+                    [&](uint32_t ahi, uint32_t alo, uint32_t b) {
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const uint64_t dah = tc::sdesc(ahi + 256u * ks, 128, 512);
+                            const uint64_t dal = tc::sdesc(alo + 256u * ks, 128, 512);
+                            for (int nb = 0; nb < nbk; ++nb) {
+                                const uint32_t boff = (uint32_t)(nb * nb_u / 8) * 512u + 256u * ks;
+                                const uint64_t dbh = tc::sdesc(b + boff, 128, 512);
+                                const uint64_t dbl = tc::sdesc(b + (uint32_t)(n2 * 64) + boff, 128, 512);
+                                const uint32_t d = tmem + (uint32_t)(nb * nb_u);
+                                tc::mma_bf16(d, dah, dbh, id_u, (kc > 0 || ks > 0) ? 1u : 0u);
+                                tc::mma_bf16(d, dah, dbl, id_u, 1u);
+                                tc::mma_bf16(d, dal, dbh, id_u, 1u);
+                            }
+                        }
+                    });
+            }
+            drain(0);
+            drain(1);
+            ok = ok && (__syncthreads_or(s_err) == 0);
+            if (!ok) break;
+            if (A.gimg) {
+                // this tile's exact G (complete in gs) as forward operand images
+                __nv_bfloat16* img = A.gimg + (size_t)fw * A.gimg_stride;
+                for (int u = tid; u < n * (TP / 8); u += NTHR) {
+                    const int r = u % n, seg = u / n;
+                    float2 g[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) g[j] = gs[(size_t)r * TP + 8 * seg + j];
+                    gimage_seg(img, n, tile * TP + 8 * seg, r, g);
+                }
+            }
+            tc::fence_after();
+            // epilogue: this thread takes elements e in [h n/2, (h+1) n/2)
+            float gr = 0.f, gi = 0.f;
+            for (int half = 0; half < 2; ++half) {            // half 0: Re U, half 1: Im U
+                for (int cb = (int)h * (n / 2); cb < ((int)h + 1) * (n / 2); cb += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + lane_off + (uint32_t)(half * n + cb), v);
+#pragma unroll 8
+                    for (int j = 0; j < 32; ++j) {
+                        const float2 ge = gs[(size_t)(cb + j) * TP + p];
+                        if (half == 0) {
+                            gr = fmaf(ge.x, v[j], gr);
+                            gi = fmaf(-ge.y, v[j], gi);
+                        } else {
+                            gr = fmaf(ge.y, v[j], gr);
+                            gi = fmaf(ge.x, v[j], gi);
                         }
                     }
-                    tc::commit(mbar);
-                }
-                ok = __syncthreads_and(tc::mbar_wait(mbar, phase, kMaxTries) ? 1 : 0) != 0;
-                phase ^= 1u;
-            }
-            if (!ok) break;
-            tc::fence_after();
-            float gr = 0.f, gi = 0.f;
-            for (int cb = 0; cb < n2; cb += 32) {
-                float v[32];
-                tc::tmem_ld32(tmem + lane_off + (uint32_t)cb, v);
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) {
-                    const int ep = cb + j;
-                    const int e = ep < n ? ep : ep - n;
-                    const float2 ge = gs[(size_t)e * TP + tid];
-                    if (ep < n) {
-                        gr = fmaf(ge.x, v[j], gr);
-                        gi = fmaf(-ge.y, v[j], gi);
-                    } else {
-                        gr = fmaf(ge.y, v[j], gr);
-                        gi = fmaf(ge.x, v[j], gi);
-                    }
                 }
             }
-            gr *= fc.w2;
-            gi *= fc.w2;
-            if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
-            acc_g += gr;
+            if (h == 1) {
+                s_red[0][p] = gr;
+                s_red[1][p] = gi;
+            }
             tc::fence_before();
             __syncthreads();
-            // ---- V = A2 W^T over K = n, chunks of 32 (accumulator reuses the first n columns) ----
-            for (int kc = 0; kc < n / 32 && ok; ++kc) {
-                synth_a2_chunk(kc * 32, gs, sa_hi, sa_lo);
-                copy_chunk(sb_hi, bw + (size_t)kc * img_w, n * 64);
-                tc::fence_proxy_async();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::fence_after();
-                    for (int ks = 0; ks < 2; ++ks) {
-                        const uint64_t ah = tc::sdesc(tc::smem_u32(sa_hi) + 256u * ks, 128, 512);
-                        const uint64_t al = tc::sdesc(tc::smem_u32(sa_lo) + 256u * ks, 128, 512);
-                        const uint64_t b = tc::sdesc(tc::smem_u32(sb_hi) + 256u * ks, 128, 512);
-                        tc::mma_bf16(tmem, ah, b, id_v, (kc > 0 || ks > 0) ? 1u : 0u);
-                        tc::mma_bf16(tmem, al, b, id_v, 1u);
-                    }
-                    tc::commit(mbar);
-                }
-                ok = __syncthreads_and(tc::mbar_wait(mbar, phase, kMaxTries) ? 1 : 0) != 0;
-                phase ^= 1u;
+            if (h == 0) {
+                gr = (gr + s_red[0][p]) * fc.w2;
+                gi = (gi + s_red[1][p]) * fc.w2;
+                if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
+                acc_g += gr;
             }
+            // ---- V over K = n (accumulator reuses the first n columns) ----
+            for (int kc = 0; kc < n / 32 && ok; ++kc) {
+                run_chunk(
+                    bw + (size_t)kc * img_w, (uint32_t)(n * 64),
+                    [&](unsigned char* ahi, unsigned char* alo) { synth_v(kc * 32, p, h, gs, ahi, alo); },
+                    [&](uint32_t ahi, uint32_t alo, uint32_t b) {
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const uint64_t dah = tc::sdesc(ahi + 256u * ks, 128, 512);
+                            const uint64_t dal = tc::sdesc(alo + 256u * ks, 128, 512);
+                            const uint64_t db = tc::sdesc(b + 256u * ks, 128, 512);
+                            tc::mma_bf16(tmem, dah, db, id_v, (kc > 0 || ks > 0) ? 1u : 0u);
+                            tc::mma_bf16(tmem, dal, db, id_v, 1u);
+                        }
+                    });
+            }
+            drain(0);
+            drain(1);
+            ok = ok && (__syncthreads_or(s_err) == 0);
             if (!ok) break;
             tc::fence_after();
             float hh = 0.f;
-            for (int cb = 0; cb < n; cb += 32) {
+            for (int cb = (int)h * (n / 2); cb < ((int)h + 1) * (n / 2); cb += 32) {
                 float v[32];
                 tc::tmem_ld32(tmem + lane_off + (uint32_t)cb, v);
 #pragma unroll 8
                 for (int j = 0; j < 32; ++j) {
-                    const float2 ge = gs[(size_t)(cb + j) * TP + tid];
+                    const float2 ge = gs[(size_t)(cb + j) * TP + p];
                     hh = fmaf(ge.x * ge.x + ge.y * ge.y, v[j], hh);
                 }
             }
-            hh *= fc.w4;
-            if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = hh;
-            acc_h += hh;
+            if (h == 1) s_red[2][p] = hh;
             tc::fence_before();
             __syncthreads();
+            if (h == 0) {
+                hh = (hh + s_red[2][p]) * fc.w4;
+                if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = hh;
+                acc_h += hh;
+            }
         }
-        if (ok && valid) {
+        if (ok && valid && h == 0) {
             if (A.gsum) A.gsum[px] = acc_g;
             if (A.hsum) A.hsum[px] = acc_h;
         }
     }
     if (!ok) {
-        // a wait ran out: report it, give the tensor core a bounded last chance to drain, then free TMEM
+        // a wait ran out: report it, give outstanding MMAs a bounded chance to drain, then free TMEM
         if (tid == 0) atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
-        tc::mbar_wait(mbar, phase ^ 1u, kMaxTries);
+        for (int s = 0; s < 2; ++s)
+            if (P.pend[s]) tc::mbar_wait(tc::smem_u32(&s_mdone[s]), P.mph[s], kMaxTries);
     }
     tc::fence_before();
     __syncthreads();
@@ -295,7 +417,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
 
 }  // namespace
 
-bool tc_adjoint_supported(int n_elem) { return n_elem >= 32 && n_elem <= 256 && n_elem % 32 == 0; }
+bool tc_adjoint_supported(int n_elem) { return n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0; }
 
 size_t tc_b_images_bytes(int n_elem) {
     const size_t n = (size_t)n_elem;
@@ -311,7 +433,7 @@ cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, c
 
 cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                               const void* images, float2* gscr, int n_ctas, float2* g_out, float* h_out, float* gsum,
-                              float* hsum, uint32_t* counters, cudaStream_t s) {
+                              float* hsum, uint32_t* counters, void* gimg, cudaStream_t s) {
     const int n = G.n_elem;
     if (!tc_adjoint_supported(n)) return cudaErrorInvalidValue;
     TcArgs A;
@@ -329,15 +451,318 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const floa
     A.gsum = gsum;
     A.hsum = hsum;
     A.counters = counters;
+    A.gimg = (__nv_bfloat16*)gimg;
+    A.gimg_stride = tc_gimage_elems(n, G.npix);
     A.n_tiles = (G.npix + TP - 1) / TP;
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * n)) cols <<= 1;
     A.tmem_cols = cols;
-    // more than half of the SM's shared memory: one CTA (one TMEM owner) per SM
-    const int sm = 120 * 1024;
+    // two pipeline stages of 80 KB: more than half of the SM's shared memory, so one
+    // CTA (one TMEM owner) per SM
+    const int sm = 2 * 80 * 1024;
     cudaError_t e = cudaFuncSetAttribute(k_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     const int grid = n_ctas < A.n_tiles ? n_ctas : A.n_tiles;
     k_adjoint_tc<<<grid, NTHR, sm, s>>>(A);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Born forward on the tensor cores:  d[e][r] = w^2 sum_x G_e(x) G_r(x) m(x)
+// Real form over K = pixels: rows e' = 2e + {0: Re, 1: Im} of A = G m and columns
+// r' = 2r + {0, 1} of B = G give D = A B^T (2n x 2n, symmetric), from which
+//   Re d = D[2e][2r] - D[2e+1][2r+1],  Im d = D[2e][2r+1] + D[2e+1][2r].
+// CTA (i, s): 128-row block i of D over pixel split s, all needed column blocks
+// in TMEM; column blocks below the diagonal are skipped (symmetry).  Partial D
+// blocks go to global memory and a second kernel sums the splits in order.
+// ===========================================================================
+namespace {
+
+constexpr int FMAXB = 8;   // max row blocks (2n / 128, n <= 256 -> 4)
+
+struct FwdArgs {
+    GeoDev G;
+    FreqC F;
+    const __nv_bfloat16* gimg;   // G operand images of this frequency
+    const float* m;
+    float* partial;            // [cta][128][2n] fp32 (only needed columns written)
+    int n_mb;                  // row blocks
+    int nbn, nb;               // column blocks and their width
+    int splits[FMAXB];         // splits per row block
+    int cta0[FMAXB + 1];       // first CTA of each row block
+    uint32_t tmem_cols;
+    uint32_t* counters;
+};
+
+__host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i) / nb; }
+
+__global__ void __launch_bounds__(NTHR, 1) k_forward_tc(FwdArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t s_bfull[2], s_mdone[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_err;
+    const GeoDev& G = A.G;
+    const int n = G.n_elem, n2 = 2 * n;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    int i = 0;
+    while (i + 1 < A.n_mb && (int)blockIdx.x >= A.cta0[i + 1]) ++i;
+    const int s = (int)blockIdx.x - A.cta0[i];
+    const int S = A.splits[i];
+    const int jmin = jmin_of(i, A.nb);
+    const int col0 = jmin * A.nb;             // first needed column (= first B row loaded)
+    const int nchunk_all = (G.npix + 31) / 32;
+    const int cpc = (nchunk_all + S - 1) / S;
+    const int cbeg = min(nchunk_all, s * cpc), cend = min(nchunk_all, cbeg + cpc);
+    const int nq = cend - cbeg;
+    const size_t cimg = (size_t)n2 * 32;                         // bf16 per hi or lo image of a chunk
+    const uint32_t rows_bytes = (uint32_t)(n2 - col0) * 64u;     // loaded rows [col0, 2n) of one image
+    const uint32_t row0_bytes = (uint32_t)col0 * 64u;
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(tc::smem_u32(&s_bfull[k]), 1);
+            tc::mbar_init(tc::smem_u32(&s_mdone[k]), 1);
+        }
+        s_err = 0;
+    }
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), A.tmem_cols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t id = tc::idesc_bf16_f32(128, (uint32_t)A.nb);
+    uint32_t bph[2] = {0u, 0u}, mph[2] = {0u, 0u};
+    bool mpend[2] = {false, false};
+    bool ok = true;
+    // stage layout: A hi | A lo | B hi (rows col0..2n) | B lo
+    auto stage = [&](int k) { return smem + k * STAGE; };
+    auto issue_copy = [&](int q) {   // thread 0: chunk q into stage q & 1
+        const int k = q & 1;
+        unsigned char* st = stage(k);
+        const __nv_bfloat16* src = A.gimg + (size_t)(cbeg + q) * 2 * cimg;
+        const uint32_t mb = tc::smem_u32(&s_bfull[k]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * rows_bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(st + OFF_B)),
+                     "l"((const char*)src + row0_bytes), "r"(rows_bytes), "r"(mb)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(st + OFF_B + rows_bytes)),
+                     "l"((const char*)(src + cimg) + row0_bytes), "r"(rows_bytes), "r"(mb)
+                     : "memory");
+    };
+    if (tid == 0 && nq > 0) issue_copy(0);
+    for (int q = 0; q < nq && ok; ++q) {
+        const int k = q & 1;
+        unsigned char* st = stage(k);
+        unsigned char* a_hi = st;
+        unsigned char* a_lo = st + OFF_ALO;
+        const unsigned char* b_hi = st + OFF_B;                   // holds rows [col0, 2n)
+        const unsigned char* b_lo = st + OFF_B + rows_bytes;
+        ok = __syncthreads_and(tc::mbar_wait(tc::smem_u32(&s_bfull[k]), bph[k], kMaxTries) ? 1 : 0) != 0;
+        bph[k] ^= 1u;
+        if (!ok) break;
+        // A = rows [128 i, 128 i + 128) of B scaled by p(x), re-split into hi / lo
+        const int p0 = (cbeg + q) * 32;
+        for (int u = tid; u < 128 * 4; u += NTHR) {
+            const int row = u & 127, kg = u >> 7;
+            const uint32_t boff = tc::chunk_offset((uint32_t)(128 * i + row - col0), 8u * kg);
+            const uint4 vh = *(const uint4*)(b_hi + boff), vl = *(const uint4*)(b_lo + boff);
+            const uint32_t hw[4] = {vh.x, vh.y, vh.z, vh.w}, lw[4] = {vl.x, vl.y, vl.z, vl.w};
+            uint32_t oh[4], ol[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int pix = p0 + 8 * kg + 2 * j;
+                const float m0 = pix < G.npix ? __ldg(A.m + pix) : 0.f;
+                const float m1 = pix + 1 < G.npix ? __ldg(A.m + pix + 1) : 0.f;
+                const float x0 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[j] & 0xffff))) +
+                                  __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[j] & 0xffff)))) * m0;
+                const float x1 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[j] >> 16))) +
+                                  __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[j] >> 16)))) * m1;
+                __nv_bfloat16 h0, l0, h1, l1;
+                tc::split_bf16(x0, h0, l0);
+                tc::split_bf16(x1, h1, l1);
+                oh[j] = pack2(h0, h1);
+                ol[j] = pack2(l0, l1);
+            }
+            const uint32_t aoff = tc::chunk_offset((uint32_t)row, 8u * kg);
+            *(uint4*)(a_hi + aoff) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+            *(uint4*)(a_lo + aoff) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t sa_hi = tc::smem_u32(a_hi), sa_lo = tc::smem_u32(a_lo);
+            const uint32_t sb_hi = tc::smem_u32(b_hi), sb_lo = tc::smem_u32(b_lo);
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t dah = tc::sdesc(sa_hi + 256u * ks, 128, 512);
+                const uint64_t dal = tc::sdesc(sa_lo + 256u * ks, 128, 512);
+                for (int j = jmin; j < A.nbn; ++j) {
+                    const uint32_t boff = (uint32_t)((j * A.nb - col0) / 8) * 512u + 256u * ks;
+                    const uint64_t dbh = tc::sdesc(sb_hi + boff, 128, 512);
+                    const uint64_t dbl = tc::sdesc(sb_lo + boff, 128, 512);
+                    const uint32_t d = tmem + (uint32_t)(j * A.nb);
+                    tc::mma_bf16(d, dah, dbh, id, (q > 0 || ks > 0) ? 1u : 0u);
+                    tc::mma_bf16(d, dah, dbl, id, 1u);
+                    tc::mma_bf16(d, dal, dbh, id, 1u);
+                }
+            }
+            tc::commit(tc::smem_u32(&s_mdone[k]));
+            // next chunk into the other stage once the MMAs that read it (chunk q - 1) are done
+            if (q + 1 < nq) {
+                const int k2 = (q + 1) & 1;
+                if (mpend[k2]) {
+                    if (!tc::mbar_wait(tc::smem_u32(&s_mdone[k2]), mph[k2], kMaxTries)) s_err = 1;
+                }
+                issue_copy(q + 1);
+            }
+        }
+        // every thread tracks the same barrier phases
+        if (q + 1 < nq && mpend[(q + 1) & 1]) {
+            mph[(q + 1) & 1] ^= 1u;
+            mpend[(q + 1) & 1] = false;
+        }
+        mpend[k] = true;
+        ok = ok && (__syncthreads_or(s_err) == 0);
+    }
+    for (int k = 0; k < 2; ++k)
+        if (mpend[k]) {
+            const bool w = tc::mbar_wait(tc::smem_u32(&s_mdone[k]), mph[k], kMaxTries);
+            ok = ok && (__syncthreads_and(w ? 1 : 0) != 0);
+            mph[k] ^= 1u;
+            mpend[k] = false;
+        }
+    tc::fence_after();
+    if (ok) {
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const int row = tid & 127, hh = tid >> 7;
+        float* out = A.partial + ((size_t)blockIdx.x * 128 + row) * n2;
+        int cnum = 0;
+        for (int cb = col0; cb < n2; cb += 32, ++cnum) {
+            if ((cnum & 1) != hh) continue;
+            float v[32];
+            if (nq > 0) {
+                tc::tmem_ld32(tmem + lane_off + (uint32_t)cb, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) *(float4*)(out + cb + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+    } else if (tid == 0) {
+        atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, A.tmem_cols);
+}
+
+// d = w^2 (sum over splits of the partial D blocks, symmetric lookup), and
+// per-block partial sums of W |d|^2.
+__global__ void k_forward_tc_reduce(FwdArgs A, float2* __restrict__ d_out, const uint8_t* __restrict__ w,
+                                    double* __restrict__ den_part) {
+    const int n = A.G.n_elem, n2 = 2 * n;
+    auto Dval = [&](int row, int col) -> float {
+        int i = row >> 7, j = col / A.nb;
+        if (j < jmin_of(i, A.nb)) {   // below the diagonal blocks: use the transpose
+            const int t = row;
+            row = col;
+            col = t;
+            i = row >> 7;
+        }
+        float acc = 0.f;
+        for (int s = 0; s < A.splits[i]; ++s)
+            acc += A.partial[((size_t)(A.cta0[i] + s) * 128 + (row & 127)) * n2 + col];
+        return acc;
+    };
+    double acc = 0.0;
+    const long long total = (long long)n * n;
+    for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < total;
+         jj += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(jj / n), r = (int)(jj % n);
+        const float dre = (Dval(2 * e, 2 * r) - Dval(2 * e + 1, 2 * r + 1)) * A.F.w2;
+        const float dim = (Dval(2 * e, 2 * r + 1) + Dval(2 * e + 1, 2 * r)) * A.F.w2;
+        if (d_out) d_out[jj] = make_float2(dre, dim);
+        if (w && w[jj]) acc += (double)dre * dre + (double)dim * dim;
+    }
+    if (den_part) {
+        __shared__ double sred[256];
+        sred[threadIdx.x] = acc;
+        __syncthreads();
+        for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+            if (threadIdx.x < k) sred[threadIdx.x] += sred[threadIdx.x + k];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) den_part[blockIdx.x] = sred[0];
+    }
+}
+
+FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const __nv_bfloat16* gimg, const float* m, float* partial,
+                      int n_ctas, uint32_t* counters) {
+    FwdArgs A;
+    A.G = G;
+    A.F = F;
+    A.gimg = gimg;
+    A.m = m;
+    A.partial = partial;
+    A.counters = counters;
+    const int n2 = 2 * G.n_elem;
+    A.n_mb = n2 / 128;
+    A.nbn = (n2 + 255) / 256;
+    A.nb = n2 / A.nbn;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)n2) cols <<= 1;
+    A.tmem_cols = cols;
+    // splits per row block in proportion to the number of column blocks it computes
+    int wsum = 0, wts[FMAXB];
+    for (int i = 0; i < A.n_mb; ++i) {
+        wts[i] = A.nbn - jmin_of(i, A.nb);
+        wsum += wts[i];
+    }
+    int c0 = 0;
+    for (int i = 0; i < A.n_mb; ++i) {
+        int s = (int)((long long)n_ctas * wts[i] / wsum);
+        if (s < 1) s = 1;
+        A.splits[i] = s;
+        A.cta0[i] = c0;
+        c0 += s;
+    }
+    A.cta0[A.n_mb] = c0;
+    return A;
+}
+
+}  // namespace
+
+size_t tc_forward_partial_bytes(int n_elem, int n_ctas) {
+    return (size_t)(n_ctas + FMAXB) * 128 * (2 * (size_t)n_elem) * sizeof(float);
+}
+
+size_t tc_gimage_elems(int n_elem, int npix) {
+    const size_t chunks = (size_t)((npix + 127) / 128) * 4;
+    return chunks * 2 * (2 * (size_t)n_elem) * 32;
+}
+
+cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F, void* img,
+                          cudaStream_t s) {
+    const long long total = (long long)G.n_elem * ((G.npix + 7) / 8);
+    long long blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_gimage<<<(int)blocks, 256, 0, s>>>(G, tables, c, F, (__nv_bfloat16*)img, tc_gimage_elems(G.n_elem, G.npix));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F, const float* m, float* partial,
+                              int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
+                              cudaStream_t s) {
+    if (!tc_adjoint_supported(G.n_elem)) return cudaErrorInvalidValue;
+    const FwdArgs A = make_fwd_args(G, F, (const __nv_bfloat16*)gimg, m, partial, n_ctas, counters);
+    const int sm = 2 * 80 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    k_forward_tc<<<A.cta0[A.n_mb], NTHR, sm, s>>>(A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_forward_tc_reduce<<<256, 256, 0, s>>>(A, d_out, w, den_part);
     return cudaGetLastError();
 }

@@ -16,17 +16,17 @@
 // registers until it leaves the cell.
 #include "rb_internal.cuh"
 
-__global__ void k_elem_positions(GeoDev G, double* xy) {
+__global__ void k_elem_positions(GeoDev G, float4* xy) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= G.n_elem) return;
     double phi = 2.0 * RB_PI_D * (double)t / (double)G.n_elem;
     double s, c;
     sincos(phi, &s, &c);
-    xy[2 * t] = G.R_d * c;
-    xy[2 * t + 1] = G.R_d * s;
+    const DF x = df_from_double(G.R_d * c), y = df_from_double(G.R_d * s);
+    xy[t] = make_float4(x.hi, x.lo, y.hi, y.lo);
 }
 
-cudaError_t launch_elem_positions(const GeoDev& G, double* elem_xy, cudaStream_t s) {
+cudaError_t launch_elem_positions(const GeoDev& G, float4* elem_xy, cudaStream_t s) {
     k_elem_positions<<<(G.n_elem + 127) / 128, 128, 0, s>>>(G, elem_xy);
     return cudaGetLastError();
 }

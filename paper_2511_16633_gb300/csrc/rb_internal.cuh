@@ -23,7 +23,7 @@ struct GeoDev {
     float j_floor;              // h / 4
     double R_d, ds_d, c_ref_d, h_d;
     long long r2max;            // support test on (2ix-(nx-1))^2 + (2iy-(ny-1))^2
-    const double* elem_xy;      // [n_elem][2] element positions (double), in workspace
+    const float4* elem_xy;      // [n_elem] element positions as float pairs {x_hi, x_lo, y_hi, y_lo}
 };
 
 // Per-frequency constants of the Green's function (host-computed in double).
@@ -138,6 +138,13 @@ __device__ __forceinline__ float2 green_eval(const rb_cell& rec, float c_px, DF 
     return make_float2(amp * co, amp * s);
 }
 
+// Element t's position as float pairs.
+__device__ __forceinline__ void elem_pos(const GeoDev& G, int t, DF& ex, DF& ey) {
+    const float4 e = G.elem_xy[t];
+    ex = DF{e.x, e.y};
+    ey = DF{e.z, e.w};
+}
+
 // |pixel - x_t| as a float pair.
 __device__ __forceinline__ DF pixel_elem_dist(const GeoDev& G, int ix, int iy, DF ex, DF ey) {
     DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
@@ -152,7 +159,7 @@ __device__ __forceinline__ DF pixel_elem_dist(const GeoDev& G, int ix, int iy, D
 // Workspace layout (host side).
 // ---------------------------------------------------------------------------
 struct WsLayout {
-    size_t elem_xy;    // [n_elem][2] double
+    size_t elem_xy;    // [n_elem] float4 {x_hi, x_lo, y_hi, y_lo}
     size_t cells;      // [(ny-1)(nx-1)][8] float4
     size_t tables;     // [n_elem][npix] rb_cell
     size_t ends;       // [n_elem][n_rays] rb_ray_end
@@ -168,12 +175,14 @@ struct WsLayout {
     size_t fwd;        // forward partial sums: [n_chunks][n_elem][n_elem] float2
     size_t tcimg;      // tensor-core path: bf16 B-operand images, [n_freq][image]
     size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
+    size_t tcfwd;      // tensor-core path: partial D blocks of the forward
+    size_t gimg;       // tensor-core path: G operand images of the forward, [n_freq][...] bf16
     size_t total;
 };
 
 #define RB_TC_MAX_CTAS 160
 size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayout* L);
-GeoDev rb_make_geo(const rb_geometry* g, const double* elem_xy);
+GeoDev rb_make_geo(const rb_geometry* g, const float4* elem_xy);
 FreqC rb_make_freq(const rb_geometry* g, double f_hz);
 
 // counters (uint32 slots)
@@ -184,7 +193,7 @@ enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files); all return cudaGetLastError().
 // ---------------------------------------------------------------------------
-cudaError_t launch_elem_positions(const GeoDev& G, double* elem_xy, cudaStream_t s);
+cudaError_t launch_elem_positions(const GeoDev& G, float4* elem_xy, cudaStream_t s);
 cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s);
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          rb_cell* tables, uint32_t* counters, cudaStream_t s);
@@ -207,9 +216,16 @@ int rb_fwd_chunks_for(int npix);
 bool tc_adjoint_supported(int n_elem);
 size_t tc_b_images_bytes(int n_elem);
 cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, cudaStream_t s);
+size_t tc_forward_partial_bytes(int n_elem, int n_ctas);
+size_t tc_gimage_elems(int n_elem, int npix);
+cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F, void* img,
+                          cudaStream_t s);
+cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F, const float* m, float* partial,
+                              int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
+                              cudaStream_t s);
 cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                               const void* images, float2* gscr, int n_ctas, float2* g_out, float* h_out, float* gsum,
-                              float* hsum, uint32_t* counters, cudaStream_t s);
+                              float* hsum, uint32_t* counters, void* gimg, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);
 cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir,

@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr size_t kElemBytes = 16u * 1024u;                    // [n_elem <= 1024][2] double
+constexpr size_t kElemBytes = 16u * 1024u;                    // [n_elem <= 1024] float4 positions
 constexpr size_t kPartialBytes = (size_t)RB_NOALLOC_SCRATCH_BYTES - kElemBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RB_NOALLOC_SCRATCH_BYTES];
@@ -66,7 +66,7 @@ extern "C" rb_status rb_born_forward_noalloc(const rb_geometry* geom, const rb_c
     if ((size_t)geom->n_elem * 16 > kElemBytes || per_chunk > kPartialBytes) return RB_ERR_SHAPE;
     void* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return RB_ERR_CUDA;
-    double* exy = (double*)base;
+    float4* exy = (float4*)base;
     float2* partial = (float2*)((char*)base + kElemBytes);
     int nch = rb_fwd_chunks_for(geom->nx * geom->ny);
     const int fit = (int)(kPartialBytes / per_chunk);

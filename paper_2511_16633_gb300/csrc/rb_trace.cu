@@ -285,8 +285,9 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     rb_cell* tab = tables ? tables + (size_t)t * G.npix : nullptr;
     uint32_t* giveup = counters + CNT_CAS_GIVEUP;
 
-    const double xs_d = G.elem_xy[2 * t], ys_d = G.elem_xy[2 * t + 1];
-    const DF xs = df_from_double(xs_d), ys = df_from_double(ys_d);
+    DF xs, ys;
+    elem_pos(G, t, xs, ys);
+    const double xs_d = (double)xs.hi + (double)xs.lo, ys_d = (double)ys.hi + (double)ys.lo;
     const double th0 = 2.0 * RB_PI_D * (double)t / (double)G.n_elem + 0.5 * RB_PI_D +
                        ((double)i + 0.5) * RB_PI_D / (double)G.n_rays;
     const DF thd = df_from_double(th0);

@@ -58,7 +58,8 @@ def _random_data(n, seed):
     return R, W
 
 
-def test_breast256_tables_and_adjoint(dev):
+@pytest.mark.parametrize("prec", [rb.RB_PREC_FP32, rb.RB_PREC_BF16X3])
+def test_breast256_tables_and_adjoint(dev, prec):
     cfg = rbgen.breast256()
     inp = rbgen.make_inputs(cfg)
     g = ogeom.from_config(cfg)
@@ -77,8 +78,9 @@ def test_breast256_tables_and_adjoint(dev):
     f = cfg.freqs_hz[-1]
     gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
     hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+    ws = rb.workspace(geom, 1, prec, dev)
     rb.rb_born_adjoint(geom, tab, _t(inp.c_init, dev), f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev),
-                       gg, ws, hh)
+                       gg, ws, hh, prec=prec)
     Go = ogreen.green(g, ot, inp.c_init, f)
     go = oborn.born_adjoint(Go, W * R.astype(np.complex128), f)
     ho = oborn.hess_diag(Go, W, f)
@@ -112,7 +114,8 @@ def test_breast512_endpoints(dev, big):
     assert np.all(relT <= np.maximum(bound, 1e-6))
 
 
-def test_breast512_sampled_tables_and_adjoint(dev, big):
+@pytest.mark.parametrize("prec", [rb.RB_PREC_FP32, rb.RB_PREC_BF16X3])
+def test_breast512_sampled_tables_and_adjoint(dev, big, prec):
     cfg, inp, g, geom = big
     rng = np.random.default_rng(12)
     sup = np.flatnonzero(ogeom.support_mask(g).ravel())
@@ -129,8 +132,9 @@ def test_breast512_sampled_tables_and_adjoint(dev, big):
     f = cfg.freqs_hz[-1]
     gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
     hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+    ws = rb.workspace(geom, 1, prec, dev)
     rb.rb_born_adjoint(geom, tab, _t(inp.c_init, dev), f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev),
-                       gg, ws, hh)
+                       gg, ws, hh, prec=prec)
     Go = ogreen.green(g, ot, inp.c_init, f, pix=pix)
     go = oborn.born_adjoint(Go, W * R.astype(np.complex128), f)
     ho = oborn.hess_diag(Go, W, f)
@@ -138,16 +142,17 @@ def test_breast512_sampled_tables_and_adjoint(dev, big):
     assert rel_l2(hh.cpu().numpy()[pix], ho) <= 1e-4
 
 
-def test_breast512_update_properties(dev, big):
+@pytest.mark.parametrize("prec", [rb.RB_PREC_FP32, rb.RB_PREC_BF16X3])
+def test_breast512_update_properties(dev, big, prec):
     cfg, inp, g, geom = big
     c0 = _t(inp.c_init, dev)
     a0 = _t(inp.alpha0, dev)
     p = synth_data(geom, c0, _t(inp.c_true, dev), a0, list(cfg.freqs_hz[:4]), inp.noise_re, inp.noise_im)
-    ws = rb.workspace(geom, 4, rb.RB_PREC_FP32, dev)
+    ws = rb.workspace(geom, 4, prec, dev)
     c = c0.clone()
     dc = torch.empty_like(c)
     diag = torch.zeros(48, dtype=torch.uint8, device=dev)
-    rb.rb_hf_update(geom, c, a0, list(cfg.freqs_hz[:4]), p, ws, dc_out=dc, diag_out=diag)
+    rb.rb_hf_update(geom, c, a0, list(cfg.freqs_hz[:4]), p, ws, prec=prec, dc_out=dc, diag_out=diag)
     torch.cuda.synchronize()
     dd = rb.decode_diag(diag)
     dcn = dc.cpu().numpy().astype(np.float64)
@@ -162,3 +167,21 @@ def test_breast512_update_properties(dev, big):
     assert dd["alpha"] > 0
     # the step lowers the linearised objective: c moved by dc exactly
     assert np.allclose(c.cpu().numpy(), inp.c_init + dc.cpu().numpy(), rtol=0, atol=1e-3)
+
+
+def test_breast256_forward_bf16x3(dev):
+    cfg = rbgen.breast256()
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    tab, _ = _tables(geom, inp.c_init, inp.alpha0, dev)
+    ot = ogrid.grid(g, inp.c_init, inp.alpha0)
+    rng = np.random.default_rng(6)
+    m = rng.standard_normal(g.npix) * 1e-9
+    f = cfg.freqs_hz[-1]
+    do = oborn.born_forward(ogreen.green(g, ot, inp.c_init, f), m, f)
+    for prec in (rb.RB_PREC_FP32, rb.RB_PREC_BF16X3):
+        ws = rb.workspace(geom, 1, prec, dev)
+        d = torch.empty((g.n_elem, g.n_elem), dtype=torch.complex64, device=dev)
+        rb.rb_born_forward(geom, tab, _t(inp.c_init, dev), f, _t(m, dev), d, ws, prec=prec)
+        assert rel_l2(d.cpu().numpy(), do) <= 1e-4, (prec, rel_l2(d.cpu().numpy(), do))

@@ -371,3 +371,22 @@ def test_hf_update_bf16x3_tiny(dev):
     err = np.sqrt(np.mean((dc.cpu().numpy() - ref.dc) ** 2))
     assert err <= 0.05 * max(1.0, np.sqrt(np.mean(ref.dc ** 2))), err
     assert abs(d["dc_norm"] - ref.dc_norm) <= 1e-3 * ref.dc_norm
+
+
+@pytest.mark.parametrize("case", ["tiny_init", "tiny_true"])
+def test_born_forward_bf16x3(dev, case):
+    cfg, inp, c = _case(case)
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    tab, _ = gpu_tables(geom, c, inp.alpha0, dev)
+    ot = ogrid.grid(g, c, inp.alpha0)
+    rng = np.random.default_rng(5)
+    m = rng.standard_normal(g.npix).astype(np.float32) * 1e-9
+    ws = rb.workspace(geom, 1, rb.RB_PREC_BF16X3, dev)
+    for f in (cfg.freqs_hz[0], cfg.freqs_hz[-1]):
+        d = torch.empty((g.n_elem, g.n_elem), dtype=torch.complex64, device=dev)
+        rb.rb_born_forward(geom, tab, _t(c, dev), f, _t(m, dev), d, ws, prec=rb.RB_PREC_BF16X3)
+        do = oborn.born_forward(ogreen.green(g, ot, c, f), m.astype(np.float64), f)
+        e = rel_l2(d.cpu().numpy(), do)
+        print(f"bf16x3 forward {case} f={f:.3g}: rel L2 {e:.3g}")
+        assert e <= 1e-4, e
