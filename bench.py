@@ -116,7 +116,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = rb.RB_PREC_FP32 if args.prec == "fp32" else rb.RB_PREC_BF16X3
+    precs = {"fp32": rb.RB_PREC_FP32, "bf16x3": rb.RB_PREC_BF16X3}
 
     cfg = rbgen.config_by_name(args.workload)
     inp = rbgen.make_inputs(cfg)
@@ -127,132 +127,148 @@ def run_ours(args):
     p_obs = synth_data(geom, c0, ct, a0, list(cfg.freqs_hz), inp.noise_re, inp.noise_im, 0.01)
     nsets = len(cfg.sets)
     nf = max(len(s) for s in cfg.sets)
-    ws = rb.workspace(geom, nf, prec, dev)
-    c = c0.clone()
-    dc = torch.empty_like(c)
-    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     nst = len(rb.STAGES)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)]
-    for e in evs:
-        e.record(stream)
-    ev_arr = rb.stage_event_array(evs)
 
-    def step(k, events=None):
-        j = k % nsets
-        if j == 0:
-            c.copy_(c0)
-        s = cfg.sets[j]
-        freqs = [cfg.freqs_hz[i] for i in s]
-        rb.rb_hf_update(geom, c, a0, freqs, p_obs[s[0]:s[-1] + 1], ws, 0.01, 1e-3, rb.RB_STEP_EXACT, prec, dc, diag,
-                        stream, events)
+    def measure(prec_name, with_clocks):
+        prec = precs[prec_name]
+        ws = rb.workspace(geom, nf, prec, dev)
+        c = c0.clone()
+        dc = torch.empty_like(c)
+        diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)]
+        for e in evs:
+            e.record(stream)
+        ev_arr = rb.stage_event_array(evs)
 
-    for k in range(args.warmup):
-        step(k)
-    torch.cuda.synchronize()
+        def step(k, events=None):
+            j = k % nsets
+            if j == 0:
+                c.copy_(c0)
+            s = cfg.sets[j]
+            rb.rb_hf_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], p_obs[s[0]:s[-1] + 1], ws, 0.01, 1e-3,
+                            rb.RB_STEP_EXACT, prec, dc, diag, stream, events)
 
-    # timed region: K steps, per-step events + per-stage events
-    per_step = []
-    stage_ms = np.zeros(nst)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    for k in range(args.steps):
-        starts[k].record(stream)
-        step(args.warmup + k, ev_arr)
-        ends[k].record(stream)
-        # stage events are reused every step: read them back after this step completes
-        ends[k].synchronize()
-        for s_ in range(nst):
-            stage_ms[s_] += evs[2 * s_].elapsed_time(evs[2 * s_ + 1])
-    g1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    wall = time.perf_counter() - t0
-    clk = clocks.stop()
-    dev_ms = g0.elapsed_time(g1)
-    per_step = np.array([starts[k].elapsed_time(ends[k]) for k in range(args.steps)])
-    ms = float(np.sum(per_step))
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
-    d = rb.decode_diag(diag)
+        for k in range(args.warmup):
+            step(k)
+        torch.cuda.synchronize()
+        stage_ms = np.zeros(nst)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(local) if with_clocks else None
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            starts[k].record(stream)
+            step(args.warmup + k, ev_arr)
+            ends[k].record(stream)
+            # the stage events are reused every step: read them after this step completes
+            ends[k].synchronize()
+            for s_ in range(nst):
+                stage_ms[s_] += evs[2 * s_].elapsed_time(evs[2 * s_ + 1])
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - t0
+        clk = clocks.stop() if clocks else None
+        per_step = np.array([starts[k].elapsed_time(ends[k]) for k in range(args.steps)])
+        ms = float(np.sum(per_step))
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        out = {"value": world * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+               "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
+               "stage_ms": {name: round(stage_ms[i] / args.steps, 4) for i, name in enumerate(rb.STAGES)},
+               "wall_s": wall, "clocks": clk, "diag": rb.decode_diag(diag)}
 
-    # end to end: pinned host data in, c and diagnostics out, every step
-    host_p = torch.empty(p_obs.shape, dtype=p_obs.dtype, pin_memory=True)
-    host_p.copy_(p_obs.cpu())
-    host_c = torch.empty(c.shape, dtype=c.dtype, pin_memory=True)
-    host_diag = torch.empty(48, dtype=torch.uint8, pin_memory=True)
-    dev_p = torch.empty((nf,) + tuple(p_obs.shape[1:]), dtype=p_obs.dtype, device=dev)
-    e2e_steps = max(3, min(args.steps, 10))
-    torch.cuda.synchronize()
-    te0 = time.perf_counter()
-    for k in range(e2e_steps):
-        j = k % nsets
-        if j == 0:
-            c.copy_(c0)
-        s = cfg.sets[j]
-        dev_p[:len(s)].copy_(host_p[s[0]:s[-1] + 1], non_blocking=True)
-        rb.rb_hf_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], dev_p[:len(s)], ws, 0.01, 1e-3, rb.RB_STEP_EXACT,
-                        prec, dc, diag, stream)
-        host_c.copy_(c, non_blocking=True)
-        host_diag.copy_(diag, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-    te = time.perf_counter() - te0
-    h2d = int(nf * p_obs.shape[1] * p_obs.shape[2] * 8)
-    d2h = int(c.numel() * 4 + 48)
+        # end to end through the same call: pinned host data in, c and diagnostics out, every step
+        host_p = torch.empty(p_obs.shape, dtype=p_obs.dtype, pin_memory=True)
+        host_p.copy_(p_obs.cpu())
+        host_c = torch.empty(c.shape, dtype=c.dtype, pin_memory=True)
+        host_diag = torch.empty(48, dtype=torch.uint8, pin_memory=True)
+        dev_p = torch.empty((nf,) + tuple(p_obs.shape[1:]), dtype=p_obs.dtype, device=dev)
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for k in range(e2e_steps):
+            j = k % nsets
+            if j == 0:
+                c.copy_(c0)
+            s = cfg.sets[j]
+            dev_p[:len(s)].copy_(host_p[s[0]:s[-1] + 1], non_blocking=True)
+            rb.rb_hf_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], dev_p[:len(s)], ws, 0.01, 1e-3,
+                            rb.RB_STEP_EXACT, prec, dc, diag, stream)
+            host_c.copy_(c, non_blocking=True)
+            host_diag.copy_(diag, non_blocking=True)
+            stream.synchronize()
+        te = time.perf_counter() - te0
+        out["e2e"] = {"value": e2e_steps / te, "unit": "updates/s",
+                      "h2d_bytes_per_step": int(nf * p_obs.shape[1] * p_obs.shape[2] * 8),
+                      "d2h_bytes_per_step": int(c.numel() * 4 + 48)}
+        del ws
+        torch.cuda.empty_cache()
+        return out
 
+    head = args.prec
+    runs = {head: measure(head, True)}
+    other = "fp32" if head == "bf16x3" else "bf16x3"
+    if not args.no_compare:
+        runs[other] = measure(other, False)
+    R = runs[head]
     peaks, peak_src = _peaks()
     work = algorithmic_work(cfg, nf)
-    st = {name: stage_ms[i] / args.steps for i, name in enumerate(rb.STAGES)}
-    dominant = max(st, key=st.get)
-    clock_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s at max SM clock
-    if dominant == "adjoint":
-        ach = work["adjoint_flop"] / (st["adjoint"] / 1e3) / 1e12
-        roof = {"kernel": "adjoint+hessian (k_adjoint_simt)", "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+    st = R["stage_ms"]
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1735.5)
+
+    def contraction_roof(stage, flop, kern):
+        t = st[stage] / 1e3
+        ach = flop / t / 1e12
+        if head == "bf16x3":
+            return {"kernel": kern, "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+                    "frac": ach / bf16_peak, "traffic": None,
+                    "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json); algorithmic FLOP, the 3-term "
+                                   "split issues 3x on the tensor pipe"}
+        return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
-    elif dominant == "forward":
-        ach = work["forward_flop"] / (st["forward"] / 1e3) / 1e12
-        roof = {"kernel": "born forward (k_forward_simt)", "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
-    else:
+
+    tc = head == "bf16x3"
+    roof_adj = contraction_roof("adjoint", work["adjoint_flop"], "k_adjoint_tc" if tc else "k_adjoint_simt")
+    roof_fwd = contraction_roof("forward", work["forward_flop"], "k_forward_tc" if tc else "k_forward_simt")
+    dominant = max(("trace_grid", "adjoint", "forward"), key=lambda k: st[k])
+    if dominant == "trace_grid":
         ach = work["trace_grid_bytes"] / (st["trace_grid"] / 1e3) / 1e9
-        roof = {"kernel": "fused ray fans + gridding (k_trace)", "bound": "hbm", "achieved": ach,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peak_src}
-    launches_per_step = 23 if prec == rb.RB_PREC_FP32 else 23
+        roof = {"kernel": "k_trace (fused ray fans + gridding)", "bound": "hbm", "achieved": ach,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                "traffic": args.trace_traffic, "peak_source": peak_src}
+    else:
+        roof = roof_adj if dominant == "adjoint" else roof_fwd
     line = {
-        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": R["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == rb.RB_PREC_FP32 else "bf16x3",
+        "dtype": "bf16x3 split products, f32 accumulate" if tc else "f32",
         "data": "synthetic (seeded breast phantom; data from the library's own ray-Born forward model + 1% noise)",
         "config": {"workload": args.workload, "n_elem": cfg.n_elem, "grid": [cfg.nx, cfg.ny], "h_m": cfg.h,
-                   "n_rays": cfg.n_rays, "freqs_per_set": nf, "n_sets": nsets, "precision": args.prec,
-                   "step_mode": "exact", "l2": "working set (1.1 GB tables) larger than L2",
+                   "n_rays": cfg.n_rays, "freqs_per_set": nf, "n_sets": nsets, "precision": head,
+                   "step_mode": "exact", "l2": "per-update working set (1.1 GB tables) larger than L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
-        "stage_ms": {k: round(v, 4) for k, v in st.items()},
-        "device_ms_total": dev_ms, "wall_s": wall,
-        "roofline": roof,
-        "clocks": clk,
-        "e2e": {"value": e2e_steps / te, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step * args.steps,
-        "diag_last": {k: d[k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
+        "p50_ms": R["p50_ms"], "p99_ms": R["p99_ms"], "stage_ms": st, "wall_s": R["wall_s"],
+        "roofline": roof, "roofline_contractions": {"adjoint": roof_adj, "forward": roof_fwd},
+        "clocks": R["clocks"], "e2e": R["e2e"],
+        "gpu_launches": (15 + 3 * nf if tc else 15 + 2 * nf) * args.steps,
+        "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
+    if other in runs:
+        o = runs[other]
+        line["compare"] = {"precision": other, "value": o["value"], "ms_per_step": o["ms_per_step"],
+                           "p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"], "stage_ms": o["stage_ms"],
+                           "e2e": o["e2e"]["value"]}
+        line["speedup_mixed_vs_plain"] = (R["value"] / o["value"]) if tc else (o["value"] / R["value"])
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         line["cpu_baseline"] = cpu_baseline(sample_fans=args.cpu_fans, sample_pix=args.cpu_pix)
     if rank == 0:
@@ -324,7 +340,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"],
+                    help="headline precision; the other one is measured beside it unless --no-compare")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--trace-traffic", type=float, default=None,
+                    help="ncu dram bytes per k_trace launch, when measured for this build")
     ap.add_argument("--workload", default=WORKLOAD, choices=["breast512", "breast256", "tiny"],
                     help="the timed workload is breast512; smaller ones are for profiling captures")
     ap.add_argument("--cpu-fans", type=int, default=32)
