@@ -141,6 +141,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->elem_xy = o; o = align256(o + ne * 16);
     L->cells = o; o = align256(o + ncell * 128);
     L->tables = o; o = align256(o + ne * npix * sizeof(rb_cell));
+    L->verts = o; o = align256(o + rb_verts_bytes(g->n_elem, g->n_rays, g->max_steps));
     L->ends = o; o = align256(o + ne * (size_t)g->n_rays * sizeof(rb_ray_end));
     L->pray = o; o = align256(o + nf * ne * ne * 8);
     L->linked = o; o = align256(o + ne * ne);
@@ -155,6 +156,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * 8 : 0));
     L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
     L->gimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_gimage_elems(g->n_elem, (int)npix) * 2 : 0));
+    L->dist = o; o = align256(o + (tcp ? ne * npix * 8 : 0));
     L->total = o;
     return o;
 }
@@ -197,7 +199,7 @@ rb_status rb_trace_rays(const rb_geometry* geom, const float* c, const float* al
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, cnt, s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, nullptr, nullptr, cnt, s));
     return RB_OK;
 }
 
@@ -221,7 +223,8 @@ rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* al
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
     RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, tables, cnt, s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, tables,
+                       W.at<void>(W.L.verts), nullptr, cnt, s));
     if (g_out) RB_CU(launch_green_out(G, tables, c, F, (float2*)g_out, s));
     return RB_OK;
 }
@@ -291,8 +294,9 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
     if (prec == RB_PREC_BF16X3) {
         RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
         RB_CU(launch_prep_b(G.n_elem, (const float2*)resid, w, W.at<void>(W.L.tcimg), s));
-        RB_CU(launch_adjoint_tc(G, tables, c, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
-                                (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, nullptr, s));
+        RB_CU(launch_dist(G, W.at<float2>(W.L.dist), s));
+        RB_CU(launch_adjoint_tc(G, tables, W.at<float2>(W.L.dist), c, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr),
+                                tc_ctas(), (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, nullptr, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c, F, (const float2*)resid, w, (float2*)g_out, hdiag_out, nullptr,
                                   nullptr, nullptr, s));
@@ -346,7 +350,8 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_FIELDS, 1));
     RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
     RB_CU(mark(RB_STAGE_TRACE_GRID, 0));
-    RB_CU(launch_trace(G, cells, ends, nullptr, tables, cnt, s));
+    float2* dist = prec == RB_PREC_BF16X3 ? W.at<float2>(W.L.dist) : nullptr;
+    RB_CU(launch_trace(G, cells, ends, nullptr, tables, W.at<void>(W.L.verts), dist, cnt, s));
     RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
     RB_CU(mark(RB_STAGE_LINK, 0));
     RB_CU(launch_link(G, c_inout, ends, F, R, linked, s));
@@ -358,8 +363,8 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
         const size_t img = tc_b_images_bytes(G.n_elem);
         for (int w = 0; w < n_freq; ++w)
             RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
-        RB_CU(launch_adjoint_tc(G, tables, c_inout, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
-                                nullptr, nullptr, gsum, hsum, cnt,
+        RB_CU(launch_adjoint_tc(G, tables, dist, c_inout, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr),
+                                tc_ctas(), nullptr, nullptr, gsum, hsum, cnt,
                                 params->step_mode == RB_STEP_EXACT ? W.at<void>(W.L.gimg) : nullptr, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));

@@ -19,7 +19,7 @@
 namespace {
 
 constexpr int TP = 128;                 // pixels per tile = MMA M
-constexpr int NTHR = 256;               // threads per CTA: two per pixel (pixel = TMEM lane)
+constexpr int NTHR = 256;               // forward: threads per CTA
 constexpr uint32_t kMaxTries = 1u << 22; // mbarrier polls before giving up (each poll suspends briefly)
 
 // ---------------------------------------------------------------------------
@@ -66,6 +66,7 @@ struct TcArgs {
     GeoDev G;
     FreqSet F;
     const rb_cell* tables;
+    const float2* dist;        // [n_elem][npix] |x - x_t| as float pairs
     const float* c;
     const __nv_bfloat16* bu;   // [n_freq][image]
     const __nv_bfloat16* bw;   // [n_freq][image]
@@ -139,49 +140,65 @@ __global__ void k_gimage(GeoDev G, const rb_cell* __restrict__ tables, const flo
     }
 }
 
+// |x - x_t| as a float pair for every element and pixel (geometry only).
+__global__ void k_dist(GeoDev G, float2* __restrict__ dist) {
+    const long long total = (long long)G.n_elem * G.npix;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(u / G.npix), pix = (int)(u % G.npix);
+        DF ex, ey;
+        elem_pos(G, r, ex, ey);
+        const DF d = pixel_elem_dist(G, pix % G.nx, pix / G.nx, ex, ey);
+        dist[u] = make_float2(d.hi, d.lo);
+    }
+}
+
 }  // namespace
 
 namespace {
 
-// Thread (p, h) of a CTA: pixel p = tid % 128 (its TMEM lane), half h = tid / 128.
-// Pack 8 (Re, -Im) or 16 real values of one pixel row into the two core-matrix
-// K-groups 2h, 2h+1 of a 32-wide chunk, as bf16 hi and lo.
-__device__ __forceinline__ void store_rows(unsigned char* a_hi, unsigned char* a_lo, uint32_t p, uint32_t h,
-                                           const uint32_t (&whi)[8], const uint32_t (&wlo)[8]) {
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        const uint32_t off = tc::chunk_offset(p, 8u * (2u * h + g));
-        *(uint4*)(a_hi + off) = make_uint4(whi[4 * g], whi[4 * g + 1], whi[4 * g + 2], whi[4 * g + 3]);
-        *(uint4*)(a_lo + off) = make_uint4(wlo[4 * g], wlo[4 * g + 1], wlo[4 * g + 2], wlo[4 * g + 3]);
-    }
-}
+constexpr int NTHR_A = 512;   // adjoint: four threads per pixel (pixel = TMEM lane, quarter = tid / 128)
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// U chunk: G_r(p) for r in [r0 + 8h, r0 + 8h + 8): exact values to gs, bf16 hi/lo of (Re, -Im) to A.
-__device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h, int px,
-                                        bool valid, int ix, int iy, float c_px, float2* gs, unsigned char* a_hi,
-                                        unsigned char* a_lo) {
-    const GeoDev& G = A.G;
-    rb_cell rec[8];
+// One core-matrix row: the 8 bf16 of K-group g of pixel row p, as hi and lo.
+__device__ __forceinline__ void store_row(unsigned char* a_hi, unsigned char* a_lo, uint32_t p, uint32_t g,
+                                          const uint32_t (&whi)[4], const uint32_t (&wlo)[4]) {
+    const uint32_t off = tc::chunk_offset(p, 8u * g);
+    *(uint4*)(a_hi + off) = make_uint4(whi[0], whi[1], whi[2], whi[3]);
+    *(uint4*)(a_lo + off) = make_uint4(wlo[0], wlo[1], wlo[2], wlo[3]);
+}
+
+// Table records and element distances of the four elements r0 + 4h + j (j < 4) at
+// this thread's pixel.
+__device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, int px, bool valid, rb_cell (&rec)[4],
+                                          float2 (&dd)[4]) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int r = r0 + 8 * (int)h + j;
-        if (valid) rec[j] = A.tables[(size_t)r * G.npix + px];
-        else rec[j].tkey = RB_HOLE;
-    }
-    uint32_t whi[8], wlo[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int r = r0 + 8 * (int)h + j;
-        float2 g = make_float2(0.f, 0.f);
-        if (rec[j].tkey != RB_HOLE) {
-            DF ex, ey;
-            elem_pos(G, r, ex, ey);
-            g = green_eval(rec[j], c_px, pixel_elem_dist(G, ix, iy, ex, ey), fc, G.j_floor);
+    for (int j = 0; j < 4; ++j) {
+        const int r = r0 + 4 * (int)h + j;
+        if (valid) {
+            rec[j] = A.tables[(size_t)r * A.G.npix + px];
+            dd[j] = __ldg(A.dist + (size_t)r * A.G.npix + px);
+        } else {
+            rec[j].tkey = RB_HOLE;
+            dd[j] = make_float2(0.f, 0.f);
         }
+    }
+}
+
+// U chunk (16 elements, K = 32): G_r(p) for r = r0 + 4h + j, exact values to gs and
+// bf16 hi / lo of (Re, -Im) to K-group h of the A tile.
+__device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h,
+                                        const rb_cell (&rec)[4], const float2 (&dd)[4], float c_px, float2* gs,
+                                        unsigned char* a_hi, unsigned char* a_lo) {
+    const GeoDev& G = A.G;
+    uint32_t whi[4], wlo[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int r = r0 + 4 * (int)h + j;
+        float2 g = make_float2(0.f, 0.f);
+        if (rec[j].tkey != RB_HOLE) g = green_eval(rec[j], c_px, DF{dd[j].x, dd[j].y}, fc, G.j_floor);
         gs[(size_t)r * TP + p] = g;
         __nv_bfloat16 h0, l0, h1, l1;
         tc::split_bf16(g.x, h0, l0);
@@ -189,16 +206,16 @@ __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0
         whi[j] = pack2(h0, h1);
         wlo[j] = pack2(l0, l1);
     }
-    store_rows(a_hi, a_lo, p, h, whi, wlo);
+    store_row(a_hi, a_lo, p, h, whi, wlo);
 }
 
-// V chunk: |G_r(p)|^2 for r in [r0 + 16h, r0 + 16h + 16) from the exact values.
+// V chunk (32 elements, K = 32): |G_r(p)|^2 for r = r0 + 8h + j from the exact values.
 __device__ __forceinline__ void synth_v(int r0, uint32_t p, uint32_t h, const float2* gs, unsigned char* a_hi,
                                         unsigned char* a_lo) {
-    uint32_t whi[8], wlo[8];
+    uint32_t whi[4], wlo[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int r = r0 + 16 * (int)h + 2 * j;
+    for (int j = 0; j < 4; ++j) {
+        const int r = r0 + 8 * (int)h + 2 * j;
         const float2 g0 = gs[(size_t)r * TP + p], g1 = gs[(size_t)(r + 1) * TP + p];
         __nv_bfloat16 h0, l0, h1, l1;
         tc::split_bf16(g0.x * g0.x + g0.y * g0.y, h0, l0);
@@ -206,7 +223,7 @@ __device__ __forceinline__ void synth_v(int r0, uint32_t p, uint32_t h, const fl
         whi[j] = pack2(h0, h1);
         wlo[j] = pack2(l0, l1);
     }
-    store_rows(a_hi, a_lo, p, h, whi, wlo);
+    store_row(a_hi, a_lo, p, h, whi, wlo);
 }
 
 constexpr uint32_t STAGE = 80u * 1024u;        // A hi (8 KB) + A lo (8 KB) + B (64 KB)
@@ -219,12 +236,12 @@ struct Pipe {
     uint32_t q;
 };
 
-__global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
+__global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_bfull[2], s_mdone[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_err;
-    __shared__ float s_red[3][TP];
+    __shared__ float s_red[3][3][TP];     // partial sums of quarters 1..3: Re g, Im g, H
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -247,6 +264,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
     const uint32_t id_u = tc::idesc_bf16_f32(128, (uint32_t)nb_u);
     const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)n);
     const size_t img_u = (size_t)n2 * 32, img_w = (size_t)n * 32;   // bf16 elements
+    const int nchu = n2 / 32, nchv = n / 32;
     float2* gs = A.gscr + (size_t)blockIdx.x * n * TP;
     Pipe P = {{0u, 0u}, {0u, 0u}, {false, false}, 0u};
     bool ok = true;
@@ -283,19 +301,29 @@ __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
     for (int tile = blockIdx.x; tile < A.n_tiles && ok; tile += gridDim.x) {
         const int px = tile * TP + (int)p;
         const bool valid = px < G.npix;
-        const int ix = valid ? px % G.nx : 0, iy = valid ? px / G.nx : 0;
         const float c_px = valid ? __ldg(A.c + px) : 0.f;
         float acc_g = 0.f, acc_h = 0.f;
         for (int fw = 0; fw < A.F.n && ok; ++fw) {
             const FreqC fc = A.F.f[fw];
             const __nv_bfloat16* bu = A.bu + (size_t)fw * A.bu_stride;
             const __nv_bfloat16* bw = A.bw + (size_t)fw * A.bw_stride;
-            // ---- U over K' = 2n ----
-            for (int kc = 0; kc < n2 / 32 && ok; ++kc) {
+            // ---- U over K' = 2n; table records fetched one chunk ahead ----
+            rb_cell nxt[4];
+            float2 nxd[4];
+            load_recs(A, 0, h, px, valid, nxt, nxd);
+            for (int kc = 0; kc < nchu && ok; ++kc) {
                 run_chunk(
                     bu + (size_t)kc * 2 * img_u, (uint32_t)(2 * n2 * 64),
                     [&](unsigned char* ahi, unsigned char* alo) {
-                        synth_u(A, fc, kc * 16, p, h, px, valid, ix, iy, c_px, gs, ahi, alo);
+                        rb_cell cur[4];
+                        float2 cud[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            cur[j] = nxt[j];
+                            cud[j] = nxd[j];
+                        }
+                        if (kc + 1 < nchu) load_recs(A, (kc + 1) * 16, h, px, valid, nxt, nxd);
+                        synth_u(A, fc, kc * 16, p, h, cur, cud, c_px, gs, ahi, alo);
                     },
                     [&](uint32_t ahi, uint32_t alo, uint32_t b) {
                         for (int ks = 0; ks < 2; ++ks) {
@@ -320,7 +348,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
             if (A.gimg) {
                 // this tile's exact G (complete in gs) as forward operand images
                 __nv_bfloat16* img = A.gimg + (size_t)fw * A.gimg_stride;
-                for (int u = tid; u < n * (TP / 8); u += NTHR) {
+                for (int u = tid; u < n * (TP / 8); u += NTHR_A) {
                     const int r = u % n, seg = u / n;
                     float2 g[8];
 #pragma unroll
@@ -329,39 +357,39 @@ __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
                 }
             }
             tc::fence_after();
-            // epilogue: this thread takes elements e in [h n/2, (h+1) n/2)
+            // epilogue: 32-column blocks b = h, h + 4, ... of the 2n columns (Re U, then Im U)
             float gr = 0.f, gi = 0.f;
-            for (int half = 0; half < 2; ++half) {            // half 0: Re U, half 1: Im U
-                for (int cb = (int)h * (n / 2); cb < ((int)h + 1) * (n / 2); cb += 32) {
-                    float v[32];
-                    tc::tmem_ld32(tmem + lane_off + (uint32_t)(half * n + cb), v);
-#pragma unroll 8
-                    for (int j = 0; j < 32; ++j) {
-                        const float2 ge = gs[(size_t)(cb + j) * TP + p];
-                        if (half == 0) {
-                            gr = fmaf(ge.x, v[j], gr);
-                            gi = fmaf(-ge.y, v[j], gi);
-                        } else {
-                            gr = fmaf(ge.y, v[j], gr);
-                            gi = fmaf(ge.x, v[j], gi);
-                        }
+            for (int b = (int)h; b < nchu; b += 4) {
+                const int half = (32 * b) >= n ? 1 : 0;
+                const int cb = 32 * b - half * n;
+                float v[32];
+                tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float2 ge = gs[(size_t)(cb + j) * TP + p];
+                    if (half == 0) {
+                        gr = fmaf(ge.x, v[j], gr);
+                        gi = fmaf(-ge.y, v[j], gi);
+                    } else {
+                        gr = fmaf(ge.y, v[j], gr);
+                        gi = fmaf(ge.x, v[j], gi);
                     }
                 }
             }
-            if (h == 1) {
-                s_red[0][p] = gr;
-                s_red[1][p] = gi;
+            if (h > 0) {
+                s_red[0][h - 1][p] = gr;
+                s_red[1][h - 1][p] = gi;
             }
             tc::fence_before();
             __syncthreads();
             if (h == 0) {
-                gr = (gr + s_red[0][p]) * fc.w2;
-                gi = (gi + s_red[1][p]) * fc.w2;
+                gr = (gr + s_red[0][0][p] + s_red[0][1][p] + s_red[0][2][p]) * fc.w2;
+                gi = (gi + s_red[1][0][p] + s_red[1][1][p] + s_red[1][2][p]) * fc.w2;
                 if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
                 acc_g += gr;
             }
             // ---- V over K = n (accumulator reuses the first n columns) ----
-            for (int kc = 0; kc < n / 32 && ok; ++kc) {
+            for (int kc = 0; kc < nchv && ok; ++kc) {
                 run_chunk(
                     bw + (size_t)kc * img_w, (uint32_t)(n * 64),
                     [&](unsigned char* ahi, unsigned char* alo) { synth_v(kc * 32, p, h, gs, ahi, alo); },
@@ -381,20 +409,20 @@ __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
             if (!ok) break;
             tc::fence_after();
             float hh = 0.f;
-            for (int cb = (int)h * (n / 2); cb < ((int)h + 1) * (n / 2); cb += 32) {
+            for (int b = (int)h; b < nchv; b += 4) {
                 float v[32];
-                tc::tmem_ld32(tmem + lane_off + (uint32_t)cb, v);
-#pragma unroll 8
+                tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), v);
+#pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float2 ge = gs[(size_t)(cb + j) * TP + p];
+                    const float2 ge = gs[(size_t)(32 * b + j) * TP + p];
                     hh = fmaf(ge.x * ge.x + ge.y * ge.y, v[j], hh);
                 }
             }
-            if (h == 1) s_red[2][p] = hh;
+            if (h > 0) s_red[2][h - 1][p] = hh;
             tc::fence_before();
             __syncthreads();
             if (h == 0) {
-                hh = (hh + s_red[2][p]) * fc.w4;
+                hh = (hh + s_red[2][0][p] + s_red[2][1][p] + s_red[2][2][p]) * fc.w4;
                 if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = hh;
                 acc_h += hh;
             }
@@ -419,6 +447,14 @@ __global__ void __launch_bounds__(NTHR, 1) k_adjoint_tc(TcArgs A) {
 
 bool tc_adjoint_supported(int n_elem) { return n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0; }
 
+cudaError_t launch_dist(const GeoDev& G, float2* dist, cudaStream_t s) {
+    const long long total = (long long)G.n_elem * G.npix;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_dist<<<(int)blocks, 256, 0, s>>>(G, dist);
+    return cudaGetLastError();
+}
+
 size_t tc_b_images_bytes(int n_elem) {
     const size_t n = (size_t)n_elem;
     return (2 * n) * (2 * n) * 2 * 2 + n * n * 2;   // bu (hi + lo) + bw, bf16
@@ -431,15 +467,16 @@ cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
-                              const void* images, float2* gscr, int n_ctas, float2* g_out, float* h_out, float* gsum,
-                              float* hsum, uint32_t* counters, void* gimg, cudaStream_t s) {
+cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float2* dist, const float* c,
+                              const FreqSet& F, const void* images, float2* gscr, int n_ctas, float2* g_out,
+                              float* h_out, float* gsum, float* hsum, uint32_t* counters, void* gimg, cudaStream_t s) {
     const int n = G.n_elem;
-    if (!tc_adjoint_supported(n)) return cudaErrorInvalidValue;
+    if (!tc_adjoint_supported(n) || !dist) return cudaErrorInvalidValue;
     TcArgs A;
     A.G = G;
     A.F = F;
     A.tables = tables;
+    A.dist = dist;
     A.c = c;
     A.bu = (const __nv_bfloat16*)images;
     A.bu_stride = tc_b_images_bytes(n) / 2;
@@ -463,7 +500,7 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const floa
     cudaError_t e = cudaFuncSetAttribute(k_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     const int grid = n_ctas < A.n_tiles ? n_ctas : A.n_tiles;
-    k_adjoint_tc<<<grid, NTHR, sm, s>>>(A);
+    k_adjoint_tc<<<grid, NTHR_A, sm, s>>>(A);
     return cudaGetLastError();
 }
 

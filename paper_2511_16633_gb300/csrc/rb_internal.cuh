@@ -83,9 +83,11 @@ __device__ __forceinline__ DF df_sqr(DF a) {
     return df_fast_two_sum(p.hi, lo);
 }
 __device__ __forceinline__ DF df_sqrt(DF a) {  // a > 0
+    // one Newton correction of s = sqrt(a.hi); the correction is below ulp(s), so an
+    // approximate 1 / (2 s) leaves the pair accurate to ~2^-46 relative
     float s = sqrtf(a.hi);
     float r = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
-    float e = __fdiv_rn(r, 2.0f * s);
+    float e = r * (0.5f * rsqrtf(a.hi));
     return df_fast_two_sum(s, e);
 }
 __host__ __device__ __forceinline__ DF df_from_double(double v) {
@@ -131,10 +133,11 @@ __device__ __forceinline__ float2 green_eval(const rb_cell& rec, float c_px, DF 
     float base = __fsub_rn(P.hi, rintf(P.hi));
     float cyc = base + P.lo + F.f_hi * tres + F.disp_cyc * rec.l + 0.125f - 0.25f * (float)(kappa & 3);
     cyc -= rintf(cyc);
+    // |2 pi cyc| <= pi: the hardware sine / cosine are accurate to ~4e-7 absolute there
     float s, co;
-    sincospif(2.0f * cyc, &s, &co);
+    __sincosf((2.0f * RB_PI_F) * cyc, &s, &co);
     const float J = fmaxf(fabsf(rec.q), j_floor);
-    const float amp = sqrtf(c_px / (8.0f * RB_PI_F * J)) * F.w_isqrt * expf(-F.a_abs * rec.l);
+    const float amp = sqrtf(c_px) * rsqrtf((8.0f * RB_PI_F) * J) * F.w_isqrt * __expf(-F.a_abs * rec.l);
     return make_float2(amp * co, amp * s);
 }
 
@@ -162,6 +165,7 @@ struct WsLayout {
     size_t elem_xy;    // [n_elem] float4 {x_hi, x_lo, y_hi, y_lo}
     size_t cells;      // [(ny-1)(nx-1)][8] float4
     size_t tables;     // [n_elem][npix] rb_cell
+    size_t verts;      // [n_elem][max_steps + 1][n_rays] ray vertices, 32 B each (gridding)
     size_t ends;       // [n_elem][n_rays] rb_ray_end
     size_t counters;   // 64 uint32 + 64 double scalars
     size_t pray;       // [n_freq][n_elem][n_elem] float2 (ray data, then residual)
@@ -177,6 +181,7 @@ struct WsLayout {
     size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
     size_t tcfwd;      // tensor-core path: partial D blocks of the forward
     size_t gimg;       // tensor-core path: G operand images of the forward, [n_freq][...] bf16
+    size_t dist;       // tensor-core path: |x - x_t| as float pairs, [n_elem][npix] float2
     size_t total;
 };
 
@@ -196,7 +201,8 @@ enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_
 cudaError_t launch_elem_positions(const GeoDev& G, float4* elem_xy, cudaStream_t s);
 cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s);
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         rb_cell* tables, uint32_t* counters, cudaStream_t s);
+                         rb_cell* tables, void* verts, float2* dist, uint32_t* counters, cudaStream_t s);
+size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);
 cudaError_t launch_link(const GeoDev& G, const float* c, const rb_ray_end* ends, const FreqSet& F,
@@ -223,9 +229,10 @@ cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c
 cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F, const float* m, float* partial,
                               int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
                               cudaStream_t s);
-cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
-                              const void* images, float2* gscr, int n_ctas, float2* g_out, float* h_out, float* gsum,
-                              float* hsum, uint32_t* counters, void* gimg, cudaStream_t s);
+cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float2* dist, const float* c,
+                              const FreqSet& F, const void* images, float2* gscr, int n_ctas, float2* g_out,
+                              float* h_out, float* gsum, float* hsum, uint32_t* counters, void* gimg, cudaStream_t s);
+cudaError_t launch_dist(const GeoDev& G, float2* dist, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);
 cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir,

@@ -150,50 +150,116 @@ __global__ void k_residual_keys(GeoDev G, int n_freq, const float2* __restrict__
     }
 }
 
-// Single-CTA exact radix select of the k-th largest 64-bit key, then W.
-__global__ void __launch_bounds__(1024) k_outlier_select(int n_total, double frac, const uint64_t* __restrict__ keys,
-                                                         uint32_t* __restrict__ counters, uint8_t* __restrict__ w) {
-    __shared__ uint32_t hist[256];
+// Exact selection of the k-th largest non-zero 64-bit key (keys are distinct: the
+// low word is the entry index), then W = 1 for the non-zero keys below it.  One CTA:
+// a 12-bit histogram of the top digit over all keys picks the bucket that holds the
+// k-th largest; that bucket's keys are compacted into shared memory and the
+// remaining 52 bits are resolved there by 8-bit radix passes.  A bucket larger than
+// the shared buffer falls back to radix passes over the global keys.
+constexpr int SEL_THREADS = 1024;
+constexpr int SEL_BINS = 4096;          // top 12 bits
+constexpr int SEL_CAP = 12288;          // compacted candidates (96 KB of shared memory)
+
+// Find, among bins [0, nb) counted in hist (largest digit = highest bin), the bin
+// that holds the rem-th largest key; returns it and leaves in *rem the rank within it.
+__device__ int sel_pick(const uint32_t* hist, int nb, long long* rem_io) {
+    // sequential from the top; called by one thread on at most 4096 bins
+    long long rem = *rem_io;
+    int d = nb - 1;
+    for (; d > 0; --d) {
+        if ((long long)hist[d] >= rem) break;
+        rem -= hist[d];
+    }
+    *rem_io = rem;
+    return d;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_outlier_select(int n_total, double frac, const uint64_t* __restrict__ keys,
+                                                                uint32_t* __restrict__ counters, uint8_t* __restrict__ w) {
+    extern __shared__ uint64_t cand[];           // [SEL_CAP]
+    __shared__ uint32_t hist[SEL_BINS];
     __shared__ uint64_t s_prefix;
-    __shared__ uint64_t s_kth;
     __shared__ long long s_rem;
+    __shared__ int s_d, s_nc;
     const uint32_t kept = counters[CNT_KEPT];
     const long long k = (long long)floor(frac * (double)kept);
-    if (threadIdx.x == 0) {
-        s_prefix = 0;
-        s_rem = k;
-        s_kth = ~0ull;  // nothing selected
-    }
-    __syncthreads();
+    uint64_t thr = ~0ull;   // nothing zeroed
     if (k > 0) {
-        uint64_t mask = 0;
-        for (int pass = 0; pass < 8; ++pass) {
-            const int shift = 56 - 8 * pass;
-            for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
-            __syncthreads();
-            const uint64_t pre = s_prefix;
+        for (int b = threadIdx.x; b < SEL_BINS; b += blockDim.x) hist[b] = 0;
+        if (threadIdx.x == 0) {
+            s_rem = k;
+            s_nc = 0;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
+            const uint64_t key = keys[j];
+            if (key != 0) atomicAdd(&hist[key >> 52], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long rem = s_rem;
+            s_d = sel_pick(hist, SEL_BINS, &rem);
+            s_rem = rem;
+            s_prefix = (uint64_t)s_d << 52;
+        }
+        __syncthreads();
+        const int nb = (int)hist[s_d];
+        uint64_t mask = 0xfffull << 52;
+        if (nb <= SEL_CAP) {
+            // compact the bucket, then 8-bit passes over bits 51..0 in shared memory
+            const uint64_t top = s_prefix;
             for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
                 const uint64_t key = keys[j];
-                if ((key & mask) == pre && key != 0) atomicAdd(&hist[(key >> shift) & 0xff], 1u);
+                if (key != 0 && (key & mask) == top) cand[atomicAdd(&s_nc, 1)] = key;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                long long rem = s_rem;
-                int d = 255;
-                for (; d > 0; --d) {
-                    if ((long long)hist[d] >= rem) break;
-                    rem -= hist[d];
+            const int nc = s_nc;
+            for (int shift = 44; shift >= -4; shift -= 8) {
+                const int sh = shift < 0 ? 0 : shift;
+                const int bits = shift < 0 ? 4 : 8;          // last pass: bits 3..0
+                const uint64_t dm = (1ull << bits) - 1;
+                for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+                __syncthreads();
+                const uint64_t pre = s_prefix;
+                for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+                    const uint64_t key = cand[j];
+                    if ((key & mask) == pre) atomicAdd(&hist[(key >> sh) & dm], 1u);
                 }
-                s_rem = rem;
-                s_prefix = pre | ((uint64_t)d << shift);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    long long rem = s_rem;
+                    const int d = sel_pick(hist, (int)dm + 1, &rem);
+                    s_rem = rem;
+                    s_prefix = pre | ((uint64_t)d << sh);
+                }
+                mask |= dm << sh;
+                __syncthreads();
             }
-            mask |= (0xffull << shift);
-            __syncthreads();
+        } else {
+            for (int shift = 44; shift >= -4; shift -= 8) {
+                const int sh = shift < 0 ? 0 : shift;
+                const int bits = shift < 0 ? 4 : 8;
+                const uint64_t dm = (1ull << bits) - 1;
+                for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+                __syncthreads();
+                const uint64_t pre = s_prefix;
+                for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
+                    const uint64_t key = keys[j];
+                    if (key != 0 && (key & mask) == pre) atomicAdd(&hist[(key >> sh) & dm], 1u);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    long long rem = s_rem;
+                    const int d = sel_pick(hist, (int)dm + 1, &rem);
+                    s_rem = rem;
+                    s_prefix = pre | ((uint64_t)d << sh);
+                }
+                mask |= dm << sh;
+                __syncthreads();
+            }
         }
-        if (threadIdx.x == 0) s_kth = s_prefix;
-        __syncthreads();
+        thr = s_prefix;
     }
-    const uint64_t thr = s_kth;
     for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
         const uint64_t key = keys[j];
         w[j] = (key != 0 && key < thr) ? 1 : 0;
@@ -226,6 +292,9 @@ cudaError_t launch_residual_keys(const GeoDev& G, int n_freq, const float2* p_ob
 
 cudaError_t launch_outlier_select(int n_total, double frac, const uint64_t* keys, const uint32_t* /*counters*/,
                                   uint8_t* w, uint32_t* counters_out, cudaStream_t s) {
-    k_outlier_select<<<1, 1024, 0, s>>>(n_total, frac, keys, counters_out, w);
+    const int sm = SEL_CAP * (int)sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(k_outlier_select, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    k_outlier_select<<<1, SEL_THREADS, sm, s>>>(n_total, frac, keys, counters_out, w);
     return cudaGetLastError();
 }

@@ -18,16 +18,22 @@
 // ended repeats its last vertex.  Support pixels inside a triangle get the
 // barycentric interpolation of T_res = T - |x - x_t|/c_ref, Q, L and the
 // KMAH index of the heaviest vertex; the smallest T_res wins (ties: smallest
-// triangle id), resolved by a 128-bit compare-and-swap on the table record.
+// triangle id).
 //
 // GB300 mapping: one warp owns 32 consecutive rays of one fan (31 tubes;
 // neighbouring warps overlap by one ray, which both trace bit-identically),
-// so a tube's four vertices are two registers and one shuffle away and the
-// ray samples never reach HBM.  Field samples come from the 128-byte cell
-// records of rb_fields.cu, kept in registers while a ray stays in its cell.
-// Positions and the direction are float pairs (compensated sums); the
-// traveltime is integrated as the residual T - |x - x_t|/c_ref in double,
-// which keeps the Green's-function phase w T accurate at MHz frequencies.
+// so a tube's four vertices are two registers and one shuffle away.  Field
+// samples come from the 128-byte cell records of rb_fields.cu, kept in
+// registers while a ray stays in its cell.  The first-arrival competition is
+// decided without waiting on memory: every covered pixel gets a fire-and-forget
+// 64-bit atomic min of (T_res key, triangle id) on the first 8 bytes of its
+// table record, and each ray's vertices are streamed out (32 B per vertex).  A
+// second kernel, k_resolve, then reads the winning triangle id of every hit
+// pixel, fetches that triangle's vertices and writes Q, L and the KMAH index
+// with the same barycentric weights the rasteriser used.
+// Positions, the direction and the traveltime residual T - |x - x_t|/c_ref
+// are float pairs (compensated sums), which keeps the Green's-function phase
+// w T accurate at MHz frequencies without the (slow) FP64 pipe.
 #include "rb_internal.cuh"
 
 namespace {
@@ -101,20 +107,21 @@ __device__ __forceinline__ Deriv eval_stage(const GeoDev& G, const float4* __res
     float f[7];
     sample(G, cells, cc, px, py, f);
     const float c = f[0];
-    const float rc = 1.0f / c;
+    const float rc = __fdividef(1.0f, c);   // ~2 ulp: far below the RK4 truncation error
     Deriv d;
     d.x = cth;
     d.y = sth;
     d.th = (f[1] * sth - f[2] * cth) * rc;
     // T_res' = 1/c - (t . r_hat)/c_ref = (c_ref - c)/(c c_ref) + (1 - t . r_hat)/c_ref,
     // with 1 - t.r_hat = (t x r)^2 / (|r| (|r| + t.r)) (no cancellation).
-    const float rr = sqrtf(rx * rx + ry * ry);
+    const float r2 = rx * rx + ry * ry;
     float one_m_cos = 0.f;
-    if (rr > 0.f) {
+    if (r2 > 0.f) {
+        const float rr = r2 * rsqrtf(r2);
         const float dot = cth * rx + sth * ry;
         const float crs = cth * ry - sth * rx;
         const float den = rr * (rr + dot);
-        one_m_cos = den > 0.f ? (crs * crs) / den : 2.f;
+        one_m_cos = den > 0.f ? __fdividef(crs * crs, den) : 2.f;
     }
     d.t = (G.c_ref - c) * (rc * G.inv_cref) + one_m_cos * G.inv_cref;
     d.q = c * ps;
@@ -149,111 +156,116 @@ __device__ __forceinline__ double exit_lambda(double ax, double ay, double bx, d
     return fmin(fmax(lam, 0.0), 1.0);
 }
 
-// Atomic "keep the smaller (tkey, tag)" on a 16-byte table record.  The first
-// attempt assumes the record is still a hole (all bytes 0xff), which is the common
-// case, so no load precedes it; a failed attempt returns the current record.
-__device__ __forceinline__ void cell_min(rb_cell* dst, uint32_t tkey, uint32_t tag, float q, float l,
-                                        uint32_t* giveup) {
-    const unsigned long long nk = ((unsigned long long)tkey << 32) | tag;
-    const unsigned long long nv = ((unsigned long long)__float_as_uint(l) << 32) | __float_as_uint(q);
-    unsigned long long ck = ~0ull, cv = ~0ull;
-    int it = 0;
-    for (; it < 256; ++it) {
-        unsigned long long ok, ov;
-        asm volatile(
-            "{\n\t.reg .b128 d, cmp, val;\n\t"
-            "mov.b128 cmp, {%2, %3};\n\t"
-            "mov.b128 val, {%4, %5};\n\t"
-            "atom.relaxed.gpu.global.cas.b128 d, [%6], cmp, val;\n\t"
-            "mov.b128 {%0, %1}, d;\n\t}"
-            : "=l"(ok), "=l"(ov)
-            : "l"(ck), "l"(cv), "l"(nk), "l"(nv), "l"(dst)
-            : "memory");
-        if (ok == ck && ov == cv) break;   // stored
-        ck = ok;
-        cv = ov;
-        if (!(nk < ck)) break;             // an earlier arrival (or tie winner) is already there
-    }
-    if (it == 256) atomicAdd(giveup, 1u);
+// Geometry of one ray-tube quad relative to its vertex A0 (float-pair differences):
+// triangle T0 = (A0, B0, B1) spans edge vectors b0, b1; T1 = (A0, B1, A1) spans b1, a1.
+// Twice the signed areas are exactly zero when two vertices coincide (frozen rays).
+struct Quad {
+    float b0x, b0y, b1x, b1y, a1x, a1y;
+    float i0, i1;   // reciprocal doubled areas (0 for a degenerate triangle)
+    bool t0, t1;
+};
+
+__device__ __forceinline__ float rel(float vh, float vl, float oh, float ol) {
+    return __fadd_rn(__fsub_rn(vh, oh), __fsub_rn(vl, ol));
 }
 
-// Rasterise one ray-tube quad: triangles T0 = (A0, B0, B1) (id base) and
-// T1 = (A0, B1, A1) (id base + 1), A = this ray, B = the next ray, 0/1 = steps k-1/k.
-// One pixel box (pixel centres inside the quad's bounding box) serves both
-// triangles; where both contain a pixel the smaller T_res (then T0) is kept.
-// Coordinates are taken relative to A0 from float-pair differences.
+__device__ __forceinline__ Quad quad_of(const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1) {
+    Quad Q;
+    Q.b0x = rel(B0.xh, B0.xl, A0.xh, A0.xl);
+    Q.b0y = rel(B0.yh, B0.yl, A0.yh, A0.yl);
+    Q.b1x = rel(B1.xh, B1.xl, A0.xh, A0.xl);
+    Q.b1y = rel(B1.yh, B1.yl, A0.yh, A0.yl);
+    Q.a1x = rel(A1.xh, A1.xl, A0.xh, A0.xl);
+    Q.a1y = rel(A1.yh, A1.yl, A0.yh, A0.yl);
+    const float ar0 = __fsub_rn(__fmul_rn(Q.b0x, Q.b1y), __fmul_rn(Q.b0y, Q.b1x));
+    const float ar1 = __fsub_rn(__fmul_rn(Q.b1x, Q.a1y), __fmul_rn(Q.b1y, Q.a1x));
+    Q.t0 = ar0 != 0.f;
+    Q.t1 = ar1 != 0.f;
+    Q.i0 = Q.t0 ? __frcp_rn(ar0) : 0.f;
+    Q.i1 = Q.t1 ? __frcp_rn(ar1) : 0.f;
+    return Q;
+}
+
+// Barycentric weights of the point A0 + (dx, dy) in the triangle with edge vectors
+// (ux, uy), (vx, vy) from A0 and reciprocal doubled area inv: w = (wa, wb, wc) for
+// (A0, A0 + u, A0 + v).
+__device__ __forceinline__ void bary(float ux, float uy, float vx, float vy, float inv, float dx, float dy, float& wa,
+                                     float& wb, float& wc) {
+    wb = __fmul_rn(__fsub_rn(__fmul_rn(dx, vy), __fmul_rn(dy, vx)), inv);
+    wc = __fmul_rn(__fsub_rn(__fmul_rn(ux, dy), __fmul_rn(uy, dx)), inv);
+    wa = __fsub_rn(__fsub_rn(1.f, wb), wc);
+}
+
+__device__ __forceinline__ float interp(float wa, float wb, float wc, float a, float b, float c) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(wa, a), __fmul_rn(wb, b)), __fmul_rn(wc, c));
+}
+
+// Keep the smaller 64-bit (T_res key << 32 | tag) in the first 8 bytes of a table
+// record ({tag, tkey} little-endian); no value is returned, so the warp never waits.
+__device__ __forceinline__ void key_min(rb_cell* dst, uint64_t key) {
+    asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(dst), "l"(key) : "memory");
+}
+
+// Rasterise one ray-tube quad: triangles T0 (id base) and T1 (id base + 1).  One
+// pixel box (pixel centres inside the quad's bounding box, cut to the support
+// disc row by row) serves both triangles; where both contain a pixel the smaller
+// T_res (then T0) is offered.  Along a row the weights and T_res are affine in
+// the pixel index: they are evaluated at the row's first pixel and then stepped
+// by their exact per-pixel increments (a few ulps of drift over a box).
 __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1,
-                                            uint32_t base, rb_cell* __restrict__ tab, uint32_t* giveup) {
-    const float b0x = (B0.xh - A0.xh) + (B0.xl - A0.xl), b0y = (B0.yh - A0.yh) + (B0.yl - A0.yl);
-    const float b1x = (B1.xh - A0.xh) + (B1.xl - A0.xl), b1y = (B1.yh - A0.yh) + (B1.yl - A0.yl);
-    const float a1x = (A1.xh - A0.xh) + (A1.xl - A0.xl), a1y = (A1.yh - A0.yh) + (A1.yl - A0.yl);
-    // twice the signed areas; exactly zero when two vertices coincide (frozen or shared vertices)
-    const float ar0 = __fsub_rn(__fmul_rn(b0x, b1y), __fmul_rn(b0y, b1x));
-    const float ar1 = __fsub_rn(__fmul_rn(b1x, a1y), __fmul_rn(b1y, a1x));
-    const bool t0 = ar0 != 0.f, t1 = ar1 != 0.f;
-    if (!t0 && !t1) return;
-    const float i0 = t0 ? 1.0f / ar0 : 0.f, i1 = t1 ? 1.0f / ar1 : 0.f;
+                                            uint32_t base, rb_cell* __restrict__ tab) {
+    const Quad Q = quad_of(A0, A1, B0, B1);
+    if (!Q.t0 && !Q.t1) return;
     // tight box of pixel centres (index space), with a 1e-3 px guard
     const float ua = fmaf(A0.xh, G.inv_h, G.cxg) + A0.xl * G.inv_h;
     const float va = fmaf(A0.yh, G.inv_h, G.cyg) + A0.yl * G.inv_h;
-    const float xmin = fminf(fminf(0.f, b0x), fminf(b1x, a1x)), xmax = fmaxf(fmaxf(0.f, b0x), fmaxf(b1x, a1x));
-    const float ymin = fminf(fminf(0.f, b0y), fminf(b1y, a1y)), ymax = fmaxf(fmaxf(0.f, b0y), fmaxf(b1y, a1y));
-    const int ix0 = max(0, (int)ceilf(fmaf(xmin, G.inv_h, ua) - 1e-3f));
-    const int ix1 = min(G.nx - 1, (int)floorf(fmaf(xmax, G.inv_h, ua) + 1e-3f));
+    const float xmin = fminf(fminf(0.f, Q.b0x), fminf(Q.b1x, Q.a1x)), xmax = fmaxf(fmaxf(0.f, Q.b0x), fmaxf(Q.b1x, Q.a1x));
+    const float ymin = fminf(fminf(0.f, Q.b0y), fminf(Q.b1y, Q.a1y)), ymax = fmaxf(fmaxf(0.f, Q.b0y), fmaxf(Q.b1y, Q.a1y));
+    const int bx0 = max(0, (int)ceilf(fmaf(xmin, G.inv_h, ua) - 1e-3f));
+    const int bx1 = min(G.nx - 1, (int)floorf(fmaf(xmax, G.inv_h, ua) + 1e-3f));
     const int iy0 = max(0, (int)ceilf(fmaf(ymin, G.inv_h, va) - 1e-3f));
     const int iy1 = min(G.ny - 1, (int)floorf(fmaf(ymax, G.inv_h, va) + 1e-3f));
+    if (bx0 > bx1) return;
     const float tol = -1e-6f;
+    // per-pixel (x) increments of the weights of T0 = (A0; u = b0, v = b1) and T1 = (A0; u = b1, v = a1)
+    const float h = G.h;
+    const float db0 = Q.b1y * Q.i0 * h, dc0 = -Q.b0y * Q.i0 * h;
+    const float db1 = Q.a1y * Q.i1 * h, dc1 = -Q.b1y * Q.i1 * h;
+    const float tb0 = B0.t - A0.t, tc0 = B1.t - A0.t;    // T = A0.t + wb (Tb - Ta) + wc (Tc - Ta)
+    const float tb1 = B1.t - A0.t, tc1 = A1.t - A0.t;
+    const DF X0 = df_pixel_coord(bx0, G.cxg, G.h_hi, G.h_lo);
+    const float dx0 = rel(X0.hi, X0.lo, A0.xh, A0.xl);
     for (int iy = iy0; iy <= iy1; ++iy) {
-        const long long jy = 2LL * iy - (G.ny - 1);
+        // support disc: (2 ix - (nx - 1))^2 + (2 iy - (ny - 1))^2 <= r2max
+        const int jy = 2 * iy - (G.ny - 1);
+        const long long rem = G.r2max - (long long)jy * jy;
+        if (rem < 0) continue;
+        int sj = (int)sqrtf((float)rem);
+        while ((long long)(sj + 1) * (sj + 1) <= rem) ++sj;
+        while (sj > 0 && (long long)sj * sj > rem) --sj;
+        const int ix0 = max(bx0, (G.nx - 1 - sj + 1) >> 1), ix1 = min(bx1, (G.nx - 1 + sj) >> 1);
+        if (ix0 > ix1) continue;
         const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
-        const float dy = (Y.hi - A0.yh) + (Y.lo - A0.yl);
-        for (int ix = ix0; ix <= ix1; ++ix) {
-            const long long jx = 2LL * ix - (G.nx - 1);
-            if (jx * jx + jy * jy > G.r2max) continue;
-            const DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
-            const float dx = (X.hi - A0.xh) + (X.lo - A0.xl);
-            bool in0 = false, in1 = false;
-            float wb0 = 0.f, wc0 = 0.f, wa0 = 0.f, wb1 = 0.f, wc1 = 0.f, wa1 = 0.f;
-            if (t0) {
-                wb0 = (dx * b1y - dy * b1x) * i0;
-                wc0 = (b0x * dy - b0y * dx) * i0;
-                wa0 = 1.f - wb0 - wc0;
-                in0 = wa0 >= tol && wb0 >= tol && wc0 >= tol;
+        const float dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
+        const float dx = dx0 + (float)(ix0 - bx0) * h;
+        float wb0 = 0.f, wc0 = 0.f, wb1 = 0.f, wc1 = 0.f, wa;
+        if (Q.t0) bary(Q.b0x, Q.b0y, Q.b1x, Q.b1y, Q.i0, dx, dy, wa, wb0, wc0);
+        if (Q.t1) bary(Q.b1x, Q.b1y, Q.a1x, Q.a1y, Q.i1, dx, dy, wa, wb1, wc1);
+        size_t o = (size_t)iy * G.nx + ix0;
+        for (int ix = ix0; ix <= ix1; ++ix, ++o) {
+            const bool in0 = Q.t0 && wb0 >= tol && wc0 >= tol && (1.f - wb0 - wc0) >= tol;
+            const bool in1 = Q.t1 && wb1 >= tol && wc1 >= tol && (1.f - wb1 - wc1) >= tol;
+            if (in0 || in1) {
+                const float tr0 = fmaf(wb0, tb0, fmaf(wc0, tc0, A0.t));
+                const float tr1 = fmaf(wb1, tb1, fmaf(wc1, tc1, A0.t));
+                const bool use1 = in1 && (!in0 || tr1 < tr0);
+                const uint32_t id = use1 ? base + 1u : base;
+                key_min(tab + o, ((uint64_t)f2key(use1 ? tr1 : tr0) << 32) | ((uint64_t)id << 8));
             }
-            if (t1) {
-                wb1 = (dx * a1y - dy * a1x) * i1;
-                wc1 = (b1x * dy - b1y * dx) * i1;
-                wa1 = 1.f - wb1 - wc1;
-                in1 = wa1 >= tol && wb1 >= tol && wc1 >= tol;
-            }
-            if (!in0 && !in1) continue;
-            const float tr0 = in0 ? wa0 * A0.t + wb0 * B0.t + wc0 * B1.t : 0.f;
-            const float tr1 = in1 ? wa1 * A0.t + wb1 * B1.t + wc1 * A1.t : 0.f;
-            const bool use1 = in1 && (!in0 || tr1 < tr0);
-            float tr, q, l;
-            int kap;
-            uint32_t id;
-            if (!use1) {
-                tr = tr0;
-                q = wa0 * A0.q + wb0 * B0.q + wc0 * B1.q;
-                l = wa0 * A0.l + wb0 * B0.l + wc0 * B1.l;
-                kap = A0.k;
-                float wbest = wa0;
-                if (wb0 > wbest) { kap = B0.k; wbest = wb0; }
-                if (wc0 > wbest) kap = B1.k;
-                id = base;
-            } else {
-                tr = tr1;
-                q = wa1 * A0.q + wb1 * B1.q + wc1 * A1.q;
-                l = wa1 * A0.l + wb1 * B1.l + wc1 * A1.l;
-                kap = A0.k;
-                float wbest = wa1;
-                if (wb1 > wbest) { kap = B1.k; wbest = wb1; }
-                if (wc1 > wbest) kap = A1.k;
-                id = base + 1u;
-            }
-            const uint32_t tag = (id << 8) | (uint32_t)min(kap, 255);
-            cell_min(tab + (size_t)iy * G.nx + ix, f2key(tr), tag, q, l, giveup);
+            wb0 += db0;
+            wc0 += dc0;
+            wb1 += db1;
+            wc1 += dc1;
         }
     }
 }
@@ -271,9 +283,20 @@ __device__ __forceinline__ Vtx shfl_down_vtx(const Vtx& v) {
     return o;
 }
 
+// Vertex k of ray i of fan t in the vertex stream: [fan][step][ray], 32 bytes each.
+__device__ __forceinline__ size_t vidx(const GeoDev& G, int t, int k, int i) {
+    return ((size_t)t * (size_t)(G.max_steps + 1) + (size_t)k) * (size_t)G.n_rays + (size_t)i;
+}
+
+__device__ __forceinline__ void put_vtx(Vtx* dst, const Vtx& v) {
+    float4* d = reinterpret_cast<float4*>(dst);
+    d[0] = make_float4(v.xh, v.xl, v.yh, v.yl);
+    d[1] = make_float4(v.t, v.q, v.l, __int_as_float(v.k));
+}
+
 __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restrict__ cells, rb_ray_end* __restrict__ ends,
                                                rb_rays S, int write_samples, rb_cell* __restrict__ tables,
-                                               uint32_t* __restrict__ counters) {
+                                               Vtx* __restrict__ verts, uint32_t* __restrict__ counters) {
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (gw >= G.n_elem * G.n_wpf) return;  // uniform per warp
@@ -283,7 +306,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     const bool owner = valid && (lane < 31 || i == G.n_rays - 1);
     const bool tube = (lane < 31) && (i + 1 < G.n_rays);
     rb_cell* tab = tables ? tables + (size_t)t * G.npix : nullptr;
-    uint32_t* giveup = counters + CNT_CAS_GIVEUP;
+    const bool put = verts && owner;
 
     DF xs, ys;
     elem_pos(G, t, xs, ys);
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     sample(G, cells, cc, xs.hi + xs.lo, ys.hi + ys.lo, f0);
 
     float xh = xs.hi, xl = xs.lo, yh = ys.hi, yl = ys.lo, thh = thd.hi, thl = thd.lo;
-    double tres = 0.0;
+    float trh = 0.f, trl = 0.f;   // T_res as a float pair (compensated sum of the RK4 increments)
     float q = 0.f, p = 1.0f / f0[0], l = 0.f;
     int kap = 0;
     bool alive = valid;
@@ -313,6 +336,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
         S.vl[sbase] = 0.f;
         S.vkappa[sbase] = 0;
     }
+    if (put) put_vtx(verts + vidx(G, t, 0, i), cur);
     Vtx nb_cur = shfl_down_vtx(cur);
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
     const float ds = G.ds, a2 = 0.5f * G.ds, ds6 = G.ds * (1.0f / 6.0f);
@@ -340,7 +364,6 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
             comp_add(nxh, nxl, ix);
             comp_add(nyh, nyl, iy);
             comp_add(nthh, nthl, ith);
-            const double ntres = tres + (double)it;
             const float nq = q + iq, np = p + ip, nl = l + il;
             // exit test: float screen, then double decision
             const float fx = nxh + nxl, fy = nyh + nyl;
@@ -355,13 +378,15 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                 const double lam = exit_lambda(ax, ay, bx, by, G.R_d);
                 const float lf = (float)lam;
                 const double ex = ax + lam * (bx - ax), ey = ay + lam * (by - ay);
-                const double etres = tres + lam * (ntres - tres);
+                const double tres = (double)trh + (double)trl;
+                const double etres = tres + lam * (double)it;
                 const double eth = ((double)thh + (double)thl) + lam * (((double)nthh + (double)nthl) - ((double)thh + (double)thl));
                 const float eq = q + lf * (nq - q), ep = p + lf * (np - p), el = l + lf * (nl - l);
                 const int ek = kap + ((k >= 2 && signbit(eq) != signbit(q)) ? 1 : 0);
                 const DF exd = df_from_double(ex), eyd = df_from_double(ey);
                 xh = exd.hi; xl = exd.lo; yh = eyd.hi; yl = eyd.lo;
-                q = eq; p = ep; l = el; kap = ek; tres = etres;
+                const DF etd = df_from_double(etres);
+                q = eq; p = ep; l = el; kap = ek; trh = etd.hi; trl = etd.lo;
                 alive = false;
                 if (owner) {
                     const double ddx = ex - xs_d, ddy = ey - ys_d;
@@ -381,13 +406,15 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
             } else {
                 if (k >= 2 && signbit(nq) != signbit(q)) ++kap;
                 xh = nxh; xl = nxl; yh = nyh; yl = nyl; thh = nthh; thl = nthl;
-                tres = ntres; q = nq; p = np; l = nl;
+                comp_add(trh, trl, it);
+                q = nq; p = np; l = nl;
                 if (k == G.max_steps) {
                     alive = false;
                     if (owner) {
                         const double ex = (double)xh + (double)xl, ey = (double)yh + (double)yl;
                         const double ddx = ex - xs_d, ddy = ey - ys_d;
                         rb_ray_end e;
+                        const double tres = (double)trh + (double)trl;
                         e.t_res = tres;
                         e.t = tres + sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
                         e.x = ex;
@@ -403,14 +430,15 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                     }
                 }
             }
-            cur = Vtx{xh, xl, yh, yl, (float)tres, q, l, kap};
+            cur = Vtx{xh, xl, yh, yl, trh + trl, q, l, kap};
+            if (put) put_vtx(verts + vidx(G, t, k, i), cur);
             if (write_samples) {
                 const size_t o = sbase + (size_t)k;
                 const double vx = (double)xh + (double)xl, vy = (double)yh + (double)yl;
                 const double ddx = vx - xs_d, ddy = vy - ys_d;
                 S.vx[o] = (float)vx;
                 S.vy[o] = (float)vy;
-                S.vt[o] = tres + sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
+                S.vt[o] = ((double)trh + (double)trl) + sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
                 S.vq[o] = q;
                 S.vl[o] = l;
                 S.vkappa[o] = kap;
@@ -419,7 +447,72 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
         nb_cur = shfl_down_vtx(cur);
         if (tab && tube) {
             const uint32_t base = ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u;
-            raster_quad(G, prev, cur, nb_prev, nb_cur, base, tab, giveup);
+            raster_quad(G, prev, cur, nb_prev, nb_cur, base, tab);
+        }
+    }
+}
+
+// Index of the last vertex of ray i of fan t: the exit vertex, or max_steps for a
+// lost ray.  Past it the ray repeats that vertex, as in the rasteriser.
+__device__ __forceinline__ int last_vertex(const GeoDev& G, const rb_ray_end* __restrict__ ends, int t, int i) {
+    const int nv = ends[(size_t)t * G.n_rays + i].n_vert;
+    return nv > 0 ? nv - 1 : G.max_steps;
+}
+
+__device__ __forceinline__ Vtx get_vtx(const Vtx* __restrict__ src) {
+    const float4* s = reinterpret_cast<const float4*>(src);
+    const float4 a = __ldg(s), b = __ldg(s + 1);
+    return Vtx{a.x, a.y, a.z, a.w, b.x, b.y, b.z, __float_as_int(b.w)};
+}
+
+// Completes every hit record: from the winning triangle id in the tag, its vertices
+// and the pixel, the barycentric weights (bit-identical to the rasteriser's), then
+// Q, L and the KMAH index of the heaviest vertex.  Holes stay all ones.
+__global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict__ verts,
+                                                 const rb_ray_end* __restrict__ ends, rb_cell* __restrict__ tables,
+                                                 float2* __restrict__ dist) {
+    const uint32_t KQ = (uint32_t)(G.max_steps + 1);
+    const long long total = (long long)G.n_elem * G.npix;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
+         u += (long long)gridDim.x * blockDim.x) {
+        const uint2 kv = *reinterpret_cast<const uint2*>(tables + u);   // {tag, tkey}
+        if (kv.y == RB_HOLE) continue;
+        const int t = (int)(u / G.npix), pix = (int)(u % G.npix);
+        const uint32_t id = kv.x >> 8;
+        const int half = (int)(id & 1u);
+        const uint32_t qk = id >> 1;
+        // ids come from the rasteriser (i + 1 < n_rays, 1 <= k1 <= max_steps); clamped all the same
+        const int i = min((int)(qk / KQ), G.n_rays - 2), k1 = min((int)(qk % KQ) + 1, G.max_steps);
+        const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+        const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
+        const Vtx A1 = get_vtx(verts + vidx(G, t, min(k1, la), i));
+        const Vtx B0 = get_vtx(verts + vidx(G, t, min(k1 - 1, lb), i + 1));
+        const Vtx B1 = get_vtx(verts + vidx(G, t, min(k1, lb), i + 1));
+        const Quad Q = quad_of(A0, A1, B0, B1);
+        const int ix = pix % G.nx, iy = pix / G.nx;
+        const DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
+        const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
+        const float dx = rel(X.hi, X.lo, A0.xh, A0.xl), dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
+        float wa, wb, wc;
+        const Vtx& Vb = half ? B1 : B0;
+        const Vtx& Vc = half ? A1 : B1;
+        if (half) bary(Q.b1x, Q.b1y, Q.a1x, Q.a1y, Q.i1, dx, dy, wa, wb, wc);
+        else bary(Q.b0x, Q.b0y, Q.b1x, Q.b1y, Q.i0, dx, dy, wa, wb, wc);
+        int kap = A0.k;
+        float wbest = wa;
+        if (wb > wbest) { kap = Vb.k; wbest = wb; }
+        if (wc > wbest) kap = Vc.k;
+        rb_cell rec;
+        rec.tag = (id << 8) | (uint32_t)min(kap, 255);
+        rec.tkey = kv.y;
+        rec.q = interp(wa, wb, wc, A0.q, Vb.q, Vc.q);
+        rec.l = interp(wa, wb, wc, A0.l, Vb.l, Vc.l);
+        tables[u] = rec;
+        if (dist) {
+            DF ex, ey;
+            elem_pos(G, t, ex, ey);
+            const DF d = pixel_elem_dist(G, ix, iy, ex, ey);
+            dist[u] = make_float2(d.hi, d.lo);
         }
     }
 }
@@ -427,7 +520,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
 }  // namespace
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         rb_cell* tables, uint32_t* counters, cudaStream_t s) {
+                         rb_cell* tables, void* verts, float2* dist, uint32_t* counters, cudaStream_t s) {
     rb_rays S{};
     int ws = 0;
     if (samples && samples->vx) {
@@ -436,6 +529,18 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     }
     const long long warps = (long long)G.n_elem * G.n_wpf;
     const int blocks = (int)((warps * 32 + 127) / 128);
-    k_trace<<<blocks, 128, 0, s>>>(G, cells, ends, S, ws, tables, counters);
+    Vtx* V = tables ? (Vtx*)verts : nullptr;
+    if (tables && !V) return cudaErrorInvalidValue;
+    k_trace<<<blocks, 128, 0, s>>>(G, cells, ends, S, ws, tables, V, counters);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !tables) return e;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm = 148;
+    k_resolve<<<nsm * 8, 256, 0, s>>>(G, V, ends, tables, dist);
     return cudaGetLastError();
+}
+
+size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps) {
+    return (size_t)n_elem * (size_t)(max_steps + 1) * (size_t)n_rays * sizeof(Vtx);
 }
