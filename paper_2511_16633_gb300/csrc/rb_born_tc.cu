@@ -23,15 +23,15 @@ constexpr int NTHR = 256;               // forward: threads per CTA
 constexpr uint32_t kMaxTries = 1u << 22; // mbarrier polls before giving up (each poll suspends briefly)
 
 // ---------------------------------------------------------------------------
-// B operand images for one frequency, chunked by 32 columns of K in the
-// core-matrix layout of rb_tc.cuh.
-//   bu: [kc = 2n/32][hi|lo][2n rows x 32]   (2n rows = e', K = 2n)
-//   bw: [kc = n/32][n rows x 32]            (W, exact)
+// B operand images for one frequency, in K slices of 16 (one pipeline stage each)
+// in the core-matrix layout of rb_tc.cuh (tile16_offset).
+//   bu: [ks = 2n/16][hi|lo][2n rows x 16]   (2n rows = e', K = 2n)
+//   bw: [ks = n/16][n rows x 16]            (W, exact)
 // ---------------------------------------------------------------------------
 __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __restrict__ W,
                          __nv_bfloat16* __restrict__ bu, __nv_bfloat16* __restrict__ bw) {
     const int n2 = 2 * n;
-    const size_t img_u = (size_t)n2 * 32;  // bf16 per hi or lo image of one chunk
+    const size_t img_u = (size_t)n2 * 16;  // bf16 per hi or lo image of one slice
     const long long total_u = (long long)n2 * n2;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total_u;
          j += (long long)gridDim.x * blockDim.x) {
@@ -45,19 +45,19 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
         else v = part == 0 ? s.y : s.x;
         __nv_bfloat16 hi, lo;
         tc::split_bf16(v, hi, lo);
-        const int kc = kp >> 5, kk = kp & 31;
-        const size_t base = (size_t)kc * 2 * img_u;
-        const uint32_t off = tc::chunk_offset((uint32_t)ep, (uint32_t)kk) / 2;
+        const int ks = kp >> 4, kk = kp & 15;
+        const size_t base = (size_t)ks * 2 * img_u;
+        const uint32_t off = tc::tile16_offset((uint32_t)ep, (uint32_t)kk) / 2;
         bu[base + off] = hi;
         bu[base + img_u + off] = lo;
     }
     const long long total_w = (long long)n * n;
-    const size_t img_w = (size_t)n * 32;
+    const size_t img_w = (size_t)n * 16;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total_w;
          j += (long long)gridDim.x * blockDim.x) {
         const int e = (int)(j / n), r = (int)(j % n);
-        const int kc = r >> 5, kk = r & 31;
-        bw[(size_t)kc * img_w + tc::chunk_offset((uint32_t)e, (uint32_t)kk) / 2] =
+        const int ks = r >> 4, kk = r & 15;
+        bw[(size_t)ks * img_w + tc::tile16_offset((uint32_t)e, (uint32_t)kk) / 2] =
             __float2bfloat16_rn(W[(size_t)e * n + r] ? 1.f : 0.f);
     }
 }
@@ -156,16 +156,36 @@ __global__ void k_dist(GeoDev G, float2* __restrict__ dist) {
 
 namespace {
 
-constexpr int NTHR_A = 512;   // adjoint: four threads per pixel (pixel = TMEM lane, quarter = tid / 128)
+// ---------------------------------------------------------------------------
+// Adjoint kernel: warp-specialised, NST-stage pipeline of K = 16 slices.
+//   warps 0..7  producers: pixel p = tid % 128 (TMEM lane), half h = tid / 128;
+//               they synthesise the A slices, write the forward images and run
+//               the epilogues (TMEM -> registers);
+//   warp 8      MMA issuer (lane 0): waits for a stage's A and B, issues its MMAs
+//               and commits their completion; it never waits on a commit except
+//               at the start of an accumulation phase;
+//   warp 9      B loader (lane 0): bulk-copies B slices into stages as soon as the
+//               MMAs that read the stage's previous contents are done.
+// Per (tile, frequency) the slice sequence is U (2n / 16 slices) then V (n / 16).
+// Barriers: full_a[s] (8 producer-warp arrivals), full_b[s] (bulk-copy bytes),
+// empty[s] (MMAs that read stage s done), acc_full (last MMA of a phase done),
+// acc_empty (8 producer-warp arrivals: the epilogue has read the accumulator).
+// Every wait is bounded; a timeout raises a shared flag that ends all loops.
+// ---------------------------------------------------------------------------
+constexpr int NPROD = 256;                   // producer threads
+constexpr int NTHR_A = NPROD + 64;           // + MMA warp + B-loader warp
+constexpr int NST = 5;                       // pipeline stages
+constexpr uint32_t ST_BYTES = 40u * 1024u;   // A hi (4 KB) + A lo (4 KB) + B (<= 32 KB)
+constexpr uint32_t ST_ALO = 4096u, ST_B = 8192u;
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// One core-matrix row: the 8 bf16 of K-group g of pixel row p, as hi and lo.
-__device__ __forceinline__ void store_row(unsigned char* a_hi, unsigned char* a_lo, uint32_t p, uint32_t g,
-                                          const uint32_t (&whi)[4], const uint32_t (&wlo)[4]) {
-    const uint32_t off = tc::chunk_offset(p, 8u * g);
+// One core-matrix row of a K = 16 slice: the 8 bf16 of K-group g of pixel row p, hi and lo.
+__device__ __forceinline__ void store_row16(unsigned char* a_hi, unsigned char* a_lo, uint32_t p, uint32_t g,
+                                            const uint32_t (&whi)[4], const uint32_t (&wlo)[4]) {
+    const uint32_t off = tc::tile16_offset(p, 8u * g);
     *(uint4*)(a_hi + off) = make_uint4(whi[0], whi[1], whi[2], whi[3]);
     *(uint4*)(a_lo + off) = make_uint4(wlo[0], wlo[1], wlo[2], wlo[3]);
 }
@@ -187,29 +207,54 @@ __device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, i
     }
 }
 
-// U chunk (16 elements, K = 32): G_r(p) for r = r0 + 4h + j, exact values to gs and
-// bf16 hi / lo of (Re, -Im) to K-group h of the A tile.
+// U slice (8 elements, K' = 16): G_r(p) for r = r0 + 4h + j, exact values to gs and
+// bf16 hi / lo of (Re, -Im) to K-group h of the A slice.  With img set, the same
+// values (Re, +Im) also go to the forward operand image (see gimage_seg): the
+// 8-lane groups of the warp transpose their words through the warp's scratch sc
+// (32 x 9 words) so that each lane stores one 16-byte row of 8 pixels, hi and lo.
 __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h,
                                         const rb_cell (&rec)[4], const float2 (&dd)[4], float c_px, float2* gs,
-                                        unsigned char* a_hi, unsigned char* a_lo) {
-    const GeoDev& G = A.G;
-    uint32_t whi[4], wlo[4];
+                                        unsigned char* a_hi, unsigned char* a_lo, __nv_bfloat16* img, int chunk,
+                                        uint32_t* sc) {
+    uint32_t whi[4], wlo[4], iw[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int r = r0 + 4 * (int)h + j;
         float2 g = make_float2(0.f, 0.f);
-        if (rec[j].tkey != RB_HOLE) g = green_eval(rec[j], c_px, DF{dd[j].x, dd[j].y}, fc, G.j_floor);
+        if (rec[j].tkey != RB_HOLE) g = green_eval(rec[j], c_px, DF{dd[j].x, dd[j].y}, fc, A.G.j_floor);
         gs[(size_t)r * TP + p] = g;
         __nv_bfloat16 h0, l0, h1, l1;
         tc::split_bf16(g.x, h0, l0);
         tc::split_bf16(-g.y, h1, l1);
         whi[j] = pack2(h0, h1);
         wlo[j] = pack2(l0, l1);
+        iw[2 * j] = pack2(h0, l0);
+        iw[2 * j + 1] = pack2(h1, l1) ^ 0x80008000u;   // split of +Im = -(split of -Im)
     }
-    store_row(a_hi, a_lo, p, h, whi, wlo);
+    store_row16(a_hi, a_lo, p, h, whi, wlo);
+    if (img) {
+        const int lane = (int)(p & 31u);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) sc[lane * 9 + m] = iw[m];
+        __syncwarp();
+        const int g8 = lane >> 3, L = lane & 7;
+        uint32_t w[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) w[m] = sc[(8 * g8 + m) * 9 + L];
+        __syncwarp();
+        const uint4 hi = make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
+                                    __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
+        const uint4 lo = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
+                                    __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
+        const int rp = 2 * (r0 + 4 * (int)h + (L >> 1)) + (L & 1);
+        const size_t cimg = (size_t)2 * A.G.n_elem * 32;
+        __nv_bfloat16* base = img + (size_t)chunk * 2 * cimg + tc::chunk_offset((uint32_t)rp, 8u * g8) / 2;
+        *(uint4*)base = hi;
+        *(uint4*)(base + cimg) = lo;
+    }
 }
 
-// V chunk (32 elements, K = 32): |G_r(p)|^2 for r = r0 + 8h + j from the exact values.
+// V slice (16 elements, K = 16): |G_r(p)|^2 for r = r0 + 8h + j from the exact values.
 __device__ __forceinline__ void synth_v(int r0, uint32_t p, uint32_t h, const float2* gs, unsigned char* a_hi,
                                         unsigned char* a_lo) {
     uint32_t whi[4], wlo[4];
@@ -223,34 +268,32 @@ __device__ __forceinline__ void synth_v(int r0, uint32_t p, uint32_t h, const fl
         whi[j] = pack2(h0, h1);
         wlo[j] = pack2(l0, l1);
     }
-    store_row(a_hi, a_lo, p, h, whi, wlo);
+    store_row16(a_hi, a_lo, p, h, whi, wlo);
 }
 
+// The forward kernel below keeps two 80 KB stages of K = 32.
 constexpr uint32_t STAGE = 80u * 1024u;        // A hi (8 KB) + A lo (8 KB) + B (64 KB)
 constexpr uint32_t OFF_ALO = 8192u, OFF_B = 16384u;
 
-// Pipeline state shared by all threads (uniform control flow).
-struct Pipe {
-    uint32_t bph[2], mph[2];
-    bool pend[2];
-    uint32_t q;
-};
-
 __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t s_bfull[2], s_mdone[2];
+    __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full, s_acc_empty;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_err;
-    __shared__ float s_red[3][3][TP];     // partial sums of quarters 1..3: Re g, Im g, H
+    __shared__ volatile int s_err;
+    __shared__ float s_red[3][TP];
+    __shared__ uint32_t s_tr[NPROD / 32][32 * 9];   // per producer warp: transpose scratch of the forward images
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t p = (uint32_t)(tid & (TP - 1)), h = (uint32_t)(tid / TP);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nU = n2 / 16, nV = n / 16, per = nU + nV;
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
-            tc::mbar_init(tc::smem_u32(&s_bfull[s]), 1);
-            tc::mbar_init(tc::smem_u32(&s_mdone[s]), 1);
+        for (int s = 0; s < NST; ++s) {
+            tc::mbar_init(tc::smem_u32(&s_full_a[s]), NPROD / 32);
+            tc::mbar_init(tc::smem_u32(&s_full_b[s]), 1);
+            tc::mbar_init(tc::smem_u32(&s_empty[s]), 1);
         }
+        tc::mbar_init(tc::smem_u32(&s_acc_full), 1);
+        tc::mbar_init(tc::smem_u32(&s_acc_empty), NPROD / 32);
         s_err = 0;
     }
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), A.tmem_cols);
@@ -258,191 +301,224 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-    const int nbk = n2 > 256 ? 2 : 1;
-    const int nb_u = n2 / nbk;
-    const uint32_t id_u = tc::idesc_bf16_f32(128, (uint32_t)nb_u);
-    const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)n);
-    const size_t img_u = (size_t)n2 * 32, img_w = (size_t)n * 32;   // bf16 elements
-    const int nchu = n2 / 32, nchv = n / 32;
-    float2* gs = A.gscr + (size_t)blockIdx.x * n * TP;
-    Pipe P = {{0u, 0u}, {0u, 0u}, {false, false}, 0u};
-    bool ok = true;
+    const int my_tiles = (int)blockIdx.x < A.n_tiles ? (A.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const long long total = (long long)my_tiles * A.F.n * per;   // slices of this CTA
+    const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 16;  // bf16 per hi (or lo) / W image slice
+    auto stage = [&](int s) { return smem + (size_t)s * ST_BYTES; };
 
-    // wait until the MMAs that read stage s are done (all threads)
-    auto drain = [&](int s) {
-        if (P.pend[s]) {
-            const bool w = tc::mbar_wait(tc::smem_u32(&s_mdone[s]), P.mph[s], kMaxTries);
-            ok = ok && (__syncthreads_and(w ? 1 : 0) != 0);
-            P.mph[s] ^= 1u;
-            P.pend[s] = false;
+    if (warp == NPROD / 32 + 1) {
+        // ------------------------------ B loader ------------------------------
+        if (lane == 0) {
+            long long ql = 0;
+            bool err = false;
+            for (; ql < total; ++ql) {
+                const int s = (int)(ql % NST);
+                if (ql >= NST && !tc::mbar_wait(tc::smem_u32(&s_empty[s]), (uint32_t)((ql / NST) - 1) & 1u, kMaxTries)) {
+                    err = true;
+                    break;
+                }
+                if (s_err) break;
+                const int fw = (int)((ql / per) % A.F.n), j = (int)(ql % per);
+                const void* src;
+                uint32_t bytes;
+                if (j < nU) {
+                    src = A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u;
+                    bytes = (uint32_t)(n2 * 64);
+                } else {
+                    src = A.bw + (size_t)fw * A.bw_stride + (size_t)(j - nU) * img_w;
+                    bytes = (uint32_t)(n * 32);
+                }
+                tc::bulk_load(tc::smem_u32(stage(s) + ST_B), src, bytes, tc::smem_u32(&s_full_b[s]));
+            }
+            if (err || s_err) {
+                s_err = 1;
+                // bounded waits for the last copies issued (at most one per stage)
+                for (long long x = (ql > NST ? ql - NST : 0); x < ql; ++x)
+                    tc::mbar_wait(tc::smem_u32(&s_full_b[x % NST]), (uint32_t)(x / NST) & 1u, kMaxTries);
+            }
         }
-    };
-    // one K chunk: stage s gets B by a bulk copy and A from the producer lambda, then the MMAs
-    auto run_chunk = [&](const void* bsrc, uint32_t bbytes, auto&& produce, auto&& issue) {
-        const int s = (int)(P.q & 1u);
-        drain(s);
-        unsigned char* st = smem + s * STAGE;
-        if (tid == 0) tc::bulk_load(tc::smem_u32(st + OFF_B), bsrc, bbytes, tc::smem_u32(&s_bfull[s]));
-        produce(st, st + OFF_ALO);
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            if (!tc::mbar_wait(tc::smem_u32(&s_bfull[s]), P.bph[s], kMaxTries)) s_err = 1;
+        __syncwarp();
+    } else if (warp == NPROD / 32) {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            const int nbk = n2 > 256 ? 2 : 1;
+            const int nb_u = n2 / nbk;
+            const uint32_t id_u = tc::idesc_bf16_f32(128, (uint32_t)nb_u);
+            const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)n);
+            long long last = -1;
+            uint32_t accp = 0;
+            bool err = false;
+            for (long long q = 0; q < total && !err; ++q) {
+                const int s = (int)(q % NST), j = (int)(q % per);
+                const uint32_t ph = (uint32_t)(q / NST) & 1u;
+                if ((j == 0 || j == nU) && q > 0) {
+                    // a new accumulation phase: the epilogue must have read the accumulator
+                    if (!tc::mbar_wait(tc::smem_u32(&s_acc_empty), accp & 1u, kMaxTries)) { err = true; break; }
+                    ++accp;
+                }
+                if (!tc::mbar_wait(tc::smem_u32(&s_full_a[s]), ph, kMaxTries)) { err = true; break; }
+                if (!tc::mbar_wait(tc::smem_u32(&s_full_b[s]), ph, kMaxTries)) { err = true; break; }
+                if (s_err) { err = true; break; }
+                tc::fence_after();
+                const uint32_t sa = tc::smem_u32(stage(s)), sal = sa + ST_ALO, sb = sa + ST_B;
+                const uint64_t dah = tc::sdesc(sa, 128, 256), dal = tc::sdesc(sal, 128, 256);
+                if (j < nU) {
+                    const uint32_t acc = j > 0 ? 1u : 0u;
+                    for (int nb = 0; nb < nbk; ++nb) {
+                        const uint32_t boff = (uint32_t)(nb * nb_u / 8) * 256u;
+                        const uint64_t dbh = tc::sdesc(sb + boff, 128, 256);
+                        const uint64_t dbl = tc::sdesc(sb + (uint32_t)(n2 * 32) + boff, 128, 256);
+                        const uint32_t d = tmem + (uint32_t)(nb * nb_u);
+                        tc::mma_bf16(d, dah, dbh, id_u, acc);
+                        tc::mma_bf16(d, dah, dbl, id_u, 1u);
+                        tc::mma_bf16(d, dal, dbh, id_u, 1u);
+                    }
+                } else {
+                    const uint64_t db = tc::sdesc(sb, 128, 256);
+                    tc::mma_bf16(tmem, dah, db, id_v, j > nU ? 1u : 0u);
+                    tc::mma_bf16(tmem, dal, db, id_v, 1u);
+                }
+                tc::commit(tc::smem_u32(&s_empty[s]));
+                if (j == nU - 1 || j == per - 1) tc::commit(tc::smem_u32(&s_acc_full));
+                last = q;
+            }
+            if (err) {
+                s_err = 1;
+                atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
+                // bounded wait for the MMAs still in flight
+                if (last >= 0)
+                    tc::mbar_wait(tc::smem_u32(&s_empty[last % NST]), (uint32_t)(last / NST) & 1u, kMaxTries);
+            }
+        }
+        __syncwarp();
+    } else {
+        // -------------------------------- producers --------------------------------
+        const uint32_t p = (uint32_t)(tid & (TP - 1)), h = (uint32_t)(tid / TP);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        float2* gs = A.gscr + (size_t)blockIdx.x * n * TP;
+        bool err = false;
+        long long q = 0;
+        uint32_t accf = 0;
+        // one slice: wait for the stage, fill A, publish it
+        auto slice = [&](auto&& produce) {
+            const int s = (int)(q % NST);
+            if (!err && q >= NST) err = !tc::mbar_wait(tc::smem_u32(&s_empty[s]), (uint32_t)((q / NST) - 1) & 1u, kMaxTries);
+            err = __any_sync(0xffffffffu, err || s_err != 0);
+            if (!err) produce(stage(s), stage(s) + ST_ALO);
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_full_a[s]));
+            ++q;
+        };
+        // wait for the accumulator of the phase just issued (warp-uniform result)
+        auto acc_wait = [&]() {
+            if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_acc_full), accf & 1u, kMaxTries);
+            ++accf;
+            err = __any_sync(0xffffffffu, err);
             tc::fence_after();
-            issue(tc::smem_u32(st), tc::smem_u32(st + OFF_ALO), tc::smem_u32(st + OFF_B));
-            tc::commit(tc::smem_u32(&s_mdone[s]));
-        }
-        P.bph[s] ^= 1u;
-        P.pend[s] = true;
-        ++P.q;
-    };
-
-    for (int tile = blockIdx.x; tile < A.n_tiles && ok; tile += gridDim.x) {
-        const int px = tile * TP + (int)p;
-        const bool valid = px < G.npix;
-        const float c_px = valid ? __ldg(A.c + px) : 0.f;
-        float acc_g = 0.f, acc_h = 0.f;
-        for (int fw = 0; fw < A.F.n && ok; ++fw) {
-            const FreqC fc = A.F.f[fw];
-            const __nv_bfloat16* bu = A.bu + (size_t)fw * A.bu_stride;
-            const __nv_bfloat16* bw = A.bw + (size_t)fw * A.bw_stride;
-            // ---- U over K' = 2n; table records fetched one chunk ahead ----
-            rb_cell nxt[4];
-            float2 nxd[4];
-            load_recs(A, 0, h, px, valid, nxt, nxd);
-            for (int kc = 0; kc < nchu && ok; ++kc) {
-                run_chunk(
-                    bu + (size_t)kc * 2 * img_u, (uint32_t)(2 * n2 * 64),
-                    [&](unsigned char* ahi, unsigned char* alo) {
+        };
+        auto acc_release = [&]() {
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_acc_empty));
+        };
+        for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
+            const int px = tile * TP + (int)p;
+            const bool valid = px < G.npix;
+            const float c_px = valid ? __ldg(A.c + px) : 0.f;
+            float acc_g = 0.f, acc_h = 0.f;
+            for (int fw = 0; fw < A.F.n; ++fw) {
+                const FreqC fc = A.F.f[fw];
+                // ---- U slices; table records fetched one slice ahead ----
+                __nv_bfloat16* img = A.gimg ? A.gimg + (size_t)fw * A.gimg_stride : nullptr;
+                rb_cell nxt[4];
+                float2 nxd[4];
+                load_recs(A, 0, h, px, valid, nxt, nxd);
+                for (int j = 0; j < nU; ++j) {
+                    slice([&](unsigned char* ahi, unsigned char* alo) {
                         rb_cell cur[4];
                         float2 cud[4];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            cur[j] = nxt[j];
-                            cud[j] = nxd[j];
+                        for (int k = 0; k < 4; ++k) {
+                            cur[k] = nxt[k];
+                            cud[k] = nxd[k];
                         }
-                        if (kc + 1 < nchu) load_recs(A, (kc + 1) * 16, h, px, valid, nxt, nxd);
-                        synth_u(A, fc, kc * 16, p, h, cur, cud, c_px, gs, ahi, alo);
-                    },
-                    [&](uint32_t ahi, uint32_t alo, uint32_t b) {
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t dah = tc::sdesc(ahi + 256u * ks, 128, 512);
-                            const uint64_t dal = tc::sdesc(alo + 256u * ks, 128, 512);
-                            for (int nb = 0; nb < nbk; ++nb) {
-                                const uint32_t boff = (uint32_t)(nb * nb_u / 8) * 512u + 256u * ks;
-                                const uint64_t dbh = tc::sdesc(b + boff, 128, 512);
-                                const uint64_t dbl = tc::sdesc(b + (uint32_t)(n2 * 64) + boff, 128, 512);
-                                const uint32_t d = tmem + (uint32_t)(nb * nb_u);
-                                tc::mma_bf16(d, dah, dbh, id_u, (kc > 0 || ks > 0) ? 1u : 0u);
-                                tc::mma_bf16(d, dah, dbl, id_u, 1u);
-                                tc::mma_bf16(d, dal, dbh, id_u, 1u);
-                            }
-                        }
+                        if (j + 1 < nU) load_recs(A, (j + 1) * 8, h, px, valid, nxt, nxd);
+                        synth_u(A, fc, j * 8, p, h, cur, cud, c_px, gs, ahi, alo, img, tile * 4 + (warp & 3),
+                                s_tr[warp]);
                     });
-            }
-            drain(0);
-            drain(1);
-            ok = ok && (__syncthreads_or(s_err) == 0);
-            if (!ok) break;
-            if (A.gimg) {
-                // this tile's exact G (complete in gs) as forward operand images
-                __nv_bfloat16* img = A.gimg + (size_t)fw * A.gimg_stride;
-                for (int u = tid; u < n * (TP / 8); u += NTHR_A) {
-                    const int r = u % n, seg = u / n;
-                    float2 g[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) g[j] = gs[(size_t)r * TP + 8 * seg + j];
-                    gimage_seg(img, n, tile * TP + 8 * seg, r, g);
                 }
-            }
-            tc::fence_after();
-            // epilogue: 32-column blocks b = h, h + 4, ... of the 2n columns (Re U, then Im U)
-            float gr = 0.f, gi = 0.f;
-            for (int b = (int)h; b < nchu; b += 4) {
-                const int half = (32 * b) >= n ? 1 : 0;
-                const int cb = 32 * b - half * n;
-                float v[32];
-                tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), v);
+                // gs (exact G of the tile) is complete
+                err = tc::named_or(1, NPROD, err);
+                if (err) break;
+                // ---- U epilogue: 32-column blocks b = h, h + 2, ... of Re U | Im U ----
+                acc_wait();
+                float gr = 0.f, gi = 0.f;
+                if (!err) {
+                    // element block b: Re U in columns [32 b, 32 b + 32), Im U in [n + 32 b, ...)
+                    for (int b = (int)h; b < n / 32; b += 2) {
+                        float vr[32], vi[32];
+                        tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), vr);
+                        tc::tmem_ld32(tmem + lane_off + (uint32_t)(n + 32 * b), vi);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float2 ge = gs[(size_t)(cb + j) * TP + p];
-                    if (half == 0) {
-                        gr = fmaf(ge.x, v[j], gr);
-                        gi = fmaf(-ge.y, v[j], gi);
-                    } else {
-                        gr = fmaf(ge.y, v[j], gr);
-                        gi = fmaf(ge.x, v[j], gi);
+                        for (int k = 0; k < 32; ++k) {
+                            const float2 ge = gs[(size_t)(32 * b + k) * TP + p];
+                            gr = fmaf(ge.x, vr[k], fmaf(ge.y, vi[k], gr));
+                            gi = fmaf(ge.x, vi[k], fmaf(-ge.y, vr[k], gi));
+                        }
                     }
                 }
-            }
-            if (h > 0) {
-                s_red[0][h - 1][p] = gr;
-                s_red[1][h - 1][p] = gi;
-            }
-            tc::fence_before();
-            __syncthreads();
-            if (h == 0) {
-                gr = (gr + s_red[0][0][p] + s_red[0][1][p] + s_red[0][2][p]) * fc.w2;
-                gi = (gi + s_red[1][0][p] + s_red[1][1][p] + s_red[1][2][p]) * fc.w2;
-                if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
-                acc_g += gr;
-            }
-            // ---- V over K = n (accumulator reuses the first n columns) ----
-            for (int kc = 0; kc < nchv && ok; ++kc) {
-                run_chunk(
-                    bw + (size_t)kc * img_w, (uint32_t)(n * 64),
-                    [&](unsigned char* ahi, unsigned char* alo) { synth_v(kc * 32, p, h, gs, ahi, alo); },
-                    [&](uint32_t ahi, uint32_t alo, uint32_t b) {
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t dah = tc::sdesc(ahi + 256u * ks, 128, 512);
-                            const uint64_t dal = tc::sdesc(alo + 256u * ks, 128, 512);
-                            const uint64_t db = tc::sdesc(b + 256u * ks, 128, 512);
-                            tc::mma_bf16(tmem, dah, db, id_v, (kc > 0 || ks > 0) ? 1u : 0u);
-                            tc::mma_bf16(tmem, dal, db, id_v, 1u);
-                        }
-                    });
-            }
-            drain(0);
-            drain(1);
-            ok = ok && (__syncthreads_or(s_err) == 0);
-            if (!ok) break;
-            tc::fence_after();
-            float hh = 0.f;
-            for (int b = (int)h; b < nchv; b += 4) {
-                float v[32];
-                tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), v);
+                acc_release();
+                if (h == 1) {
+                    s_red[0][p] = gr;
+                    s_red[1][p] = gi;
+                }
+                err = tc::named_or(1, NPROD, err);
+                if (err) break;
+                if (h == 0) {
+                    gr = (gr + s_red[0][p]) * fc.w2;
+                    gi = (gi + s_red[1][p]) * fc.w2;
+                    if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
+                    acc_g += gr;
+                }
+                // ---- V slices ----
+                for (int j = 0; j < nV; ++j)
+                    slice([&](unsigned char* ahi, unsigned char* alo) { synth_v(j * 16, p, h, gs, ahi, alo); });
+                // ---- V epilogue ----
+                acc_wait();
+                float hh = 0.f;
+                if (!err) {
+                    for (int b = (int)h; b < n / 32; b += 2) {
+                        float v[32];
+                        tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float2 ge = gs[(size_t)(32 * b + j) * TP + p];
-                    hh = fmaf(ge.x * ge.x + ge.y * ge.y, v[j], hh);
+                        for (int k = 0; k < 32; ++k) {
+                            const float2 ge = gs[(size_t)(32 * b + k) * TP + p];
+                            hh = fmaf(ge.x * ge.x + ge.y * ge.y, v[k], hh);
+                        }
+                    }
+                }
+                acc_release();
+                if (h == 1) s_red[2][p] = hh;
+                err = tc::named_or(1, NPROD, err);
+                if (err) break;
+                if (h == 0) {
+                    hh = (hh + s_red[2][p]) * fc.w4;
+                    if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = hh;
+                    acc_h += hh;
                 }
             }
-            if (h > 0) s_red[2][h - 1][p] = hh;
-            tc::fence_before();
-            __syncthreads();
-            if (h == 0) {
-                hh = (hh + s_red[2][0][p] + s_red[2][1][p] + s_red[2][2][p]) * fc.w4;
-                if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = hh;
-                acc_h += hh;
+            if (err) break;
+            if (valid && h == 0) {
+                if (A.gsum) A.gsum[px] = acc_g;
+                if (A.hsum) A.hsum[px] = acc_h;
             }
         }
-        if (ok && valid && h == 0) {
-            if (A.gsum) A.gsum[px] = acc_g;
-            if (A.hsum) A.hsum[px] = acc_h;
-        }
-    }
-    if (!ok) {
-        // a wait ran out: report it, give outstanding MMAs a bounded chance to drain, then free TMEM
-        if (tid == 0) atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
-        for (int s = 0; s < 2; ++s)
-            if (P.pend[s]) tc::mbar_wait(tc::smem_u32(&s_mdone[s]), P.mph[s], kMaxTries);
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, A.tmem_cols);
 }
-
 }  // namespace
 
 bool tc_adjoint_supported(int n_elem) { return n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0; }
@@ -494,9 +570,8 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const floa
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * n)) cols <<= 1;
     A.tmem_cols = cols;
-    // two pipeline stages of 80 KB: more than half of the SM's shared memory, so one
-    // CTA (one TMEM owner) per SM
-    const int sm = 2 * 80 * 1024;
+    // NST stages of 40 KB: most of the SM's shared memory, so one CTA (one TMEM owner) per SM
+    const int sm = NST * (int)ST_BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     const int grid = n_ctas < A.n_tiles ? n_ctas : A.n_tiles;

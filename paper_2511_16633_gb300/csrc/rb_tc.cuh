@@ -21,6 +21,13 @@ __device__ __forceinline__ uint32_t chunk_offset(uint32_t r, uint32_t k) {
     return (r >> 3) * kRowGroupBytes + (k >> 3) * kCoreBytes + (r & 7u) * 16u + (k & 7u) * 2u;
 }
 
+// The same layout for a tile of 16 bf16 per row (two core matrices along K):
+// LBO = 128 B, SBO = 256 B.
+constexpr uint32_t kRowGroupBytes16 = 256;
+__host__ __device__ __forceinline__ uint32_t tile16_offset(uint32_t r, uint32_t k) {
+    return (r >> 3) * kRowGroupBytes16 + (k >> 3) * kCoreBytes + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -63,6 +70,29 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Barrier over the first `nthreads` threads of the CTA (a multiple of 32) on hardware barrier `id`.
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Barrier over the first `nthreads` threads that also ORs a predicate across them.
+__device__ __forceinline__ bool named_or(uint32_t id, uint32_t nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %3, 0;\n\t"
+        "bar.red.or.pred p, %1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"(id), "r"(nthreads), "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
 }
 
 // Bounded wait for the phase with parity `parity` to complete.  Returns false on timeout.
