@@ -19,7 +19,6 @@
 namespace {
 
 constexpr int TP = 128;                 // pixels per tile = MMA M
-constexpr int NTHR = 256;               // forward: threads per CTA
 constexpr uint32_t kMaxTries = 1u << 22; // mbarrier polls before giving up (each poll suspends briefly)
 
 // ---------------------------------------------------------------------------
@@ -83,13 +82,14 @@ struct TcArgs {
     size_t gimg_stride;        // bf16 elements per frequency
 };
 
-// G operand image of the forward, per frequency: chunks of 32 pixels, each a hi
-// image then a lo image of 2n rows (r' = 2r + {0: Re, 1: Im}) x 32 pixels in the
-// core-matrix layout.  One call writes the 8-pixel segment starting at pixel
-// pix0 (a multiple of 8) for element r.
+// G operand image of the forward, per frequency: chunks of 16 pixels (one K = 16
+// pipeline slice of the forward), each a hi image then a lo image of 2n rows
+// (r' = 2r + {0: Re, 1: Im}) x 16 pixels in the core-matrix layout (tile16_offset).
+// One call writes the 8-pixel segment starting at pixel pix0 (a multiple of 8) for
+// element r.
 __device__ __forceinline__ void gimage_seg(__nv_bfloat16* img, int n, int pix0, int r, const float2 (&g)[8]) {
-    const int chunk = pix0 >> 5, kg = (pix0 & 31) >> 3;
-    const size_t cimg = (size_t)2 * n * 32;
+    const int chunk = pix0 >> 4, kg = (pix0 & 15) >> 3;
+    const size_t cimg = (size_t)2 * n * 16;
     __nv_bfloat16* base = img + (size_t)chunk * 2 * cimg;
 #pragma unroll
     for (int part = 0; part < 2; ++part) {
@@ -102,7 +102,7 @@ __device__ __forceinline__ void gimage_seg(__nv_bfloat16* img, int n, int pix0, 
             wh[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
             wl[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
         }
-        const uint32_t off = tc::chunk_offset((uint32_t)(2 * r + part), 8u * kg) / 2;
+        const uint32_t off = tc::tile16_offset((uint32_t)(2 * r + part), 8u * kg) / 2;
         *(uint4*)(base + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
         *(uint4*)(base + cimg + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
@@ -211,7 +211,8 @@ __device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, i
 // bf16 hi / lo of (Re, -Im) to K-group h of the A slice.  With img set, the same
 // values (Re, +Im) also go to the forward operand image (see gimage_seg): the
 // 8-lane groups of the warp transpose their words through the warp's scratch sc
-// (32 x 9 words) so that each lane stores one 16-byte row of 8 pixels, hi and lo.
+// (32 x 9 words) so that each lane stores one 16-byte row of 8 pixels, hi and lo;
+// chunk is the first of the warp's two 16-pixel image chunks.
 __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h,
                                         const rb_cell (&rec)[4], const float2 (&dd)[4], float c_px, float2* gs,
                                         unsigned char* a_hi, unsigned char* a_lo, __nv_bfloat16* img, int chunk,
@@ -247,8 +248,8 @@ __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0
         const uint4 lo = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
                                     __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
         const int rp = 2 * (r0 + 4 * (int)h + (L >> 1)) + (L & 1);
-        const size_t cimg = (size_t)2 * A.G.n_elem * 32;
-        __nv_bfloat16* base = img + (size_t)chunk * 2 * cimg + tc::chunk_offset((uint32_t)rp, 8u * g8) / 2;
+        const size_t cimg = (size_t)2 * A.G.n_elem * 16;
+        __nv_bfloat16* base = img + (size_t)(chunk + (g8 >> 1)) * 2 * cimg + tc::tile16_offset((uint32_t)rp, 8u * (g8 & 1)) / 2;
         *(uint4*)base = hi;
         *(uint4*)(base + cimg) = lo;
     }
@@ -270,10 +271,6 @@ __device__ __forceinline__ void synth_v(int r0, uint32_t p, uint32_t h, const fl
     }
     store_row16(a_hi, a_lo, p, h, whi, wlo);
 }
-
-// The forward kernel below keeps two 80 KB stages of K = 32.
-constexpr uint32_t STAGE = 80u * 1024u;        // A hi (8 KB) + A lo (8 KB) + B (64 KB)
-constexpr uint32_t OFF_ALO = 8192u, OFF_B = 16384u;
 
 __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -444,7 +441,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                             cud[k] = nxd[k];
                         }
                         if (j + 1 < nU) load_recs(A, (j + 1) * 8, h, px, valid, nxt, nxd);
-                        synth_u(A, fc, j * 8, p, h, cur, cud, c_px, gs, ahi, alo, img, tile * 4 + (warp & 3),
+                        synth_u(A, fc, j * 8, p, h, cur, cud, c_px, gs, ahi, alo, img, tile * 8 + (warp & 3) * 2,
                                 s_tr[warp]);
                     });
                 }
@@ -608,32 +605,38 @@ struct FwdArgs {
 
 __host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i) / nb; }
 
-__global__ void __launch_bounds__(NTHR, 1) k_forward_tc(FwdArgs A) {
+// Forward kernel: the adjoint's warp-specialised pipeline over K = 16 pixel slices.
+//   warps 0..7  producers: thread (row = tid % 128, g = tid / 128) builds K-group g of
+//               row `row` of A = (B rows 128 i + row) * m(x), re-split into hi / lo,
+//               once the slice's B has landed; then the epilogue;
+//   warp 8      MMA issuer; warp 9 B loader (image rows [col0, 2n), hi and lo).
+__global__ void __launch_bounds__(NTHR_A, 1) k_forward_tc(FwdArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t s_bfull[2], s_mdone[2];
+    __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_err;
+    __shared__ volatile int s_err;
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int i = 0;
     while (i + 1 < A.n_mb && (int)blockIdx.x >= A.cta0[i + 1]) ++i;
-    const int s = (int)blockIdx.x - A.cta0[i];
+    const int sp = (int)blockIdx.x - A.cta0[i];
     const int S = A.splits[i];
     const int jmin = jmin_of(i, A.nb);
-    const int col0 = jmin * A.nb;             // first needed column (= first B row loaded)
-    const int nchunk_all = (G.npix + 31) / 32;
-    const int cpc = (nchunk_all + S - 1) / S;
-    const int cbeg = min(nchunk_all, s * cpc), cend = min(nchunk_all, cbeg + cpc);
-    const int nq = cend - cbeg;
-    const size_t cimg = (size_t)n2 * 32;                         // bf16 per hi or lo image of a chunk
-    const uint32_t rows_bytes = (uint32_t)(n2 - col0) * 64u;     // loaded rows [col0, 2n) of one image
-    const uint32_t row0_bytes = (uint32_t)col0 * 64u;
+    const int col0 = jmin * A.nb;                       // first needed column (= first B row loaded)
+    const int nsl_all = (G.npix + 15) / 16;
+    const int cps = (nsl_all + S - 1) / S;
+    const int sbeg = min(nsl_all, sp * cps), send = min(nsl_all, sbeg + cps);
+    const int nq = send - sbeg;
+    const size_t cimg = (size_t)n2 * 16;                           // bf16 per hi or lo image of a slice
+    const uint32_t rows_bytes = (uint32_t)(n2 - col0) * 32u;      // loaded rows [col0, 2n) of one image
     if (tid == 0) {
-        for (int k = 0; k < 2; ++k) {
-            tc::mbar_init(tc::smem_u32(&s_bfull[k]), 1);
-            tc::mbar_init(tc::smem_u32(&s_mdone[k]), 1);
+        for (int k = 0; k < NST; ++k) {
+            tc::mbar_init(tc::smem_u32(&s_full_a[k]), NPROD / 32);
+            tc::mbar_init(tc::smem_u32(&s_full_b[k]), 1);
+            tc::mbar_init(tc::smem_u32(&s_empty[k]), 1);
         }
+        tc::mbar_init(tc::smem_u32(&s_acc_full), 1);
         s_err = 0;
     }
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), A.tmem_cols);
@@ -641,129 +644,140 @@ __global__ void __launch_bounds__(NTHR, 1) k_forward_tc(FwdArgs A) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t id = tc::idesc_bf16_f32(128, (uint32_t)A.nb);
-    uint32_t bph[2] = {0u, 0u}, mph[2] = {0u, 0u};
-    bool mpend[2] = {false, false};
-    bool ok = true;
-    // stage layout: A hi | A lo | B hi (rows col0..2n) | B lo
-    auto stage = [&](int k) { return smem + k * STAGE; };
-    auto issue_copy = [&](int q) {   // thread 0: chunk q into stage q & 1
-        const int k = q & 1;
-        unsigned char* st = stage(k);
-        const __nv_bfloat16* src = A.gimg + (size_t)(cbeg + q) * 2 * cimg;
-        const uint32_t mb = tc::smem_u32(&s_bfull[k]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * rows_bytes) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         tc::smem_u32(st + OFF_B)),
-                     "l"((const char*)src + row0_bytes), "r"(rows_bytes), "r"(mb)
-                     : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         tc::smem_u32(st + OFF_B + rows_bytes)),
-                     "l"((const char*)(src + cimg) + row0_bytes), "r"(rows_bytes), "r"(mb)
-                     : "memory");
-    };
-    if (tid == 0 && nq > 0) issue_copy(0);
-    for (int q = 0; q < nq && ok; ++q) {
-        const int k = q & 1;
-        unsigned char* st = stage(k);
-        unsigned char* a_hi = st;
-        unsigned char* a_lo = st + OFF_ALO;
-        const unsigned char* b_hi = st + OFF_B;                   // holds rows [col0, 2n)
-        const unsigned char* b_lo = st + OFF_B + rows_bytes;
-        ok = __syncthreads_and(tc::mbar_wait(tc::smem_u32(&s_bfull[k]), bph[k], kMaxTries) ? 1 : 0) != 0;
-        bph[k] ^= 1u;
-        if (!ok) break;
-        // A = rows [128 i, 128 i + 128) of B scaled by p(x), re-split into hi / lo
-        const int p0 = (cbeg + q) * 32;
-        for (int u = tid; u < 128 * 4; u += NTHR) {
-            const int row = u & 127, kg = u >> 7;
-            const uint32_t boff = tc::chunk_offset((uint32_t)(128 * i + row - col0), 8u * kg);
-            const uint4 vh = *(const uint4*)(b_hi + boff), vl = *(const uint4*)(b_lo + boff);
-            const uint32_t hw[4] = {vh.x, vh.y, vh.z, vh.w}, lw[4] = {vl.x, vl.y, vl.z, vl.w};
-            uint32_t oh[4], ol[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int pix = p0 + 8 * kg + 2 * j;
-                const float m0 = pix < G.npix ? __ldg(A.m + pix) : 0.f;
-                const float m1 = pix + 1 < G.npix ? __ldg(A.m + pix + 1) : 0.f;
-                const float x0 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[j] & 0xffff))) +
-                                  __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[j] & 0xffff)))) * m0;
-                const float x1 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[j] >> 16))) +
-                                  __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[j] >> 16)))) * m1;
-                __nv_bfloat16 h0, l0, h1, l1;
-                tc::split_bf16(x0, h0, l0);
-                tc::split_bf16(x1, h1, l1);
-                oh[j] = pack2(h0, h1);
-                ol[j] = pack2(l0, l1);
+    auto stage = [&](int k) { return smem + (size_t)k * ST_BYTES; };
+
+    if (warp == NPROD / 32 + 1) {
+        // ------------------------------ B loader ------------------------------
+        if (lane == 0) {
+            int ql = 0;
+            bool err = false;
+            for (; ql < nq; ++ql) {
+                const int k = ql % NST;
+                if (ql >= NST && !tc::mbar_wait(tc::smem_u32(&s_empty[k]), (uint32_t)((ql / NST) - 1) & 1u, kMaxTries)) {
+                    err = true;
+                    break;
+                }
+                if (s_err) break;
+                const __nv_bfloat16* src = A.gimg + (size_t)(sbeg + ql) * 2 * cimg;
+                const uint32_t mb = tc::smem_u32(&s_full_b[k]);
+                const uint32_t dst = tc::smem_u32(stage(k) + ST_B);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * rows_bytes) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                             "l"((const char*)src + (size_t)col0 * 32), "r"(rows_bytes), "r"(mb)
+                             : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                 dst + rows_bytes),
+                             "l"((const char*)(src + cimg) + (size_t)col0 * 32), "r"(rows_bytes), "r"(mb)
+                             : "memory");
             }
-            const uint32_t aoff = tc::chunk_offset((uint32_t)row, 8u * kg);
-            *(uint4*)(a_hi + aoff) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
-            *(uint4*)(a_lo + aoff) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+            if (err || s_err) {
+                s_err = 1;
+                for (int x = (ql > NST ? ql - NST : 0); x < ql; ++x)
+                    tc::mbar_wait(tc::smem_u32(&s_full_b[x % NST]), (uint32_t)(x / NST) & 1u, kMaxTries);
+            }
         }
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after();
-            const uint32_t sa_hi = tc::smem_u32(a_hi), sa_lo = tc::smem_u32(a_lo);
-            const uint32_t sb_hi = tc::smem_u32(b_hi), sb_lo = tc::smem_u32(b_lo);
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t dah = tc::sdesc(sa_hi + 256u * ks, 128, 512);
-                const uint64_t dal = tc::sdesc(sa_lo + 256u * ks, 128, 512);
+        __syncwarp();
+    } else if (warp == NPROD / 32) {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            const uint32_t id = tc::idesc_bf16_f32(128, (uint32_t)A.nb);
+            int last = -1;
+            bool err = false;
+            for (int q = 0; q < nq && !err; ++q) {
+                const int k = q % NST;
+                const uint32_t ph = (uint32_t)(q / NST) & 1u;
+                if (!tc::mbar_wait(tc::smem_u32(&s_full_a[k]), ph, kMaxTries)) { err = true; break; }
+                if (!tc::mbar_wait(tc::smem_u32(&s_full_b[k]), ph, kMaxTries)) { err = true; break; }
+                if (s_err) { err = true; break; }
+                tc::fence_after();
+                const uint32_t sa = tc::smem_u32(stage(k)), sb = sa + ST_B;
+                const uint64_t dah = tc::sdesc(sa, 128, 256), dal = tc::sdesc(sa + ST_ALO, 128, 256);
                 for (int j = jmin; j < A.nbn; ++j) {
-                    const uint32_t boff = (uint32_t)((j * A.nb - col0) / 8) * 512u + 256u * ks;
-                    const uint64_t dbh = tc::sdesc(sb_hi + boff, 128, 512);
-                    const uint64_t dbl = tc::sdesc(sb_lo + boff, 128, 512);
+                    const uint32_t boff = (uint32_t)((j * A.nb - col0) / 8) * 256u;
+                    const uint64_t dbh = tc::sdesc(sb + boff, 128, 256);
+                    const uint64_t dbl = tc::sdesc(sb + rows_bytes + boff, 128, 256);
                     const uint32_t d = tmem + (uint32_t)(j * A.nb);
-                    tc::mma_bf16(d, dah, dbh, id, (q > 0 || ks > 0) ? 1u : 0u);
+                    tc::mma_bf16(d, dah, dbh, id, q > 0 ? 1u : 0u);
                     tc::mma_bf16(d, dah, dbl, id, 1u);
                     tc::mma_bf16(d, dal, dbh, id, 1u);
                 }
+                tc::commit(tc::smem_u32(&s_empty[k]));
+                if (q == nq - 1) tc::commit(tc::smem_u32(&s_acc_full));
+                last = q;
             }
-            tc::commit(tc::smem_u32(&s_mdone[k]));
-            // next chunk into the other stage once the MMAs that read it (chunk q - 1) are done
-            if (q + 1 < nq) {
-                const int k2 = (q + 1) & 1;
-                if (mpend[k2]) {
-                    if (!tc::mbar_wait(tc::smem_u32(&s_mdone[k2]), mph[k2], kMaxTries)) s_err = 1;
+            if (err) {
+                s_err = 1;
+                atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
+                if (last >= 0) tc::mbar_wait(tc::smem_u32(&s_empty[last % NST]), (uint32_t)(last / NST) & 1u, kMaxTries);
+            }
+        }
+        __syncwarp();
+    } else {
+        // -------------------------------- producers --------------------------------
+        const int row = tid & 127, g = tid >> 7;
+        bool err = false;
+        for (int q = 0; q < nq; ++q) {
+            const int k = q % NST;
+            const uint32_t ph = (uint32_t)(q / NST) & 1u;
+            if (!err && q >= NST) err = !tc::mbar_wait(tc::smem_u32(&s_empty[k]), ph ^ 1u, kMaxTries);
+            if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_full_b[k]), ph, kMaxTries);
+            err = __any_sync(0xffffffffu, err || s_err != 0);
+            if (!err) {
+                const unsigned char* b_hi = stage(k) + ST_B;
+                const unsigned char* b_lo = b_hi + rows_bytes;
+                const uint32_t boff = tc::tile16_offset((uint32_t)(128 * i + row - col0), 8u * g);
+                const uint4 vh = *(const uint4*)(b_hi + boff), vl = *(const uint4*)(b_lo + boff);
+                const uint32_t hw[4] = {vh.x, vh.y, vh.z, vh.w}, lw[4] = {vl.x, vl.y, vl.z, vl.w};
+                const int p0 = (sbeg + q) * 16 + 8 * g;
+                float mm[8];
+                if (p0 + 8 <= G.npix) {
+                    const float4 m0 = __ldg((const float4*)(A.m + p0)), m1 = __ldg((const float4*)(A.m + p0 + 4));
+                    mm[0] = m0.x; mm[1] = m0.y; mm[2] = m0.z; mm[3] = m0.w;
+                    mm[4] = m1.x; mm[5] = m1.y; mm[6] = m1.z; mm[7] = m1.w;
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) mm[t] = p0 + t < G.npix ? __ldg(A.m + p0 + t) : 0.f;
                 }
-                issue_copy(q + 1);
+                uint32_t oh[4], ol[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float x0 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[t] & 0xffff))) +
+                                      __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[t] & 0xffff)))) * mm[2 * t];
+                    const float x1 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[t] >> 16))) +
+                                      __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[t] >> 16)))) * mm[2 * t + 1];
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    tc::split_bf16(x0, h0, l0);
+                    tc::split_bf16(x1, h1, l1);
+                    oh[t] = pack2(h0, h1);
+                    ol[t] = pack2(l0, l1);
+                }
+                store_row16(stage(k), stage(k) + ST_ALO, (uint32_t)row, (uint32_t)g, oh, ol);
+            }
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_full_a[k]));
+        }
+        // epilogue: this CTA's partial D block (128 rows x needed columns) to global memory
+        if (!err && nq > 0) err = !tc::mbar_wait(tc::smem_u32(&s_acc_full), 0u, kMaxTries);
+        err = __any_sync(0xffffffffu, err || s_err != 0);
+        tc::fence_after();
+        if (!err) {
+            const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+            float* out = A.partial + ((size_t)blockIdx.x * 128 + row) * n2;
+            int cnum = 0;
+            for (int cb = col0; cb < n2; cb += 32, ++cnum) {
+                if ((cnum & 1) != g) continue;
+                float v[32];
+                if (nq > 0) {
+                    tc::tmem_ld32(tmem + lane_off + (uint32_t)cb, v);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) v[t] = 0.f;
+                }
+#pragma unroll
+                for (int t = 0; t < 32; t += 4) *(float4*)(out + cb + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
             }
         }
-        // every thread tracks the same barrier phases
-        if (q + 1 < nq && mpend[(q + 1) & 1]) {
-            mph[(q + 1) & 1] ^= 1u;
-            mpend[(q + 1) & 1] = false;
-        }
-        mpend[k] = true;
-        ok = ok && (__syncthreads_or(s_err) == 0);
-    }
-    for (int k = 0; k < 2; ++k)
-        if (mpend[k]) {
-            const bool w = tc::mbar_wait(tc::smem_u32(&s_mdone[k]), mph[k], kMaxTries);
-            ok = ok && (__syncthreads_and(w ? 1 : 0) != 0);
-            mph[k] ^= 1u;
-            mpend[k] = false;
-        }
-    tc::fence_after();
-    if (ok) {
-        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-        const int row = tid & 127, hh = tid >> 7;
-        float* out = A.partial + ((size_t)blockIdx.x * 128 + row) * n2;
-        int cnum = 0;
-        for (int cb = col0; cb < n2; cb += 32, ++cnum) {
-            if ((cnum & 1) != hh) continue;
-            float v[32];
-            if (nq > 0) {
-                tc::tmem_ld32(tmem + lane_off + (uint32_t)cb, v);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0.f;
-            }
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) *(float4*)(out + cb + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
-    } else if (tid == 0) {
-        atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
     }
     tc::fence_before();
     __syncthreads();
@@ -851,8 +865,8 @@ size_t tc_forward_partial_bytes(int n_elem, int n_ctas) {
 }
 
 size_t tc_gimage_elems(int n_elem, int npix) {
-    const size_t chunks = (size_t)((npix + 127) / 128) * 4;
-    return chunks * 2 * (2 * (size_t)n_elem) * 32;
+    const size_t chunks = (size_t)((npix + 127) / 128) * 8;   // 16-pixel chunks, whole 128-pixel tiles
+    return chunks * 2 * (2 * (size_t)n_elem) * 16;
 }
 
 cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F, void* img,
@@ -869,10 +883,10 @@ cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F,
                               cudaStream_t s) {
     if (!tc_adjoint_supported(G.n_elem)) return cudaErrorInvalidValue;
     const FwdArgs A = make_fwd_args(G, F, (const __nv_bfloat16*)gimg, m, partial, n_ctas, counters);
-    const int sm = 2 * 80 * 1024;
+    const int sm = NST * (int)ST_BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    k_forward_tc<<<A.cta0[A.n_mb], NTHR, sm, s>>>(A);
+    k_forward_tc<<<A.cta0[A.n_mb], NTHR_A, sm, s>>>(A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_forward_tc_reduce<<<256, 256, 0, s>>>(A, d_out, w, den_part);
