@@ -35,8 +35,6 @@ GeoDev make_geo(const rb_geometry* g, const float4* elem_xy) {
     G.ny = g->ny;
     G.n_rays = g->n_rays;
     G.max_steps = g->max_steps;
-    G.n_wpf = (g->n_rays - 1 + 30) / 31;
-    if (G.n_wpf < 1) G.n_wpf = 1;
     G.npix = g->nx * g->ny;
     G.h = (float)g->h;
     G.inv_h = (float)(1.0 / g->h);

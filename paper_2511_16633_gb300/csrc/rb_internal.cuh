@@ -14,7 +14,6 @@
 // ---------------------------------------------------------------------------
 struct GeoDev {
     int n_elem, nx, ny, n_rays, max_steps;
-    int n_wpf;            // warps per fan in the tracer: ceil((n_rays - 1) / 31)
     int npix;
     float h, inv_h, cxg, cyg;   // cxg = (nx - 1) / 2
     float h_hi, h_lo;           // h as a float pair

@@ -191,9 +191,17 @@ __global__ void __launch_bounds__(SEL_THREADS) k_outlier_select(int n_total, dou
             s_nc = 0;
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
-            const uint64_t key = keys[j];
-            if (key != 0) atomicAdd(&hist[key >> 52], 1u);
+        // four independent loads in flight per thread and iteration
+        for (int j0 = threadIdx.x; j0 < n_total; j0 += 4 * blockDim.x) {
+            uint64_t kk[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = j0 + t * blockDim.x;
+                kk[t] = j < n_total ? keys[j] : 0ull;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (kk[t] != 0) atomicAdd(&hist[kk[t] >> 52], 1u);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -208,9 +216,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_outlier_select(int n_total, dou
         if (nb <= SEL_CAP) {
             // compact the bucket, then 8-bit passes over bits 51..0 in shared memory
             const uint64_t top = s_prefix;
-            for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
-                const uint64_t key = keys[j];
-                if (key != 0 && (key & mask) == top) cand[atomicAdd(&s_nc, 1)] = key;
+            for (int j0 = threadIdx.x; j0 < n_total; j0 += 4 * blockDim.x) {
+                uint64_t kk[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int j = j0 + t * blockDim.x;
+                    kk[t] = j < n_total ? keys[j] : 0ull;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (kk[t] != 0 && (kk[t] & mask) == top) cand[atomicAdd(&s_nc, 1)] = kk[t];
             }
             __syncthreads();
             const int nc = s_nc;
@@ -260,9 +275,18 @@ __global__ void __launch_bounds__(SEL_THREADS) k_outlier_select(int n_total, dou
         }
         thr = s_prefix;
     }
-    for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
-        const uint64_t key = keys[j];
-        w[j] = (key != 0 && key < thr) ? 1 : 0;
+    for (int j0 = threadIdx.x; j0 < n_total; j0 += 4 * blockDim.x) {
+        uint64_t kk[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = j0 + t * blockDim.x;
+            kk[t] = j < n_total ? keys[j] : 0ull;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = j0 + t * blockDim.x;
+            if (j < n_total) w[j] = (kk[t] != 0 && kk[t] < thr) ? 1 : 0;
+        }
     }
     if (threadIdx.x == 0) counters[CNT_ZEROED] = (uint32_t)k;
 }

@@ -20,17 +20,14 @@
 // KMAH index of the heaviest vertex; the smallest T_res wins (ties: smallest
 // triangle id).
 //
-// GB300 mapping: one warp owns 32 consecutive rays of one fan (31 tubes;
-// neighbouring warps overlap by one ray, which both trace bit-identically),
-// so a tube's four vertices are two registers and one shuffle away.  Field
-// samples come from the 128-byte cell records of rb_fields.cu, kept in
-// registers while a ray stays in its cell.  The first-arrival competition is
-// decided without waiting on memory: every covered pixel gets a fire-and-forget
-// 64-bit atomic min of (T_res key, triangle id) on the first 8 bytes of its
-// table record, and each ray's vertices are streamed out (32 B per vertex).  A
-// second kernel, k_resolve, then reads the winning triangle id of every hit
-// pixel, fetches that triangle's vertices and writes Q, L and the KMAH index
-// with the same barycentric weights the rasteriser used.
+// GB300 mapping: three kernels.  k_trace runs one thread per ray (field samples
+// from the 128-byte cell records of rb_fields.cu, kept in registers while a ray
+// stays in its cell) and streams every vertex out (32 B).  k_raster gives each
+// thread a tube and a block of 8 steps, so the rasterisation runs at full
+// occupancy; every covered pixel gets a fire-and-forget 64-bit atomic min of
+// (T_res key, triangle id) on the first 8 bytes of its table record.  k_resolve
+// then reads the winning triangle id of every hit pixel, fetches that triangle's
+// vertices and writes Q, L and the KMAH index.
 // Positions, the direction and the traveltime residual T - |x - x_t|/c_ref
 // are float pairs (compensated sums), which keeps the Green's-function phase
 // w T accurate at MHz frequencies without the (slow) FP64 pipe.
@@ -270,19 +267,6 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
     }
 }
 
-__device__ __forceinline__ Vtx shfl_down_vtx(const Vtx& v) {
-    Vtx o;
-    o.xh = __shfl_down_sync(0xffffffffu, v.xh, 1);
-    o.xl = __shfl_down_sync(0xffffffffu, v.xl, 1);
-    o.yh = __shfl_down_sync(0xffffffffu, v.yh, 1);
-    o.yl = __shfl_down_sync(0xffffffffu, v.yl, 1);
-    o.t = __shfl_down_sync(0xffffffffu, v.t, 1);
-    o.q = __shfl_down_sync(0xffffffffu, v.q, 1);
-    o.l = __shfl_down_sync(0xffffffffu, v.l, 1);
-    o.k = __shfl_down_sync(0xffffffffu, v.k, 1);
-    return o;
-}
-
 // Vertex k of ray i of fan t in the vertex stream: [fan][step][ray], 32 bytes each.
 __device__ __forceinline__ size_t vidx(const GeoDev& G, int t, int k, int i) {
     return ((size_t)t * (size_t)(G.max_steps + 1) + (size_t)k) * (size_t)G.n_rays + (size_t)i;
@@ -294,19 +278,16 @@ __device__ __forceinline__ void put_vtx(Vtx* dst, const Vtx& v) {
     d[1] = make_float4(v.t, v.q, v.l, __int_as_float(v.k));
 }
 
+// One thread per ray: RK4 from the element to the ring, the end record, and (when
+// verts is set) every vertex into the vertex stream for the rasteriser.
 __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restrict__ cells, rb_ray_end* __restrict__ ends,
-                                               rb_rays S, int write_samples, rb_cell* __restrict__ tables,
-                                               Vtx* __restrict__ verts, uint32_t* __restrict__ counters) {
-    const int lane = threadIdx.x & 31;
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (gw >= G.n_elem * G.n_wpf) return;  // uniform per warp
-    const int t = gw / G.n_wpf, wi = gw % G.n_wpf;
-    const int i = wi * 31 + lane;
-    const bool valid = i < G.n_rays;
-    const bool owner = valid && (lane < 31 || i == G.n_rays - 1);
-    const bool tube = (lane < 31) && (i + 1 < G.n_rays);
-    rb_cell* tab = tables ? tables + (size_t)t * G.npix : nullptr;
-    const bool put = verts && owner;
+                                               rb_rays S, int write_samples, Vtx* __restrict__ verts,
+                                               uint32_t* __restrict__ counters) {
+    const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= (long long)G.n_elem * G.n_rays) return;
+    const int t = (int)(u / G.n_rays), i = (int)(u % G.n_rays);
+    const bool valid = true, owner = true;
+    const bool put = verts != nullptr;
 
     DF xs, ys;
     elem_pos(G, t, xs, ys);
@@ -337,13 +318,10 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
         S.vkappa[sbase] = 0;
     }
     if (put) put_vtx(verts + vidx(G, t, 0, i), cur);
-    Vtx nb_cur = shfl_down_vtx(cur);
-    const uint32_t KQ = (uint32_t)(G.max_steps + 1);
     const float ds = G.ds, a2 = 0.5f * G.ds, ds6 = G.ds * (1.0f / 6.0f);
 
     for (int k = 1; k <= G.max_steps; ++k) {
-        if (!__any_sync(0xffffffffu, alive)) break;
-        const Vtx prev = cur, nb_prev = nb_cur;
+        if (!alive) break;
         if (alive) {
             float C0, S0;
             sincosf(thh, &S0, &C0);
@@ -444,11 +422,6 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                 S.vkappa[o] = kap;
             }
         }
-        nb_cur = shfl_down_vtx(cur);
-        if (tab && tube) {
-            const uint32_t base = ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u;
-            raster_quad(G, prev, cur, nb_prev, nb_cur, base, tab);
-        }
     }
 }
 
@@ -463,6 +436,39 @@ __device__ __forceinline__ Vtx get_vtx(const Vtx* __restrict__ src) {
     const float4* s = reinterpret_cast<const float4*>(src);
     const float4 a = __ldg(s), b = __ldg(s + 1);
     return Vtx{a.x, a.y, a.z, a.w, b.x, b.y, b.z, __float_as_int(b.w)};
+}
+
+// Rasteriser: thread (t, i, kb) rasterises the quads k in [KB kb + 1, KB kb + KB] of
+// tube (i, i + 1) of fan t from the vertex stream, up to the later of the two rays'
+// last vertices (beyond it both triangles are degenerate).  Consecutive threads take
+// consecutive tubes, so the vertex loads of a warp are contiguous.
+constexpr int KB = 8;
+
+__global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict__ verts,
+                                                const rb_ray_end* __restrict__ ends, rb_cell* __restrict__ tables) {
+    const int NT = G.n_rays - 1;
+    const int nkb = (G.max_steps + KB - 1) / KB;
+    const uint32_t KQ = (uint32_t)(G.max_steps + 1);
+    const long long total = (long long)G.n_elem * nkb * NT;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
+         u += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(u % NT);
+        const long long rest = u / NT;
+        const int kb = (int)(rest % nkb), t = (int)(rest / nkb);
+        const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+        const int k0 = kb * KB + 1, k1 = min(k0 + KB - 1, max(la, lb));
+        if (k0 > k1) continue;
+        rb_cell* tab = tables + (size_t)t * G.npix;
+        Vtx A0 = get_vtx(verts + vidx(G, t, min(k0 - 1, la), i));
+        Vtx B0 = get_vtx(verts + vidx(G, t, min(k0 - 1, lb), i + 1));
+        for (int k = k0; k <= k1; ++k) {
+            const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
+            const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
+            raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, tab);
+            A0 = A1;
+            B0 = B1;
+        }
+    }
 }
 
 // Completes every hit record: from the winning triangle id in the tag, its vertices
@@ -527,16 +533,18 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
         S = *samples;
         ws = 1;
     }
-    const long long warps = (long long)G.n_elem * G.n_wpf;
-    const int blocks = (int)((warps * 32 + 127) / 128);
     Vtx* V = tables ? (Vtx*)verts : nullptr;
     if (tables && !V) return cudaErrorInvalidValue;
-    k_trace<<<blocks, 128, 0, s>>>(G, cells, ends, S, ws, tables, V, counters);
+    const long long rays = (long long)G.n_elem * G.n_rays;
+    k_trace<<<(int)((rays + 127) / 128), 128, 0, s>>>(G, cells, ends, S, ws, V, counters);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !tables) return e;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         nsm = 148;
+    k_raster<<<nsm * 16, 256, 0, s>>>(G, V, ends, tables);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_resolve<<<nsm * 8, 256, 0, s>>>(G, V, ends, tables, dist);
     return cudaGetLastError();
 }
