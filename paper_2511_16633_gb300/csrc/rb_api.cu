@@ -33,6 +33,8 @@ GeoDev make_geo(const rb_geometry* g, const float4* elem_xy) {
     G.n_elem = g->n_elem;
     G.nx = g->nx;
     G.ny = g->ny;
+    G.fxmax = (float)(g->nx - 1);
+    G.fymax = (float)(g->ny - 1);
     G.n_rays = g->n_rays;
     G.max_steps = g->max_steps;
     G.npix = g->nx * g->ny;
@@ -47,6 +49,7 @@ GeoDev make_geo(const rb_geometry* g, const float4* elem_xy) {
     G.R = (float)g->ring_radius;
     G.R2 = (float)(g->ring_radius * g->ring_radius);
     G.inv_cref = (float)(1.0 / g->c_ref);
+    G.inv_cref_lo = (float)(1.0 / g->c_ref - (double)G.inv_cref);
     G.c_ref = (float)g->c_ref;
     G.j_floor = (float)(0.25 * g->h);
     G.R_d = g->ring_radius;
@@ -72,6 +75,7 @@ FreqC make_freq(const rb_geometry* g, double f) {
     const double w = 2.0 * M_PI * f;
     F.f_d = f;
     F.f_hi = (float)f;
+    F.f_lo = (float)(f - (double)F.f_hi);
     const DF kf = df_from_double(f / g->c_ref);
     F.kf_hi = kf.hi;
     F.kf_lo = kf.lo;
@@ -151,10 +155,11 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->part = o; o = align256(o + (size_t)(RB_MAX_FREQ + 2) * 256 * 8);
     L->fwd = o; o = align256(o + (size_t)rb_fwd_chunks_for((int)npix) * ne * ne * 8);
     L->tcimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_b_images_bytes(g->n_elem) : 0));
-    L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * 8 : 0));
+    // exact G per persistent CTA, then its |G|^2 A slices (bf16 hi and lo)
+    L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * (8 + 4) : 0));
     L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
     L->gimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_gimage_elems(g->n_elem, (int)npix) * 2 : 0));
-    L->dist = o; o = align256(o + (tcp ? ne * npix * 8 : 0));
+    L->srec = o; o = align256(o + (tcp ? ne * npix * 16 : 0));
     L->total = o;
     return o;
 }
@@ -197,7 +202,7 @@ rb_status rb_trace_rays(const rb_geometry* geom, const float* c, const float* al
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, nullptr, nullptr, cnt, s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, nullptr, nullptr, nullptr, cnt, s));
     return RB_OK;
 }
 
@@ -222,7 +227,7 @@ rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* al
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
     RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
     RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, tables,
-                       W.at<void>(W.L.verts), nullptr, cnt, s));
+                       W.at<void>(W.L.verts), nullptr, nullptr, cnt, s));
     if (g_out) RB_CU(launch_green_out(G, tables, c, F, (float2*)g_out, s));
     return RB_OK;
 }
@@ -292,9 +297,9 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
     if (prec == RB_PREC_BF16X3) {
         RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
         RB_CU(launch_prep_b(G.n_elem, (const float2*)resid, w, W.at<void>(W.L.tcimg), s));
-        RB_CU(launch_dist(G, W.at<float2>(W.L.dist), s));
-        RB_CU(launch_adjoint_tc(G, tables, W.at<float2>(W.L.dist), c, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr),
-                                tc_ctas(), (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, nullptr, s));
+        RB_CU(launch_srec(G, tables, c, W.at<float4>(W.L.srec), s));
+        RB_CU(launch_adjoint_tc(G, W.at<float4>(W.L.srec), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
+                                (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, nullptr, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c, F, (const float2*)resid, w, (float2*)g_out, hdiag_out, nullptr,
                                   nullptr, nullptr, s));
@@ -348,8 +353,8 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_FIELDS, 1));
     RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
     RB_CU(mark(RB_STAGE_TRACE_GRID, 0));
-    float2* dist = prec == RB_PREC_BF16X3 ? W.at<float2>(W.L.dist) : nullptr;
-    RB_CU(launch_trace(G, cells, ends, nullptr, tables, W.at<void>(W.L.verts), dist, cnt, s));
+    float4* srec = prec == RB_PREC_BF16X3 ? W.at<float4>(W.L.srec) : nullptr;
+    RB_CU(launch_trace(G, cells, ends, nullptr, tables, W.at<void>(W.L.verts), c_inout, srec, cnt, s));
     RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
     RB_CU(mark(RB_STAGE_LINK, 0));
     RB_CU(launch_link(G, c_inout, ends, F, R, linked, s));
@@ -361,8 +366,8 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
         const size_t img = tc_b_images_bytes(G.n_elem);
         for (int w = 0; w < n_freq; ++w)
             RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
-        RB_CU(launch_adjoint_tc(G, tables, dist, c_inout, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr),
-                                tc_ctas(), nullptr, nullptr, gsum, hsum, cnt,
+        RB_CU(launch_adjoint_tc(G, srec, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(), nullptr,
+                                nullptr, gsum, hsum, cnt,
                                 params->step_mode == RB_STEP_EXACT ? W.at<void>(W.L.gimg) : nullptr, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));

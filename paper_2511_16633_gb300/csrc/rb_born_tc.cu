@@ -64,13 +64,12 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
 struct TcArgs {
     GeoDev G;
     FreqSet F;
-    const rb_cell* tables;
-    const float2* dist;        // [n_elem][npix] |x - x_t| as float pairs
-    const float* c;
+    const float4* srec;        // [n_elem][npix] synthesis records
     const __nv_bfloat16* bu;   // [n_freq][image]
     const __nv_bfloat16* bw;   // [n_freq][image]
     size_t bu_stride, bw_stride;  // bf16 elements per frequency
     float2* gscr;              // [gridDim.x][n][TP] exact G per CTA
+    __nv_bfloat16* vimg;       // [gridDim.x][n / 16][hi|lo][TP x 16] |G|^2 A slices of the Hessian contraction
     float2* g_out;             // [n_freq][npix] or null
     float* h_out;              // [n_freq][npix] or null
     float* gsum;               // [npix] or null (sum over w of Re g)
@@ -140,15 +139,17 @@ __global__ void k_gimage(GeoDev G, const rb_cell* __restrict__ tables, const flo
     }
 }
 
-// |x - x_t| as a float pair for every element and pixel (geometry only).
-__global__ void k_dist(GeoDev G, float2* __restrict__ dist) {
+// Synthesis records of every element and pixel from the tables.
+__global__ void k_srec(GeoDev G, const rb_cell* __restrict__ tables, const float* __restrict__ c,
+                       float4* __restrict__ srec) {
     const long long total = (long long)G.n_elem * G.npix;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(u / G.npix), pix = (int)(u % G.npix);
+        const rb_cell rec = tables[u];
         DF ex, ey;
         elem_pos(G, r, ex, ey);
-        const DF d = pixel_elem_dist(G, pix % G.nx, pix / G.nx, ex, ey);
-        dist[u] = make_float2(d.hi, d.lo);
+        srec[u] = synth_record(rec, __ldg(c + pix), pixel_elem_dist(G, pix % G.nx, pix / G.nx, ex, ey), G.inv_cref,
+                               G.inv_cref_lo, G.j_floor);
     }
 }
 
@@ -159,17 +160,20 @@ namespace {
 // ---------------------------------------------------------------------------
 // Adjoint kernel: warp-specialised, NST-stage pipeline of K = 16 slices.
 //   warps 0..7  producers: pixel p = tid % 128 (TMEM lane), half h = tid / 128;
-//               they synthesise the A slices, write the forward images and run
-//               the epilogues (TMEM -> registers);
+//               they synthesise the U slices from the synthesis records, write
+//               the forward images and the |G|^2 slices of V, and run the
+//               epilogues (TMEM -> registers);
 //   warp 8      MMA issuer (lane 0): waits for a stage's A and B, issues its MMAs
 //               and commits their completion; it never waits on a commit except
 //               at the start of an accumulation phase;
-//   warp 9      B loader (lane 0): bulk-copies B slices into stages as soon as the
-//               MMAs that read the stage's previous contents are done.
+//   warp 9      B loader (lane 0): bulk-copies B slices (and, for V, the |G|^2 A
+//               slices) into stages as soon as the MMAs that read the stage's
+//               previous contents are done.
 // Per (tile, frequency) the slice sequence is U (2n / 16 slices) then V (n / 16).
 // Barriers: full_a[s] (8 producer-warp arrivals), full_b[s] (bulk-copy bytes),
 // empty[s] (MMAs that read stage s done), acc_full (last MMA of a phase done),
-// acc_empty (8 producer-warp arrivals: the epilogue has read the accumulator).
+// acc_empty (8 producer-warp arrivals: the epilogue has read the accumulator),
+// vready (8 producer-warp arrivals: the |G|^2 slices of this tile are written).
 // Every wait is bounded; a timeout raises a shared flag that ends all loops.
 // ---------------------------------------------------------------------------
 constexpr int NPROD = 256;                   // producer threads
@@ -190,20 +194,12 @@ __device__ __forceinline__ void store_row16(unsigned char* a_hi, unsigned char* 
     *(uint4*)(a_lo + off) = make_uint4(wlo[0], wlo[1], wlo[2], wlo[3]);
 }
 
-// Table records and element distances of the four elements r0 + 4h + j (j < 4) at
-// this thread's pixel.
-__device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, int px, bool valid, rb_cell (&rec)[4],
-                                          float2 (&dd)[4]) {
+// Synthesis records of the four elements r0 + 4h + j (j < 4) at this thread's pixel.
+__device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, int px, bool valid, float4 (&sr)[4]) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int r = r0 + 4 * (int)h + j;
-        if (valid) {
-            rec[j] = A.tables[(size_t)r * A.G.npix + px];
-            dd[j] = __ldg(A.dist + (size_t)r * A.G.npix + px);
-        } else {
-            rec[j].tkey = RB_HOLE;
-            dd[j] = make_float2(0.f, 0.f);
-        }
+        sr[j] = valid ? __ldg(A.srec + (size_t)r * A.G.npix + px) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -214,15 +210,14 @@ __device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, i
 // (32 x 9 words) so that each lane stores one 16-byte row of 8 pixels, hi and lo;
 // chunk is the first of the warp's two 16-pixel image chunks.
 __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h,
-                                        const rb_cell (&rec)[4], const float2 (&dd)[4], float c_px, float2* gs,
-                                        unsigned char* a_hi, unsigned char* a_lo, __nv_bfloat16* img, int chunk,
-                                        uint32_t* sc) {
+                                        const float4 (&sr)[4], float2* gs, unsigned char* a_hi, unsigned char* a_lo,
+                                        __nv_bfloat16* img, int chunk, uint32_t* sc, __nv_bfloat16* vimg) {
     uint32_t whi[4], wlo[4], iw[8];
+    __nv_bfloat16 vh[4], vl[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int r = r0 + 4 * (int)h + j;
-        float2 g = make_float2(0.f, 0.f);
-        if (rec[j].tkey != RB_HOLE) g = green_eval(rec[j], c_px, DF{dd[j].x, dd[j].y}, fc, A.G.j_floor);
+        const float2 g = green_srec(sr[j], fc);
         gs[(size_t)r * TP + p] = g;
         __nv_bfloat16 h0, l0, h1, l1;
         tc::split_bf16(g.x, h0, l0);
@@ -231,8 +226,16 @@ __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0
         wlo[j] = pack2(l0, l1);
         iw[2 * j] = pack2(h0, l0);
         iw[2 * j + 1] = pack2(h1, l1) ^ 0x80008000u;   // split of +Im = -(split of -Im)
+        tc::split_bf16(g.x * g.x + g.y * g.y, vh[j], vl[j]);
     }
     store_row16(a_hi, a_lo, p, h, whi, wlo);
+    {
+        // |G|^2 of elements r0 + 4h + j: V slice r0 / 16, K positions (r0 % 16) + 4h + j
+        __nv_bfloat16* vs = vimg + (size_t)(r0 >> 4) * (2 * TP * 16);
+        const uint32_t off = tc::tile16_offset(p, (uint32_t)(r0 & 15)) / 2 + 4u * h;
+        *(uint2*)(vs + off) = make_uint2(pack2(vh[0], vh[1]), pack2(vh[2], vh[3]));
+        *(uint2*)(vs + TP * 16 + off) = make_uint2(pack2(vl[0], vl[1]), pack2(vl[2], vl[3]));
+    }
     if (img) {
         const int lane = (int)(p & 31u);
 #pragma unroll
@@ -255,26 +258,9 @@ __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0
     }
 }
 
-// V slice (16 elements, K = 16): |G_r(p)|^2 for r = r0 + 8h + j from the exact values.
-__device__ __forceinline__ void synth_v(int r0, uint32_t p, uint32_t h, const float2* gs, unsigned char* a_hi,
-                                        unsigned char* a_lo) {
-    uint32_t whi[4], wlo[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int r = r0 + 8 * (int)h + 2 * j;
-        const float2 g0 = gs[(size_t)r * TP + p], g1 = gs[(size_t)(r + 1) * TP + p];
-        __nv_bfloat16 h0, l0, h1, l1;
-        tc::split_bf16(g0.x * g0.x + g0.y * g0.y, h0, l0);
-        tc::split_bf16(g1.x * g1.x + g1.y * g1.y, h1, l1);
-        whi[j] = pack2(h0, h1);
-        wlo[j] = pack2(l0, l1);
-    }
-    store_row16(a_hi, a_lo, p, h, whi, wlo);
-}
-
 __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full, s_acc_empty;
+    __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full, s_acc_empty, s_vready;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_err;
     __shared__ float s_red[3][TP];
@@ -291,6 +277,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
         }
         tc::mbar_init(tc::smem_u32(&s_acc_full), 1);
         tc::mbar_init(tc::smem_u32(&s_acc_empty), NPROD / 32);
+        tc::mbar_init(tc::smem_u32(&s_vready), NPROD / 32);
         s_err = 0;
     }
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), A.tmem_cols);
@@ -298,6 +285,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
+    __nv_bfloat16* vimg = A.vimg + (size_t)blockIdx.x * (size_t)(n / 16) * (2 * TP * 16);
     const int my_tiles = (int)blockIdx.x < A.n_tiles ? (A.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const long long total = (long long)my_tiles * A.F.n * per;   // slices of this CTA
     const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 16;  // bf16 per hi (or lo) / W image slice
@@ -307,6 +295,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
         // ------------------------------ B loader ------------------------------
         if (lane == 0) {
             long long ql = 0;
+            uint32_t vrp = 0;
             bool err = false;
             for (; ql < total; ++ql) {
                 const int s = (int)(ql % NST);
@@ -316,16 +305,31 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 }
                 if (s_err) break;
                 const int fw = (int)((ql / per) % A.F.n), j = (int)(ql % per);
-                const void* src;
-                uint32_t bytes;
                 if (j < nU) {
-                    src = A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u;
-                    bytes = (uint32_t)(n2 * 64);
+                    tc::bulk_load(tc::smem_u32(stage(s) + ST_B), A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u,
+                                  (uint32_t)(n2 * 64), tc::smem_u32(&s_full_b[s]));
                 } else {
-                    src = A.bw + (size_t)fw * A.bw_stride + (size_t)(j - nU) * img_w;
-                    bytes = (uint32_t)(n * 32);
+                    if (j == nU) {
+                        // this (tile, frequency)'s |G|^2 slices are written by the producers
+                        if (!tc::mbar_wait(tc::smem_u32(&s_vready), vrp & 1u, kMaxTries)) {
+                            err = true;
+                            break;
+                        }
+                        ++vrp;
+                    }
+                    const uint32_t mb = tc::smem_u32(&s_full_b[s]);
+                    const uint32_t wbytes = (uint32_t)(n * 32), abytes = 2u * TP * 16 * 2;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(wbytes + abytes)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc::smem_u32(stage(s) + ST_B)),
+                                 "l"(A.bw + (size_t)fw * A.bw_stride + (size_t)(j - nU) * img_w), "r"(wbytes), "r"(mb)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc::smem_u32(stage(s))), "l"(vimg + (size_t)(j - nU) * (2 * TP * 16)), "r"(abytes),
+                                 "r"(mb)
+                                 : "memory");
                 }
-                tc::bulk_load(tc::smem_u32(stage(s) + ST_B), src, bytes, tc::smem_u32(&s_full_b[s]));
             }
             if (err || s_err) {
                 s_err = 1;
@@ -353,6 +357,8 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     if (!tc::mbar_wait(tc::smem_u32(&s_acc_empty), accp & 1u, kMaxTries)) { err = true; break; }
                     ++accp;
                 }
+                // U slices: A from the producers; V slices: A and B both by bulk copy (the
+                // producers' arrival then only marks the stage's turn)
                 if (!tc::mbar_wait(tc::smem_u32(&s_full_a[s]), ph, kMaxTries)) { err = true; break; }
                 if (!tc::mbar_wait(tc::smem_u32(&s_full_b[s]), ph, kMaxTries)) { err = true; break; }
                 if (s_err) { err = true; break; }
@@ -422,29 +428,26 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
         for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
             const int px = tile * TP + (int)p;
             const bool valid = px < G.npix;
-            const float c_px = valid ? __ldg(A.c + px) : 0.f;
             float acc_g = 0.f, acc_h = 0.f;
             for (int fw = 0; fw < A.F.n; ++fw) {
                 const FreqC fc = A.F.f[fw];
                 // ---- U slices; table records fetched one slice ahead ----
                 __nv_bfloat16* img = A.gimg ? A.gimg + (size_t)fw * A.gimg_stride : nullptr;
-                rb_cell nxt[4];
-                float2 nxd[4];
-                load_recs(A, 0, h, px, valid, nxt, nxd);
+                float4 nxt[4];
+                load_recs(A, 0, h, px, valid, nxt);
                 for (int j = 0; j < nU; ++j) {
                     slice([&](unsigned char* ahi, unsigned char* alo) {
-                        rb_cell cur[4];
-                        float2 cud[4];
+                        float4 cur[4];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            cur[k] = nxt[k];
-                            cud[k] = nxd[k];
-                        }
-                        if (j + 1 < nU) load_recs(A, (j + 1) * 8, h, px, valid, nxt, nxd);
-                        synth_u(A, fc, j * 8, p, h, cur, cud, c_px, gs, ahi, alo, img, tile * 8 + (warp & 3) * 2,
-                                s_tr[warp]);
+                        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+                        if (j + 1 < nU) load_recs(A, (j + 1) * 8, h, px, valid, nxt);
+                        synth_u(A, fc, j * 8, p, h, cur, gs, ahi, alo, img, tile * 8 + (warp & 3) * 2, s_tr[warp], vimg);
                     });
                 }
+                // the |G|^2 slices (read next by the bulk copies of the B loader) are complete
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __syncwarp();
+                if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_vready));
                 // gs (exact G of the tile) is complete
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
@@ -478,9 +481,9 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
                     acc_g += gr;
                 }
-                // ---- V slices ----
-                for (int j = 0; j < nV; ++j)
-                    slice([&](unsigned char* ahi, unsigned char* alo) { synth_v(j * 16, p, h, gs, ahi, alo); });
+                // ---- V slices: A and B come by bulk copy; the producers only pass the stage
+                // barriers, which keeps every stage's full_a phases in step with its uses ----
+                for (int j = 0; j < nV; ++j) slice([&](unsigned char*, unsigned char*) {});
                 // ---- V epilogue ----
                 acc_wait();
                 float hh = 0.f;
@@ -520,11 +523,11 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
 
 bool tc_adjoint_supported(int n_elem) { return n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0; }
 
-cudaError_t launch_dist(const GeoDev& G, float2* dist, cudaStream_t s) {
+cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s) {
     const long long total = (long long)G.n_elem * G.npix;
     long long blocks = (total + 255) / 256;
     if (blocks > 8192) blocks = 8192;
-    k_dist<<<(int)blocks, 256, 0, s>>>(G, dist);
+    k_srec<<<(int)blocks, 256, 0, s>>>(G, tables, c, srec);
     return cudaGetLastError();
 }
 
@@ -540,22 +543,21 @@ cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float2* dist, const float* c,
-                              const FreqSet& F, const void* images, float2* gscr, int n_ctas, float2* g_out,
-                              float* h_out, float* gsum, float* hsum, uint32_t* counters, void* gimg, cudaStream_t s) {
+cudaError_t launch_adjoint_tc(const GeoDev& G, const float4* srec, const FreqSet& F, const void* images, float2* gscr,
+                              int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
+                              void* gimg, cudaStream_t s) {
     const int n = G.n_elem;
-    if (!tc_adjoint_supported(n) || !dist) return cudaErrorInvalidValue;
+    if (!tc_adjoint_supported(n) || !srec) return cudaErrorInvalidValue;
     TcArgs A;
     A.G = G;
     A.F = F;
-    A.tables = tables;
-    A.dist = dist;
-    A.c = c;
+    A.srec = srec;
     A.bu = (const __nv_bfloat16*)images;
     A.bu_stride = tc_b_images_bytes(n) / 2;
     A.bw = A.bu + (size_t)(2 * n) * (2 * n) * 2;
     A.bw_stride = A.bu_stride;
     A.gscr = gscr;
+    A.vimg = (__nv_bfloat16*)(gscr + (size_t)RB_TC_MAX_CTAS * n * TP);   // after the exact-G scratch
     A.g_out = g_out;
     A.h_out = h_out;
     A.gsum = gsum;

@@ -10,10 +10,12 @@
 // neighbours.  Each grid is sampled by bilinear interpolation.
 //
 // Layout: one 128-byte record per grid cell (i0, j0), i0 < nx-1, j0 < ny-1,
-// holding the four corner values (i0,j0), (i0+1,j0), (i0,j0+1), (i0+1,j0+1)
-// of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 as seven float4 (+1 pad).  A ray
-// lane that enters a cell loads one aligned 128-byte line and keeps it in
-// registers until it leaves the cell.
+// holding for each of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 the coefficients
+// (a, b, c, d) of its bilinear interpolant a + b u + c v + d u v over the cell
+// (u, v in [0, 1]), from the corner values q00 = (i0, j0), q10, q01, q11:
+// a = q00, b = q10 - q00, c = q01 - q00, d = q11 - q10 - q01 + q00; seven
+// float4 (+1 pad).  A ray that enters a cell loads one aligned 128-byte line and
+// keeps it in registers until it leaves the cell.
 #include "rb_internal.cuh"
 
 __global__ void k_elem_positions(GeoDev G, float4* xy) {
@@ -65,13 +67,16 @@ __global__ void k_fields(GeoDev G, const float* __restrict__ c, const float* __r
         a[k] = __ldg(a0 + (size_t)cj[k] * G.nx + ci[k]);
     }
     float4* o = cells + (size_t)cell * 8;
-    o[0] = make_float4(q[0].c, q[1].c, q[2].c, q[3].c);
-    o[1] = make_float4(q[0].cx, q[1].cx, q[2].cx, q[3].cx);
-    o[2] = make_float4(q[0].cy, q[1].cy, q[2].cy, q[3].cy);
-    o[3] = make_float4(q[0].cxx, q[1].cxx, q[2].cxx, q[3].cxx);
-    o[4] = make_float4(q[0].cxy, q[1].cxy, q[2].cxy, q[3].cxy);
-    o[5] = make_float4(q[0].cyy, q[1].cyy, q[2].cyy, q[3].cyy);
-    o[6] = make_float4(a[0], a[1], a[2], a[3]);
+    auto coef = [](float q00, float q10, float q01, float q11) {
+        return make_float4(q00, q10 - q00, q01 - q00, (q11 - q10) - (q01 - q00));
+    };
+    o[0] = coef(q[0].c, q[1].c, q[2].c, q[3].c);
+    o[1] = coef(q[0].cx, q[1].cx, q[2].cx, q[3].cx);
+    o[2] = coef(q[0].cy, q[1].cy, q[2].cy, q[3].cy);
+    o[3] = coef(q[0].cxx, q[1].cxx, q[2].cxx, q[3].cxx);
+    o[4] = coef(q[0].cxy, q[1].cxy, q[2].cxy, q[3].cxy);
+    o[5] = coef(q[0].cyy, q[1].cyy, q[2].cyy, q[3].cyy);
+    o[6] = coef(a[0], a[1], a[2], a[3]);
     o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 

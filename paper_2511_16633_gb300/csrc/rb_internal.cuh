@@ -16,9 +16,11 @@ struct GeoDev {
     int n_elem, nx, ny, n_rays, max_steps;
     int npix;
     float h, inv_h, cxg, cyg;   // cxg = (nx - 1) / 2
+    float fxmax, fymax;         // nx - 1, ny - 1 as floats
     float h_hi, h_lo;           // h as a float pair
     float ds, R, R2;
     float inv_cref, c_ref;
+    float inv_cref_lo;          // 1 / c_ref - inv_cref
     float j_floor;              // h / 4
     double R_d, ds_d, c_ref_d, h_d;
     long long r2max;            // support test on (2ix-(nx-1))^2 + (2iy-(ny-1))^2
@@ -28,7 +30,7 @@ struct GeoDev {
 // Per-frequency constants of the Green's function (host-computed in double).
 struct FreqC {
     double f_d;           // f [Hz]
-    float f_hi;           // f as a float
+    float f_hi, f_lo;     // f as a float pair
     float kf_hi, kf_lo;   // f / c_ref as a float pair  [cycles per metre]
     float w_isqrt;        // 1 / sqrt(w)
     float a_abs;          // K_a f_MHz^y: amplitude decay per unit alpha0 integral
@@ -140,6 +142,43 @@ __device__ __forceinline__ float2 green_eval(const rb_cell& rec, float c_px, DF 
     return make_float2(amp * co, amp * s);
 }
 
+// Synthesis record of one gridded entry (element r, pixel x): everything of the
+// Green's function that does not depend on the frequency, in 16 bytes:
+//   x, y = T = |x - x_r| / c_ref + T_res as a float pair [s],
+//   z    = L (>= 0), its sign bit carrying bit 0 of kappa mod 4,
+//   w    = A0 = sqrt(c(x) / (8 pi J)), its sign bit carrying bit 1 of kappa mod 4.
+// A hole is all zeros (A0 = 0).
+__device__ __forceinline__ float4 synth_record(const rb_cell& rec, float c_px, DF dist, float inv_cref,
+                                               float inv_cref_lo, float j_floor) {
+    if (rec.tkey == RB_HOLE) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const DF T = df_add(df_mul(dist, DF{inv_cref, inv_cref_lo}), DF{key2f(rec.tkey), 0.f});
+    const uint32_t kappa = rec.tag & 3u;
+    const float J = fmaxf(fabsf(rec.q), j_floor);
+    const float A0 = sqrtf(c_px) * rsqrtf((8.0f * RB_PI_F) * J);
+    const float L = __uint_as_float(__float_as_uint(fabsf(rec.l)) | ((kappa & 1u) << 31));
+    const float Aw = __uint_as_float(__float_as_uint(A0) | ((kappa >> 1) << 31));
+    return make_float4(T.hi, T.lo, L, Aw);
+}
+
+// The Green's function of Eqs. 4-5 at one frequency from a synthesis record:
+//   G = A0 w^-1/2 exp(-a_abs L) exp(i 2 pi [f T + disp L + 1/8]) (-i)^kappa.
+__device__ __forceinline__ float2 green_srec(float4 sr, const FreqC& F) {
+    const uint32_t bz = __float_as_uint(sr.z), bw = __float_as_uint(sr.w);
+    const float L = __uint_as_float(bz & 0x7fffffffu), A0 = __uint_as_float(bw & 0x7fffffffu);
+    const DF P = df_mul(DF{F.f_hi, F.f_lo}, DF{sr.x, sr.y});
+    float cyc = __fsub_rn(P.hi, rintf(P.hi)) + P.lo + fmaf(F.disp_cyc, L, 0.125f);
+    cyc -= rintf(cyc);
+    float s, c;
+    __sincosf((2.0f * RB_PI_F) * cyc, &s, &c);
+    const float amp = A0 * F.w_isqrt * __expf(-F.a_abs * L);
+    float re = (bz >> 31) ? s : c, im = (bz >> 31) ? -c : s;   // kappa bit 0: times -i
+    if (bw >> 31) {                                              // kappa bit 1: times -1
+        re = -re;
+        im = -im;
+    }
+    return make_float2(amp * re, amp * im);
+}
+
 // Element t's position as float pairs.
 __device__ __forceinline__ void elem_pos(const GeoDev& G, int t, DF& ex, DF& ey) {
     const float4 e = G.elem_xy[t];
@@ -180,7 +219,7 @@ struct WsLayout {
     size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
     size_t tcfwd;      // tensor-core path: partial D blocks of the forward
     size_t gimg;       // tensor-core path: G operand images of the forward, [n_freq][...] bf16
-    size_t dist;       // tensor-core path: |x - x_t| as float pairs, [n_elem][npix] float2
+    size_t srec;       // tensor-core path: synthesis records, [n_elem][npix] float4
     size_t total;
 };
 
@@ -200,7 +239,8 @@ enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_
 cudaError_t launch_elem_positions(const GeoDev& G, float4* elem_xy, cudaStream_t s);
 cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s);
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         rb_cell* tables, void* verts, float2* dist, uint32_t* counters, cudaStream_t s);
+                         rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
+                         cudaStream_t s);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);
@@ -228,10 +268,10 @@ cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c
 cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F, const float* m, float* partial,
                               int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
                               cudaStream_t s);
-cudaError_t launch_adjoint_tc(const GeoDev& G, const rb_cell* tables, const float2* dist, const float* c,
-                              const FreqSet& F, const void* images, float2* gscr, int n_ctas, float2* g_out,
-                              float* h_out, float* gsum, float* hsum, uint32_t* counters, void* gimg, cudaStream_t s);
-cudaError_t launch_dist(const GeoDev& G, float2* dist, cudaStream_t s);
+cudaError_t launch_adjoint_tc(const GeoDev& G, const float4* srec, const FreqSet& F, const void* images, float2* gscr,
+                              int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
+                              void* gimg, cudaStream_t s);
+cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);
 cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir,

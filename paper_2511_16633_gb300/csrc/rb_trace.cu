@@ -36,7 +36,7 @@
 namespace {
 
 struct Cache {
-    int id;
+    float fi, fj;   // cell indices of the cached record (as floats; -1 = none)
     float4 c, cx, cy, cxx, cxy, cyy, a0;
 };
 
@@ -44,15 +44,18 @@ struct Deriv { float x, y, th, t, q, p, l; };
 
 struct Vtx { float xh, xl, yh, yl, t, q, l; int k; };
 
+// Bilinear samples of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 at (px, py).  Each cell
+// record holds per field the coefficients (a, b, c, d) of a + b u + c v + d u v over
+// the cell's unit square; the cell indices stay floats (floorf), and the record is
+// reloaded only when the ray changes cell.
 __device__ __forceinline__ void sample(const GeoDev& G, const float4* __restrict__ cells, Cache& cc, float px, float py,
                                        float f[7]) {
-    float u = fminf(fmaxf(fmaf(px, G.inv_h, G.cxg), 0.f), (float)(G.nx - 1));
-    float v = fminf(fmaxf(fmaf(py, G.inv_h, G.cyg), 0.f), (float)(G.ny - 1));
-    const int i0 = min((int)u, G.nx - 2), j0 = min((int)v, G.ny - 2);
-    const float fu = u - (float)i0, fv = v - (float)j0;
-    const int id = j0 * (G.nx - 1) + i0;
-    if (id != cc.id) {
-        const float4* p = cells + (size_t)id * 8;
+    const float u = fminf(fmaxf(fmaf(px, G.inv_h, G.cxg), 0.f), G.fxmax);
+    const float v = fminf(fmaxf(fmaf(py, G.inv_h, G.cyg), 0.f), G.fymax);
+    const float fi = fminf(floorf(u), G.fxmax - 1.f), fj = fminf(floorf(v), G.fymax - 1.f);
+    const float fu = u - fi, fv = v - fj;
+    if (fi != cc.fi || fj != cc.fj) {
+        const float4* p = cells + ((size_t)(int)fj * (size_t)(G.nx - 1) + (size_t)(int)fi) * 8;
         cc.c = __ldg(p + 0);
         cc.cx = __ldg(p + 1);
         cc.cy = __ldg(p + 2);
@@ -60,10 +63,11 @@ __device__ __forceinline__ void sample(const GeoDev& G, const float4* __restrict
         cc.cxy = __ldg(p + 4);
         cc.cyy = __ldg(p + 5);
         cc.a0 = __ldg(p + 6);
-        cc.id = id;
+        cc.fi = fi;
+        cc.fj = fj;
     }
-    const float w00 = (1.f - fu) * (1.f - fv), w10 = fu * (1.f - fv), w01 = (1.f - fu) * fv, w11 = fu * fv;
-#define RB_BL(q) (w00 * (q).x + w10 * (q).y + w01 * (q).z + w11 * (q).w)
+    const float uv = fu * fv;
+#define RB_BL(q) fmaf((q).w, uv, fmaf((q).z, fv, fmaf((q).y, fu, (q).x)))
     f[0] = RB_BL(cc.c);
     f[1] = RB_BL(cc.cx);
     f[2] = RB_BL(cc.cy);
@@ -93,13 +97,13 @@ struct RayCtx {
 
 __device__ __forceinline__ Deriv eval_stage(const GeoDev& G, const float4* __restrict__ cells, Cache& cc,
                                             float xh, float xl, float yh, float yl, float rxh, float rxl, float ryh,
-                                            float ryl, float C0, float S0, float thh, float thl, float q, float p,
+                                            float ryl, float Ca, float Sa, float tha, float dth, float q, float p,
                                             float a, const Deriv& kp) {
     const float ox = fmaf(a, kp.x, xl), oy = fmaf(a, kp.y, yl);
     const float px = xh + ox, py = yh + oy;
     const float rx = rxh + fmaf(a, kp.x, rxl), ry = ryh + fmaf(a, kp.y, ryl);
     float cth, sth;
-    rotate(C0, S0, thh, fmaf(a, kp.th, thl), cth, sth);
+    rotate(Ca, Sa, tha, fmaf(a, kp.th, dth), cth, sth);
     const float qs = fmaf(a, kp.q, q), ps = fmaf(a, kp.p, p);
     float f[7];
     sample(G, cells, cc, px, py, f);
@@ -210,7 +214,7 @@ __device__ __forceinline__ void key_min(rb_cell* dst, uint64_t key) {
 // the pixel index: they are evaluated at the row's first pixel and then stepped
 // by their exact per-pixel increments (a few ulps of drift over a box).
 __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1,
-                                            uint32_t base, rb_cell* __restrict__ tab) {
+                                            uint32_t base, rb_cell* __restrict__ tab, const short2* __restrict__ supp) {
     const Quad Q = quad_of(A0, A1, B0, B1);
     if (!Q.t0 && !Q.t1) return;
     // tight box of pixel centres (index space), with a 1e-3 px guard
@@ -233,14 +237,8 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
     const DF X0 = df_pixel_coord(bx0, G.cxg, G.h_hi, G.h_lo);
     const float dx0 = rel(X0.hi, X0.lo, A0.xh, A0.xl);
     for (int iy = iy0; iy <= iy1; ++iy) {
-        // support disc: (2 ix - (nx - 1))^2 + (2 iy - (ny - 1))^2 <= r2max
-        const int jy = 2 * iy - (G.ny - 1);
-        const long long rem = G.r2max - (long long)jy * jy;
-        if (rem < 0) continue;
-        int sj = (int)sqrtf((float)rem);
-        while ((long long)(sj + 1) * (sj + 1) <= rem) ++sj;
-        while (sj > 0 && (long long)sj * sj > rem) --sj;
-        const int ix0 = max(bx0, (G.nx - 1 - sj + 1) >> 1), ix1 = min(bx1, (G.nx - 1 + sj) >> 1);
+        const short2 sr = supp[iy];   // support disc columns of this row
+        const int ix0 = max(bx0, (int)sr.x), ix1 = min(bx1, (int)sr.y);
         if (ix0 > ix1) continue;
         const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
         const float dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
@@ -297,11 +295,14 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     const DF thd = df_from_double(th0);
 
     Cache cc;
-    cc.id = -1;
+    cc.fi = -1.f;
+    cc.fj = -1.f;
     float f0[7];
     sample(G, cells, cc, xs.hi + xs.lo, ys.hi + ys.lo, f0);
 
     float xh = xs.hi, xl = xs.lo, yh = ys.hi, yl = ys.lo, thh = thd.hi, thl = thd.lo;
+    float tha = thh, Ca, Sa;
+    sincosf(tha, &Sa, &Ca);
     float trh = 0.f, trl = 0.f;   // T_res as a float pair (compensated sum of the RK4 increments)
     float q = 0.f, p = 1.0f / f0[0], l = 0.f;
     int kap = 0;
@@ -323,14 +324,19 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     for (int k = 1; k <= G.max_steps; ++k) {
         if (!alive) break;
         if (alive) {
-            float C0, S0;
-            sincosf(thh, &S0, &C0);
+            // direction relative to the anchor angle tha (cos / sin exact there); the
+            // anchor follows the ray whenever it has turned by more than 0.05 rad
+            if (fabsf(thh - tha) > 0.05f) {
+                tha = thh;
+                sincosf(tha, &Sa, &Ca);
+            }
+            const float dth = (thh - tha) + thl;
             const float rxh = xh - xs.hi, rxl = xl - xs.lo, ryh = yh - ys.hi, ryl = yl - ys.lo;
             const Deriv z{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const Deriv k1 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, C0, S0, thh, thl, q, p, 0.f, z);
-            const Deriv k2 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, C0, S0, thh, thl, q, p, a2, k1);
-            const Deriv k3 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, C0, S0, thh, thl, q, p, a2, k2);
-            const Deriv k4 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, C0, S0, thh, thl, q, p, ds, k3);
+            const Deriv k1 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, 0.f, z);
+            const Deriv k2 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, a2, k1);
+            const Deriv k3 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, a2, k2);
+            const Deriv k4 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, ds, k3);
             const float ix = ds6 * (k1.x + 2.f * k2.x + 2.f * k3.x + k4.x);
             const float iy = ds6 * (k1.y + 2.f * k2.y + 2.f * k3.y + k4.y);
             const float ith = ds6 * (k1.th + 2.f * k2.th + 2.f * k3.th + k4.th);
@@ -444,8 +450,24 @@ __device__ __forceinline__ Vtx get_vtx(const Vtx* __restrict__ src) {
 // consecutive tubes, so the vertex loads of a warp are contiguous.
 constexpr int KB = 8;
 
+// Columns [lo, hi] of row iy inside the support disc (2 ix - (nx - 1))^2 +
+// (2 iy - (ny - 1))^2 <= r2max, exact in integers; lo > hi for an empty row.
+__device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
+    const int jy = 2 * iy - (G.ny - 1);
+    const long long rem = G.r2max - (long long)jy * jy;
+    if (rem < 0) return make_short2(1, 0);
+    int sj = (int)sqrtf((float)rem);
+    while ((long long)(sj + 1) * (sj + 1) <= rem) ++sj;
+    while (sj > 0 && (long long)sj * sj > rem) --sj;
+    const int lo = max(0, (G.nx - 1 - sj + 1) >> 1), hi = min(G.nx - 1, (G.nx - 1 + sj) >> 1);
+    return make_short2((short)lo, (short)hi);
+}
+
 __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict__ verts,
                                                 const rb_ray_end* __restrict__ ends, rb_cell* __restrict__ tables) {
+    extern __shared__ short2 s_supp[];   // [ny]
+    for (int iy = threadIdx.x; iy < G.ny; iy += blockDim.x) s_supp[iy] = support_row(G, iy);
+    __syncthreads();
     const int NT = G.n_rays - 1;
     const int nkb = (G.max_steps + KB - 1) / KB;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
@@ -464,7 +486,7 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
         for (int k = k0; k <= k1; ++k) {
             const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
             const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
-            raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, tab);
+            raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, tab, s_supp);
             A0 = A1;
             B0 = B1;
         }
@@ -476,13 +498,16 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
 // Q, L and the KMAH index of the heaviest vertex.  Holes stay all ones.
 __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict__ verts,
                                                  const rb_ray_end* __restrict__ ends, rb_cell* __restrict__ tables,
-                                                 float2* __restrict__ dist) {
+                                                 const float* __restrict__ c, float4* __restrict__ srec) {
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
     const long long total = (long long)G.n_elem * G.npix;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
          u += (long long)gridDim.x * blockDim.x) {
         const uint2 kv = *reinterpret_cast<const uint2*>(tables + u);   // {tag, tkey}
-        if (kv.y == RB_HOLE) continue;
+        if (kv.y == RB_HOLE) {
+            if (srec) srec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         const int t = (int)(u / G.npix), pix = (int)(u % G.npix);
         const uint32_t id = kv.x >> 8;
         const int half = (int)(id & 1u);
@@ -514,11 +539,11 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
         rec.q = interp(wa, wb, wc, A0.q, Vb.q, Vc.q);
         rec.l = interp(wa, wb, wc, A0.l, Vb.l, Vc.l);
         tables[u] = rec;
-        if (dist) {
+        if (srec) {
             DF ex, ey;
             elem_pos(G, t, ex, ey);
-            const DF d = pixel_elem_dist(G, ix, iy, ex, ey);
-            dist[u] = make_float2(d.hi, d.lo);
+            srec[u] = synth_record(rec, __ldg(c + pix), pixel_elem_dist(G, ix, iy, ex, ey), G.inv_cref, G.inv_cref_lo,
+                                   G.j_floor);
         }
     }
 }
@@ -526,7 +551,8 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
 }  // namespace
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         rb_cell* tables, void* verts, float2* dist, uint32_t* counters, cudaStream_t s) {
+                         rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
+                         cudaStream_t s) {
     rb_rays S{};
     int ws = 0;
     if (samples && samples->vx) {
@@ -542,10 +568,10 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         nsm = 148;
-    k_raster<<<nsm * 16, 256, 0, s>>>(G, V, ends, tables);
+    k_raster<<<nsm * 16, 256, (size_t)G.ny * sizeof(short2), s>>>(G, V, ends, tables);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resolve<<<nsm * 8, 256, 0, s>>>(G, V, ends, tables, dist);
+    k_resolve<<<nsm * 8, 256, 0, s>>>(G, V, ends, tables, c, srec);
     return cudaGetLastError();
 }
 
