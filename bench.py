@@ -49,7 +49,7 @@ def _cores():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -60,7 +60,7 @@ class ClockSampler:
         self.path = os.path.join("/tmp", f"rb_clocks_{os.getpid()}.csv")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -95,12 +95,22 @@ class ClockSampler:
 
 
 def algorithmic_work(cfg, n_freq):
-    """Per-update algorithmic work of the stages (FLOP or bytes), documented in the design doc."""
+    """Per-update algorithmic work of the contractions (FLOP), as defined in the design doc section 6."""
     ne, npix = cfg.n_elem, cfg.nx * cfg.ny
     adj_flop = n_freq * (8.0 * ne * ne * npix + 2.0 * ne * ne * npix + 10.0 * ne * npix)
     fwd_flop = n_freq * 8.0 * ne * ne * npix
     table_bytes = ne * npix * 16.0
     return dict(adjoint_flop=adj_flop, forward_flop=fwd_flop, trace_grid_bytes=table_bytes)
+
+
+# Tensor FLOPs the BF16 x3 path issues per algorithmic FLOP: the gradient contraction
+# (8 n^2 npix per frequency) takes three bf16 products (hi.hi, hi.lo, lo.hi), the Hessian
+# contraction (2 n^2 npix) two (W is exact in bf16): (3 x 8 + 2 x 2) / (8 + 2).
+ADJ_ISSUE_RATIO = 2.8
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512
+# (ncu --metrics, 1 pass; profiles/k_adjoint_tc.md), None when not measured for the
+# kernel as built.
+ADJ_TRAFFIC_BYTES = 6037211904 + 5165807104
 
 
 def run_ours(args):
@@ -224,29 +234,36 @@ def run_ours(args):
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     bf16_peak = peaks.get("bf16_tflops_sustained", 1735.5)
 
-    def contraction_roof(stage, flop, kern):
+    def contraction_roof(stage, flop, kern, issue_ratio):
         t = st[stage] / 1e3
         ach = flop / t / 1e12
         if head == "bf16x3":
-            return {"kernel": kern, "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
-                    "frac": ach / bf16_peak, "traffic": None,
-                    "peak_source": "measured bf16 sustained (MEASURED_PEAKS.json); algorithmic FLOP, the 3-term "
-                                   "split issues 3x on the tensor pipe"}
+            peak = bf16_peak / issue_ratio
+            return {"kernel": kern, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "tensor_issued_tflops": ach * issue_ratio, "frac_of_bf16_sustained": ach * issue_ratio / bf16_peak,
+                    "peak_source": f"measured bf16 sustained (MEASURED_PEAKS.json, {bf16_peak} TFLOP/s) / "
+                                   f"{issue_ratio:.2f} bf16 tensor FLOPs issued per algorithmic FLOP (3-product split)"}
         return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak, "traffic": None,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
 
     tc = head == "bf16x3"
-    roof_adj = contraction_roof("adjoint", work["adjoint_flop"], "k_adjoint_tc" if tc else "k_adjoint_simt")
-    roof_fwd = contraction_roof("forward", work["forward_flop"], "k_forward_tc" if tc else "k_forward_simt")
-    dominant = max(("trace_grid", "adjoint", "forward"), key=lambda k: st[k])
-    if dominant == "trace_grid":
-        ach = work["trace_grid_bytes"] / (st["trace_grid"] / 1e3) / 1e9
-        roof = {"kernel": "k_trace (fused ray fans + gridding)", "bound": "hbm", "achieved": ach,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-                "traffic": args.trace_traffic, "peak_source": peak_src}
-    else:
-        roof = roof_adj if dominant == "adjoint" else roof_fwd
+    # forward: the kernels compute the column blocks on and above the block diagonal of the
+    # symmetric real-form product (for 2n = 512 and 256-wide blocks: 6 of 8 block pairs)
+    nbn = (2 * cfg.n_elem + 255) // 256
+    nb = 2 * cfg.n_elem // nbn
+    nmb = 2 * cfg.n_elem // 128
+    done = sum(nbn - (128 * i) // nb for i in range(nmb))
+    fwd_ratio = 3.0 * done / (nmb * nbn)
+    roof_adj = contraction_roof("adjoint", work["adjoint_flop"], "k_adjoint_tc" if tc else "k_adjoint_simt",
+                                ADJ_ISSUE_RATIO)
+    roof_fwd = contraction_roof("forward", work["forward_flop"], "k_forward_tc" if tc else "k_forward_simt", fwd_ratio)
+    # the dominant kernel: the adjoint contraction (one launch per update; its stage adds
+    # only the B-image preparation, under 1 % of it)
+    roof = dict(roof_adj)
+    if tc:
+        roof["traffic"] = ADJ_TRAFFIC_BYTES
     line = {
         "metric": METRIC, "value": R["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
@@ -260,7 +277,10 @@ def run_ours(args):
         "p50_ms": R["p50_ms"], "p99_ms": R["p99_ms"], "stage_ms": st, "wall_s": R["wall_s"],
         "roofline": roof, "roofline_contractions": {"adjoint": roof_adj, "forward": roof_fwd},
         "clocks": R["clocks"], "e2e": R["e2e"],
-        "gpu_launches": (15 + 3 * nf if tc else 15 + 2 * nf) * args.steps,
+        # launches per update: positions, fields, trace/raster/resolve, link/keys/select, adjoint
+        # (+ one B-image prep per frequency on the mixed path), 4 direction kernels, forward +
+        # reduce per frequency, 4 apply/norm kernels
+        "gpu_launches": (17 + 3 * nf if tc else 17 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
     if other in runs:
@@ -337,14 +357,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"],
                     help="headline precision; the other one is measured beside it unless --no-compare")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--trace-traffic", type=float, default=None,
-                    help="ncu dram bytes per k_trace launch, when measured for this build")
     ap.add_argument("--workload", default=WORKLOAD, choices=["breast512", "breast256", "tiny"],
                     help="the timed workload is breast512; smaller ones are for profiling captures")
     ap.add_argument("--cpu-fans", type=int, default=32)

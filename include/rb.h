@@ -149,7 +149,7 @@ typedef struct rb_diag {
     uint32_t unlinked;      /* masked (e, r) pairs no ray interval bracketed */
     uint32_t kept;          /* masked, linked data entries over the set */
     uint32_t zeroed;        /* of those, zeroed as outliers */
-    uint32_t pad;
+    uint32_t tc_timeouts;   /* tensor-core pipeline waits that ran out (0 unless the device misbehaves) */
 } rb_diag;                  /* 48 bytes */
 
 /* Largest n_freq per call to rb_green_grid / rb_ray_forward / rb_hf_update. */

@@ -229,7 +229,7 @@ GeoDev rb_make_geo(const rb_geometry* g, const float4* elem_xy);
 FreqC rb_make_freq(const rb_geometry* g, double f_hz);
 
 // counters (uint32 slots)
-enum { CNT_LOST = 0, CNT_HOLES = 1, CNT_UNLINKED = 2, CNT_KEPT = 3, CNT_ZEROED = 4, CNT_CAS_GIVEUP = 5, CNT_TC_TIMEOUT = 6, CNT_N = 64 };
+enum { CNT_LOST = 0, CNT_HOLES = 1, CNT_UNLINKED = 2, CNT_KEPT = 3, CNT_ZEROED = 4, CNT_TC_TIMEOUT = 6, CNT_N = 64 };
 // double scalars after the uint32 block
 enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_HMEAN = 5, DBL_N = 64 };
 

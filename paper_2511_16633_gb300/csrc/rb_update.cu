@@ -132,7 +132,7 @@ __global__ void k_finish(const double* __restrict__ dbl, const uint32_t* __restr
     d.unlinked = cnt[CNT_UNLINKED];
     d.kept = cnt[CNT_KEPT];
     d.zeroed = cnt[CNT_ZEROED];
-    d.pad = cnt[CNT_CAS_GIVEUP];
+    d.tc_timeouts = cnt[CNT_TC_TIMEOUT];
     *diag = d;
 }
 

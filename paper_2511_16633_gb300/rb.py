@@ -57,7 +57,7 @@ RAY_END_DTYPE = np.dtype([("t", "<f8"), ("t_res", "<f8"), ("x", "<f8"), ("y", "<
 CELL_DTYPE = np.dtype([("tag", "<u4"), ("tkey", "<u4"), ("q", "<f4"), ("l", "<f4")])
 DIAG_DTYPE = np.dtype([("dc_norm", "<f8"), ("alpha", "<f8"), ("eps", "<f8"), ("lost_rays", "<u4"),
                        ("holes", "<u4"), ("unlinked", "<u4"), ("kept", "<u4"), ("zeroed", "<u4"),
-                       ("cas_giveup", "<u4")])
+                       ("tc_timeouts", "<u4")])
 assert RAY_END_DTYPE.itemsize == 56 and CELL_DTYPE.itemsize == 16 and DIAG_DTYPE.itemsize == 48
 
 _lib = None

@@ -160,7 +160,7 @@ def test_breast512_update_properties(dev, big, prec):
     assert np.all(np.isfinite(dcn))
     assert np.all(dcn[~sup] == 0.0)
     assert abs(dd["dc_norm"] - np.sqrt(np.sum(dcn[sup] ** 2))) <= 1e-4 * dd["dc_norm"]
-    assert dd["lost_rays"] == 0 and dd["cas_giveup"] == 0
+    assert dd["lost_rays"] == 0 and dd["tc_timeouts"] == 0
     min_sep = math.ceil(g.n_elem / 8)
     assert dd["kept"] + 4 * dd["unlinked"] == 4 * g.n_elem * (g.n_elem - 2 * min_sep + 1)
     assert dd["zeroed"] == math.floor(0.01 * dd["kept"])

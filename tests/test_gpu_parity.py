@@ -286,7 +286,7 @@ def test_hf_update_tiny(dev, step):
     freqs = [cfg.freqs_hz[0]]
     p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, freqs, inp.noise_re, inp.noise_im)
     ref, c_new, dc, d = _update_pair(cfg, inp, inp.c_init, freqs, p_obs, dev, step=step)
-    assert d["lost_rays"] == 0 and d["cas_giveup"] == 0
+    assert d["lost_rays"] == 0 and d["tc_timeouts"] == 0
     assert d["kept"] == ref.n_kept and d["zeroed"] == ref.n_zeroed
     assert d["unlinked"] == ref.n_unlinked
     assert abs(d["alpha"] - ref.alpha) <= 1e-3 * abs(ref.alpha)
@@ -367,7 +367,7 @@ def test_hf_update_bf16x3_tiny(dev):
                     prec=rb.RB_PREC_BF16X3, dc_out=dc, diag_out=diag)
     torch.cuda.synchronize()
     d = rb.decode_diag(diag)
-    assert d["cas_giveup"] == 0
+    assert d["tc_timeouts"] == 0
     err = np.sqrt(np.mean((dc.cpu().numpy() - ref.dc) ** 2))
     assert err <= 0.05 * max(1.0, np.sqrt(np.mean(ref.dc ** 2))), err
     assert abs(d["dc_norm"] - ref.dc_norm) <= 1e-3 * ref.dc_norm
