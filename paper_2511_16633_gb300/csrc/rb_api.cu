@@ -144,6 +144,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->cells = o; o = align256(o + ncell * 128);
     L->tables = o; o = align256(o + ne * npix * sizeof(rb_cell));
     L->verts = o; o = align256(o + rb_verts_bytes(g->n_elem, g->n_rays, g->max_steps));
+    L->gkeys = o; o = align256(o + ne * npix * 8);
     L->ends = o; o = align256(o + ne * (size_t)g->n_rays * sizeof(rb_ray_end));
     L->pray = o; o = align256(o + nf * ne * ne * 8);
     L->linked = o; o = align256(o + ne * ne);
@@ -202,7 +203,8 @@ rb_status rb_trace_rays(const rb_geometry* geom, const float* c, const float* al
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, nullptr, nullptr, nullptr, cnt, s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, nullptr, nullptr, nullptr, nullptr, cnt,
+                       s));
     return RB_OK;
 }
 
@@ -225,8 +227,7 @@ rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* al
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
-    RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, tables,
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, W.at<void>(W.L.gkeys), tables,
                        W.at<void>(W.L.verts), nullptr, nullptr, cnt, s));
     if (g_out) RB_CU(launch_green_out(G, tables, c, F, (float2*)g_out, s));
     return RB_OK;
@@ -351,10 +352,11 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c_inout, alpha0, cells, s));
     RB_CU(mark(RB_STAGE_FIELDS, 1));
-    RB_CU(cudaMemsetAsync(tables, 0xff, (size_t)G.n_elem * G.npix * sizeof(rb_cell), s));
     RB_CU(mark(RB_STAGE_TRACE_GRID, 0));
+    // the mixed path reads only the synthesis records, the plain path only the tables
     float4* srec = prec == RB_PREC_BF16X3 ? W.at<float4>(W.L.srec) : nullptr;
-    RB_CU(launch_trace(G, cells, ends, nullptr, tables, W.at<void>(W.L.verts), c_inout, srec, cnt, s));
+    RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), prec == RB_PREC_BF16X3 ? nullptr : tables,
+                       W.at<void>(W.L.verts), c_inout, srec, cnt, s));
     RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
     RB_CU(mark(RB_STAGE_LINK, 0));
     RB_CU(launch_link(G, c_inout, ends, F, R, linked, s));

@@ -24,9 +24,8 @@ constexpr int RCP = RC + 1;  // padded row (conflict-free reads by the 4 element
 
 // G tile synthesis: Gs[t][p] for t < n_elem, p < AP (zero beyond npix).
 __device__ __forceinline__ void synth_tile(const GeoDev& G, const rb_cell* __restrict__ tables, const float* __restrict__ c,
-                                           const FreqC& F, int p0, float2* Gs, int count_holes, uint32_t* hole_acc) {
+                                           const FreqC& F, int p0, float2* Gs) {
     const int n = G.n_elem;
-    uint32_t holes = 0;
     for (int idx = threadIdx.x; idx < n * AP; idx += blockDim.x) {
         const int t = idx / AP, p = idx % AP;
         const int pix = p0 + p;
@@ -39,16 +38,9 @@ __device__ __forceinline__ void synth_tile(const GeoDev& G, const rb_cell* __res
                 elem_pos(G, t, ex, ey);
                 const DF dist = pixel_elem_dist(G, ix, iy, ex, ey);
                 v = green_eval(rec, __ldg(c + pix), dist, F, G.j_floor);
-            } else if (count_holes) {
-                const long long jx = 2LL * ix - (G.nx - 1), jy = 2LL * iy - (G.ny - 1);
-                if (jx * jx + jy * jy <= G.r2max) ++holes;
             }
         }
         Gs[t * AP + p] = v;
-    }
-    if (count_holes) {
-        for (int o = 16; o > 0; o >>= 1) holes += __shfl_down_sync(0xffffffffu, holes, o);
-        if ((threadIdx.x & 31) == 0 && holes) atomicAdd(hole_acc, holes);
     }
 }
 
@@ -74,7 +66,7 @@ __global__ void __launch_bounds__(AT) k_adjoint_simt(GeoDev G, const rb_cell* __
         const float2* Rw = resid + (size_t)fw * n * n;
         const uint8_t* Ww = w + (size_t)fw * n * n;
         __syncthreads();
-        synth_tile(G, tables, c, fc, p0, Gs, fw == 0 && counters != nullptr, counters + CNT_HOLES);
+        synth_tile(G, tables, c, fc, p0, Gs);
         float ur[EPT][4], ui[EPT][4], vv[EPT][4];
 #pragma unroll
         for (int i = 0; i < EPT; ++i)

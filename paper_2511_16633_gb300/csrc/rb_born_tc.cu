@@ -159,25 +159,27 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Adjoint kernel: warp-specialised, NST-stage pipeline of K = 16 slices.
-//   warps 0..7  producers: pixel p = tid % 128 (TMEM lane), half h = tid / 128;
+//   warps 0..15 producers: pixel p = tid % 128 (TMEM lane), quarter h = tid / 128;
 //               they synthesise the U slices from the synthesis records, write
 //               the forward images and the |G|^2 slices of V, and run the
 //               epilogues (TMEM -> registers);
-//   warp 8      MMA issuer (lane 0): waits for a stage's A and B, issues its MMAs
+//   warp 16     MMA issuer (lane 0): waits for a stage's A and B, issues its MMAs
 //               and commits their completion; it never waits on a commit except
 //               at the start of an accumulation phase;
-//   warp 9      B loader (lane 0): bulk-copies B slices (and, for V, the |G|^2 A
+//   warp 17     B loader (lane 0): bulk-copies B slices (and, for V, the |G|^2 A
 //               slices) into stages as soon as the MMAs that read the stage's
 //               previous contents are done.
 // Per (tile, frequency) the slice sequence is U (2n / 16 slices) then V (n / 16).
-// Barriers: full_a[s] (8 producer-warp arrivals), full_b[s] (bulk-copy bytes),
+// Barriers: full_a[s] (16 producer-warp arrivals), full_b[s] (bulk-copy bytes),
 // empty[s] (MMAs that read stage s done), acc_full (last MMA of a phase done),
-// acc_empty (8 producer-warp arrivals: the epilogue has read the accumulator),
-// vready (8 producer-warp arrivals: the |G|^2 slices of this tile are written).
+// acc_empty (16 producer-warp arrivals: the epilogue has read the accumulator),
+// vready (16 producer-warp arrivals: the |G|^2 slices of this tile are written).
 // Every wait is bounded; a timeout raises a shared flag that ends all loops.
 // ---------------------------------------------------------------------------
-constexpr int NPROD = 256;                   // producer threads
+constexpr int NPROD = 512;                   // adjoint producer threads: four per pixel row
 constexpr int NTHR_A = NPROD + 64;           // + MMA warp + B-loader warp
+constexpr int NPROD_F = 256;                 // forward producer threads: two per A row
+constexpr int NTHR_F = NPROD_F + 64;
 constexpr int NST = 5;                       // pipeline stages
 constexpr uint32_t ST_BYTES = 40u * 1024u;   // A hi (4 KB) + A lo (4 KB) + B (<= 32 KB)
 constexpr uint32_t ST_ALO = 4096u, ST_B = 8192u;
@@ -194,29 +196,30 @@ __device__ __forceinline__ void store_row16(unsigned char* a_hi, unsigned char* 
     *(uint4*)(a_lo + off) = make_uint4(wlo[0], wlo[1], wlo[2], wlo[3]);
 }
 
-// Synthesis records of the four elements r0 + 4h + j (j < 4) at this thread's pixel.
-__device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, int px, bool valid, float4 (&sr)[4]) {
+// Synthesis records of the two elements r0 + 2h + j (j < 2) at this thread's pixel.
+__device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, int px, bool valid, float4 (&sr)[2]) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int r = r0 + 4 * (int)h + j;
+    for (int j = 0; j < 2; ++j) {
+        const int r = r0 + 2 * (int)h + j;
         sr[j] = valid ? __ldg(A.srec + (size_t)r * A.G.npix + px) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-// U slice (8 elements, K' = 16): G_r(p) for r = r0 + 4h + j, exact values to gs and
-// bf16 hi / lo of (Re, -Im) to K-group h of the A slice.  With img set, the same
-// values (Re, +Im) also go to the forward operand image (see gimage_seg): the
-// 8-lane groups of the warp transpose their words through the warp's scratch sc
-// (32 x 9 words) so that each lane stores one 16-byte row of 8 pixels, hi and lo;
+// U slice (8 elements, K' = 16): thread (p, h), h < 4, takes elements r0 + 2h + j
+// (j < 2), i.e. K' positions 4h .. 4h + 3: exact G to gs, bf16 hi / lo of (Re, -Im) to
+// half of K-group h / 2 of A row p, and |G|^2 (hi / lo) to the V slice r0 / 16.  With
+// img set, the values (Re, +Im) also go to the forward operand image (see gimage_seg):
+// each 8-lane group of the warp transposes its words through the warp's scratch sc
+// (32 x 5 words) so that each lane stores one 16-byte row of 8 pixels (hi or lo);
 // chunk is the first of the warp's two 16-pixel image chunks.
 __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h,
-                                        const float4 (&sr)[4], float2* gs, unsigned char* a_hi, unsigned char* a_lo,
+                                        const float4 (&sr)[2], float2* gs, unsigned char* a_hi, unsigned char* a_lo,
                                         __nv_bfloat16* img, int chunk, uint32_t* sc, __nv_bfloat16* vimg) {
-    uint32_t whi[4], wlo[4], iw[8];
-    __nv_bfloat16 vh[4], vl[4];
+    uint32_t whi[2], wlo[2], iw[4];
+    __nv_bfloat16 vh[2], vl[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int r = r0 + 4 * (int)h + j;
+    for (int j = 0; j < 2; ++j) {
+        const int r = r0 + 2 * (int)h + j;
         const float2 g = green_srec(sr[j], fc);
         gs[(size_t)r * TP + p] = g;
         __nv_bfloat16 h0, l0, h1, l1;
@@ -228,33 +231,33 @@ __device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0
         iw[2 * j + 1] = pack2(h1, l1) ^ 0x80008000u;   // split of +Im = -(split of -Im)
         tc::split_bf16(g.x * g.x + g.y * g.y, vh[j], vl[j]);
     }
-    store_row16(a_hi, a_lo, p, h, whi, wlo);
+    const uint32_t off = tc::tile16_offset(p, 8u * (h >> 1)) + 8u * (h & 1u);
+    *(uint2*)(a_hi + off) = make_uint2(whi[0], whi[1]);
+    *(uint2*)(a_lo + off) = make_uint2(wlo[0], wlo[1]);
     {
-        // |G|^2 of elements r0 + 4h + j: V slice r0 / 16, K positions (r0 % 16) + 4h + j
         __nv_bfloat16* vs = vimg + (size_t)(r0 >> 4) * (2 * TP * 16);
-        const uint32_t off = tc::tile16_offset(p, (uint32_t)(r0 & 15)) / 2 + 4u * h;
-        *(uint2*)(vs + off) = make_uint2(pack2(vh[0], vh[1]), pack2(vh[2], vh[3]));
-        *(uint2*)(vs + TP * 16 + off) = make_uint2(pack2(vl[0], vl[1]), pack2(vl[2], vl[3]));
+        const uint32_t voff = tc::tile16_offset(p, (uint32_t)(r0 & 15) + 2u * h) / 2;
+        *(uint32_t*)(vs + voff) = pack2(vh[0], vh[1]);
+        *(uint32_t*)(vs + TP * 16 + voff) = pack2(vl[0], vl[1]);
     }
     if (img) {
         const int lane = (int)(p & 31u);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) sc[lane * 9 + m] = iw[m];
+        for (int m = 0; m < 4; ++m) sc[lane * 5 + m] = iw[m];
         __syncwarp();
-        const int g8 = lane >> 3, L = lane & 7;
+        const int g8 = lane >> 3, L = lane & 7, kp = L & 3, hl = L >> 2;
         uint32_t w[8];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) w[m] = sc[(8 * g8 + m) * 9 + L];
+        for (int m = 0; m < 8; ++m) w[m] = sc[(8 * g8 + m) * 5 + kp];
         __syncwarp();
-        const uint4 hi = make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
-                                    __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
-        const uint4 lo = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
-                                    __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
-        const int rp = 2 * (r0 + 4 * (int)h + (L >> 1)) + (L & 1);
+        const uint32_t sel = hl ? 0x7632u : 0x5410u;   // lo halves or hi halves of the 8 pixels' words
+        const uint4 row = make_uint4(__byte_perm(w[0], w[1], sel), __byte_perm(w[2], w[3], sel),
+                                     __byte_perm(w[4], w[5], sel), __byte_perm(w[6], w[7], sel));
+        const int rp = 2 * (r0 + 2 * (int)h + (kp >> 1)) + (kp & 1);
         const size_t cimg = (size_t)2 * A.G.n_elem * 16;
-        __nv_bfloat16* base = img + (size_t)(chunk + (g8 >> 1)) * 2 * cimg + tc::tile16_offset((uint32_t)rp, 8u * (g8 & 1)) / 2;
-        *(uint4*)base = hi;
-        *(uint4*)(base + cimg) = lo;
+        __nv_bfloat16* base = img + (size_t)(chunk + (g8 >> 1)) * 2 * cimg + (hl ? cimg : 0) +
+                              tc::tile16_offset((uint32_t)rp, 8u * (g8 & 1)) / 2;
+        *(uint4*)base = row;
     }
 }
 
@@ -263,8 +266,8 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full, s_acc_empty, s_vready;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_err;
-    __shared__ float s_red[3][TP];
-    __shared__ uint32_t s_tr[NPROD / 32][32 * 9];   // per producer warp: transpose scratch of the forward images
+    __shared__ float s_red[3][3][TP];             // partial sums of quarters 1..3: Re g, Im g, H
+    __shared__ uint32_t s_tr[NPROD / 32][32 * 5];   // per producer warp: transpose scratch of the forward images
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -433,13 +436,13 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 const FreqC fc = A.F.f[fw];
                 // ---- U slices; table records fetched one slice ahead ----
                 __nv_bfloat16* img = A.gimg ? A.gimg + (size_t)fw * A.gimg_stride : nullptr;
-                float4 nxt[4];
+                float4 nxt[2];
                 load_recs(A, 0, h, px, valid, nxt);
                 for (int j = 0; j < nU; ++j) {
                     slice([&](unsigned char* ahi, unsigned char* alo) {
-                        float4 cur[4];
+                        float4 cur[2];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+                        for (int k = 0; k < 2; ++k) cur[k] = nxt[k];
                         if (j + 1 < nU) load_recs(A, (j + 1) * 8, h, px, valid, nxt);
                         synth_u(A, fc, j * 8, p, h, cur, gs, ahi, alo, img, tile * 8 + (warp & 3) * 2, s_tr[warp], vimg);
                     });
@@ -451,33 +454,37 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 // gs (exact G of the tile) is complete
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
-                // ---- U epilogue: 32-column blocks b = h, h + 2, ... of Re U | Im U ----
+                // ---- U epilogue: element blocks b = h, h + 4, ... (32 elements; Re U in columns
+                // [32 b, 32 b + 32), Im U in [n + 32 b, ...)), read 16 columns at a time ----
                 acc_wait();
                 float gr = 0.f, gi = 0.f;
                 if (!err) {
-                    // element block b: Re U in columns [32 b, 32 b + 32), Im U in [n + 32 b, ...)
-                    for (int b = (int)h; b < n / 32; b += 2) {
-                        float vr[32], vi[32];
-                        tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), vr);
-                        tc::tmem_ld32(tmem + lane_off + (uint32_t)(n + 32 * b), vi);
+                    for (int b = (int)h; b < n / 32; b += 4) {
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            const float2 ge = gs[(size_t)(32 * b + k) * TP + p];
-                            gr = fmaf(ge.x, vr[k], fmaf(ge.y, vi[k], gr));
-                            gi = fmaf(ge.x, vi[k], fmaf(-ge.y, vr[k], gi));
+                        for (int hb = 0; hb < 2; ++hb) {
+                            const int c0 = 32 * b + 16 * hb;
+                            float vr[16], vi[16];
+                            tc::tmem_ld16(tmem + lane_off + (uint32_t)c0, vr);
+                            tc::tmem_ld16(tmem + lane_off + (uint32_t)(n + c0), vi);
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) {
+                                const float2 ge = gs[(size_t)(c0 + k) * TP + p];
+                                gr = fmaf(ge.x, vr[k], fmaf(ge.y, vi[k], gr));
+                                gi = fmaf(ge.x, vi[k], fmaf(-ge.y, vr[k], gi));
+                            }
                         }
                     }
                 }
                 acc_release();
-                if (h == 1) {
-                    s_red[0][p] = gr;
-                    s_red[1][p] = gi;
+                if (h > 0) {
+                    s_red[0][h - 1][p] = gr;
+                    s_red[1][h - 1][p] = gi;
                 }
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
                 if (h == 0) {
-                    gr = (gr + s_red[0][p]) * fc.w2;
-                    gi = (gi + s_red[1][p]) * fc.w2;
+                    gr = (gr + s_red[0][0][p] + s_red[0][1][p] + s_red[0][2][p]) * fc.w2;
+                    gi = (gi + s_red[1][0][p] + s_red[1][1][p] + s_red[1][2][p]) * fc.w2;
                     if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
                     acc_g += gr;
                 }
@@ -488,22 +495,26 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 acc_wait();
                 float hh = 0.f;
                 if (!err) {
-                    for (int b = (int)h; b < n / 32; b += 2) {
-                        float v[32];
-                        tc::tmem_ld32(tmem + lane_off + (uint32_t)(32 * b), v);
+                    for (int b = (int)h; b < n / 32; b += 4) {
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            const float2 ge = gs[(size_t)(32 * b + k) * TP + p];
-                            hh = fmaf(ge.x * ge.x + ge.y * ge.y, v[k], hh);
+                        for (int hb = 0; hb < 2; ++hb) {
+                            const int c0 = 32 * b + 16 * hb;
+                            float v[16];
+                            tc::tmem_ld16(tmem + lane_off + (uint32_t)c0, v);
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) {
+                                const float2 ge = gs[(size_t)(c0 + k) * TP + p];
+                                hh = fmaf(ge.x * ge.x + ge.y * ge.y, v[k], hh);
+                            }
                         }
                     }
                 }
                 acc_release();
-                if (h == 1) s_red[2][p] = hh;
+                if (h > 0) s_red[2][h - 1][p] = hh;
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
                 if (h == 0) {
-                    hh = (hh + s_red[2][p]) * fc.w4;
+                    hh = (hh + s_red[2][0][p] + s_red[2][1][p] + s_red[2][2][p]) * fc.w4;
                     if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = hh;
                     acc_h += hh;
                 }
@@ -612,7 +623,7 @@ __host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i
 //               row `row` of A = (B rows 128 i + row) * m(x), re-split into hi / lo,
 //               once the slice's B has landed; then the epilogue;
 //   warp 8      MMA issuer; warp 9 B loader (image rows [col0, 2n), hi and lo).
-__global__ void __launch_bounds__(NTHR_A, 1) k_forward_tc(FwdArgs A) {
+__global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full;
     __shared__ uint32_t s_tmem;
@@ -634,7 +645,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_forward_tc(FwdArgs A) {
     const uint32_t rows_bytes = (uint32_t)(n2 - col0) * 32u;      // loaded rows [col0, 2n) of one image
     if (tid == 0) {
         for (int k = 0; k < NST; ++k) {
-            tc::mbar_init(tc::smem_u32(&s_full_a[k]), NPROD / 32);
+            tc::mbar_init(tc::smem_u32(&s_full_a[k]), NPROD_F / 32);
             tc::mbar_init(tc::smem_u32(&s_full_b[k]), 1);
             tc::mbar_init(tc::smem_u32(&s_empty[k]), 1);
         }
@@ -648,7 +659,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_forward_tc(FwdArgs A) {
     const uint32_t tmem = s_tmem;
     auto stage = [&](int k) { return smem + (size_t)k * ST_BYTES; };
 
-    if (warp == NPROD / 32 + 1) {
+    if (warp == NPROD_F / 32 + 1) {
         // ------------------------------ B loader ------------------------------
         if (lane == 0) {
             int ql = 0;
@@ -679,7 +690,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_forward_tc(FwdArgs A) {
             }
         }
         __syncwarp();
-    } else if (warp == NPROD / 32) {
+    } else if (warp == NPROD_F / 32) {
         // ------------------------------ MMA issuer ------------------------------
         if (lane == 0) {
             const uint32_t id = tc::idesc_bf16_f32(128, (uint32_t)A.nb);
@@ -718,9 +729,28 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_forward_tc(FwdArgs A) {
         // -------------------------------- producers --------------------------------
         const int row = tid & 127, g = tid >> 7;
         bool err = false;
+        // m(x) of the thread's 8 pixels of slice q (fetched one slice ahead)
+        auto load_m = [&](int q, float (&mm)[8]) {
+            if (q >= nq) return;
+            const int p0 = (sbeg + q) * 16 + 8 * g;
+            if (p0 + 8 <= G.npix && ((reinterpret_cast<uintptr_t>(A.m + p0) & 15u) == 0)) {
+                const float4 m0 = __ldg((const float4*)(A.m + p0)), m1 = __ldg((const float4*)(A.m + p0 + 4));
+                mm[0] = m0.x; mm[1] = m0.y; mm[2] = m0.z; mm[3] = m0.w;
+                mm[4] = m1.x; mm[5] = m1.y; mm[6] = m1.z; mm[7] = m1.w;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) mm[t] = p0 + t < G.npix ? __ldg(A.m + p0 + t) : 0.f;
+            }
+        };
+        float mnext[8];
+        load_m(0, mnext);
         for (int q = 0; q < nq; ++q) {
             const int k = q % NST;
             const uint32_t ph = (uint32_t)(q / NST) & 1u;
+            float mm[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) mm[t] = mnext[t];
+            load_m(q + 1, mnext);
             if (!err && q >= NST) err = !tc::mbar_wait(tc::smem_u32(&s_empty[k]), ph ^ 1u, kMaxTries);
             if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_full_b[k]), ph, kMaxTries);
             err = __any_sync(0xffffffffu, err || s_err != 0);
@@ -730,16 +760,6 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_forward_tc(FwdArgs A) {
                 const uint32_t boff = tc::tile16_offset((uint32_t)(128 * i + row - col0), 8u * g);
                 const uint4 vh = *(const uint4*)(b_hi + boff), vl = *(const uint4*)(b_lo + boff);
                 const uint32_t hw[4] = {vh.x, vh.y, vh.z, vh.w}, lw[4] = {vl.x, vl.y, vl.z, vl.w};
-                const int p0 = (sbeg + q) * 16 + 8 * g;
-                float mm[8];
-                if (p0 + 8 <= G.npix) {
-                    const float4 m0 = __ldg((const float4*)(A.m + p0)), m1 = __ldg((const float4*)(A.m + p0 + 4));
-                    mm[0] = m0.x; mm[1] = m0.y; mm[2] = m0.z; mm[3] = m0.w;
-                    mm[4] = m1.x; mm[5] = m1.y; mm[6] = m1.z; mm[7] = m1.w;
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) mm[t] = p0 + t < G.npix ? __ldg(A.m + p0 + t) : 0.f;
-                }
                 uint32_t oh[4], ol[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -888,7 +908,7 @@ cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F,
     const int sm = NST * (int)ST_BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    k_forward_tc<<<A.cta0[A.n_mb], NTHR_A, sm, s>>>(A);
+    k_forward_tc<<<A.cta0[A.n_mb], NTHR_F, sm, s>>>(A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_forward_tc_reduce<<<256, 256, 0, s>>>(A, d_out, w, den_part);

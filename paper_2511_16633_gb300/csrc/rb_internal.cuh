@@ -204,6 +204,7 @@ struct WsLayout {
     size_t cells;      // [(ny-1)(nx-1)][8] float4
     size_t tables;     // [n_elem][npix] rb_cell
     size_t verts;      // [n_elem][max_steps + 1][n_rays] ray vertices, 32 B each (gridding)
+    size_t gkeys;      // [n_elem][npix] u64 first-arrival keys (gridding)
     size_t ends;       // [n_elem][n_rays] rb_ray_end
     size_t counters;   // 64 uint32 + 64 double scalars
     size_t pray;       // [n_freq][n_elem][n_elem] float2 (ray data, then residual)
@@ -238,8 +239,10 @@ enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_
 // ---------------------------------------------------------------------------
 cudaError_t launch_elem_positions(const GeoDev& G, float4* elem_xy, cudaStream_t s);
 cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s);
+// Rays; with keys set also the gridding: keys are reset here, tables and/or srec are
+// written for every (element, pixel).
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
+                         void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
                          cudaStream_t s);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,

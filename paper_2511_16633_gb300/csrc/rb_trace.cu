@@ -25,9 +25,10 @@
 // stays in its cell) and streams every vertex out (32 B).  k_raster gives each
 // thread a tube and a block of 8 steps, so the rasterisation runs at full
 // occupancy; every covered pixel gets a fire-and-forget 64-bit atomic min of
-// (T_res key, triangle id) on the first 8 bytes of its table record.  k_resolve
-// then reads the winning triangle id of every hit pixel, fetches that triangle's
-// vertices and writes Q, L and the KMAH index.
+// (T_res key, triangle id) in an 8-byte key array.  k_resolve then reads the
+// winning triangle id of every hit pixel, fetches that triangle's vertices and
+// writes the table record (Q, L and the KMAH index) and/or the synthesis record,
+// and counts the support pixels no triangle covered.
 // Positions, the direction and the traveltime residual T - |x - x_t|/c_ref
 // are float pairs (compensated sums), which keeps the Green's-function phase
 // w T accurate at MHz frequencies without the (slow) FP64 pipe.
@@ -201,9 +202,10 @@ __device__ __forceinline__ float interp(float wa, float wb, float wc, float a, f
     return __fadd_rn(__fadd_rn(__fmul_rn(wa, a), __fmul_rn(wb, b)), __fmul_rn(wc, c));
 }
 
-// Keep the smaller 64-bit (T_res key << 32 | tag) in the first 8 bytes of a table
-// record ({tag, tkey} little-endian); no value is returned, so the warp never waits.
-__device__ __forceinline__ void key_min(rb_cell* dst, uint64_t key) {
+// Keep the smaller 64-bit key (T_res key << 32 | triangle id << 8) of a pixel: the
+// order of the first 8 bytes of a table record ({tag, tkey} little-endian).  No
+// value is returned, so the warp never waits.
+__device__ __forceinline__ void key_min(unsigned long long* dst, uint64_t key) {
     asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(dst), "l"(key) : "memory");
 }
 
@@ -214,7 +216,8 @@ __device__ __forceinline__ void key_min(rb_cell* dst, uint64_t key) {
 // the pixel index: they are evaluated at the row's first pixel and then stepped
 // by their exact per-pixel increments (a few ulps of drift over a box).
 __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1,
-                                            uint32_t base, rb_cell* __restrict__ tab, const short2* __restrict__ supp) {
+                                            uint32_t base, unsigned long long* __restrict__ tab,
+                                            const short2* __restrict__ supp) {
     const Quad Q = quad_of(A0, A1, B0, B1);
     if (!Q.t0 && !Q.t1) return;
     // tight box of pixel centres (index space), with a 1e-3 px guard
@@ -464,7 +467,7 @@ __device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
 }
 
 __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict__ verts,
-                                                const rb_ray_end* __restrict__ ends, rb_cell* __restrict__ tables) {
+                                                const rb_ray_end* __restrict__ ends, unsigned long long* __restrict__ keys) {
     extern __shared__ short2 s_supp[];   // [ny]
     for (int iy = threadIdx.x; iy < G.ny; iy += blockDim.x) s_supp[iy] = support_row(G, iy);
     __syncthreads();
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
         const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
         const int k0 = kb * KB + 1, k1 = min(k0 + KB - 1, max(la, lb));
         if (k0 > k1) continue;
-        rb_cell* tab = tables + (size_t)t * G.npix;
+        unsigned long long* tab = keys + (size_t)t * G.npix;
         Vtx A0 = get_vtx(verts + vidx(G, t, min(k0 - 1, la), i));
         Vtx B0 = get_vtx(verts + vidx(G, t, min(k0 - 1, lb), i + 1));
         for (int k = k0; k <= k1; ++k) {
@@ -497,15 +500,30 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
 // and the pixel, the barycentric weights (bit-identical to the rasteriser's), then
 // Q, L and the KMAH index of the heaviest vertex.  Holes stay all ones.
 __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict__ verts,
-                                                 const rb_ray_end* __restrict__ ends, rb_cell* __restrict__ tables,
-                                                 const float* __restrict__ c, float4* __restrict__ srec) {
+                                                 const rb_ray_end* __restrict__ ends,
+                                                 const unsigned long long* __restrict__ keys, rb_cell* __restrict__ tables,
+                                                 const float* __restrict__ c, float4* __restrict__ srec,
+                                                 uint32_t* __restrict__ counters) {
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
     const long long total = (long long)G.n_elem * G.npix;
+    uint32_t holes = 0;   // support pixels that no triangle of the fan covered
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
          u += (long long)gridDim.x * blockDim.x) {
-        const uint2 kv = *reinterpret_cast<const uint2*>(tables + u);   // {tag, tkey}
+        const unsigned long long key = keys[u];
+        const uint2 kv = make_uint2((uint32_t)key, (uint32_t)(key >> 32));   // {tag, tkey}
         if (kv.y == RB_HOLE) {
+            if (tables) {
+                rb_cell hole;
+                hole.tag = RB_HOLE;
+                hole.tkey = RB_HOLE;
+                hole.q = __uint_as_float(RB_HOLE);
+                hole.l = __uint_as_float(RB_HOLE);
+                tables[u] = hole;
+            }
             if (srec) srec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int hp = (int)(u % G.npix);
+            const long long jx = 2LL * (hp % G.nx) - (G.nx - 1), jy = 2LL * (hp / G.nx) - (G.ny - 1);
+            if (jx * jx + jy * jy <= G.r2max) ++holes;
             continue;
         }
         const int t = (int)(u / G.npix), pix = (int)(u % G.npix);
@@ -538,7 +556,7 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
         rec.tkey = kv.y;
         rec.q = interp(wa, wb, wc, A0.q, Vb.q, Vc.q);
         rec.l = interp(wa, wb, wc, A0.l, Vb.l, Vc.l);
-        tables[u] = rec;
+        if (tables) tables[u] = rec;
         if (srec) {
             DF ex, ey;
             elem_pos(G, t, ex, ey);
@@ -546,12 +564,14 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
                                    G.j_floor);
         }
     }
+    for (int o = 16; o > 0; o >>= 1) holes += __shfl_down_sync(0xffffffffu, holes, o);
+    if ((threadIdx.x & 31) == 0 && holes) atomicAdd(counters + CNT_HOLES, holes);
 }
 
 }  // namespace
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
+                         void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
                          cudaStream_t s) {
     rb_rays S{};
     int ws = 0;
@@ -559,19 +579,25 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
         S = *samples;
         ws = 1;
     }
-    Vtx* V = tables ? (Vtx*)verts : nullptr;
-    if (tables && !V) return cudaErrorInvalidValue;
+    const bool grid = keys != nullptr;
+    Vtx* V = grid ? (Vtx*)verts : nullptr;
+    if (grid && (!V || (!tables && !srec))) return cudaErrorInvalidValue;
+    unsigned long long* K = (unsigned long long*)keys;
+    if (grid) {
+        cudaError_t e = cudaMemsetAsync(K, 0xff, (size_t)G.n_elem * G.npix * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
     const long long rays = (long long)G.n_elem * G.n_rays;
     k_trace<<<(int)((rays + 127) / 128), 128, 0, s>>>(G, cells, ends, S, ws, V, counters);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !tables) return e;
+    if (e != cudaSuccess || !grid) return e;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         nsm = 148;
-    k_raster<<<nsm * 16, 256, (size_t)G.ny * sizeof(short2), s>>>(G, V, ends, tables);
+    k_raster<<<nsm * 16, 256, (size_t)G.ny * sizeof(short2), s>>>(G, V, ends, K);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resolve<<<nsm * 8, 256, 0, s>>>(G, V, ends, tables, c, srec);
+    k_resolve<<<nsm * 8, 256, 0, s>>>(G, V, ends, K, tables, c, srec, counters);
     return cudaGetLastError();
 }
 
