@@ -277,10 +277,10 @@ def run_ours(args):
         "p50_ms": R["p50_ms"], "p99_ms": R["p99_ms"], "stage_ms": st, "wall_s": R["wall_s"],
         "roofline": roof, "roofline_contractions": {"adjoint": roof_adj, "forward": roof_fwd},
         "clocks": R["clocks"], "e2e": R["e2e"],
-        # launches per update: positions, fields, trace/raster/resolve, link/keys/select, adjoint
-        # (+ one B-image prep per frequency on the mixed path), 4 direction kernels, forward +
-        # reduce per frequency, 4 apply/norm kernels
-        "gpu_launches": (17 + 3 * nf if tc else 17 + 2 * nf) * args.steps,
+        # launches per update: positions, fields, trace/raster/resolve, link, residual keys and
+        # the three selection passes, adjoint (+ one B-image prep per frequency on the mixed
+        # path), 4 direction kernels, forward + reduce per frequency, 4 apply/norm kernels
+        "gpu_launches": (19 + 3 * nf if tc else 19 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
     if other in runs:

@@ -150,6 +150,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->linked = o; o = align256(o + ne * ne);
     L->wts = o; o = align256(o + nf * ne * ne);
     L->keys = o; o = align256(o + nf * ne * ne * 8);
+    L->sel = o; o = align256(o + rb_sel_bytes());
     L->gsum = o; o = align256(o + npix * 4);
     L->hsum = o; o = align256(o + npix * 4);
     L->pdir = o; o = align256(o + npix * 4);
@@ -360,8 +361,8 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
     RB_CU(mark(RB_STAGE_LINK, 0));
     RB_CU(launch_link(G, c_inout, ends, F, R, linked, s));
-    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, s));
-    RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, cnt, s));
+    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, W.at<void>(W.L.sel), s));
+    RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, W.at<void>(W.L.sel), s));
     RB_CU(mark(RB_STAGE_LINK, 1));
     RB_CU(mark(RB_STAGE_ADJOINT, 0));
     if (prec == RB_PREC_BF16X3) {

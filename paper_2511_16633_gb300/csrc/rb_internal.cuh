@@ -211,6 +211,7 @@ struct WsLayout {
     size_t linked;     // [n_elem][n_elem] u8
     size_t wts;        // [n_freq][n_elem][n_elem] u8
     size_t keys;       // [n_freq][n_elem][n_elem] u64
+    size_t sel;        // outlier selection scratch (rb_sel_bytes)
     size_t gsum;       // [npix] float
     size_t hsum;       // [npix] float
     size_t pdir;       // [npix] float
@@ -249,10 +250,13 @@ cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float
                              float2* g_out, cudaStream_t s);
 cudaError_t launch_link(const GeoDev& G, const float* c, const rb_ray_end* ends, const FreqSet& F,
                         float2* p_out, uint8_t* linked, cudaStream_t s);
+// outlier selection: histogram, scalars and candidates (rb_sel_bytes) in sel_ws
+size_t rb_sel_bytes();
 cudaError_t launch_residual_keys(const GeoDev& G, int n_freq, const float2* p_obs, float2* r_inout,
-                                 const uint8_t* linked, uint64_t* keys, uint32_t* counters, cudaStream_t s);
-cudaError_t launch_outlier_select(int n_total, double frac, const uint64_t* keys, const uint32_t* counters,
-                                  uint8_t* w, uint32_t* counters_out, cudaStream_t s);
+                                 const uint8_t* linked, uint64_t* keys, uint32_t* counters, void* sel_ws,
+                                 cudaStream_t s);
+cudaError_t launch_outlier_select(int n_total, double frac, const uint64_t* keys, uint32_t* counters, uint8_t* w,
+                                  void* sel_ws, cudaStream_t s);
 cudaError_t launch_adjoint_simt(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                                 const float2* resid, const uint8_t* w, float2* g_out, float* h_out,
                                 float* gsum, float* hsum, uint32_t* counters, cudaStream_t s);

@@ -30,19 +30,49 @@ __device__ __forceinline__ float bilinear_c(const GeoDev& G, const float* __rest
     return (1.f - fu) * (1.f - fv) * p[0] + fu * (1.f - fv) * p[1] + (1.f - fu) * fv * p[G.nx] + fu * fv * p[G.nx + 1];
 }
 
+// Traveltime of receiver dr's bracket by interval i, in explicitly rounded steps so
+// that every evaluation of the same bracket gives the same bits.
+__device__ __forceinline__ double bracket_T(double chord_t, double a, double b, double thr, double tri, double tri1,
+                                            double* lam_out) {
+    const double den = __dsub_rn(b, a);
+    const double lam = den != 0.0 ? __ddiv_rn(__dsub_rn(thr, a), den) : 0.0;
+    *lam_out = lam;
+    return __dadd_rn(chord_t, __dadd_rn(__dmul_rn(__dsub_rn(1.0, lam), tri), __dmul_rn(lam, tri1)));
+}
+
+// Order-preserving map of a double to uint64 (for the first-arrival minimum).
+__device__ __forceinline__ unsigned long long d2key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// One CTA per emitter e.  The end angles of its fan go to shared memory; then each
+// thread takes ray intervals (i, i + 1) and visits only the receivers whose angle
+// lies in that interval's range, so the work is O(n_rays + brackets) rather than
+// O(n_rays x n_elem).  The first arrival per receiver is the minimum of an
+// order-preserving 64-bit traveltime key (shared-memory atomic min), ties to the
+// smallest interval index in a second pass, which reproduces a sequential scan
+// over i that keeps the first strictly smaller T.
 __global__ void __launch_bounds__(256) k_link(GeoDev G, const float* __restrict__ c, const rb_ray_end* __restrict__ ends,
                                               FreqSet F, float2* __restrict__ p_out, uint8_t* __restrict__ linked) {
     extern __shared__ unsigned char smem[];
-    const int n = G.n_rays;
-    double* th = (double*)smem;            // [n]
-    double* tr = th + n;                   // [n]
-    float* qq = (float*)(tr + n);          // [n]
-    float* ll = qq + n;                    // [n]
-    int* kk = (int*)(ll + n);              // [n]
-    int* ok = kk + n;                      // [n]
+    const int n = G.n_rays, N = G.n_elem;
+    double* th = (double*)smem;                             // [n]
+    double* tr = th + n;                                    // [n]
+    double* cht = tr + n;                                   // [N] chord / c_ref per receiver offset dr
+    unsigned long long* best = (unsigned long long*)(cht + N);   // [N] first-arrival key per dr
+    float* qq = (float*)(best + N);                         // [n]
+    float* ll = qq + n;                                     // [n]
+    int* kk = (int*)(ll + n);                               // [n]
+    int* ok = kk + n;                                       // [n]
+    int* bi = ok + n;                                       // [N] winning interval per dr
     const int e = blockIdx.x;
     const double two_pi = 2.0 * RB_PI_D;
-    const double phi_e = two_pi * (double)e / (double)G.n_elem;
+    const double phi_e = two_pi * (double)e / (double)N;
+    double xe, ye;
+    sincos(phi_e, &ye, &xe);
+    xe *= G.R_d;
+    ye *= G.R_d;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const rb_ray_end E = ends[(size_t)e * n + i];
         double a = atan2(E.y, E.x) - phi_e;
@@ -56,46 +86,58 @@ __global__ void __launch_bounds__(256) k_link(GeoDev G, const float* __restrict_
         kk[i] = E.kappa;
         ok[i] = E.n_vert > 0;
     }
-    __syncthreads();
-    double xe, ye;
-    sincos(phi_e, &ye, &xe);
-    xe *= G.R_d;
-    ye *= G.R_d;
-    for (int r = threadIdx.x; r < G.n_elem; r += blockDim.x) {
-        const int dr = ((r - e) % G.n_elem + G.n_elem) % G.n_elem;
-        const double thr = two_pi * (double)dr / (double)G.n_elem;
+    for (int dr = threadIdx.x; dr < N; dr += blockDim.x) {
+        const int r = (e + dr) % N;
         double xr, yr;
-        sincos(two_pi * (double)r / (double)G.n_elem, &yr, &xr);
+        sincos(two_pi * (double)r / (double)N, &yr, &xr);
         xr *= G.R_d;
         yr *= G.R_d;
-        const double chord = sqrt((xr - xe) * (xr - xe) + (yr - ye) * (yr - ye));
-        double bestT = 1e300, bestLam = 0.0;
-        int best = -1;
-        for (int i = 0; i + 1 < n; ++i) {
+        cht[dr] = sqrt((xr - xe) * (xr - xe) + (yr - ye) * (yr - ye)) / G.c_ref_d;
+        best[dr] = ~0ull;
+        bi[dr] = 0x7fffffff;
+    }
+    __syncthreads();
+    const double dN = (double)N / two_pi;
+    // pass 1: first-arrival key per receiver; pass 2: smallest interval with that key
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = threadIdx.x; i + 1 < n; i += blockDim.x) {
             if (!ok[i] || !ok[i + 1]) continue;
             const double a = th[i], b = th[i + 1];
             if (fabs(b - a) > RB_PI_D) continue;
             const double lo = fmin(a, b), hi = fmax(a, b);
-            if (thr < lo || thr > hi) continue;
-            const double den = b - a;
-            const double lam = den != 0.0 ? (thr - a) / den : 0.0;
-            const double T = chord / G.c_ref_d + (1.0 - lam) * tr[i] + lam * tr[i + 1];
-            if (T < bestT) {
-                bestT = T;
-                bestLam = lam;
-                best = i;
+            // receiver offsets whose angle 2 pi dr / N can lie in [lo, hi] (one spare each side)
+            const int d0 = max(0, (int)floor(lo * dN) - 1), d1 = min(N - 1, (int)ceil(hi * dN) + 1);
+            for (int dr = d0; dr <= d1; ++dr) {
+                const double thr = two_pi * (double)dr / (double)N;
+                if (thr < lo || thr > hi) continue;
+                double lam;
+                const unsigned long long key = d2key(bracket_T(cht[dr], a, b, thr, tr[i], tr[i + 1], &lam));
+                if (pass == 0) atomicMin(&best[dr], key);
+                else if (key == best[dr]) atomicMin(&bi[dr], i);
             }
         }
-        const size_t o = (size_t)e * G.n_elem + r;
-        if (linked) linked[o] = best >= 0 ? 1 : 0;
-        if (best < 0) {
-            for (int w = 0; w < F.n; ++w) p_out[(size_t)w * G.n_elem * G.n_elem + o] = make_float2(0.f, 0.f);
+        __syncthreads();
+    }
+    for (int dr = threadIdx.x; dr < N; dr += blockDim.x) {
+        const int r = (e + dr) % N;
+        const size_t o = (size_t)e * N + r;
+        const int bsel = bi[dr];
+        if (linked) linked[o] = bsel != 0x7fffffff ? 1 : 0;
+        if (bsel == 0x7fffffff) {
+            for (int w = 0; w < F.n; ++w) p_out[(size_t)w * N * N + o] = make_float2(0.f, 0.f);
             continue;
         }
+        const double thr = two_pi * (double)dr / (double)N;
+        double bestLam;
+        const double bestT = bracket_T(cht[dr], th[bsel], th[bsel + 1], thr, tr[bsel], tr[bsel + 1], &bestLam);
+        double xr, yr;
+        sincos(two_pi * (double)r / (double)N, &yr, &xr);
+        xr *= G.R_d;
+        yr *= G.R_d;
         const float lf = (float)bestLam;
-        const float q = (1.f - lf) * qq[best] + lf * qq[best + 1];
-        const float L = (1.f - lf) * ll[best] + lf * ll[best + 1];
-        const int kap = bestLam <= 0.5 ? kk[best] : kk[best + 1];
+        const float q = (1.f - lf) * qq[bsel] + lf * qq[bsel + 1];
+        const float L = (1.f - lf) * ll[bsel] + lf * ll[bsel + 1];
+        const int kap = bestLam <= 0.5 ? kk[bsel] : kk[bsel + 1];
         const float crx = bilinear_c(G, c, (float)xr, (float)yr);
         const float J = fmaxf(fabsf(q), G.j_floor);
         for (int w = 0; w < F.n; ++w) {
@@ -107,15 +149,34 @@ __global__ void __launch_bounds__(256) k_link(GeoDev G, const float* __restrict_
             float s, co;
             sincospif(2.0f * (float)cyc, &s, &co);
             const float amp = sqrtf(crx / (8.0f * RB_PI_F * J)) * fc.w_isqrt * expf(-fc.a_abs * L);
-            p_out[(size_t)w * G.n_elem * G.n_elem + o] = make_float2(amp * co, amp * s);
+            p_out[(size_t)w * N * N + o] = make_float2(amp * co, amp * s);
         }
     }
 }
 
-// R = p_ray - p_obs in place; keys for the outlier selection; kept count.
-__global__ void k_residual_keys(GeoDev G, int n_freq, const float2* __restrict__ p_obs, float2* __restrict__ r,
-                                const uint8_t* __restrict__ linked, uint64_t* __restrict__ keys,
-                                uint32_t* __restrict__ counters) {
+// Workspace of the outlier selection (rb_sel_bytes): a 12-bit histogram of the top
+// digit of the keys, a few scalars, then the compacted candidates of one bucket.
+constexpr int SEL_THREADS = 1024;
+constexpr int SEL_BINS = 4096;          // top 12 bits
+constexpr int SEL_CAP = 12288;          // compacted candidates (96 KB of shared memory)
+constexpr int SEL_BLOCKS = 64;          // CTAs of the grid-wide passes
+struct SelHdr {
+    uint32_t hist[SEL_BINS];
+    uint32_t n_cand;                    // candidates found in the bucket (may exceed SEL_CAP)
+    uint32_t pad[3];
+    unsigned long long thr;             // selected threshold (keys below it keep W = 1)
+};
+
+// R = p_ray - p_obs in place; keys for the outlier selection; kept count; the
+// histogram of the keys' top 12 bits (per CTA in shared memory, then added to
+// the global one, which the caller zeroed).
+__global__ void __launch_bounds__(SEL_THREADS) k_residual_keys(GeoDev G, int n_freq, const float2* __restrict__ p_obs,
+                                                               float2* __restrict__ r, const uint8_t* __restrict__ linked,
+                                                               uint64_t* __restrict__ keys, uint32_t* __restrict__ counters,
+                                                               SelHdr* __restrict__ sel) {
+    __shared__ uint32_t hist[SEL_BINS];
+    for (int b = threadIdx.x; b < SEL_BINS; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     const int N = G.n_elem;
     const long long total = (long long)n_freq * N * N;
     const int min_sep = (N + 7) / 8;
@@ -134,6 +195,7 @@ __global__ void k_residual_keys(GeoDev G, int n_freq, const float2* __restrict__
         if (in_mask && lk) {
             const float m2 = R.x * R.x + R.y * R.y;
             key = ((uint64_t)__float_as_uint(m2) << 32) | (uint64_t)(0xffffffffu - (uint32_t)j);
+            atomicAdd(&hist[key >> 52], 1u);
             ++kept;
         }
         if (in_mask && !lk && j < (long long)N * N) ++unlinked;
@@ -148,147 +210,167 @@ __global__ void k_residual_keys(GeoDev G, int n_freq, const float2* __restrict__
         if (kept) atomicAdd(counters + CNT_KEPT, kept);
         if (unlinked) atomicAdd(counters + CNT_UNLINKED, unlinked);
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < SEL_BINS; b += blockDim.x)
+        if (hist[b]) atomicAdd(&sel->hist[b], hist[b]);
 }
 
-// Exact selection of the k-th largest non-zero 64-bit key (keys are distinct: the
-// low word is the entry index), then W = 1 for the non-zero keys below it.  One CTA:
-// a 12-bit histogram of the top digit over all keys picks the bucket that holds the
-// k-th largest; that bucket's keys are compacted into shared memory and the
-// remaining 52 bits are resolved there by 8-bit radix passes.  A bucket larger than
-// the shared buffer falls back to radix passes over the global keys.
-constexpr int SEL_THREADS = 1024;
-constexpr int SEL_BINS = 4096;          // top 12 bits
-constexpr int SEL_CAP = 12288;          // compacted candidates (96 KB of shared memory)
+// Exact selection of the k-th largest non-zero 64-bit key, k = floor(frac * kept)
+// (keys are distinct: the low word is the entry index); W = 1 for the non-zero keys
+// below it.  Grid-wide passes: the histogram above picks the top-digit bucket that
+// holds the k-th largest (k_sel_compact, every CTA computes the same bucket by a
+// block-wide suffix scan), the bucket's keys are compacted, one CTA resolves the
+// remaining 52 bits by 8-bit radix passes in shared memory (k_sel_final; a bucket
+// larger than the shared buffer is resolved by passes over the global keys), and
+// the weights are written grid-wide (k_sel_write).
 
-// Find, among bins [0, nb) counted in hist (largest digit = highest bin), the bin
-// that holds the rem-th largest key; returns it and leaves in *rem the rank within it.
-__device__ int sel_pick(const uint32_t* hist, int nb, long long* rem_io) {
-    // sequential from the top; called by one thread on at most 4096 bins
-    long long rem = *rem_io;
-    int d = nb - 1;
-    for (; d > 0; --d) {
-        if ((long long)hist[d] >= rem) break;
-        rem -= hist[d];
+// Bucket d (top 12 bits) holding the k-th largest key and the rank rem of that key
+// within it, from the global histogram; called by all SEL_THREADS threads of a CTA.
+__device__ void sel_bucket(const uint32_t* __restrict__ ghist, long long k, int* d_out, long long* rem_out) {
+    __shared__ long long warp_tot[SEL_THREADS / 32];
+    __shared__ int s_d;
+    __shared__ long long s_rem;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    uint32_t h4[4];
+    long long own = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h4[q] = ghist[4 * t + q];
+        own += h4[q];
     }
-    *rem_io = rem;
-    return d;
+    // inclusive suffix sum over threads (thread t covers bins 4t .. 4t + 3): scan in
+    // reverse thread order within warps, then over the warps
+    long long v = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + o < 32) v += u;
+    }
+    if (lane == 0) warp_tot[wid] = v;
+    if (t == 0) s_d = -1;
+    __syncthreads();
+    long long above = 0;
+    for (int w2 = wid + 1; w2 < SEL_THREADS / 32; ++w2) above += warp_tot[w2];
+    const long long incl = v + above, excl = incl - own;
+    if (excl < k && k <= incl) {
+        long long rem = k - excl;
+        int d = 4 * t;
+        for (int q = 3; q >= 0; --q) {
+            if ((long long)h4[q] >= rem) {
+                d = 4 * t + q;
+                break;
+            }
+            rem -= h4[q];
+        }
+        s_d = d;
+        s_rem = rem;
+    }
+    __syncthreads();
+    *d_out = s_d;
+    *rem_out = s_rem;
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) k_outlier_select(int n_total, double frac, const uint64_t* __restrict__ keys,
-                                                                uint32_t* __restrict__ counters, uint8_t* __restrict__ w) {
-    extern __shared__ uint64_t cand[];           // [SEL_CAP]
-    __shared__ uint32_t hist[SEL_BINS];
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_compact(int n_total, double frac, const uint64_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ counters,
+                                                             SelHdr* __restrict__ sel, uint64_t* __restrict__ cand) {
+    const long long k = (long long)floor(frac * (double)counters[CNT_KEPT]);
+    if (k <= 0) return;
+    int d;
+    long long rem;
+    sel_bucket(sel->hist, k, &d, &rem);
+    if (d < 0) return;
+    const uint64_t top = (uint64_t)d << 52;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform loop bounds: every lane takes part in the ballot
+    for (int j0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < n_total; j0 += gridDim.x * blockDim.x) {
+        const int j = j0 + lane;
+        const uint64_t key = j < n_total ? keys[j] : 0ull;
+        const bool hit = key != 0 && (key & (0xfffull << 52)) == top;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (!m) continue;
+        uint32_t base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(&sel->n_cand, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (hit) {
+            const uint32_t idx = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+            if (idx < (uint32_t)SEL_CAP) cand[idx] = key;
+        }
+    }
+}
+
+// Resolve bits 51..0 of the k-th largest key within the bucket given by prefix /
+// rem from `src` (n entries; shared or global), 8 bits per pass (4 in the last).
+__device__ uint64_t sel_resolve(const uint64_t* src, int n, uint64_t prefix, long long rem, uint32_t* hist) {
     __shared__ uint64_t s_prefix;
     __shared__ long long s_rem;
-    __shared__ int s_d, s_nc;
-    const uint32_t kept = counters[CNT_KEPT];
-    const long long k = (long long)floor(frac * (double)kept);
+    if (threadIdx.x == 0) {
+        s_prefix = prefix;
+        s_rem = rem;
+    }
+    uint64_t mask = 0xfffull << 52;
+    for (int shift = 44; shift >= -4; shift -= 8) {
+        const int sh = shift < 0 ? 0 : shift;
+        const int bits = shift < 0 ? 4 : 8;          // last pass: bits 3..0
+        const uint64_t dm = (1ull << bits) - 1;
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint64_t pre = s_prefix;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const uint64_t key = src[j];
+            if (key != 0 && (key & mask) == pre) atomicAdd(&hist[(key >> sh) & dm], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long r = s_rem;
+            int d = (int)dm;
+            for (; d > 0; --d) {
+                if ((long long)hist[d] >= r) break;
+                r -= hist[d];
+            }
+            s_rem = r;
+            s_prefix = pre | ((uint64_t)d << sh);
+        }
+        mask |= dm << sh;
+        __syncthreads();
+    }
+    return s_prefix;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_final(int n_total, double frac, const uint64_t* __restrict__ keys,
+                                                           uint32_t* __restrict__ counters, SelHdr* __restrict__ sel,
+                                                           const uint64_t* __restrict__ cand) {
+    extern __shared__ uint64_t scand[];          // [SEL_CAP]
+    __shared__ uint32_t hist[256];
+    const long long k = (long long)floor(frac * (double)counters[CNT_KEPT]);
     uint64_t thr = ~0ull;   // nothing zeroed
     if (k > 0) {
-        for (int b = threadIdx.x; b < SEL_BINS; b += blockDim.x) hist[b] = 0;
-        if (threadIdx.x == 0) {
-            s_rem = k;
-            s_nc = 0;
-        }
-        __syncthreads();
-        // four independent loads in flight per thread and iteration
-        for (int j0 = threadIdx.x; j0 < n_total; j0 += 4 * blockDim.x) {
-            uint64_t kk[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int j = j0 + t * blockDim.x;
-                kk[t] = j < n_total ? keys[j] : 0ull;
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (kk[t] != 0) atomicAdd(&hist[kk[t] >> 52], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long rem = s_rem;
-            s_d = sel_pick(hist, SEL_BINS, &rem);
-            s_rem = rem;
-            s_prefix = (uint64_t)s_d << 52;
-        }
-        __syncthreads();
-        const int nb = (int)hist[s_d];
-        uint64_t mask = 0xfffull << 52;
-        if (nb <= SEL_CAP) {
-            // compact the bucket, then 8-bit passes over bits 51..0 in shared memory
-            const uint64_t top = s_prefix;
-            for (int j0 = threadIdx.x; j0 < n_total; j0 += 4 * blockDim.x) {
-                uint64_t kk[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int j = j0 + t * blockDim.x;
-                    kk[t] = j < n_total ? keys[j] : 0ull;
-                }
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (kk[t] != 0 && (kk[t] & mask) == top) cand[atomicAdd(&s_nc, 1)] = kk[t];
-            }
+        int d;
+        long long rem;
+        sel_bucket(sel->hist, k, &d, &rem);
+        const int nc = (int)sel->n_cand;
+        if (d < 0) {
+            // fewer non-zero keys than k (not reachable: k < kept): nothing is zeroed
+        } else if (nc <= SEL_CAP) {
+            for (int j = threadIdx.x; j < nc; j += blockDim.x) scand[j] = cand[j];
             __syncthreads();
-            const int nc = s_nc;
-            for (int shift = 44; shift >= -4; shift -= 8) {
-                const int sh = shift < 0 ? 0 : shift;
-                const int bits = shift < 0 ? 4 : 8;          // last pass: bits 3..0
-                const uint64_t dm = (1ull << bits) - 1;
-                for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
-                __syncthreads();
-                const uint64_t pre = s_prefix;
-                for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-                    const uint64_t key = cand[j];
-                    if ((key & mask) == pre) atomicAdd(&hist[(key >> sh) & dm], 1u);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    long long rem = s_rem;
-                    const int d = sel_pick(hist, (int)dm + 1, &rem);
-                    s_rem = rem;
-                    s_prefix = pre | ((uint64_t)d << sh);
-                }
-                mask |= dm << sh;
-                __syncthreads();
-            }
+            thr = sel_resolve(scand, nc, (uint64_t)d << 52, rem, hist);
         } else {
-            for (int shift = 44; shift >= -4; shift -= 8) {
-                const int sh = shift < 0 ? 0 : shift;
-                const int bits = shift < 0 ? 4 : 8;
-                const uint64_t dm = (1ull << bits) - 1;
-                for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
-                __syncthreads();
-                const uint64_t pre = s_prefix;
-                for (int j = threadIdx.x; j < n_total; j += blockDim.x) {
-                    const uint64_t key = keys[j];
-                    if (key != 0 && (key & mask) == pre) atomicAdd(&hist[(key >> sh) & dm], 1u);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    long long rem = s_rem;
-                    const int d = sel_pick(hist, (int)dm + 1, &rem);
-                    s_rem = rem;
-                    s_prefix = pre | ((uint64_t)d << sh);
-                }
-                mask |= dm << sh;
-                __syncthreads();
-            }
-        }
-        thr = s_prefix;
-    }
-    for (int j0 = threadIdx.x; j0 < n_total; j0 += 4 * blockDim.x) {
-        uint64_t kk[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int j = j0 + t * blockDim.x;
-            kk[t] = j < n_total ? keys[j] : 0ull;
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int j = j0 + t * blockDim.x;
-            if (j < n_total) w[j] = (kk[t] != 0 && kk[t] < thr) ? 1 : 0;
+            thr = sel_resolve(keys, n_total, (uint64_t)d << 52, rem, hist);
         }
     }
-    if (threadIdx.x == 0) counters[CNT_ZEROED] = (uint32_t)k;
+    if (threadIdx.x == 0) {
+        sel->thr = thr;
+        counters[CNT_ZEROED] = (uint32_t)(k > 0 ? k : 0);
+    }
+}
+
+__global__ void k_sel_write(int n_total, const uint64_t* __restrict__ keys, const SelHdr* __restrict__ sel,
+                            uint8_t* __restrict__ w) {
+    const uint64_t thr = sel->thr;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_total; j += gridDim.x * blockDim.x) {
+        const uint64_t key = keys[j];
+        w[j] = (key != 0 && key < thr) ? 1 : 0;
+    }
 }
 
 }  // namespace
@@ -296,7 +378,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_outlier_select(int n_total, dou
 cudaError_t launch_link(const GeoDev& G, const float* c, const rb_ray_end* ends, const FreqSet& F, float2* p_out,
                         uint8_t* linked, cudaStream_t s) {
     if (G.n_rays > LINK_MAX_RAYS) return cudaErrorInvalidValue;
-    const size_t sm = (size_t)G.n_rays * (8 + 8 + 4 + 4 + 4 + 4);
+    const size_t sm = (size_t)G.n_rays * (8 + 8 + 4 + 4 + 4 + 4) + (size_t)G.n_elem * (8 + 8 + 4);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_link, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -305,20 +387,40 @@ cudaError_t launch_link(const GeoDev& G, const float* c, const rb_ray_end* ends,
     return cudaGetLastError();
 }
 
+size_t rb_sel_bytes() { return sizeof(SelHdr) + (size_t)SEL_CAP * sizeof(uint64_t); }
+
 cudaError_t launch_residual_keys(const GeoDev& G, int n_freq, const float2* p_obs, float2* r_inout,
-                                 const uint8_t* linked, uint64_t* keys, uint32_t* counters, cudaStream_t s) {
+                                 const uint8_t* linked, uint64_t* keys, uint32_t* counters, void* sel_ws,
+                                 cudaStream_t s) {
+    SelHdr* sel = (SelHdr*)sel_ws;
+    cudaError_t e = cudaMemsetAsync(sel, 0, sizeof(SelHdr), s);
+    if (e != cudaSuccess) return e;
     const long long total = (long long)n_freq * G.n_elem * G.n_elem;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
-    k_residual_keys<<<blocks, 256, 0, s>>>(G, n_freq, p_obs, r_inout, linked, keys, counters);
+    long long blocks = (total + SEL_THREADS - 1) / SEL_THREADS;
+    if (blocks > SEL_BLOCKS) blocks = SEL_BLOCKS;
+    k_residual_keys<<<(int)blocks, SEL_THREADS, 0, s>>>(G, n_freq, p_obs, r_inout, linked, keys, counters, sel);
     return cudaGetLastError();
 }
 
-cudaError_t launch_outlier_select(int n_total, double frac, const uint64_t* keys, const uint32_t* /*counters*/,
-                                  uint8_t* w, uint32_t* counters_out, cudaStream_t s) {
-    const int sm = SEL_CAP * (int)sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(k_outlier_select, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+cudaError_t launch_outlier_select(int n_total, double frac, const uint64_t* keys, uint32_t* counters, uint8_t* w,
+                                  void* sel_ws, cudaStream_t s) {
+    SelHdr* sel = (SelHdr*)sel_ws;
+    uint64_t* cand = (uint64_t*)((char*)sel_ws + sizeof(SelHdr));
+    long long blocks = ((long long)n_total + SEL_THREADS - 1) / SEL_THREADS;
+    if (blocks > SEL_BLOCKS) blocks = SEL_BLOCKS;
+    if (blocks < 1) blocks = 1;
+    k_sel_compact<<<(int)blocks, SEL_THREADS, 0, s>>>(n_total, frac, keys, counters, sel, cand);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_outlier_select<<<1, SEL_THREADS, sm, s>>>(n_total, frac, keys, counters_out, w);
+    const int sm = SEL_CAP * (int)sizeof(uint64_t);
+    e = cudaFuncSetAttribute(k_sel_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    k_sel_final<<<1, SEL_THREADS, sm, s>>>(n_total, frac, keys, counters, sel, cand);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long wb = ((long long)n_total + 255) / 256;
+    if (wb > 1024) wb = 1024;
+    if (wb < 1) wb = 1;
+    k_sel_write<<<(int)wb, 256, 0, s>>>(n_total, keys, sel, w);
     return cudaGetLastError();
 }
