@@ -278,9 +278,10 @@ def run_ours(args):
         "roofline": roof, "roofline_contractions": {"adjoint": roof_adj, "forward": roof_fwd},
         "clocks": R["clocks"], "e2e": R["e2e"],
         # launches per update: positions, fields, trace/raster/resolve, link, residual keys and
-        # the three selection passes, adjoint (+ one B-image prep per frequency on the mixed
+        # the three selection passes, adjoint (+ the operand-image synthesis and one B-image
+        # prep per frequency on the mixed
         # path), 4 direction kernels, forward + reduce per frequency, 4 apply/norm kernels
-        "gpu_launches": (19 + 3 * nf if tc else 19 + 2 * nf) * args.steps,
+        "gpu_launches": (20 + 3 * nf if tc else 19 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
     if other in runs:

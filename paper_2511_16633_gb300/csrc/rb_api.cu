@@ -162,6 +162,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
     L->gimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_gimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->srec = o; o = align256(o + (tcp ? ne * npix * 16 : 0));
+    L->aimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_aimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->total = o;
     return o;
 }
@@ -300,8 +301,9 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
         RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
         RB_CU(launch_prep_b(G.n_elem, (const float2*)resid, w, W.at<void>(W.L.tcimg), s));
         RB_CU(launch_srec(G, tables, c, W.at<float4>(W.L.srec), s));
-        RB_CU(launch_adjoint_tc(G, W.at<float4>(W.L.srec), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
-                                (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, nullptr, s));
+        RB_CU(launch_synth_images(G, W.at<float4>(W.L.srec), F, W.at<void>(W.L.aimg), nullptr, s));
+        RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
+                                (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c, F, (const float2*)resid, w, (float2*)g_out, hdiag_out, nullptr,
                                   nullptr, nullptr, s));
@@ -369,9 +371,10 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
         const size_t img = tc_b_images_bytes(G.n_elem);
         for (int w = 0; w < n_freq; ++w)
             RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
-        RB_CU(launch_adjoint_tc(G, srec, F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(), nullptr,
-                                nullptr, gsum, hsum, cnt,
-                                params->step_mode == RB_STEP_EXACT ? W.at<void>(W.L.gimg) : nullptr, s));
+        RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg),
+                                  params->step_mode == RB_STEP_EXACT ? W.at<void>(W.L.gimg) : nullptr, s));
+        RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
+                                nullptr, nullptr, gsum, hsum, cnt, s));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));
     }

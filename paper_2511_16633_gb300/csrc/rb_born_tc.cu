@@ -64,7 +64,8 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
 struct TcArgs {
     GeoDev G;
     FreqSet F;
-    const float4* srec;        // [n_elem][npix] synthesis records
+    const __nv_bfloat16* aimg; // [n_freq][tiles][2n / 16 slices][hi|lo][TP x 16] A images (k_synth_images)
+    size_t aimg_stride;        // bf16 elements per frequency
     const __nv_bfloat16* bu;   // [n_freq][image]
     const __nv_bfloat16* bw;   // [n_freq][image]
     size_t bu_stride, bw_stride;  // bf16 elements per frequency
@@ -77,8 +78,6 @@ struct TcArgs {
     uint32_t* counters;
     int n_tiles;
     uint32_t tmem_cols;
-    __nv_bfloat16* gimg;       // optional: per-frequency G operand images for the forward (see gimage_seg)
-    size_t gimg_stride;        // bf16 elements per frequency
 };
 
 // G operand image of the forward, per frequency: chunks of 16 pixels (one K = 16
@@ -196,91 +195,145 @@ __device__ __forceinline__ void store_row16(unsigned char* a_hi, unsigned char* 
     *(uint4*)(a_lo + off) = make_uint4(wlo[0], wlo[1], wlo[2], wlo[3]);
 }
 
-// Synthesis records of the two elements r0 + 2h + j (j < 2) at this thread's pixel.
-__device__ __forceinline__ void load_recs(const TcArgs& A, int r0, uint32_t h, int px, bool valid, float4 (&sr)[2]) {
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int r = r0 + 2 * (int)h + j;
-        sr[j] = valid ? __ldg(A.srec + (size_t)r * A.G.npix + px) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
-// U slice (8 elements, K' = 16): thread (p, h), h < 4, takes elements r0 + 2h + j
-// (j < 2), i.e. K' positions 4h .. 4h + 3: exact G to gs, bf16 hi / lo of (Re, -Im) to
-// half of K-group h / 2 of A row p, and |G|^2 (hi / lo) to the V slice r0 / 16.  With
-// img set, the values (Re, +Im) also go to the forward operand image (see gimage_seg):
-// each 8-lane group of the warp transposes its words through the warp's scratch sc
-// (32 x 5 words) so that each lane stores one 16-byte row of 8 pixels (hi or lo);
-// chunk is the first of the warp's two 16-pixel image chunks.
-__device__ __forceinline__ void synth_u(const TcArgs& A, const FreqC& fc, int r0, uint32_t p, uint32_t h,
-                                        const float4 (&sr)[2], float2* gs, unsigned char* a_hi, unsigned char* a_lo,
-                                        __nv_bfloat16* img, int chunk, uint32_t* sc, __nv_bfloat16* vimg) {
-    uint32_t whi[2], wlo[2], iw[4];
+// Producer work of one U slice (8 elements, K' = 16) for thread (p, h), h < 4: the
+// A slice in shared memory holds, at K' positions 4h .. 4h + 3 of row p, the bf16
+// hi / lo parts of (Re G, -Im G) of elements r0 + 2h + j (j < 2).  Their sums give
+// G to ~2^-17 relative for the epilogue (gs), and |G|^2 (hi / lo) goes to the V
+// slice r0 / 16 of this CTA.
+__device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const unsigned char* a_hi,
+                                          const unsigned char* a_lo, float2* gs, __nv_bfloat16* vimg) {
+    const uint32_t off = tc::tile16_offset(p, 8u * (h >> 1)) + 8u * (h & 1u);
+    const uint2 wh = *(const uint2*)(a_hi + off), wl = *(const uint2*)(a_lo + off);
+    const uint32_t hw[2] = {wh.x, wh.y}, lw[2] = {wl.x, wl.y};
     __nv_bfloat16 vh[2], vl[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        const int r = r0 + 2 * (int)h + j;
-        const float2 g = green_srec(sr[j], fc);
-        gs[(size_t)r * TP + p] = g;
-        __nv_bfloat16 h0, l0, h1, l1;
-        tc::split_bf16(g.x, h0, l0);
-        tc::split_bf16(-g.y, h1, l1);
-        whi[j] = pack2(h0, h1);
-        wlo[j] = pack2(l0, l1);
-        iw[2 * j] = pack2(h0, l0);
-        iw[2 * j + 1] = pack2(h1, l1) ^ 0x80008000u;   // split of +Im = -(split of -Im)
-        tc::split_bf16(g.x * g.x + g.y * g.y, vh[j], vl[j]);
+        const float re = __bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[j] & 0xffffu))) +
+                         __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[j] & 0xffffu)));
+        const float mim = __bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[j] >> 16))) +
+                          __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[j] >> 16)));
+        gs[(size_t)(r0 + 2 * (int)h + j) * TP + p] = make_float2(re, -mim);
+        tc::split_bf16(re * re + mim * mim, vh[j], vl[j]);
     }
-    const uint32_t off = tc::tile16_offset(p, 8u * (h >> 1)) + 8u * (h & 1u);
-    *(uint2*)(a_hi + off) = make_uint2(whi[0], whi[1]);
-    *(uint2*)(a_lo + off) = make_uint2(wlo[0], wlo[1]);
-    {
-        __nv_bfloat16* vs = vimg + (size_t)(r0 >> 4) * (2 * TP * 16);
-        const uint32_t voff = tc::tile16_offset(p, (uint32_t)(r0 & 15) + 2u * h) / 2;
-        *(uint32_t*)(vs + voff) = pack2(vh[0], vh[1]);
-        *(uint32_t*)(vs + TP * 16 + voff) = pack2(vl[0], vl[1]);
-    }
-    if (img) {
-        const int lane = (int)(p & 31u);
+    __nv_bfloat16* vs = vimg + (size_t)(r0 >> 4) * (2 * TP * 16);
+    const uint32_t voff = tc::tile16_offset(p, (uint32_t)(r0 & 15) + 2u * h) / 2;
+    *(uint32_t*)(vs + voff) = pack2(vh[0], vh[1]);
+    *(uint32_t*)(vs + TP * 16 + voff) = pack2(vl[0], vl[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Operand images of one frequency set, synthesised once at full occupancy from the
+// synthesis records:
+//   aimg (the adjoint's A operand): per frequency, tile of 128 pixels and K' slice
+//        j of 16 (elements 8j .. 8j + 7), a hi then a lo [128 rows x 16] image in the
+//        core-matrix layout, row x = pixel, K' = 2r + {0: Re G_r, 1: -Im G_r};
+//   gimg (the forward's B operand, optional): per frequency, 16-pixel chunks of a hi
+//        and a lo [2n rows (r' = 2r + {0: Re, 1: Im}) x 16 pixels] image (gimage_seg).
+// CTA (tile, element block of 16): thread (p, half) synthesises elements
+// 16 eb + 8 half + k (k < 8) at pixel p for every frequency; the A image rows are
+// written from registers, the forward image through a transpose in shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __restrict__ srec, FreqSet F,
+                                                      __nv_bfloat16* __restrict__ aimg, size_t a_stride,
+                                                      __nv_bfloat16* __restrict__ gimg, size_t g_stride) {
+    __shared__ __align__(16) __nv_bfloat16 s_t[2][32][TP];   // hi / lo, r' within the block, pixel
+    const int n = G.n_elem, n2 = 2 * n, nU = n2 / 16;
+    const int neb = n / 16;
+    const int tile = (int)blockIdx.x / neb, eb = (int)blockIdx.x % neb;
+    const int tid = threadIdx.x, p = tid & (TP - 1), half = tid >> 7;
+    const int px = tile * TP + p;
+    const bool valid = px < G.npix;
+    const int e0 = 16 * eb + 8 * half;
+    float4 sr[8];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) sc[lane * 5 + m] = iw[m];
-        __syncwarp();
-        const int g8 = lane >> 3, L = lane & 7, kp = L & 3, hl = L >> 2;
-        uint32_t w[8];
+    for (int k = 0; k < 8; ++k)
+        sr[k] = valid ? __ldg(srec + (size_t)(e0 + k) * G.npix + px) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const size_t cimg = (size_t)n2 * 16;
+    const int j = 2 * eb + half;   // the A slice of these 8 elements
+    for (int fw = 0; fw < F.n; ++fw) {
+        const FreqC& fc = F.f[fw];
+        uint32_t ah[4], al[4];   // one K-group (4 elements) of A row p, hi / lo
 #pragma unroll
-        for (int m = 0; m < 8; ++m) w[m] = sc[(8 * g8 + m) * 5 + kp];
-        __syncwarp();
-        const uint32_t sel = hl ? 0x7632u : 0x5410u;   // lo halves or hi halves of the 8 pixels' words
-        const uint4 row = make_uint4(__byte_perm(w[0], w[1], sel), __byte_perm(w[2], w[3], sel),
-                                     __byte_perm(w[4], w[5], sel), __byte_perm(w[6], w[7], sel));
-        const int rp = 2 * (r0 + 2 * (int)h + (kp >> 1)) + (kp & 1);
-        const size_t cimg = (size_t)2 * A.G.n_elem * 16;
-        __nv_bfloat16* base = img + (size_t)(chunk + (g8 >> 1)) * 2 * cimg + (hl ? cimg : 0) +
-                              tc::tile16_offset((uint32_t)rp, 8u * (g8 & 1)) / 2;
-        *(uint4*)base = row;
+        for (int kg = 0; kg < 2; ++kg) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * kg + q;
+                const float2 g = green_srec(sr[k], fc);
+                __nv_bfloat16 h0, l0, h1, l1;
+                tc::split_bf16(g.x, h0, l0);
+                tc::split_bf16(-g.y, h1, l1);
+                ah[q] = pack2(h0, h1);
+                al[q] = pack2(l0, l1);
+                if (gimg) {
+                    // forward image rows r' = 2e (Re) and 2e + 1 (+Im = -(split of -Im))
+                    const int rl = 16 * half + 2 * k;
+                    s_t[0][rl][p] = h0;
+                    s_t[1][rl][p] = l0;
+                    s_t[0][rl + 1][p] = __ushort_as_bfloat16(__bfloat16_as_ushort(h1) ^ 0x8000u);
+                    s_t[1][rl + 1][p] = __ushort_as_bfloat16(__bfloat16_as_ushort(l1) ^ 0x8000u);
+                }
+            }
+            __nv_bfloat16* dst = aimg + (size_t)fw * a_stride + ((size_t)tile * nU + j) * (2 * TP * 16) +
+                                 tc::tile16_offset((uint32_t)p, 8u * (uint32_t)kg) / 2;
+            *(uint4*)dst = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+            *(uint4*)(dst + TP * 16) = make_uint4(al[0], al[1], al[2], al[3]);
+        }
+        if (gimg) {
+            __syncthreads();
+            // 2 (hi / lo) x 32 rows x 16 groups of 8 pixels: 16 bytes each, four per thread;
+            // consecutive threads take consecutive pixel groups of a row
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const int id = it * 256 + tid;
+                const int hl = id >> 9, row = (id >> 4) & 31, pg = id & 15;
+                const uint4 v = *(const uint4*)&s_t[hl][row][8 * pg];
+                __nv_bfloat16* dst = gimg + (size_t)fw * g_stride + ((size_t)tile * 8 + (pg >> 1)) * 2 * cimg +
+                                     (hl ? cimg : 0) + tc::tile16_offset((uint32_t)(32 * eb + row), 8u * (pg & 1)) / 2;
+                *(uint4*)dst = v;
+            }
+            __syncthreads();
+        }
     }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint kernel: warp-specialised, NST-stage pipeline of K = 16 slices.
+//   warps 0..15 producers: pixel p = tid % 128 (TMEM lane), quarter h = tid / 128;
+//               from each U slice's A (in shared memory) they keep G for the
+//               epilogue (gs) and write the |G|^2 A slices of V; then the
+//               epilogues (TMEM -> registers);
+//   warp 16     MMA issuer (lane 0): waits for a stage, issues its MMAs and
+//               commits their completion to the stage's "empty" barrier;
+//   warp 17     loader (lane 0): bulk-copies A and B of each slice (U: the A image
+//               and S; V: the |G|^2 slices and W) into a stage as soon as the
+//               stage's previous contents have been used.
+// Per (tile, frequency) the slice sequence is U (2n / 16 slices) then V (n / 16).
+// Barriers: full[s] (bulk-copy bytes), empty[s] (the MMAs that read stage s done,
+// plus 16 producer-warp arrivals: A read), acc_full (last MMA of a phase done),
+// acc_empty (16 producer-warp arrivals: the epilogue has read the accumulator),
+// vready (16 producer-warp arrivals: the |G|^2 slices of this tile are written),
+// drain (MMA completion on the error path).  Every wait is bounded; a timeout
+// raises a shared flag that ends all loops.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full, s_acc_empty, s_vready;
+    __shared__ uint64_t s_full[NST], s_empty[NST], s_acc_full, s_acc_empty, s_vready, s_drain;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_err;
     __shared__ float s_red[3][3][TP];             // partial sums of quarters 1..3: Re g, Im g, H
-    __shared__ uint32_t s_tr[NPROD / 32][32 * 5];   // per producer warp: transpose scratch of the forward images
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nU = n2 / 16, nV = n / 16, per = nU + nV;
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
-            tc::mbar_init(tc::smem_u32(&s_full_a[s]), NPROD / 32);
-            tc::mbar_init(tc::smem_u32(&s_full_b[s]), 1);
-            tc::mbar_init(tc::smem_u32(&s_empty[s]), 1);
+            tc::mbar_init(tc::smem_u32(&s_full[s]), 1);
+            tc::mbar_init(tc::smem_u32(&s_empty[s]), 1 + NPROD / 32);
         }
         tc::mbar_init(tc::smem_u32(&s_acc_full), 1);
         tc::mbar_init(tc::smem_u32(&s_acc_empty), NPROD / 32);
         tc::mbar_init(tc::smem_u32(&s_vready), NPROD / 32);
+        tc::mbar_init(tc::smem_u32(&s_drain), 1);
         s_err = 0;
     }
     if (warp == 0) tc::tmem_alloc(tc::smem_u32(&s_tmem), A.tmem_cols);
@@ -290,27 +343,38 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     const uint32_t tmem = s_tmem;
     __nv_bfloat16* vimg = A.vimg + (size_t)blockIdx.x * (size_t)(n / 16) * (2 * TP * 16);
     const int my_tiles = (int)blockIdx.x < A.n_tiles ? (A.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const long long total = (long long)my_tiles * A.F.n * per;   // slices of this CTA
+    // slices of this CTA (a few thousand: 32-bit counters, stage and phase advanced
+    // incrementally, no divisions in the loops)
+    const int total = my_tiles * A.F.n * per;
     const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 16;  // bf16 per hi (or lo) / W image slice
     auto stage = [&](int s) { return smem + (size_t)s * ST_BYTES; };
 
     if (warp == NPROD / 32 + 1) {
-        // ------------------------------ B loader ------------------------------
+        // ------------------------------ loader ------------------------------
         if (lane == 0) {
-            long long ql = 0;
-            uint32_t vrp = 0;
+            int ql = 0, s = 0, j = 0, fw = 0, tile = blockIdx.x;
+            uint32_t ph = 0, vrp = 0;
             bool err = false;
             for (; ql < total; ++ql) {
-                const int s = (int)(ql % NST);
-                if (ql >= NST && !tc::mbar_wait(tc::smem_u32(&s_empty[s]), (uint32_t)((ql / NST) - 1) & 1u, kMaxTries)) {
+                // stage s = ql % NST with phase ph = (ql / NST) & 1; slice j of frequency fw of tile
+                if (ql >= NST && !tc::mbar_wait(tc::smem_u32(&s_empty[s]), ph ^ 1u, kMaxTries)) {
                     err = true;
                     break;
                 }
                 if (s_err) break;
-                const int fw = (int)((ql / per) % A.F.n), j = (int)(ql % per);
+                const uint32_t mb = tc::smem_u32(&s_full[s]);
                 if (j < nU) {
-                    tc::bulk_load(tc::smem_u32(stage(s) + ST_B), A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u,
-                                  (uint32_t)(n2 * 64), tc::smem_u32(&s_full_b[s]));
+                    const uint32_t abytes = 2u * TP * 16 * 2, bbytes = (uint32_t)(n2 * 64);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(abytes + bbytes)
+                                 : "memory");
+                    const __nv_bfloat16* asrc = A.aimg + (size_t)fw * A.aimg_stride + ((size_t)tile * nU + j) * (2 * TP * 16);
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc::smem_u32(stage(s))), "l"(asrc), "r"(abytes), "r"(mb)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc::smem_u32(stage(s) + ST_B)),
+                                 "l"(A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u), "r"(bbytes), "r"(mb)
+                                 : "memory");
                 } else {
                     if (j == nU) {
                         // this (tile, frequency)'s |G|^2 slices are written by the producers
@@ -320,7 +384,6 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                         }
                         ++vrp;
                     }
-                    const uint32_t mb = tc::smem_u32(&s_full_b[s]);
                     const uint32_t wbytes = (uint32_t)(n * 32), abytes = 2u * TP * 16 * 2;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(wbytes + abytes)
                                  : "memory");
@@ -333,12 +396,17 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                                  "r"(mb)
                                  : "memory");
                 }
+                if (++s == NST) { s = 0; ph ^= 1u; }
+                if (++j == per) {
+                    j = 0;
+                    if (++fw == A.F.n) { fw = 0; tile += gridDim.x; }
+                }
             }
             if (err || s_err) {
                 s_err = 1;
                 // bounded waits for the last copies issued (at most one per stage)
-                for (long long x = (ql > NST ? ql - NST : 0); x < ql; ++x)
-                    tc::mbar_wait(tc::smem_u32(&s_full_b[x % NST]), (uint32_t)(x / NST) & 1u, kMaxTries);
+                for (int x = (ql > NST ? ql - NST : 0); x < ql; ++x)
+                    tc::mbar_wait(tc::smem_u32(&s_full[x % NST]), (uint32_t)(x / NST) & 1u, kMaxTries);
             }
         }
         __syncwarp();
@@ -349,21 +417,16 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
             const int nb_u = n2 / nbk;
             const uint32_t id_u = tc::idesc_bf16_f32(128, (uint32_t)nb_u);
             const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)n);
-            long long last = -1;
-            uint32_t accp = 0;
-            bool err = false;
-            for (long long q = 0; q < total && !err; ++q) {
-                const int s = (int)(q % NST), j = (int)(q % per);
-                const uint32_t ph = (uint32_t)(q / NST) & 1u;
+            int s = 0, j = 0;
+            uint32_t accp = 0, ph = 0;
+            bool err = false, issued = false;
+            for (int q = 0; q < total && !err; ++q) {
                 if ((j == 0 || j == nU) && q > 0) {
                     // a new accumulation phase: the epilogue must have read the accumulator
                     if (!tc::mbar_wait(tc::smem_u32(&s_acc_empty), accp & 1u, kMaxTries)) { err = true; break; }
                     ++accp;
                 }
-                // U slices: A from the producers; V slices: A and B both by bulk copy (the
-                // producers' arrival then only marks the stage's turn)
-                if (!tc::mbar_wait(tc::smem_u32(&s_full_a[s]), ph, kMaxTries)) { err = true; break; }
-                if (!tc::mbar_wait(tc::smem_u32(&s_full_b[s]), ph, kMaxTries)) { err = true; break; }
+                if (!tc::mbar_wait(tc::smem_u32(&s_full[s]), ph, kMaxTries)) { err = true; break; }
                 if (s_err) { err = true; break; }
                 tc::fence_after();
                 const uint32_t sa = tc::smem_u32(stage(s)), sal = sa + ST_ALO, sb = sa + ST_B;
@@ -384,16 +447,20 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     tc::mma_bf16(tmem, dah, db, id_v, j > nU ? 1u : 0u);
                     tc::mma_bf16(tmem, dal, db, id_v, 1u);
                 }
+                issued = true;
                 tc::commit(tc::smem_u32(&s_empty[s]));
                 if (j == nU - 1 || j == per - 1) tc::commit(tc::smem_u32(&s_acc_full));
-                last = q;
+                if (++s == NST) { s = 0; ph ^= 1u; }
+                if (++j == per) j = 0;
             }
             if (err) {
                 s_err = 1;
                 atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
                 // bounded wait for the MMAs still in flight
-                if (last >= 0)
-                    tc::mbar_wait(tc::smem_u32(&s_empty[last % NST]), (uint32_t)(last / NST) & 1u, kMaxTries);
+                if (issued) {
+                    tc::commit(tc::smem_u32(&s_drain));
+                    tc::mbar_wait(tc::smem_u32(&s_drain), 0u, kMaxTries);
+                }
             }
         }
         __syncwarp();
@@ -403,18 +470,18 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         float2* gs = A.gscr + (size_t)blockIdx.x * n * TP;
         bool err = false;
-        long long q = 0;
+        int qs = 0;                // stage of the next slice
+        uint32_t qph = 0;          // its phase
         uint32_t accf = 0;
-        // one slice: wait for the stage, fill A, publish it
-        auto slice = [&](auto&& produce) {
-            const int s = (int)(q % NST);
-            if (!err && q >= NST) err = !tc::mbar_wait(tc::smem_u32(&s_empty[s]), (uint32_t)((q / NST) - 1) & 1u, kMaxTries);
+        // one slice: wait for its stage to be filled, use it, release it
+        auto slice = [&](auto&& consume) {
+            const int s = qs;
+            if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_full[s]), qph, kMaxTries);
             err = __any_sync(0xffffffffu, err || s_err != 0);
-            if (!err) produce(stage(s), stage(s) + ST_ALO);
-            tc::fence_proxy_async();
+            if (!err) consume(stage(s), stage(s) + ST_ALO);
             __syncwarp();
-            if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_full_a[s]));
-            ++q;
+            if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_empty[s]));
+            if (++qs == NST) { qs = 0; qph ^= 1u; }
         };
         // wait for the accumulator of the phase just issued (warp-uniform result)
         auto acc_wait = [&]() {
@@ -434,24 +501,16 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
             float acc_g = 0.f, acc_h = 0.f;
             for (int fw = 0; fw < A.F.n; ++fw) {
                 const FreqC fc = A.F.f[fw];
-                // ---- U slices; table records fetched one slice ahead ----
-                __nv_bfloat16* img = A.gimg ? A.gimg + (size_t)fw * A.gimg_stride : nullptr;
-                float4 nxt[2];
-                load_recs(A, 0, h, px, valid, nxt);
-                for (int j = 0; j < nU; ++j) {
-                    slice([&](unsigned char* ahi, unsigned char* alo) {
-                        float4 cur[2];
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) cur[k] = nxt[k];
-                        if (j + 1 < nU) load_recs(A, (j + 1) * 8, h, px, valid, nxt);
-                        synth_u(A, fc, j * 8, p, h, cur, gs, ahi, alo, img, tile * 8 + (warp & 3) * 2, s_tr[warp], vimg);
+                // ---- U slices: exact-enough G for the epilogue and the |G|^2 slices ----
+                for (int j = 0; j < nU; ++j)
+                    slice([&](const unsigned char* ahi, const unsigned char* alo) {
+                        consume_u(j * 8, p, h, ahi, alo, gs, vimg);
                     });
-                }
-                // the |G|^2 slices (read next by the bulk copies of the B loader) are complete
+                // the |G|^2 slices (read next by the bulk copies of the loader) are complete
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __syncwarp();
                 if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_vready));
-                // gs (exact G of the tile) is complete
+                // gs (G of the tile) is complete
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
                 // ---- U epilogue: element blocks b = h, h + 4, ... (32 elements; Re U in columns
@@ -488,9 +547,9 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
                     acc_g += gr;
                 }
-                // ---- V slices: A and B come by bulk copy; the producers only pass the stage
-                // barriers, which keeps every stage's full_a phases in step with its uses ----
-                for (int j = 0; j < nV; ++j) slice([&](unsigned char*, unsigned char*) {});
+                // ---- V slices: A and B come by bulk copy; the producers only pass the
+                // stage barriers, which keeps every stage's phases in step with its uses ----
+                for (int j = 0; j < nV; ++j) slice([&](const unsigned char*, const unsigned char*) {});
                 // ---- V epilogue ----
                 acc_wait();
                 float hh = 0.f;
@@ -554,28 +613,42 @@ cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_tc(const GeoDev& G, const float4* srec, const FreqSet& F, const void* images, float2* gscr,
+size_t tc_aimage_elems(int n_elem, int npix) {
+    return (size_t)((npix + TP - 1) / TP) * (size_t)(2 * n_elem / 16) * (2 * TP * 16);
+}
+
+cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, void* gimg,
+                                cudaStream_t s) {
+    if (!tc_adjoint_supported(G.n_elem) || !srec || !aimg) return cudaErrorInvalidValue;
+    const int n_tiles = (G.npix + TP - 1) / TP;
+    const long long blocks = (long long)n_tiles * (G.n_elem / 16);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_synth_images<<<(int)blocks, 256, 0, s>>>(G, srec, F, (__nv_bfloat16*)aimg, tc_aimage_elems(G.n_elem, G.npix),
+                                               (__nv_bfloat16*)gimg, tc_gimage_elems(G.n_elem, G.npix));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& F, const void* images, float2* gscr,
                               int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
-                              void* gimg, cudaStream_t s) {
+                              cudaStream_t s) {
     const int n = G.n_elem;
-    if (!tc_adjoint_supported(n) || !srec) return cudaErrorInvalidValue;
+    if (!tc_adjoint_supported(n) || !aimg) return cudaErrorInvalidValue;
     TcArgs A;
     A.G = G;
     A.F = F;
-    A.srec = srec;
+    A.aimg = (const __nv_bfloat16*)aimg;
+    A.aimg_stride = tc_aimage_elems(n, G.npix);
     A.bu = (const __nv_bfloat16*)images;
     A.bu_stride = tc_b_images_bytes(n) / 2;
     A.bw = A.bu + (size_t)(2 * n) * (2 * n) * 2;
     A.bw_stride = A.bu_stride;
     A.gscr = gscr;
-    A.vimg = (__nv_bfloat16*)(gscr + (size_t)RB_TC_MAX_CTAS * n * TP);   // after the exact-G scratch
+    A.vimg = (__nv_bfloat16*)(gscr + (size_t)RB_TC_MAX_CTAS * n * TP);   // after the G scratch
     A.g_out = g_out;
     A.h_out = h_out;
     A.gsum = gsum;
     A.hsum = hsum;
     A.counters = counters;
-    A.gimg = (__nv_bfloat16*)gimg;
-    A.gimg_stride = tc_gimage_elems(n, G.npix);
     A.n_tiles = (G.npix + TP - 1) / TP;
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * n)) cols <<= 1;

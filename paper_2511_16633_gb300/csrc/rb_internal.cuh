@@ -221,6 +221,7 @@ struct WsLayout {
     size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
     size_t tcfwd;      // tensor-core path: partial D blocks of the forward
     size_t gimg;       // tensor-core path: G operand images of the forward, [n_freq][...] bf16
+    size_t aimg;       // tensor-core path: A operand images of the adjoint, [n_freq][...] bf16
     size_t srec;       // tensor-core path: synthesis records, [n_elem][npix] float4
     size_t total;
 };
@@ -275,9 +276,13 @@ cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c
 cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F, const float* m, float* partial,
                               int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
                               cudaStream_t s);
-cudaError_t launch_adjoint_tc(const GeoDev& G, const float4* srec, const FreqSet& F, const void* images, float2* gscr,
+// A images of the adjoint (and optionally the forward's G images) from the synthesis records
+size_t tc_aimage_elems(int n_elem, int npix);
+cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, void* gimg,
+                                cudaStream_t s);
+cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& F, const void* images, float2* gscr,
                               int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
-                              void* gimg, cudaStream_t s);
+                              cudaStream_t s);
 cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);

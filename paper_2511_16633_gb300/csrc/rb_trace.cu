@@ -79,6 +79,10 @@ __device__ __forceinline__ void sample(const GeoDev& G, const float4* __restrict
 #undef RB_BL
 }
 
+// sincosf behind a call: the fallbacks below are (almost) never taken, and an inlined
+// copy per RK4 stage costs registers, a local-memory frame and issue slots on every step.
+__device__ __noinline__ void sincos_call(float x, float* s, float* c) { sincosf(x, s, c); }
+
 // cos/sin of (th_hi + d) from cos/sin of th_hi and a small d (Taylor to d^7).
 __device__ __forceinline__ void rotate(float C0, float S0, float th_hi, float d, float& c, float& s) {
     if (fabsf(d) < 0.2f) {
@@ -88,7 +92,7 @@ __device__ __forceinline__ void rotate(float C0, float S0, float th_hi, float d,
         c = C0 * cd - S0 * sd;
         s = S0 * cd + C0 * sd;
     } else {
-        sincosf(th_hi + d, &s, &c);
+        sincos_call(th_hi + d, &s, &c);
     }
 }
 
@@ -138,6 +142,14 @@ __device__ __forceinline__ void comp_add(float& hi, float& lo, float inc) {
     DF r = df_fast_two_sum(s.hi, __fadd_rn(lo, s.lo));
     hi = r.hi;
     lo = r.lo;
+}
+
+// Exact ring test of a float-pair position, in double.  Not inlined: GB300's FP64
+// pipe is slow, and an inlined copy would be predicated into every RK4 step
+// instead of running only on the few steps the float screen lets through.
+__device__ __noinline__ bool outside_ring(float xh, float xl, float yh, float yl, double R) {
+    const double dx = (double)xh + (double)xl, dy = (double)yh + (double)yl;
+    return dx * dx + dy * dy >= R * R;
 }
 
 __device__ __forceinline__ double exit_lambda(double ax, double ay, double bx, double by, double R) {
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
             // anchor follows the ray whenever it has turned by more than 0.05 rad
             if (fabsf(thh - tha) > 0.05f) {
                 tha = thh;
-                sincosf(tha, &Sa, &Ca);
+                sincos_call(tha, &Sa, &Ca);
             }
             const float dth = (thh - tha) + thl;
             const float rxh = xh - xs.hi, rxl = xl - xs.lo, ryh = yh - ys.hi, ryl = yl - ys.lo;
@@ -355,10 +367,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
             // exit test: float screen, then double decision
             const float fx = nxh + nxl, fy = nyh + nyl;
             bool out = false;
-            if (fx * fx + fy * fy >= G.R2 * (1.0f - 4e-6f)) {
-                const double dx = (double)nxh + (double)nxl, dy = (double)nyh + (double)nyl;
-                out = dx * dx + dy * dy >= G.R_d * G.R_d;
-            }
+            if (fx * fx + fy * fy >= G.R2 * (1.0f - 4e-6f)) out = outside_ring(nxh, nxl, nyh, nyl, G.R_d);
             if (out) {
                 const double ax = (double)xh + (double)xl, ay = (double)yh + (double)yl;
                 const double bx = (double)nxh + (double)nxl, by = (double)nyh + (double)nyl;
