@@ -25,7 +25,7 @@ constexpr uint32_t kMaxTries = 1u << 22; // mbarrier polls before giving up (eac
 // B operand images for one frequency, in K slices of 16 (one pipeline stage each)
 // in the core-matrix layout of rb_tc.cuh (tile16_offset).
 //   bu: [ks = 2n/16][hi|lo][2n rows x 16]   (2n rows = e', K = 2n)
-//   bw: [ks = n/16][n rows x 16]            (W, exact)
+//   bw: [ks = n/32][n rows x 32]            (W, exact; K = 32 slices, chunk_offset)
 // ---------------------------------------------------------------------------
 __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __restrict__ W,
                          __nv_bfloat16* __restrict__ bu, __nv_bfloat16* __restrict__ bw) {
@@ -51,12 +51,12 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
         bu[base + img_u + off] = lo;
     }
     const long long total_w = (long long)n * n;
-    const size_t img_w = (size_t)n * 16;
+    const size_t img_w = (size_t)n * 32;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total_w;
          j += (long long)gridDim.x * blockDim.x) {
         const int e = (int)(j / n), r = (int)(j % n);
-        const int ks = r >> 4, kk = r & 15;
-        bw[(size_t)ks * img_w + tc::tile16_offset((uint32_t)e, (uint32_t)kk) / 2] =
+        const int ks = r >> 5, kk = r & 31;
+        bw[(size_t)ks * img_w + tc::chunk_offset((uint32_t)e, (uint32_t)kk) / 2] =
             __float2bfloat16_rn(W[(size_t)e * n + r] ? 1.f : 0.f);
     }
 }
@@ -70,7 +70,7 @@ struct TcArgs {
     const __nv_bfloat16* bw;   // [n_freq][image]
     size_t bu_stride, bw_stride;  // bf16 elements per frequency
     float2* gscr;              // [gridDim.x][n][TP] exact G per CTA
-    __nv_bfloat16* vimg;       // [gridDim.x][n / 16][hi|lo][TP x 16] |G|^2 A slices of the Hessian contraction
+    __nv_bfloat16* vimg;       // [gridDim.x][n / 32][hi|lo][TP x 32] |G|^2 A slices of the Hessian contraction
     float2* g_out;             // [n_freq][npix] or null
     float* h_out;              // [n_freq][npix] or null
     float* gsum;               // [npix] or null (sum over w of Re g)
@@ -168,7 +168,8 @@ namespace {
 //   warp 17     B loader (lane 0): bulk-copies B slices (and, for V, the |G|^2 A
 //               slices) into stages as soon as the MMAs that read the stage's
 //               previous contents are done.
-// Per (tile, frequency) the slice sequence is U (2n / 16 slices) then V (n / 16).
+// Per (tile, frequency) the slice sequence is U (2n / 16 slices of K = 16) then V
+// (n / 32 slices of K = 32).
 // Barriers: full_a[s] (16 producer-warp arrivals), full_b[s] (bulk-copy bytes),
 // empty[s] (MMAs that read stage s done), acc_full (last MMA of a phase done),
 // acc_empty (16 producer-warp arrivals: the epilogue has read the accumulator),
@@ -182,6 +183,8 @@ constexpr int NTHR_F = NPROD_F + 64;
 constexpr int NST = 5;                       // pipeline stages
 constexpr uint32_t ST_BYTES = 40u * 1024u;   // A hi (4 KB) + A lo (4 KB) + B (<= 32 KB)
 constexpr uint32_t ST_ALO = 4096u, ST_B = 8192u;
+// V slices of the adjoint (K = 32): A hi (8 KB) + A lo (8 KB) + W (n rows x 32, <= 16 KB)
+constexpr uint32_t ST_VALO = 8192u, ST_VB = 16384u;
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
@@ -215,10 +218,10 @@ __device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const 
         gs[(size_t)(r0 + 2 * (int)h + j) * TP + p] = make_float2(re, -mim);
         tc::split_bf16(re * re + mim * mim, vh[j], vl[j]);
     }
-    __nv_bfloat16* vs = vimg + (size_t)(r0 >> 4) * (2 * TP * 16);
-    const uint32_t voff = tc::tile16_offset(p, (uint32_t)(r0 & 15) + 2u * h) / 2;
+    __nv_bfloat16* vs = vimg + (size_t)(r0 >> 5) * (2 * TP * 32);
+    const uint32_t voff = tc::chunk_offset(p, (uint32_t)(r0 & 31) + 2u * h) / 2;
     *(uint32_t*)(vs + voff) = pack2(vh[0], vh[1]);
-    *(uint32_t*)(vs + TP * 16 + voff) = pack2(vl[0], vl[1]);
+    *(uint32_t*)(vs + TP * 32 + voff) = pack2(vl[0], vl[1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -307,7 +310,8 @@ __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __
 //   warp 17     loader (lane 0): bulk-copies A and B of each slice (U: the A image
 //               and S; V: the |G|^2 slices and W) into a stage as soon as the
 //               stage's previous contents have been used.
-// Per (tile, frequency) the slice sequence is U (2n / 16 slices) then V (n / 16).
+// Per (tile, frequency) the slice sequence is U (2n / 16 slices of K = 16) then V
+// (n / 32 slices of K = 32).
 // Barriers: full[s] (bulk-copy bytes), empty[s] (the MMAs that read stage s done,
 // plus 16 producer-warp arrivals: A read), acc_full (last MMA of a phase done),
 // acc_empty (16 producer-warp arrivals: the epilogue has read the accumulator),
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nU = n2 / 16, nV = n / 16, per = nU + nV;
+    const int nU = n2 / 16, nV = n / 32, per = nU + nV;
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             tc::mbar_init(tc::smem_u32(&s_full[s]), 1);
@@ -341,12 +345,12 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    __nv_bfloat16* vimg = A.vimg + (size_t)blockIdx.x * (size_t)(n / 16) * (2 * TP * 16);
+    __nv_bfloat16* vimg = A.vimg + (size_t)blockIdx.x * (size_t)(n / 32) * (2 * TP * 32);
     const int my_tiles = (int)blockIdx.x < A.n_tiles ? (A.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // slices of this CTA (a few thousand: 32-bit counters, stage and phase advanced
     // incrementally, no divisions in the loops)
     const int total = my_tiles * A.F.n * per;
-    const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 16;  // bf16 per hi (or lo) / W image slice
+    const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 32;  // bf16 per hi (or lo) / W image slice
     auto stage = [&](int s) { return smem + (size_t)s * ST_BYTES; };
 
     if (warp == NPROD / 32 + 1) {
@@ -384,15 +388,15 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                         }
                         ++vrp;
                     }
-                    const uint32_t wbytes = (uint32_t)(n * 32), abytes = 2u * TP * 16 * 2;
+                    const uint32_t wbytes = (uint32_t)(n * 64), abytes = 2u * TP * 32 * 2;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(wbytes + abytes)
                                  : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 ::"r"(tc::smem_u32(stage(s) + ST_B)),
+                                 ::"r"(tc::smem_u32(stage(s) + ST_VB)),
                                  "l"(A.bw + (size_t)fw * A.bw_stride + (size_t)(j - nU) * img_w), "r"(wbytes), "r"(mb)
                                  : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 ::"r"(tc::smem_u32(stage(s))), "l"(vimg + (size_t)(j - nU) * (2 * TP * 16)), "r"(abytes),
+                                 ::"r"(tc::smem_u32(stage(s))), "l"(vimg + (size_t)(j - nU) * (2 * TP * 32)), "r"(abytes),
                                  "r"(mb)
                                  : "memory");
                 }
@@ -443,9 +447,15 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                         tc::mma_bf16(d, dal, dbh, id_u, 1u);
                     }
                 } else {
-                    const uint64_t db = tc::sdesc(sb, 128, 256);
-                    tc::mma_bf16(tmem, dah, db, id_v, j > nU ? 1u : 0u);
-                    tc::mma_bf16(tmem, dal, db, id_v, 1u);
+                    // K = 32 slice in the chunk_offset layout (SBO = 512): two K = 16 steps
+#pragma unroll
+                    for (int kh = 0; kh < 2; ++kh) {
+                        const uint64_t vah = tc::sdesc(sa + 256u * kh, 128, 512);
+                        const uint64_t val = tc::sdesc(sa + ST_VALO + 256u * kh, 128, 512);
+                        const uint64_t vb = tc::sdesc(sa + ST_VB + 256u * kh, 128, 512);
+                        tc::mma_bf16(tmem, vah, vb, id_v, (j > nU || kh > 0) ? 1u : 0u);
+                        tc::mma_bf16(tmem, val, vb, id_v, 1u);
+                    }
                 }
                 issued = true;
                 tc::commit(tc::smem_u32(&s_empty[s]));
@@ -513,25 +523,37 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 // gs (G of the tile) is complete
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
-                // ---- U epilogue: element blocks b = h, h + 4, ... (32 elements; Re U in columns
-                // [32 b, 32 b + 32), Im U in [n + 32 b, ...)), read 16 columns at a time ----
+                // ---- U epilogue: element chunks of 8, e0 = 32 b + 8 c for blocks b = h, h + 4, ...
+                // and c < 4 (Re U in column e, Im U in column n + e); G of the next chunk is
+                // loaded while the current one is used, the first before the accumulator wait ----
+                const int nch = 4 * ((n / 32 - (int)h + 3) / 4);
+                auto ce0 = [&](int k) { return 32 * ((int)h + 4 * (k >> 2)) + 8 * (k & 3); };
+                auto gload = [&](int k, float2 (&g)[8]) {
+                    const int e0 = ce0(k);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) g[i] = gs[(size_t)(e0 + i) * TP + p];
+                };
+                auto gchunk = [&](int k, const float2 (&g)[8], float& ar, float& ai) {
+                    const int e0 = ce0(k);
+                    float vr[8], vi[8];
+                    tc::tmem_ld8(tmem + lane_off + (uint32_t)e0, vr);
+                    tc::tmem_ld8(tmem + lane_off + (uint32_t)(n + e0), vi);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        ar = fmaf(g[i].x, vr[i], fmaf(g[i].y, vi[i], ar));
+                        ai = fmaf(g[i].x, vi[i], fmaf(-g[i].y, vr[i], ai));
+                    }
+                };
+                float2 ga[8], gb[8];
+                if (nch > 0) gload(0, ga);
                 acc_wait();
                 float gr = 0.f, gi = 0.f;
                 if (!err) {
-                    for (int b = (int)h; b < n / 32; b += 4) {
-#pragma unroll
-                        for (int hb = 0; hb < 2; ++hb) {
-                            const int c0 = 32 * b + 16 * hb;
-                            float vr[16], vi[16];
-                            tc::tmem_ld16(tmem + lane_off + (uint32_t)c0, vr);
-                            tc::tmem_ld16(tmem + lane_off + (uint32_t)(n + c0), vi);
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                const float2 ge = gs[(size_t)(c0 + k) * TP + p];
-                                gr = fmaf(ge.x, vr[k], fmaf(ge.y, vi[k], gr));
-                                gi = fmaf(ge.x, vi[k], fmaf(-ge.y, vr[k], gi));
-                            }
-                        }
+                    for (int k = 0; k < nch; k += 2) {
+                        gload(k + 1, gb);
+                        gchunk(k, ga, gr, gi);
+                        if (k + 2 < nch) gload(k + 2, ga);
+                        gchunk(k + 1, gb, gr, gi);
                     }
                 }
                 acc_release();
@@ -550,22 +572,22 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 // ---- V slices: A and B come by bulk copy; the producers only pass the
                 // stage barriers, which keeps every stage's phases in step with its uses ----
                 for (int j = 0; j < nV; ++j) slice([&](const unsigned char*, const unsigned char*) {});
-                // ---- V epilogue ----
+                // ---- V epilogue (same chunks, |G|^2 against V in columns e) ----
+                if (nch > 0) gload(0, ga);
                 acc_wait();
                 float hh = 0.f;
                 if (!err) {
-                    for (int b = (int)h; b < n / 32; b += 4) {
+                    auto hchunk = [&](int k, const float2 (&g)[8]) {
+                        float v[8];
+                        tc::tmem_ld8(tmem + lane_off + (uint32_t)ce0(k), v);
 #pragma unroll
-                        for (int hb = 0; hb < 2; ++hb) {
-                            const int c0 = 32 * b + 16 * hb;
-                            float v[16];
-                            tc::tmem_ld16(tmem + lane_off + (uint32_t)c0, v);
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                const float2 ge = gs[(size_t)(c0 + k) * TP + p];
-                                hh = fmaf(ge.x * ge.x + ge.y * ge.y, v[k], hh);
-                            }
-                        }
+                        for (int i = 0; i < 8; ++i) hh = fmaf(g[i].x * g[i].x + g[i].y * g[i].y, v[i], hh);
+                    };
+                    for (int k = 0; k < nch; k += 2) {
+                        gload(k + 1, gb);
+                        hchunk(k, ga);
+                        if (k + 2 < nch) gload(k + 2, ga);
+                        hchunk(k + 1, gb);
                     }
                 }
                 acc_release();

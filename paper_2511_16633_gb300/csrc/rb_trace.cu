@@ -280,6 +280,19 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
     }
 }
 
+// q / d and q % d for q < 2^31, d >= 1, with m = floor(2^32 / d): the high word of q m
+// is the quotient or one less.
+__device__ __forceinline__ void udivmod(uint32_t q, uint32_t d, uint32_t m, uint32_t& quo, uint32_t& rem) {
+    uint32_t x = __umulhi(q, m);
+    uint32_t r = q - x * d;
+    if (r >= d) {
+        ++x;
+        r -= d;
+    }
+    quo = x;
+    rem = r;
+}
+
 // Vertex k of ray i of fan t in the vertex stream: [fan][step][ray], 32 bytes each.
 __device__ __forceinline__ size_t vidx(const GeoDev& G, int t, int k, int i) {
     return ((size_t)t * (size_t)(G.max_steps + 1) + (size_t)k) * (size_t)G.n_rays + (size_t)i;
@@ -476,19 +489,21 @@ __device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
 }
 
 __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict__ verts,
-                                                const rb_ray_end* __restrict__ ends, unsigned long long* __restrict__ keys) {
+                                                const rb_ray_end* __restrict__ ends, unsigned long long* __restrict__ keys,
+                                                uint32_t nt_magic) {
     extern __shared__ short2 s_supp[];   // [ny]
     for (int iy = threadIdx.x; iy < G.ny; iy += blockDim.x) s_supp[iy] = support_row(G, iy);
     __syncthreads();
     const int NT = G.n_rays - 1;
     const int nkb = (G.max_steps + KB - 1) / KB;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
-    const long long total = (long long)G.n_elem * nkb * NT;
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
-         u += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(u % NT);
-        const long long rest = u / NT;
-        const int kb = (int)(rest % nkb), t = (int)(rest / nkb);
+    const int per_fan = nkb * NT;   // < 2^31 (the triangle ids fit 24 bits)
+    // fans t = blockIdx.y + k gridDim.y; within a fan, item = kb NT + i
+    for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y)
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < per_fan; item += gridDim.x * blockDim.x) {
+        uint32_t ukb, ui;
+        udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukb, ui);
+        const int i = (int)ui, kb = (int)ukb;
         const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
         const int k0 = kb * KB + 1, k1 = min(k0 + KB - 1, max(la, lb));
         if (k0 > k1) continue;
@@ -507,70 +522,75 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
 
 // Completes every hit record: from the winning triangle id in the tag, its vertices
 // and the pixel, the barycentric weights (bit-identical to the rasteriser's), then
-// Q, L and the KMAH index of the heaviest vertex.  Holes stay all ones.
+// Q, L and the KMAH index of the heaviest vertex.  Holes stay all ones.  Thread =
+// pixel (its coordinates and support test computed once), looping over the
+// elements t = blockIdx.y, blockIdx.y + gridDim.y, ...; consecutive threads take
+// consecutive pixels, so every key load and record store is coalesced.
 __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict__ verts,
                                                  const rb_ray_end* __restrict__ ends,
                                                  const unsigned long long* __restrict__ keys, rb_cell* __restrict__ tables,
                                                  const float* __restrict__ c, float4* __restrict__ srec,
-                                                 uint32_t* __restrict__ counters) {
+                                                 uint32_t* __restrict__ counters, uint32_t kq_magic) {
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
-    const long long total = (long long)G.n_elem * G.npix;
     uint32_t holes = 0;   // support pixels that no triangle of the fan covered
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
-         u += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long key = keys[u];
-        const uint2 kv = make_uint2((uint32_t)key, (uint32_t)(key >> 32));   // {tag, tkey}
-        if (kv.y == RB_HOLE) {
-            if (tables) {
-                rb_cell hole;
-                hole.tag = RB_HOLE;
-                hole.tkey = RB_HOLE;
-                hole.q = __uint_as_float(RB_HOLE);
-                hole.l = __uint_as_float(RB_HOLE);
-                tables[u] = hole;
-            }
-            if (srec) srec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int hp = (int)(u % G.npix);
-            const long long jx = 2LL * (hp % G.nx) - (G.nx - 1), jy = 2LL * (hp / G.nx) - (G.ny - 1);
-            if (jx * jx + jy * jy <= G.r2max) ++holes;
-            continue;
-        }
-        const int t = (int)(u / G.npix), pix = (int)(u % G.npix);
-        const uint32_t id = kv.x >> 8;
-        const int half = (int)(id & 1u);
-        const uint32_t qk = id >> 1;
-        // ids come from the rasteriser (i + 1 < n_rays, 1 <= k1 <= max_steps); clamped all the same
-        const int i = min((int)(qk / KQ), G.n_rays - 2), k1 = min((int)(qk % KQ) + 1, G.max_steps);
-        const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
-        const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
-        const Vtx A1 = get_vtx(verts + vidx(G, t, min(k1, la), i));
-        const Vtx B0 = get_vtx(verts + vidx(G, t, min(k1 - 1, lb), i + 1));
-        const Vtx B1 = get_vtx(verts + vidx(G, t, min(k1, lb), i + 1));
-        const Quad Q = quad_of(A0, A1, B0, B1);
-        const int ix = pix % G.nx, iy = pix / G.nx;
+    for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < G.npix; pix += gridDim.x * blockDim.x) {
+        const int iy = pix / G.nx, ix = pix - iy * G.nx;
         const DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
         const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
-        const float dx = rel(X.hi, X.lo, A0.xh, A0.xl), dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
-        float wa, wb, wc;
-        const Vtx& Vb = half ? B1 : B0;
-        const Vtx& Vc = half ? A1 : B1;
-        if (half) bary(Q.b1x, Q.b1y, Q.a1x, Q.a1y, Q.i1, dx, dy, wa, wb, wc);
-        else bary(Q.b0x, Q.b0y, Q.b1x, Q.b1y, Q.i0, dx, dy, wa, wb, wc);
-        int kap = A0.k;
-        float wbest = wa;
-        if (wb > wbest) { kap = Vb.k; wbest = wb; }
-        if (wc > wbest) kap = Vc.k;
-        rb_cell rec;
-        rec.tag = (id << 8) | (uint32_t)min(kap, 255);
-        rec.tkey = kv.y;
-        rec.q = interp(wa, wb, wc, A0.q, Vb.q, Vc.q);
-        rec.l = interp(wa, wb, wc, A0.l, Vb.l, Vc.l);
-        if (tables) tables[u] = rec;
-        if (srec) {
-            DF ex, ey;
-            elem_pos(G, t, ex, ey);
-            srec[u] = synth_record(rec, __ldg(c + pix), pixel_elem_dist(G, ix, iy, ex, ey), G.inv_cref, G.inv_cref_lo,
-                                   G.j_floor);
+        const long long jx = 2LL * ix - (G.nx - 1), jy = 2LL * iy - (G.ny - 1);
+        const bool in_support = jx * jx + jy * jy <= G.r2max;
+        const float c_px = srec ? __ldg(c + pix) : 0.f;
+        for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y) {
+            const size_t u = (size_t)t * G.npix + pix;
+            const unsigned long long key = keys[u];
+            const uint2 kv = make_uint2((uint32_t)key, (uint32_t)(key >> 32));   // {tag, tkey}
+            if (kv.y == RB_HOLE) {
+                if (tables) {
+                    rb_cell hole;
+                    hole.tag = RB_HOLE;
+                    hole.tkey = RB_HOLE;
+                    hole.q = __uint_as_float(RB_HOLE);
+                    hole.l = __uint_as_float(RB_HOLE);
+                    tables[u] = hole;
+                }
+                if (srec) srec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (in_support) ++holes;
+                continue;
+            }
+            const uint32_t id = kv.x >> 8;
+            const int half = (int)(id & 1u);
+            uint32_t qi, qk1;
+            udivmod(id >> 1, KQ, kq_magic, qi, qk1);
+            // ids come from the rasteriser (i + 1 < n_rays, 1 <= k1 <= max_steps); clamped all the same
+            const int i = min((int)qi, G.n_rays - 2), k1 = min((int)qk1 + 1, G.max_steps);
+            const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+            const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
+            const Vtx A1 = get_vtx(verts + vidx(G, t, min(k1, la), i));
+            const Vtx B0 = get_vtx(verts + vidx(G, t, min(k1 - 1, lb), i + 1));
+            const Vtx B1 = get_vtx(verts + vidx(G, t, min(k1, lb), i + 1));
+            const Quad Q = quad_of(A0, A1, B0, B1);
+            const float dx = rel(X.hi, X.lo, A0.xh, A0.xl), dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
+            float wa, wb, wc;
+            const Vtx& Vb = half ? B1 : B0;
+            const Vtx& Vc = half ? A1 : B1;
+            if (half) bary(Q.b1x, Q.b1y, Q.a1x, Q.a1y, Q.i1, dx, dy, wa, wb, wc);
+            else bary(Q.b0x, Q.b0y, Q.b1x, Q.b1y, Q.i0, dx, dy, wa, wb, wc);
+            int kap = A0.k;
+            float wbest = wa;
+            if (wb > wbest) { kap = Vb.k; wbest = wb; }
+            if (wc > wbest) kap = Vc.k;
+            rb_cell rec;
+            rec.tag = (id << 8) | (uint32_t)min(kap, 255);
+            rec.tkey = kv.y;
+            rec.q = interp(wa, wb, wc, A0.q, Vb.q, Vc.q);
+            rec.l = interp(wa, wb, wc, A0.l, Vb.l, Vc.l);
+            if (tables) tables[u] = rec;
+            if (srec) {
+                DF ex, ey;
+                elem_pos(G, t, ex, ey);
+                srec[u] = synth_record(rec, c_px, pixel_elem_dist(G, ix, iy, ex, ey), G.inv_cref, G.inv_cref_lo,
+                                       G.j_floor);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) holes += __shfl_down_sync(0xffffffffu, holes, o);
@@ -603,10 +623,17 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         nsm = 148;
-    k_raster<<<nsm * 16, 256, (size_t)G.ny * sizeof(short2), s>>>(G, V, ends, K);
+    const int ry = G.n_elem < 16 ? G.n_elem : 16;
+    k_raster<<<dim3(nsm * 16 / ry, ry), 256, (size_t)G.ny * sizeof(short2), s>>>(
+        G, V, ends, K, (uint32_t)(0x100000000ull / (uint32_t)(G.n_rays - 1)));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resolve<<<nsm * 8, 256, 0, s>>>(G, V, ends, K, tables, c, srec, counters);
+    const uint32_t KQ = (uint32_t)(G.max_steps + 1);
+    const uint32_t kq_magic = (uint32_t)(0x100000000ull / KQ);
+    int bx = (G.npix + 255) / 256;
+    int by = 1;
+    while (by < 16 && by * 2 <= G.n_elem && (long long)bx * by < (long long)nsm * 16) by *= 2;
+    k_resolve<<<dim3(bx, by), 256, 0, s>>>(G, V, ends, K, tables, c, srec, counters, kq_magic);
     return cudaGetLastError();
 }
 
