@@ -957,10 +957,13 @@ FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const __nv_bfloat16* gimg
     uint32_t cols = 32;
     while (cols < (uint32_t)n2) cols <<= 1;
     A.tmem_cols = cols;
-    // splits per row block in proportion to the number of column blocks it computes
+    // splits per row block: equal.  A pixel slice costs about the same on every row
+    // block, whether it issues MMAs for one column block or two (the operand delivery
+    // and producer work per slice, not the tensor pipe, set the pace), so splits in
+    // proportion to the column blocks left the lower row blocks twice as long.
     int wsum = 0, wts[FMAXB];
     for (int i = 0; i < A.n_mb; ++i) {
-        wts[i] = A.nbn - jmin_of(i, A.nb);
+        wts[i] = 1;
         wsum += wts[i];
     }
     int c0 = 0;
