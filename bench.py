@@ -110,7 +110,7 @@ ADJ_ISSUE_RATIO = 2.8
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512
 # (ncu --metrics, 1 pass; profiles/k_adjoint_tc.md), None when not measured for the
 # kernel as built.
-ADJ_TRAFFIC_BYTES = 6037211904 + 5165807104
+ADJ_TRAFFIC_BYTES = None
 
 
 def run_ours(args):
@@ -259,11 +259,22 @@ def run_ours(args):
     roof_adj = contraction_roof("adjoint", work["adjoint_flop"], "k_adjoint_tc" if tc else "k_adjoint_simt",
                                 ADJ_ISSUE_RATIO)
     roof_fwd = contraction_roof("forward", work["forward_flop"], "k_forward_tc" if tc else "k_forward_simt", fwd_ratio)
-    # the dominant kernel: the adjoint contraction (one launch per update; its stage adds
-    # only the B-image preparation, under 1 % of it)
+    # the dominant kernel: the adjoint contraction (one launch per update, alone in its stage)
     roof = dict(roof_adj)
     if tc:
         roof["traffic"] = ADJ_TRAFFIC_BYTES
+    # the operand-image synthesis (mixed path): HBM-bound; algorithmic bytes = the synthesis
+    # records read once and the operand image (bf16 hi and lo of 2n x npix) of every
+    # frequency of the set written once
+    roof_img = None
+    if tc and st.get("images", 0.0) > 0:
+        npix = cfg.nx * cfg.ny
+        img_bytes = cfg.n_elem * npix * 16.0 + nf * (2 * cfg.n_elem) * npix * 2 * 2.0
+        ach = img_bytes / (st["images"] / 1e3) / 1e9
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof_img = {"kernel": "k_synth_images", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "bytes_per_launch": img_bytes,
+                    "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"}
     line = {
         "metric": METRIC, "value": R["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
@@ -276,6 +287,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "p50_ms": R["p50_ms"], "p99_ms": R["p99_ms"], "stage_ms": st, "wall_s": R["wall_s"],
         "roofline": roof, "roofline_contractions": {"adjoint": roof_adj, "forward": roof_fwd},
+        "roofline_images": roof_img,
         "clocks": R["clocks"], "e2e": R["e2e"],
         # launches per update: positions, fields, trace/raster/resolve, link, residual keys and
         # the three selection passes, adjoint (+ the operand-image synthesis and one B-image

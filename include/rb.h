@@ -122,6 +122,7 @@ typedef enum {
     RB_STAGE_FIELDS = 0,    /* derivative grids */
     RB_STAGE_TRACE_GRID,    /* fused ray fans + first-arrival gridding */
     RB_STAGE_LINK,          /* ray linking, residuals, data weights */
+    RB_STAGE_IMAGES,        /* tensor-core operand images of the set (BF16X3; empty for FP32) */
     RB_STAGE_ADJOINT,       /* Born adjoint + Hessian diagonal over the set */
     RB_STAGE_DIRECTION,     /* eps, direction, numerator of the step */
     RB_STAGE_FORWARD,       /* Born forward of the direction over the set (step mode exact) */

@@ -160,7 +160,6 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     // exact G per persistent CTA, then its |G|^2 A slices (bf16 hi and lo)
     L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * (8 + 4) : 0));
     L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
-    L->gimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_gimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->srec = o; o = align256(o + (tcp ? ne * npix * 16 : 0));
     L->aimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_aimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->total = o;
@@ -268,8 +267,9 @@ rb_status rb_born_forward(const rb_geometry* geom, const rb_cell* tables, const 
         FreqSet F1;
         F1.n = 1;
         F1.f[0] = F;
-        RB_CU(launch_gimage(G, tables, c, F1, W.at<void>(W.L.gimg), s));
-        RB_CU(launch_forward_tc(G, W.at<void>(W.L.gimg), F, m, W.at<float>(W.L.tcfwd), tc_ctas(), (float2*)d_out,
+        RB_CU(launch_srec(G, tables, c, W.at<float4>(W.L.srec), s));
+        RB_CU(launch_synth_images(G, W.at<float4>(W.L.srec), F1, W.at<void>(W.L.aimg), s));
+        RB_CU(launch_forward_tc(G, W.at<void>(W.L.aimg), F, m, W.at<float>(W.L.tcfwd), tc_ctas(), (float2*)d_out,
                                 nullptr, nullptr, cnt, s));
     } else {
         RB_CU(launch_forward_simt(G, tables, c, F, m, W.at<float2>(W.L.fwd), nch, s));
@@ -301,7 +301,7 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
         RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
         RB_CU(launch_prep_b(G.n_elem, (const float2*)resid, w, W.at<void>(W.L.tcimg), s));
         RB_CU(launch_srec(G, tables, c, W.at<float4>(W.L.srec), s));
-        RB_CU(launch_synth_images(G, W.at<float4>(W.L.srec), F, W.at<void>(W.L.aimg), nullptr, s));
+        RB_CU(launch_synth_images(G, W.at<float4>(W.L.srec), F, W.at<void>(W.L.aimg), s));
         RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
                                 (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, s));
     } else {
@@ -366,13 +366,16 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, W.at<void>(W.L.sel), s));
     RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, W.at<void>(W.L.sel), s));
     RB_CU(mark(RB_STAGE_LINK, 1));
-    RB_CU(mark(RB_STAGE_ADJOINT, 0));
+    RB_CU(mark(RB_STAGE_IMAGES, 0));
     if (prec == RB_PREC_BF16X3) {
         const size_t img = tc_b_images_bytes(G.n_elem);
         for (int w = 0; w < n_freq; ++w)
             RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
-        RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg),
-                                  params->step_mode == RB_STEP_EXACT ? W.at<void>(W.L.gimg) : nullptr, s));
+        RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg), s));
+    }
+    RB_CU(mark(RB_STAGE_IMAGES, 1));
+    RB_CU(mark(RB_STAGE_ADJOINT, 0));
+    if (prec == RB_PREC_BF16X3) {
         RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
                                 nullptr, nullptr, gsum, hsum, cnt, s));
     } else {
@@ -387,7 +390,7 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     if (params->step_mode == RB_STEP_EXACT) {
         for (int w = 0; w < n_freq; ++w) {
             if (prec == RB_PREC_BF16X3) {
-                RB_CU(launch_forward_tc(G, W.at<char>(W.L.gimg) + (size_t)w * tc_gimage_elems(G.n_elem, G.npix) * 2,
+                RB_CU(launch_forward_tc(G, W.at<char>(W.L.aimg) + (size_t)w * tc_aimage_elems(G.n_elem, G.npix) * 2,
                                         F.f[w], pdir, W.at<float>(W.L.tcfwd), tc_ctas(), nullptr,
                                         wts + (size_t)w * ne2, part + (size_t)w * 256, cnt, s));
             } else {

@@ -13,6 +13,8 @@
 // keeps ~2^-16 relative accuracy per product.  The epilogue uses the exact fp32
 // G values, kept per CTA in a small L2-resident scratch while the K loop streams
 // bf16 chunks of A through shared memory.
+#include <cuda.h>
+
 #include "rb_internal.cuh"
 #include "rb_tc.cuh"
 
@@ -64,7 +66,7 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
 struct TcArgs {
     GeoDev G;
     FreqSet F;
-    const __nv_bfloat16* aimg; // [n_freq][tiles][2n / 16 slices][hi|lo][TP x 16] A images (k_synth_images)
+    const __nv_bfloat16* aimg; // [n_freq][tiles][hi|lo][2n / 8 rows][1024] A image (k_synth_images)
     size_t aimg_stride;        // bf16 elements per frequency
     const __nv_bfloat16* bu;   // [n_freq][image]
     const __nv_bfloat16* bw;   // [n_freq][image]
@@ -79,64 +81,6 @@ struct TcArgs {
     int n_tiles;
     uint32_t tmem_cols;
 };
-
-// G operand image of the forward, per frequency: chunks of 16 pixels (one K = 16
-// pipeline slice of the forward), each a hi image then a lo image of 2n rows
-// (r' = 2r + {0: Re, 1: Im}) x 16 pixels in the core-matrix layout (tile16_offset).
-// One call writes the 8-pixel segment starting at pixel pix0 (a multiple of 8) for
-// element r.
-__device__ __forceinline__ void gimage_seg(__nv_bfloat16* img, int n, int pix0, int r, const float2 (&g)[8]) {
-    const int chunk = pix0 >> 4, kg = (pix0 & 15) >> 3;
-    const size_t cimg = (size_t)2 * n * 16;
-    __nv_bfloat16* base = img + (size_t)chunk * 2 * cimg;
-#pragma unroll
-    for (int part = 0; part < 2; ++part) {
-        uint32_t wh[4], wl[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            __nv_bfloat16 h0, l0, h1, l1;
-            tc::split_bf16(part == 0 ? g[2 * j].x : g[2 * j].y, h0, l0);
-            tc::split_bf16(part == 0 ? g[2 * j + 1].x : g[2 * j + 1].y, h1, l1);
-            wh[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            wl[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-        }
-        const uint32_t off = tc::tile16_offset((uint32_t)(2 * r + part), 8u * kg) / 2;
-        *(uint4*)(base + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-        *(uint4*)(base + cimg + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-    }
-}
-
-// Standalone G images: G_r(x) for every element and pixel at each frequency.
-__global__ void k_gimage(GeoDev G, const rb_cell* __restrict__ tables, const float* __restrict__ c, FreqSet F,
-                         __nv_bfloat16* __restrict__ img, size_t stride) {
-    const int n = G.n_elem;
-    const int nseg = (G.npix + 7) / 8;
-    const long long total = (long long)n * nseg;
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(u % n), seg = (int)(u / n);
-        DF ex, ey;
-        elem_pos(G, r, ex, ey);
-        rb_cell rec[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int pix = 8 * seg + j;
-            if (pix < G.npix) rec[j] = tables[(size_t)r * G.npix + pix];
-            else rec[j].tkey = RB_HOLE;
-        }
-        for (int w = 0; w < F.n; ++w) {
-            float2 g[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int pix = 8 * seg + j;
-                g[j] = make_float2(0.f, 0.f);
-                if (rec[j].tkey != RB_HOLE)
-                    g[j] = green_eval(rec[j], __ldg(c + pix), pixel_elem_dist(G, pix % G.nx, pix / G.nx, ex, ey), F.f[w],
-                                      G.j_floor);
-            }
-            gimage_seg(img + (size_t)w * stride, n, 8 * seg, r, g);
-        }
-    }
-}
 
 // Synthesis records of every element and pixel from the tables.
 __global__ void k_srec(GeoDev G, const rb_cell* __restrict__ tables, const float* __restrict__ c,
@@ -199,13 +143,15 @@ __device__ __forceinline__ void store_row16(unsigned char* a_hi, unsigned char* 
 }
 
 // Producer work of one U slice (8 elements, K' = 16) for thread (p, h), h < 4: the
-// A slice in shared memory holds, at K' positions 4h .. 4h + 3 of row p, the bf16
+// A slice in shared memory (two rows of the A image, see k_synth_images) holds, at
+// K' positions 4h .. 4h + 3 of row p, the bf16
 // hi / lo parts of (Re G, -Im G) of elements r0 + 2h + j (j < 2).  Their sums give
 // G to ~2^-17 relative for the epilogue (gs), and |G|^2 (hi / lo) goes to the V
 // slice r0 / 16 of this CTA.
 __device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const unsigned char* a_hi,
                                           const unsigned char* a_lo, float2* gs, __nv_bfloat16* vimg) {
-    const uint32_t off = tc::tile16_offset(p, 8u * (h >> 1)) + 8u * (h & 1u);
+    // A slice = two image rows (K cores) of 2 KB: K core h / 2, pixel core p / 8, row p % 8
+    const uint32_t off = (h >> 1) * 2048u + (p >> 3) * 128u + (p & 7u) * 16u + 8u * (h & 1u);
     const uint2 wh = *(const uint2*)(a_hi + off), wl = *(const uint2*)(a_lo + off);
     const uint32_t hw[2] = {wh.x, wh.y}, lw[2] = {wl.x, wl.y};
     __nv_bfloat16 vh[2], vl[2];
@@ -225,22 +171,20 @@ __device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const 
 }
 
 // ---------------------------------------------------------------------------
-// Operand images of one frequency set, synthesised once at full occupancy from the
-// synthesis records:
-//   aimg (the adjoint's A operand): per frequency, tile of 128 pixels and K' slice
-//        j of 16 (elements 8j .. 8j + 7), a hi then a lo [128 rows x 16] image in the
-//        core-matrix layout, row x = pixel, K' = 2r + {0: Re G_r, 1: -Im G_r};
-//   gimg (the forward's B operand, optional): per frequency, 16-pixel chunks of a hi
-//        and a lo [2n rows (r' = 2r + {0: Re, 1: Im}) x 16 pixels] image (gimage_seg).
+// Operand image of one frequency set, synthesised once at full occupancy from the
+// synthesis records.  Per frequency, tile of 128 pixels and plane (bf16 hi, lo):
+// n / 4 rows, row rc holding r' = 8 rc .. 8 rc + 7 (r' = 2r + {0: Re G_r, 1: -Im G_r})
+// for the 128 pixels as 16 core matrices of 8 pixels x 16 bytes:
+//   element (rc, x, r') at rc * 1024 + (x / 8) * 64 + (x % 8) * 8 + r' % 8.
+// The adjoint reads it K-major (a K = 16 slice is two rows: one 4 KB bulk copy per
+// plane), the forward MN-major (a 16-pixel slice of every row is one 2-D TMA box).
 // CTA (tile, element block of 16): thread (p, half) synthesises elements
-// 16 eb + 8 half + k (k < 8) at pixel p for every frequency; the A image rows are
-// written from registers, the forward image through a transpose in shared memory.
+// 16 eb + 8 half + k (k < 8) at pixel p for every frequency and writes rows
+// 4 eb + 2 half + {0, 1} of the pixel's core row (coalesced: 128 threads, 2 KB).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __restrict__ srec, FreqSet F,
-                                                      __nv_bfloat16* __restrict__ aimg, size_t a_stride,
-                                                      __nv_bfloat16* __restrict__ gimg, size_t g_stride) {
-    __shared__ __align__(16) __nv_bfloat16 s_t[2][32][TP];   // hi / lo, r' within the block, pixel
-    const int n = G.n_elem, n2 = 2 * n, nU = n2 / 16;
+                                                      __nv_bfloat16* __restrict__ aimg, size_t a_stride) {
+    const int n = G.n_elem, rcn = 2 * n / 8;
     const int neb = n / 16;
     const int tile = (int)blockIdx.x / neb, eb = (int)blockIdx.x % neb;
     const int tid = threadIdx.x, p = tid & (TP - 1), half = tid >> 7;
@@ -251,50 +195,25 @@ __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         sr[k] = valid ? __ldg(srec + (size_t)(e0 + k) * G.npix + px) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const size_t cimg = (size_t)n2 * 16;
-    const int j = 2 * eb + half;   // the A slice of these 8 elements
+    const size_t pix_off = (size_t)(p >> 3) * 64 + (size_t)(p & 7) * 8;
     for (int fw = 0; fw < F.n; ++fw) {
         const FreqC& fc = F.f[fw];
-        uint32_t ah[4], al[4];   // one K-group (4 elements) of A row p, hi / lo
+        __nv_bfloat16* plane = aimg + (size_t)fw * a_stride + (size_t)tile * 2 * rcn * 1024;
 #pragma unroll
         for (int kg = 0; kg < 2; ++kg) {
+            uint32_t ah[4], al[4];   // 8 r' (4 elements) of this pixel, hi / lo
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int k = 4 * kg + q;
-                const float2 g = green_srec(sr[k], fc);
+                const float2 g = green_srec(sr[4 * kg + q], fc);
                 __nv_bfloat16 h0, l0, h1, l1;
                 tc::split_bf16(g.x, h0, l0);
                 tc::split_bf16(-g.y, h1, l1);
                 ah[q] = pack2(h0, h1);
                 al[q] = pack2(l0, l1);
-                if (gimg) {
-                    // forward image rows r' = 2e (Re) and 2e + 1 (+Im = -(split of -Im))
-                    const int rl = 16 * half + 2 * k;
-                    s_t[0][rl][p] = h0;
-                    s_t[1][rl][p] = l0;
-                    s_t[0][rl + 1][p] = __ushort_as_bfloat16(__bfloat16_as_ushort(h1) ^ 0x8000u);
-                    s_t[1][rl + 1][p] = __ushort_as_bfloat16(__bfloat16_as_ushort(l1) ^ 0x8000u);
-                }
             }
-            __nv_bfloat16* dst = aimg + (size_t)fw * a_stride + ((size_t)tile * nU + j) * (2 * TP * 16) +
-                                 tc::tile16_offset((uint32_t)p, 8u * (uint32_t)kg) / 2;
-            *(uint4*)dst = make_uint4(ah[0], ah[1], ah[2], ah[3]);
-            *(uint4*)(dst + TP * 16) = make_uint4(al[0], al[1], al[2], al[3]);
-        }
-        if (gimg) {
-            __syncthreads();
-            // 2 (hi / lo) x 32 rows x 16 groups of 8 pixels: 16 bytes each, four per thread;
-            // consecutive threads take consecutive pixel groups of a row
-#pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                const int id = it * 256 + tid;
-                const int hl = id >> 9, row = (id >> 4) & 31, pg = id & 15;
-                const uint4 v = *(const uint4*)&s_t[hl][row][8 * pg];
-                __nv_bfloat16* dst = gimg + (size_t)fw * g_stride + ((size_t)tile * 8 + (pg >> 1)) * 2 * cimg +
-                                     (hl ? cimg : 0) + tc::tile16_offset((uint32_t)(32 * eb + row), 8u * (pg & 1)) / 2;
-                *(uint4*)dst = v;
-            }
-            __syncthreads();
+            const int rc = 4 * eb + 2 * half + kg;
+            *(uint4*)(plane + (size_t)rc * 1024 + pix_off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+            *(uint4*)(plane + (size_t)(rcn + rc) * 1024 + pix_off) = make_uint4(al[0], al[1], al[2], al[3]);
         }
     }
 }
@@ -368,12 +287,18 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 if (s_err) break;
                 const uint32_t mb = tc::smem_u32(&s_full[s]);
                 if (j < nU) {
-                    const uint32_t abytes = 2u * TP * 16 * 2, bbytes = (uint32_t)(n2 * 64);
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(abytes + bbytes)
+                    const uint32_t abytes = TP * 16 * 2, bbytes = (uint32_t)(n2 * 64);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * abytes + bbytes)
                                  : "memory");
-                    const __nv_bfloat16* asrc = A.aimg + (size_t)fw * A.aimg_stride + ((size_t)tile * nU + j) * (2 * TP * 16);
+                    // image rows 2j, 2j + 1 of the hi plane, then of the lo plane
+                    const __nv_bfloat16* asrc =
+                        A.aimg + (size_t)fw * A.aimg_stride + ((size_t)tile * 2 * (n2 / 8) + 2 * j) * 1024;
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                                  ::"r"(tc::smem_u32(stage(s))), "l"(asrc), "r"(abytes), "r"(mb)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc::smem_u32(stage(s) + ST_ALO)), "l"(asrc + (size_t)(n2 / 8) * 1024), "r"(abytes),
+                                 "r"(mb)
                                  : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                                  ::"r"(tc::smem_u32(stage(s) + ST_B)),
@@ -434,7 +359,9 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 if (s_err) { err = true; break; }
                 tc::fence_after();
                 const uint32_t sa = tc::smem_u32(stage(s)), sal = sa + ST_ALO, sb = sa + ST_B;
-                const uint64_t dah = tc::sdesc(sa, 128, 256), dal = tc::sdesc(sal, 128, 256);
+                // U: A K-major in the image's arrangement: K cores 2048 B apart (LBO), 8-pixel
+                // cores 128 B apart (SBO)
+                const uint64_t dah = tc::sdesc(sa, 2048, 128), dal = tc::sdesc(sal, 2048, 128);
                 if (j < nU) {
                     const uint32_t acc = j > 0 ? 1u : 0u;
                     for (int nb = 0; nb < nbk; ++nb) {
@@ -636,17 +563,15 @@ cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, c
 }
 
 size_t tc_aimage_elems(int n_elem, int npix) {
-    return (size_t)((npix + TP - 1) / TP) * (size_t)(2 * n_elem / 16) * (2 * TP * 16);
+    return (size_t)((npix + TP - 1) / TP) * 2 * (size_t)(2 * n_elem / 8) * 1024;
 }
 
-cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, void* gimg,
-                                cudaStream_t s) {
+cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, cudaStream_t s) {
     if (!tc_adjoint_supported(G.n_elem) || !srec || !aimg) return cudaErrorInvalidValue;
     const int n_tiles = (G.npix + TP - 1) / TP;
     const long long blocks = (long long)n_tiles * (G.n_elem / 16);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_synth_images<<<(int)blocks, 256, 0, s>>>(G, srec, F, (__nv_bfloat16*)aimg, tc_aimage_elems(G.n_elem, G.npix),
-                                               (__nv_bfloat16*)gimg, tc_gimage_elems(G.n_elem, G.npix));
+    k_synth_images<<<(int)blocks, 256, 0, s>>>(G, srec, F, (__nv_bfloat16*)aimg, tc_aimage_elems(G.n_elem, G.npix));
     return cudaGetLastError();
 }
 
@@ -686,21 +611,26 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
 
 // ===========================================================================
 // Born forward on the tensor cores:  d[e][r] = w^2 sum_x G_e(x) G_r(x) m(x)
-// Real form over K = pixels: rows e' = 2e + {0: Re, 1: Im} of A = G m and columns
-// r' = 2r + {0, 1} of B = G give D = A B^T (2n x 2n, symmetric), from which
-//   Re d = D[2e][2r] - D[2e+1][2r+1],  Im d = D[2e][2r+1] + D[2e+1][2r].
-// CTA (i, s): 128-row block i of D over pixel split s, all needed column blocks
-// in TMEM; column blocks below the diagonal are skipped (symmetry).  Partial D
-// blocks go to global memory and a second kernel sums the splits in order.
+// Real form over K = pixels: rows e' = 2e + {0: Re, 1: -Im} of A = conj(G) m and
+// columns r' = 2r + {0, 1} of B = conj(G) give D = A B^T (2n x 2n, symmetric) =
+// the real form of conj(d), from which
+//   Re d = D[2e][2r] - D[2e+1][2r+1],  Im d = -(D[2e][2r+1] + D[2e+1][2r]).
+// Both operands come from the adjoint's A image (k_synth_images), read MN-major:
+// a core matrix there is 8 pixels (K) x 8 consecutive r' (16 bytes each), and a
+// 16-pixel K slice of all r' rows is one 2-D TMA box per plane.  CTA (i, s):
+// 128-row block i of D over pixel split s, the needed column blocks in TMEM;
+// column blocks below the diagonal are skipped (symmetry).  Partial D blocks go to
+// global memory and a second kernel sums the splits in order.
 // ===========================================================================
 namespace {
 
 constexpr int FMAXB = 8;   // max row blocks (2n / 128, n <= 256 -> 4)
+constexpr int FBOX_MAX = 32;   // rows (of 8 r') per TMA box, at most
+constexpr uint32_t ST_FB = 8192u;   // forward stage: A hi (4 KB), A lo (4 KB), then B hi and B lo
 
 struct FwdArgs {
     GeoDev G;
     FreqC F;
-    const __nv_bfloat16* gimg;   // G operand images of this frequency
     const float* m;
     float* partial;            // [cta][128][2n] fp32 (only needed columns written)
     int n_mb;                  // row blocks
@@ -709,16 +639,18 @@ struct FwdArgs {
     int cta0[FMAXB + 1];       // first CTA of each row block
     uint32_t tmem_cols;
     uint32_t* counters;
+    int fbox;                  // rows per TMA box: divides the rows loaded by every row block
 };
 
 __host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i) / nb; }
 
-// Forward kernel: the adjoint's warp-specialised pipeline over K = 16 pixel slices.
-//   warps 0..7  producers: thread (row = tid % 128, g = tid / 128) builds K-group g of
-//               row `row` of A = (B rows 128 i + row) * m(x), re-split into hi / lo,
-//               once the slice's B has landed; then the epilogue;
-//   warp 8      MMA issuer; warp 9 B loader (image rows [col0, 2n), hi and lo).
-__global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
+// Forward kernel: warp-specialised pipeline over K = 16 pixel slices.
+//   warps 0..7  producers: thread u takes the 16-byte row (8 r', one pixel) u of the
+//               row block's A slice: B rows 128 i .. 128 i + 127 scaled by m(x) and
+//               re-split into hi / lo, once the slice's B has landed; then the epilogue;
+//   warp 8      MMA issuer; warp 9 loader (TMA boxes of the rows [col0, 2n) of the
+//               slice, hi and lo planes).
+__global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full;
     __shared__ uint32_t s_tmem;
@@ -732,12 +664,14 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
     const int S = A.splits[i];
     const int jmin = jmin_of(i, A.nb);
     const int col0 = jmin * A.nb;                       // first needed column (= first B row loaded)
-    const int nsl_all = (G.npix + 15) / 16;
+    const int rcn = n2 / 8, rc0 = col0 / 8;             // rows of 8 r' per plane; first one loaded
+    const int nrow = rcn - rc0;                         // rows loaded per plane (a multiple of fbox)
+    const uint32_t plane_bytes = (uint32_t)nrow * 256u;
+    const int n_tiles = (G.npix + TP - 1) / TP;
+    const int nsl_all = n_tiles * 8;
     const int cps = (nsl_all + S - 1) / S;
     const int sbeg = min(nsl_all, sp * cps), send = min(nsl_all, sbeg + cps);
     const int nq = send - sbeg;
-    const size_t cimg = (size_t)n2 * 16;                           // bf16 per hi or lo image of a slice
-    const uint32_t rows_bytes = (uint32_t)(n2 - col0) * 32u;      // loaded rows [col0, 2n) of one image
     if (tid == 0) {
         for (int k = 0; k < NST; ++k) {
             tc::mbar_init(tc::smem_u32(&s_full_a[k]), NPROD_F / 32);
@@ -755,10 +689,11 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
     auto stage = [&](int k) { return smem + (size_t)k * ST_BYTES; };
 
     if (warp == NPROD_F / 32 + 1) {
-        // ------------------------------ B loader ------------------------------
+        // ------------------------------ loader ------------------------------
         if (lane == 0) {
             int ql = 0;
             bool err = false;
+            const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
             for (; ql < nq; ++ql) {
                 const int k = ql % NST;
                 if (ql >= NST && !tc::mbar_wait(tc::smem_u32(&s_empty[k]), (uint32_t)((ql / NST) - 1) & 1u, kMaxTries)) {
@@ -766,17 +701,19 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
                     break;
                 }
                 if (s_err) break;
-                const __nv_bfloat16* src = A.gimg + (size_t)(sbeg + ql) * 2 * cimg;
+                const int sg = sbeg + ql, t = sg >> 3, x = (sg & 7) * 128;
                 const uint32_t mb = tc::smem_u32(&s_full_b[k]);
-                const uint32_t dst = tc::smem_u32(stage(k) + ST_B);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * rows_bytes) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                             "l"((const char*)src + (size_t)col0 * 32), "r"(rows_bytes), "r"(mb)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * plane_bytes)
                              : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                 dst + rows_bytes),
-                             "l"((const char*)(src + cimg) + (size_t)col0 * 32), "r"(rows_bytes), "r"(mb)
-                             : "memory");
+                for (int hl = 0; hl < 2; ++hl)
+                    for (int b = 0; b < nrow / A.fbox; ++b) {
+                        const uint32_t dst = tc::smem_u32(stage(k) + ST_FB + hl * plane_bytes + (uint32_t)(b * A.fbox) * 256u);
+                        const int y = (t * 2 + hl) * rcn + rc0 + b * A.fbox;
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                            ::"r"(dst), "l"(tm), "r"(x), "r"(y), "r"(mb)
+                            : "memory");
+                    }
             }
             if (err || s_err) {
                 s_err = 1;
@@ -788,7 +725,9 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
     } else if (warp == NPROD_F / 32) {
         // ------------------------------ MMA issuer ------------------------------
         if (lane == 0) {
-            const uint32_t id = tc::idesc_bf16_f32(128, (uint32_t)A.nb);
+            // both operands MN-major (transpose bits 15 and 16): LBO = stride between the
+            // two 8-pixel K cores (128 B), SBO = stride between 8-r' cores (256 B)
+            const uint32_t id = tc::idesc_bf16_f32(128, (uint32_t)A.nb) | (1u << 15) | (1u << 16);
             int last = -1;
             bool err = false;
             for (int q = 0; q < nq && !err; ++q) {
@@ -798,12 +737,12 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
                 if (!tc::mbar_wait(tc::smem_u32(&s_full_b[k]), ph, kMaxTries)) { err = true; break; }
                 if (s_err) { err = true; break; }
                 tc::fence_after();
-                const uint32_t sa = tc::smem_u32(stage(k)), sb = sa + ST_B;
+                const uint32_t sa = tc::smem_u32(stage(k)), sb = sa + ST_FB;
                 const uint64_t dah = tc::sdesc(sa, 128, 256), dal = tc::sdesc(sa + ST_ALO, 128, 256);
                 for (int j = jmin; j < A.nbn; ++j) {
-                    const uint32_t boff = (uint32_t)((j * A.nb - col0) / 8) * 256u;
+                    const uint32_t boff = (uint32_t)((j * A.nb) / 8 - rc0) * 256u;
                     const uint64_t dbh = tc::sdesc(sb + boff, 128, 256);
-                    const uint64_t dbl = tc::sdesc(sb + rows_bytes + boff, 128, 256);
+                    const uint64_t dbl = tc::sdesc(sb + plane_bytes + boff, 128, 256);
                     const uint32_t d = tmem + (uint32_t)(j * A.nb);
                     tc::mma_bf16(d, dah, dbh, id, q > 0 ? 1u : 0u);
                     tc::mma_bf16(d, dah, dbl, id, 1u);
@@ -822,53 +761,45 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
         __syncwarp();
     } else {
         // -------------------------------- producers --------------------------------
-        const int row = tid & 127, g = tid >> 7;
+        // thread tid: row rl = tid / 16 of 8 r' (of the row block's 16), K core pc = (tid / 8) % 2,
+        // pixel row x8 = tid % 8 of that core
+        const int rl = tid >> 4, pc = (tid >> 3) & 1, x8 = tid & 7;
+        const uint32_t boff = (uint32_t)((16 * i - rc0 + rl) * 256 + pc * 128 + x8 * 16);
+        const uint32_t aoff = (uint32_t)(rl * 256 + pc * 128 + x8 * 16);
         bool err = false;
-        // m(x) of the thread's 8 pixels of slice q (fetched one slice ahead)
-        auto load_m = [&](int q, float (&mm)[8]) {
-            if (q >= nq) return;
-            const int p0 = (sbeg + q) * 16 + 8 * g;
-            if (p0 + 8 <= G.npix && ((reinterpret_cast<uintptr_t>(A.m + p0) & 15u) == 0)) {
-                const float4 m0 = __ldg((const float4*)(A.m + p0)), m1 = __ldg((const float4*)(A.m + p0 + 4));
-                mm[0] = m0.x; mm[1] = m0.y; mm[2] = m0.z; mm[3] = m0.w;
-                mm[4] = m1.x; mm[5] = m1.y; mm[6] = m1.z; mm[7] = m1.w;
-            } else {
-#pragma unroll
-                for (int t = 0; t < 8; ++t) mm[t] = p0 + t < G.npix ? __ldg(A.m + p0 + t) : 0.f;
-            }
+        auto load_m = [&](int q) -> float {
+            if (q >= nq) return 0.f;
+            const int px = (sbeg + q) * 16 + pc * 8 + x8;
+            return px < G.npix ? __ldg(A.m + px) : 0.f;
         };
-        float mnext[8];
-        load_m(0, mnext);
+        float mnext = load_m(0);
         for (int q = 0; q < nq; ++q) {
             const int k = q % NST;
             const uint32_t ph = (uint32_t)(q / NST) & 1u;
-            float mm[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) mm[t] = mnext[t];
-            load_m(q + 1, mnext);
+            const float mm = mnext;
+            mnext = load_m(q + 1);
             if (!err && q >= NST) err = !tc::mbar_wait(tc::smem_u32(&s_empty[k]), ph ^ 1u, kMaxTries);
             if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_full_b[k]), ph, kMaxTries);
             err = __any_sync(0xffffffffu, err || s_err != 0);
             if (!err) {
-                const unsigned char* b_hi = stage(k) + ST_B;
-                const unsigned char* b_lo = b_hi + rows_bytes;
-                const uint32_t boff = tc::tile16_offset((uint32_t)(128 * i + row - col0), 8u * g);
-                const uint4 vh = *(const uint4*)(b_hi + boff), vl = *(const uint4*)(b_lo + boff);
+                const unsigned char* b_hi = stage(k) + ST_FB;
+                const uint4 vh = *(const uint4*)(b_hi + boff), vl = *(const uint4*)(b_hi + plane_bytes + boff);
                 const uint32_t hw[4] = {vh.x, vh.y, vh.z, vh.w}, lw[4] = {vl.x, vl.y, vl.z, vl.w};
                 uint32_t oh[4], ol[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const float x0 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[t] & 0xffff))) +
-                                      __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[t] & 0xffff)))) * mm[2 * t];
+                                      __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[t] & 0xffff)))) * mm;
                     const float x1 = (__bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[t] >> 16))) +
-                                      __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[t] >> 16)))) * mm[2 * t + 1];
+                                      __bfloat162float(__ushort_as_bfloat16((unsigned short)(lw[t] >> 16)))) * mm;
                     __nv_bfloat16 h0, l0, h1, l1;
                     tc::split_bf16(x0, h0, l0);
                     tc::split_bf16(x1, h1, l1);
                     oh[t] = pack2(h0, h1);
                     ol[t] = pack2(l0, l1);
                 }
-                store_row16(stage(k), stage(k) + ST_ALO, (uint32_t)row, (uint32_t)g, oh, ol);
+                *(uint4*)(stage(k) + aoff) = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+                *(uint4*)(stage(k) + ST_ALO + aoff) = make_uint4(ol[0], ol[1], ol[2], ol[3]);
             }
             tc::fence_proxy_async();
             __syncwarp();
@@ -879,6 +810,7 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A) {
         err = __any_sync(0xffffffffu, err || s_err != 0);
         tc::fence_after();
         if (!err) {
+            const int row = tid & 127, g = tid >> 7;
             const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
             float* out = A.partial + ((size_t)blockIdx.x * 128 + row) * n2;
             int cnum = 0;
@@ -924,8 +856,10 @@ __global__ void k_forward_tc_reduce(FwdArgs A, float2* __restrict__ d_out, const
     for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < total;
          jj += (long long)gridDim.x * blockDim.x) {
         const int e = (int)(jj / n), r = (int)(jj % n);
+        // the image rows 2r + 1 hold -Im G_r (the conjugate, as the adjoint uses it), so the
+        // product of the two images is conj(d): Re d as is, Im d negated
         const float dre = (Dval(2 * e, 2 * r) - Dval(2 * e + 1, 2 * r + 1)) * A.F.w2;
-        const float dim = (Dval(2 * e, 2 * r + 1) + Dval(2 * e + 1, 2 * r)) * A.F.w2;
+        const float dim = -(Dval(2 * e, 2 * r + 1) + Dval(2 * e + 1, 2 * r)) * A.F.w2;
         if (d_out) d_out[jj] = make_float2(dre, dim);
         if (w && w[jj]) acc += (double)dre * dre + (double)dim * dim;
     }
@@ -941,12 +875,11 @@ __global__ void k_forward_tc_reduce(FwdArgs A, float2* __restrict__ d_out, const
     }
 }
 
-FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const __nv_bfloat16* gimg, const float* m, float* partial,
-                      int n_ctas, uint32_t* counters) {
+FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const float* m, float* partial, int n_ctas,
+                      uint32_t* counters) {
     FwdArgs A;
     A.G = G;
     A.F = F;
-    A.gimg = gimg;
     A.m = m;
     A.partial = partial;
     A.counters = counters;
@@ -975,6 +908,11 @@ FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const __nv_bfloat16* gimg
         c0 += s;
     }
     A.cta0[A.n_mb] = c0;
+    // TMA box height: the largest power of two up to FBOX_MAX dividing every row block's
+    // loaded rows (2n - col0) / 8
+    A.fbox = FBOX_MAX;
+    for (int i = 0; i < A.n_mb; ++i)
+        while ((n2 / 8 - (jmin_of(i, A.nb) * A.nb) / 8) % A.fbox != 0) A.fbox >>= 1;
     return A;
 }
 
@@ -984,29 +922,22 @@ size_t tc_forward_partial_bytes(int n_elem, int n_ctas) {
     return (size_t)(n_ctas + FMAXB) * 128 * (2 * (size_t)n_elem) * sizeof(float);
 }
 
-size_t tc_gimage_elems(int n_elem, int npix) {
-    const size_t chunks = (size_t)((npix + 127) / 128) * 8;   // 16-pixel chunks, whole 128-pixel tiles
-    return chunks * 2 * (2 * (size_t)n_elem) * 16;
-}
-
-cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F, void* img,
-                          cudaStream_t s) {
-    const long long total = (long long)G.n_elem * ((G.npix + 7) / 8);
-    long long blocks = (total + 255) / 256;
-    if (blocks > 8192) blocks = 8192;
-    k_gimage<<<(int)blocks, 256, 0, s>>>(G, tables, c, F, (__nv_bfloat16*)img, tc_gimage_elems(G.n_elem, G.npix));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F, const float* m, float* partial,
+cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F, const float* m, float* partial,
                               int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
                               cudaStream_t s) {
-    if (!tc_adjoint_supported(G.n_elem)) return cudaErrorInvalidValue;
-    const FwdArgs A = make_fwd_args(G, F, (const __nv_bfloat16*)gimg, m, partial, n_ctas, counters);
+    if (!tc_adjoint_supported(G.n_elem) || !aimg) return cudaErrorInvalidValue;
+    const FwdArgs A = make_fwd_args(G, F, m, partial, n_ctas, counters);
+    // the A image of this frequency as a 2-D tensor: rows of 8 r' x 128 pixels (1024 bf16),
+    // (tile, plane, row) major; boxes of 128 elements (one 16-pixel slice) x fbox rows
+    const int rcn = 2 * G.n_elem / 8;
+    const int n_tiles = (G.npix + TP - 1) / TP;
+    CUtensorMap tmap;
+    if (A.fbox < 1 || !tc::encode_tmap_2d(&tmap, aimg, 1024, (uint64_t)n_tiles * 2 * rcn, 2048, 128, (uint32_t)A.fbox))
+        return cudaErrorUnknown;
     const int sm = NST * (int)ST_BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    k_forward_tc<<<A.cta0[A.n_mb], NTHR_F, sm, s>>>(A);
+    k_forward_tc<<<A.cta0[A.n_mb], NTHR_F, sm, s>>>(A, tmap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_forward_tc_reduce<<<256, 256, 0, s>>>(A, d_out, w, den_part);

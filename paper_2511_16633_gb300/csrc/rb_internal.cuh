@@ -220,7 +220,6 @@ struct WsLayout {
     size_t tcimg;      // tensor-core path: bf16 B-operand images, [n_freq][image]
     size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
     size_t tcfwd;      // tensor-core path: partial D blocks of the forward
-    size_t gimg;       // tensor-core path: G operand images of the forward, [n_freq][...] bf16
     size_t aimg;       // tensor-core path: A operand images of the adjoint, [n_freq][...] bf16
     size_t srec;       // tensor-core path: synthesis records, [n_elem][npix] float4
     size_t total;
@@ -270,16 +269,12 @@ bool tc_adjoint_supported(int n_elem);
 size_t tc_b_images_bytes(int n_elem);
 cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, cudaStream_t s);
 size_t tc_forward_partial_bytes(int n_elem, int n_ctas);
-size_t tc_gimage_elems(int n_elem, int npix);
-cudaError_t launch_gimage(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F, void* img,
-                          cudaStream_t s);
-cudaError_t launch_forward_tc(const GeoDev& G, const void* gimg, const FreqC& F, const float* m, float* partial,
+cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F, const float* m, float* partial,
                               int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
                               cudaStream_t s);
 // A images of the adjoint (and optionally the forward's G images) from the synthesis records
 size_t tc_aimage_elems(int n_elem, int npix);
-cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, void* gimg,
-                                cudaStream_t s);
+cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, cudaStream_t s);
 cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& F, const void* images, float2* gscr,
                               int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
                               cudaStream_t s);

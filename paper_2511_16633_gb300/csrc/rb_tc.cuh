@@ -8,10 +8,38 @@
 // and the MMA over k in [16 s, 16 s + 16) starts at byte 256 s.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace tc {
+
+// Host: a 2-D tiled TMA descriptor for a bf16 tensor of `rows` rows of `width`
+// elements, `row_stride` bytes apart, copied in boxes of box_w x box_h elements (no
+// swizzle, no interleave, zero fill out of range).  The driver's encoder is looked up
+// once through the runtime and kept.  Returns false when it is unavailable or rejects
+// the arguments.
+inline bool encode_tmap_2d(CUtensorMap* map, const void* base, uint64_t width, uint64_t rows, uint64_t row_stride,
+                           uint32_t box_w, uint32_t box_h) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {width, rows};
+    const cuuint64_t strides[1] = {row_stride};
+    const cuuint32_t box[2] = {box_w, box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 constexpr uint32_t kChunkK = 32;                 // bf16 per row of a staged chunk
 constexpr uint32_t kRowGroupBytes = 512;         // SBO for kChunkK = 32

@@ -48,7 +48,7 @@ class rb_update_params(ctypes.Structure):
                 ("pad", ctypes.c_int32), ("stage_events", ctypes.c_void_p)]
 
 
-STAGES = ("fields", "trace_grid", "link", "adjoint", "direction", "forward", "apply")
+STAGES = ("fields", "trace_grid", "link", "images", "adjoint", "direction", "forward", "apply")
 
 
 # numpy views of the device records
