@@ -110,7 +110,7 @@ ADJ_ISSUE_RATIO = 2.8
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512
 # (ncu --metrics, 1 pass; profiles/k_adjoint_tc.md), None when not measured for the
 # kernel as built.
-ADJ_TRAFFIC_BYTES = None
+ADJ_TRAFFIC_BYTES = 2309901312 + 1443407616
 
 
 def run_ours(args):
