@@ -79,9 +79,35 @@ __device__ __forceinline__ void sample(const GeoDev& G, const float4* __restrict
 #undef RB_BL
 }
 
-// sincosf behind a call: the fallbacks below are (almost) never taken, and an inlined
-// copy per RK4 stage costs registers, a local-memory frame and issue slots on every step.
-__device__ __noinline__ void sincos_call(float x, float* s, float* c) { sincosf(x, s, c); }
+// sin and cos of a ray angle (|x| < 1e4 rad), inline and branch-light: Cody-Waite
+// reduction by pi/2 in three float parts (r = x - k pi/2 to ~1e-9 absolute for these
+// arguments), Taylor polynomials on |r| <= pi/4 (sin to r^11, cos to r^12: truncation
+// below 1e-9), then the quadrant.  Used for the anchor angle instead of the library
+// call, whose large-argument path, inlined into the step loop, cost registers and
+// issue slots on every step.
+__device__ __forceinline__ void ray_sincos(float x, float* s, float* c) {
+    const float k = rintf(x * 0.636619772367581343f);   // x / (pi / 2)
+    float r = fmaf(-k, 1.5707962513e+00f, x);             // pi/2 = p1 + p2 + p3
+    r = fmaf(-k, 7.5497894159e-08f, r);
+    r = fmaf(-k, 5.3903029534e-15f, r);
+    const float r2 = r * r;
+    // sin r = r (1 - r^2/3! + r^4/5! - ...), cos r = 1 - r^2/2! + r^4/4! - ...
+    float ps = fmaf(r2, -2.50521083854e-08f, 2.75573192240e-06f);   // -1/11!, 1/9!
+    ps = fmaf(r2, ps, -1.98412698413e-04f);                           // -1/7!
+    ps = fmaf(r2, ps, 8.33333333333e-03f);                            // 1/5!
+    ps = fmaf(r2, ps, -1.66666666667e-01f);                           // -1/3!
+    const float sn = fmaf(r * r2, ps, r);
+    float pc = fmaf(r2, 2.08767569879e-09f, -2.75573192240e-07f);     // 1/12!, -1/10!
+    pc = fmaf(r2, pc, 2.48015873016e-05f);                            // 1/8!
+    pc = fmaf(r2, pc, -1.38888888889e-03f);                           // -1/6!
+    pc = fmaf(r2, pc, 4.16666666667e-02f);                            // 1/4!
+    pc = fmaf(r2, pc, -0.5f);                                         // -1/2!
+    const float cs = fmaf(r2, pc, 1.0f);
+    const int q = (int)k & 3;
+    const float ss = (q & 1) ? cs : sn, cc = (q & 1) ? sn : cs;
+    *s = (q & 2) ? -ss : ss;
+    *c = ((q + 1) & 2) ? -cc : cc;
+}
 
 // cos/sin of (th_hi + d) from cos/sin of th_hi and a small d (Taylor to d^7).
 __device__ __forceinline__ void rotate(float C0, float S0, float th_hi, float d, float& c, float& s) {
@@ -92,7 +118,9 @@ __device__ __forceinline__ void rotate(float C0, float S0, float th_hi, float d,
         c = C0 * cd - S0 * sd;
         s = S0 * cd + C0 * sd;
     } else {
-        sincos_call(th_hi + d, &s, &c);
+        // a turn of 0.2 rad within half a step (gradients far beyond tissue): the hardware
+        // approximation (~1e-6 absolute), small enough not to weigh on the common path
+        __sincosf(th_hi + d, &s, &c);
     }
 }
 
@@ -348,17 +376,35 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     }
     if (put) put_vtx(verts + vidx(G, t, 0, i), cur);
     const float ds = G.ds, a2 = 0.5f * G.ds, ds6 = G.ds * (1.0f / 6.0f);
+    float pfi = -1.f, pfj = -1.f;   // cell of the last touch
 
     for (int k = 1; k <= G.max_steps; ++k) {
         if (!alive) break;
         if (alive) {
             // direction relative to the anchor angle tha (cos / sin exact there); the
             // anchor follows the ray whenever it has turned by more than 0.05 rad
-            if (fabsf(thh - tha) > 0.05f) {
+            // a loop rather than an if: the compiler keeps it a branch instead of evaluating
+            // the refresh on every step (it runs at most once)
+            while (fabsf(thh - tha) > 0.05f) {
                 tha = thh;
-                sincos_call(tha, &Sa, &Ca);
+                ray_sincos(tha, &Sa, &Ca);
             }
             const float dth = (thh - tha) + thl;
+            {
+                // touch the field cell one step ahead (a load whose value is never used, so
+                // the warp does not wait for it): its record is in L1 when the stages get there
+                const float lx = (xh + xl) + ds * Ca, ly = (yh + yl) + ds * Sa;
+                const float u = fminf(fmaxf(fmaf(lx, G.inv_h, G.cxg), 0.f), G.fxmax);
+                const float v = fminf(fmaxf(fmaf(ly, G.inv_h, G.cyg), 0.f), G.fymax);
+                const float fi = fminf(floorf(u), G.fxmax - 1.f), fj = fminf(floorf(v), G.fymax - 1.f);
+                if (fi != pfi || fj != pfj) {
+                    pfi = fi;
+                    pfj = fj;
+                    const float4* pc = cells + ((size_t)(int)fj * (size_t)(G.nx - 1) + (size_t)(int)fi) * 8;
+                    float dummy;
+                    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(dummy) : "l"(pc));
+                }
+            }
             const float rxh = xh - xs.hi, rxl = xl - xs.lo, ryh = yh - ys.hi, ryl = yl - ys.lo;
             const Deriv z{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const Deriv k1 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, 0.f, z);
