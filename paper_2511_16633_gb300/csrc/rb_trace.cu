@@ -258,8 +258,15 @@ __device__ __forceinline__ void key_min(unsigned long long* dst, uint64_t key) {
 __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1,
                                             uint32_t base, unsigned long long* __restrict__ tab,
                                             const short2* __restrict__ supp) {
-    const Quad Q = quad_of(A0, A1, B0, B1);
-    if (!Q.t0 && !Q.t1) return;
+    // edge vectors first: most quads are about one pixel, and a box with no pixel centre
+    // ends here before the areas and their reciprocals are formed
+    Quad Q;
+    Q.b0x = rel(B0.xh, B0.xl, A0.xh, A0.xl);
+    Q.b0y = rel(B0.yh, B0.yl, A0.yh, A0.yl);
+    Q.b1x = rel(B1.xh, B1.xl, A0.xh, A0.xl);
+    Q.b1y = rel(B1.yh, B1.yl, A0.yh, A0.yl);
+    Q.a1x = rel(A1.xh, A1.xl, A0.xh, A0.xl);
+    Q.a1y = rel(A1.yh, A1.yl, A0.yh, A0.yl);
     // tight box of pixel centres (index space), with a 1e-3 px guard
     const float ua = fmaf(A0.xh, G.inv_h, G.cxg) + A0.xl * G.inv_h;
     const float va = fmaf(A0.yh, G.inv_h, G.cyg) + A0.yl * G.inv_h;
@@ -269,7 +276,17 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
     const int bx1 = min(G.nx - 1, (int)floorf(fmaf(xmax, G.inv_h, ua) + 1e-3f));
     const int iy0 = max(0, (int)ceilf(fmaf(ymin, G.inv_h, va) - 1e-3f));
     const int iy1 = min(G.ny - 1, (int)floorf(fmaf(ymax, G.inv_h, va) + 1e-3f));
-    if (bx0 > bx1) return;
+    if (bx0 > bx1 || iy0 > iy1) return;
+    {
+        // as quad_of
+        const float ar0 = __fsub_rn(__fmul_rn(Q.b0x, Q.b1y), __fmul_rn(Q.b0y, Q.b1x));
+        const float ar1 = __fsub_rn(__fmul_rn(Q.b1x, Q.a1y), __fmul_rn(Q.b1y, Q.a1x));
+        Q.t0 = ar0 != 0.f;
+        Q.t1 = ar1 != 0.f;
+        Q.i0 = Q.t0 ? __frcp_rn(ar0) : 0.f;
+        Q.i1 = Q.t1 ? __frcp_rn(ar1) : 0.f;
+    }
+    if (!Q.t0 && !Q.t1) return;
     const float tol = -1e-6f;
     // per-pixel (x) increments of the weights of T0 = (A0; u = b0, v = b1) and T1 = (A0; u = b1, v = a1)
     const float h = G.h;
@@ -610,17 +627,18 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
             // ids come from the rasteriser (i + 1 < n_rays, 1 <= k1 <= max_steps); clamped all the same
             const int i = min((int)qi, G.n_rays - 2), k1 = min((int)qk1 + 1, G.max_steps);
             const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+            // the winning triangle only: T0 = (A0, B0, B1), T1 = (A0, B1, A1); edge vectors,
+            // doubled area and weights as in quad_of / bary
             const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
-            const Vtx A1 = get_vtx(verts + vidx(G, t, min(k1, la), i));
-            const Vtx B0 = get_vtx(verts + vidx(G, t, min(k1 - 1, lb), i + 1));
-            const Vtx B1 = get_vtx(verts + vidx(G, t, min(k1, lb), i + 1));
-            const Quad Q = quad_of(A0, A1, B0, B1);
+            const Vtx Vb = get_vtx(half ? verts + vidx(G, t, min(k1, lb), i + 1) : verts + vidx(G, t, min(k1 - 1, lb), i + 1));
+            const Vtx Vc = get_vtx(half ? verts + vidx(G, t, min(k1, la), i) : verts + vidx(G, t, min(k1, lb), i + 1));
+            const float ux = rel(Vb.xh, Vb.xl, A0.xh, A0.xl), uy = rel(Vb.yh, Vb.yl, A0.yh, A0.yl);
+            const float vx = rel(Vc.xh, Vc.xl, A0.xh, A0.xl), vy = rel(Vc.yh, Vc.yl, A0.yh, A0.yl);
+            const float ar = __fsub_rn(__fmul_rn(ux, vy), __fmul_rn(uy, vx));
+            const float inv = ar != 0.f ? __frcp_rn(ar) : 0.f;
             const float dx = rel(X.hi, X.lo, A0.xh, A0.xl), dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
             float wa, wb, wc;
-            const Vtx& Vb = half ? B1 : B0;
-            const Vtx& Vc = half ? A1 : B1;
-            if (half) bary(Q.b1x, Q.b1y, Q.a1x, Q.a1y, Q.i1, dx, dy, wa, wb, wc);
-            else bary(Q.b0x, Q.b0y, Q.b1x, Q.b1y, Q.i0, dx, dy, wa, wb, wc);
+            bary(ux, uy, vx, vy, inv, dx, dy, wa, wb, wc);
             int kap = A0.k;
             float wbest = wa;
             if (wb > wbest) { kap = Vb.k; wbest = wb; }
