@@ -29,9 +29,10 @@
 // winning triangle id of every hit pixel, fetches that triangle's vertices and
 // writes the table record (Q, L and the KMAH index) and/or the synthesis record,
 // and counts the support pixels no triangle covered.
-// Positions, the direction and the traveltime residual T - |x - x_t|/c_ref
-// are float pairs (compensated sums), which keeps the Green's-function phase
-// w T accurate at MHz frequencies without the (slow) FP64 pipe.
+// Positions, the direction and the traveltime T are float pairs (compensated
+// sums; the vertex residual T - |x - x_t|/c_ref is formed in float pairs too),
+// which keeps the Green's-function phase w T accurate at MHz frequencies without
+// the (slow) FP64 pipe.
 #include "rb_internal.cuh"
 
 namespace {
@@ -129,12 +130,11 @@ struct RayCtx {
 };
 
 __device__ __forceinline__ Deriv eval_stage(const GeoDev& G, const float4* __restrict__ cells, Cache& cc,
-                                            float xh, float xl, float yh, float yl, float rxh, float rxl, float ryh,
-                                            float ryl, float Ca, float Sa, float tha, float dth, float q, float p,
+                                            float xh, float xl, float yh, float yl, float Ca, float Sa, float tha,
+                                            float dth, float q, float p,
                                             float a, const Deriv& kp) {
     const float ox = fmaf(a, kp.x, xl), oy = fmaf(a, kp.y, yl);
     const float px = xh + ox, py = yh + oy;
-    const float rx = rxh + fmaf(a, kp.x, rxl), ry = ryh + fmaf(a, kp.y, ryl);
     float cth, sth;
     rotate(Ca, Sa, tha, fmaf(a, kp.th, dth), cth, sth);
     const float qs = fmaf(a, kp.q, q), ps = fmaf(a, kp.p, p);
@@ -146,18 +146,7 @@ __device__ __forceinline__ Deriv eval_stage(const GeoDev& G, const float4* __res
     d.x = cth;
     d.y = sth;
     d.th = (f[1] * sth - f[2] * cth) * rc;
-    // T_res' = 1/c - (t . r_hat)/c_ref = (c_ref - c)/(c c_ref) + (1 - t . r_hat)/c_ref,
-    // with 1 - t.r_hat = (t x r)^2 / (|r| (|r| + t.r)) (no cancellation).
-    const float r2 = rx * rx + ry * ry;
-    float one_m_cos = 0.f;
-    if (r2 > 0.f) {
-        const float rr = r2 * rsqrtf(r2);
-        const float dot = cth * rx + sth * ry;
-        const float crs = cth * ry - sth * rx;
-        const float den = rr * (rr + dot);
-        one_m_cos = den > 0.f ? __fdividef(crs * crs, den) : 2.f;
-    }
-    d.t = (G.c_ref - c) * (rc * G.inv_cref) + one_m_cos * G.inv_cref;
+    d.t = rc;   // T' = 1 / c (the residual T - |x - x_t| / c_ref is formed per vertex)
     d.q = c * ps;
     const float cnn = f[3] * sth * sth - 2.f * f[4] * sth * cth + f[5] * cth * cth;
     d.p = -(cnn * rc * rc) * qs;
@@ -376,7 +365,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     float xh = xs.hi, xl = xs.lo, yh = ys.hi, yl = ys.lo, thh = thd.hi, thl = thd.lo;
     float tha = thh, Ca, Sa;
     sincosf(tha, &Sa, &Ca);
-    float trh = 0.f, trl = 0.f;   // T_res as a float pair (compensated sum of the RK4 increments)
+    float trh = 0.f, trl = 0.f;   // T as a float pair (compensated sum of the RK4 increments)
     float q = 0.f, p = 1.0f / f0[0], l = 0.f;
     int kap = 0;
     bool alive = valid;
@@ -422,12 +411,11 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                     asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(dummy) : "l"(pc));
                 }
             }
-            const float rxh = xh - xs.hi, rxl = xl - xs.lo, ryh = yh - ys.hi, ryl = yl - ys.lo;
             const Deriv z{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const Deriv k1 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, 0.f, z);
-            const Deriv k2 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, a2, k1);
-            const Deriv k3 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, a2, k2);
-            const Deriv k4 = eval_stage(G, cells, cc, xh, xl, yh, yl, rxh, rxl, ryh, ryl, Ca, Sa, tha, dth, q, p, ds, k3);
+            const Deriv k1 = eval_stage(G, cells, cc, xh, xl, yh, yl, Ca, Sa, tha, dth, q, p, 0.f, z);
+            const Deriv k2 = eval_stage(G, cells, cc, xh, xl, yh, yl, Ca, Sa, tha, dth, q, p, a2, k1);
+            const Deriv k3 = eval_stage(G, cells, cc, xh, xl, yh, yl, Ca, Sa, tha, dth, q, p, a2, k2);
+            const Deriv k4 = eval_stage(G, cells, cc, xh, xl, yh, yl, Ca, Sa, tha, dth, q, p, ds, k3);
             const float ix = ds6 * (k1.x + 2.f * k2.x + 2.f * k3.x + k4.x);
             const float iy = ds6 * (k1.y + 2.f * k2.y + 2.f * k3.y + k4.y);
             const float ith = ds6 * (k1.th + 2.f * k2.th + 2.f * k3.th + k4.th);
@@ -450,21 +438,21 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                 const double lam = exit_lambda(ax, ay, bx, by, G.R_d);
                 const float lf = (float)lam;
                 const double ex = ax + lam * (bx - ax), ey = ay + lam * (by - ay);
-                const double tres = (double)trh + (double)trl;
-                const double etres = tres + lam * (double)it;
+                const double tt = (double)trh + (double)trl;
+                const double et = tt + lam * (double)it;
                 const double eth = ((double)thh + (double)thl) + lam * (((double)nthh + (double)nthl) - ((double)thh + (double)thl));
                 const float eq = q + lf * (nq - q), ep = p + lf * (np - p), el = l + lf * (nl - l);
                 const int ek = kap + ((k >= 2 && signbit(eq) != signbit(q)) ? 1 : 0);
                 const DF exd = df_from_double(ex), eyd = df_from_double(ey);
                 xh = exd.hi; xl = exd.lo; yh = eyd.hi; yl = eyd.lo;
-                const DF etd = df_from_double(etres);
+                const DF etd = df_from_double(et);
                 q = eq; p = ep; l = el; kap = ek; trh = etd.hi; trl = etd.lo;
                 alive = false;
                 if (owner) {
                     const double ddx = ex - xs_d, ddy = ey - ys_d;
                     rb_ray_end e;
-                    e.t_res = etres;
-                    e.t = etres + sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
+                    e.t = et;
+                    e.t_res = et - sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
                     e.x = ex;
                     e.y = ey;
                     e.theta = (float)eth;
@@ -486,9 +474,9 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                         const double ex = (double)xh + (double)xl, ey = (double)yh + (double)yl;
                         const double ddx = ex - xs_d, ddy = ey - ys_d;
                         rb_ray_end e;
-                        const double tres = (double)trh + (double)trl;
-                        e.t_res = tres;
-                        e.t = tres + sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
+                        const double tt = (double)trh + (double)trl;
+                        e.t = tt;
+                        e.t_res = tt - sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
                         e.x = ex;
                         e.y = ey;
                         e.theta = thh + thl;
@@ -502,15 +490,21 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                     }
                 }
             }
-            cur = Vtx{xh, xl, yh, yl, trh + trl, q, l, kap};
-            if (put) put_vtx(verts + vidx(G, t, k, i), cur);
+            if (put) {
+                // vertex residual T - |x - x_t| / c_ref in float pairs
+                const DF dx = df_sub(DF{xh, xl}, xs), dy = df_sub(DF{yh, yl}, ys);
+                const DF d2 = df_add(df_sqr(dx), df_sqr(dy));
+                const DF dist = d2.hi > 0.f ? df_sqrt(d2) : DF{0.f, 0.f};
+                const DF tr = df_sub(DF{trh, trl}, df_mul(dist, DF{G.inv_cref, G.inv_cref_lo}));
+                cur = Vtx{xh, xl, yh, yl, tr.hi + tr.lo, q, l, kap};
+                put_vtx(verts + vidx(G, t, k, i), cur);
+            }
             if (write_samples) {
                 const size_t o = sbase + (size_t)k;
                 const double vx = (double)xh + (double)xl, vy = (double)yh + (double)yl;
-                const double ddx = vx - xs_d, ddy = vy - ys_d;
                 S.vx[o] = (float)vx;
                 S.vy[o] = (float)vy;
-                S.vt[o] = ((double)trh + (double)trl) + sqrt(ddx * ddx + ddy * ddy) * (1.0 / G.c_ref_d);
+                S.vt[o] = (double)trh + (double)trl;
                 S.vq[o] = q;
                 S.vl[o] = l;
                 S.vkappa[o] = kap;
