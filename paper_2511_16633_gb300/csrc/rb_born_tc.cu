@@ -38,11 +38,15 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
          j += (long long)gridDim.x * blockDim.x) {
         const int ep = (int)(j / n2), kp = (int)(j % n2);
         const int r = kp >> 1, part = kp & 1;
-        const int e = ep % n, blk = ep / n;
+        // rows e' in N-blocks of nb columns (the adjoint's MMA width), each holding the
+        // Re U rows then the Im U rows of nb / 2 consecutive elements
+        const int nb = n2 > 256 ? n2 / 2 : n2, eb = nb / 2;
+        const int blk = ep / nb, w = ep % nb;
+        const int e = blk * eb + w % eb, im = w / eb;
         float2 s = make_float2(0.f, 0.f);
         if (W[(size_t)e * n + r]) s = R[(size_t)e * n + r];
         float v;
-        if (blk == 0) v = part == 0 ? s.x : -s.y;
+        if (im == 0) v = part == 0 ? s.x : -s.y;
         else v = part == 0 ? s.y : s.x;
         __nv_bfloat16 hi, lo;
         tc::split_bf16(v, hi, lo);
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t s_full[NST], s_empty[NST], s_acc_full, s_acc_empty, s_vready, s_drain;
+    __shared__ uint64_t s_full[NST], s_empty[NST], s_acc_full, s_acc_empty, s_acc_low, s_vready, s_drain;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_err;
     __shared__ float s_red[3][3][TP];             // partial sums of quarters 1..3: Re g, Im g, H
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
         }
         tc::mbar_init(tc::smem_u32(&s_acc_full), 1);
         tc::mbar_init(tc::smem_u32(&s_acc_empty), NPROD / 32);
+        tc::mbar_init(tc::smem_u32(&s_acc_low), NPROD / 32);
         tc::mbar_init(tc::smem_u32(&s_vready), NPROD / 32);
         tc::mbar_init(tc::smem_u32(&s_drain), 1);
         s_err = 0;
@@ -347,13 +352,18 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
             const uint32_t id_u = tc::idesc_bf16_f32(128, (uint32_t)nb_u);
             const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)n);
             int s = 0, j = 0;
-            uint32_t accp = 0, ph = 0;
+            uint32_t acce = 0, accl = 0, ph = 0;
             bool err = false, issued = false;
             for (int q = 0; q < total && !err; ++q) {
-                if ((j == 0 || j == nU) && q > 0) {
-                    // a new accumulation phase: the epilogue must have read the accumulator
-                    if (!tc::mbar_wait(tc::smem_u32(&s_acc_empty), accp & 1u, kMaxTries)) { err = true; break; }
-                    ++accp;
+                if (j == nU) {
+                    // V overwrites the columns of the first N-block of U: its part of the U
+                    // epilogue must be done (the rest of it overlaps the V MMAs)
+                    if (!tc::mbar_wait(tc::smem_u32(&s_acc_low), accl & 1u, kMaxTries)) { err = true; break; }
+                    ++accl;
+                } else if (j == 0 && q > 0) {
+                    // a new U phase: the V epilogue must have read the accumulator
+                    if (!tc::mbar_wait(tc::smem_u32(&s_acc_empty), acce & 1u, kMaxTries)) { err = true; break; }
+                    ++acce;
                 }
                 if (!tc::mbar_wait(tc::smem_u32(&s_full[s]), ph, kMaxTries)) { err = true; break; }
                 if (s_err) { err = true; break; }
@@ -451,10 +461,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
                 // ---- U epilogue: element chunks of 8, e0 = 32 b + 8 c for blocks b = h, h + 4, ...
-                // and c < 4 (Re U in column e, Im U in column n + e); G of the next chunk is
-                // loaded while the current one is used, the first before the accumulator wait ----
+                // and c < 4 (in increasing e); element e's Re U is in column nbu (e / ebu) + e % ebu
+                // and its Im U ebu columns further (N-blocks of nbu columns, ebu = nbu / 2
+                // elements each); G of the next chunk is loaded while the current one is used,
+                // the first before the accumulator wait ----
                 const int nch = 4 * ((n / 32 - (int)h + 3) / 4);
+                const int nbu = n2 > 256 ? n2 / 2 : n2, ebu = nbu / 2;
                 auto ce0 = [&](int k) { return 32 * ((int)h + 4 * (k >> 2)) + 8 * (k & 3); };
+                auto recol = [&](int e) { return (e / ebu) * nbu + e % ebu; };
                 auto gload = [&](int k, float2 (&g)[8]) {
                     const int e0 = ce0(k);
 #pragma unroll
@@ -463,13 +477,22 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 auto gchunk = [&](int k, const float2 (&g)[8], float& ar, float& ai) {
                     const int e0 = ce0(k);
                     float vr[8], vi[8];
-                    tc::tmem_ld8(tmem + lane_off + (uint32_t)e0, vr);
-                    tc::tmem_ld8(tmem + lane_off + (uint32_t)(n + e0), vi);
+                    tc::tmem_ld8(tmem + lane_off + (uint32_t)recol(e0), vr);
+                    tc::tmem_ld8(tmem + lane_off + (uint32_t)(recol(e0) + ebu), vi);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         ar = fmaf(g[i].x, vr[i], fmaf(g[i].y, vi[i], ar));
                         ai = fmaf(g[i].x, vi[i], fmaf(-g[i].y, vr[i], ai));
                     }
+                };
+                // the V MMAs write columns [0, n), inside the first N-block: released once this
+                // warp has read its chunks of elements < ebu
+                bool low = false;
+                auto release_low = [&]() {
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_acc_low));
+                    low = true;
                 };
                 float2 ga[8], gb[8];
                 if (nch > 0) gload(0, ga);
@@ -477,13 +500,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 float gr = 0.f, gi = 0.f;
                 if (!err) {
                     for (int k = 0; k < nch; k += 2) {
+                        if (!low && ce0(k) >= ebu) release_low();
                         gload(k + 1, gb);
                         gchunk(k, ga, gr, gi);
                         if (k + 2 < nch) gload(k + 2, ga);
                         gchunk(k + 1, gb, gr, gi);
                     }
                 }
-                acc_release();
+                if (!low) release_low();
                 if (h > 0) {
                     s_red[0][h - 1][p] = gr;
                     s_red[1][h - 1][p] = gi;

@@ -267,13 +267,15 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
     const int iy1 = min(G.ny - 1, (int)floorf(fmaf(ymax, G.inv_h, va) + 1e-3f));
     if (bx0 > bx1 || iy0 > iy1) return;
     {
-        // as quad_of
+        // as quad_of, with the hardware reciprocal: these weights only decide coverage and
+        // the residual offered as the key; the table record's weights are formed exactly
+        // by the resolve pass
         const float ar0 = __fsub_rn(__fmul_rn(Q.b0x, Q.b1y), __fmul_rn(Q.b0y, Q.b1x));
         const float ar1 = __fsub_rn(__fmul_rn(Q.b1x, Q.a1y), __fmul_rn(Q.b1y, Q.a1x));
         Q.t0 = ar0 != 0.f;
         Q.t1 = ar1 != 0.f;
-        Q.i0 = Q.t0 ? __frcp_rn(ar0) : 0.f;
-        Q.i1 = Q.t1 ? __frcp_rn(ar1) : 0.f;
+        Q.i0 = Q.t0 ? __fdividef(1.0f, ar0) : 0.f;
+        Q.i1 = Q.t1 ? __fdividef(1.0f, ar1) : 0.f;
     }
     if (!Q.t0 && !Q.t1) return;
     const float tol = -1e-6f;
