@@ -859,33 +859,42 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
 
 // d = w^2 (sum over splits of the partial D blocks, symmetric lookup), and
 // per-block partial sums of W |d|^2.
+// d = w^2 (sum over splits of the partial D blocks), and per-block partial sums of
+// W |d|^2.  D and d are symmetric, and for e <= r the 2 x 2 block of D at (2e, 2r) lies in
+// a computed block (on or above the block diagonal), so thread (e, r), e <= r, reads it
+// row-wise (consecutive threads, consecutive r: coalesced) and writes d[e][r] and d[r][e].
 __global__ void k_forward_tc_reduce(FwdArgs A, float2* __restrict__ d_out, const uint8_t* __restrict__ w,
                                     double* __restrict__ den_part) {
     const int n = A.G.n_elem, n2 = 2 * n;
-    auto Dval = [&](int row, int col) -> float {
-        int i = row >> 7, j = col / A.nb;
-        if (j < jmin_of(i, A.nb)) {   // below the diagonal blocks: use the transpose
-            const int t = row;
-            row = col;
-            col = t;
-            i = row >> 7;
-        }
-        float acc = 0.f;
-        for (int s = 0; s < A.splits[i]; ++s)
-            acc += A.partial[((size_t)(A.cta0[i] + s) * 128 + (row & 127)) * n2 + col];
-        return acc;
-    };
     double acc = 0.0;
     const long long total = (long long)n * n;
     for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < total;
          jj += (long long)gridDim.x * blockDim.x) {
         const int e = (int)(jj / n), r = (int)(jj % n);
+        if (e > r) continue;
+        const int i = (2 * e) >> 7, row = (2 * e) & 127;
+        float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);   // D[2e][2r..2r+1], D[2e+1][2r..2r+1]
+        for (int sp = 0; sp < A.splits[i]; ++sp) {
+            const float* blk = A.partial + ((size_t)(A.cta0[i] + sp) * 128 + row) * n2 + 2 * r;
+            const float2 a0 = *(const float2*)blk, a1 = *(const float2*)(blk + n2);
+            d0.x += a0.x;
+            d0.y += a0.y;
+            d1.x += a1.x;
+            d1.y += a1.y;
+        }
         // the image rows 2r + 1 hold -Im G_r (the conjugate, as the adjoint uses it), so the
         // product of the two images is conj(d): Re d as is, Im d negated
-        const float dre = (Dval(2 * e, 2 * r) - Dval(2 * e + 1, 2 * r + 1)) * A.F.w2;
-        const float dim = -(Dval(2 * e, 2 * r + 1) + Dval(2 * e + 1, 2 * r)) * A.F.w2;
-        if (d_out) d_out[jj] = make_float2(dre, dim);
-        if (w && w[jj]) acc += (double)dre * dre + (double)dim * dim;
+        const float dre = (d0.x - d1.y) * A.F.w2;
+        const float dim = -(d0.y + d1.x) * A.F.w2;
+        const size_t er = (size_t)e * n + r, re = (size_t)r * n + e;
+        if (d_out) {
+            d_out[er] = make_float2(dre, dim);
+            if (e != r) d_out[re] = make_float2(dre, dim);
+        }
+        if (w) {
+            const int cnt = (w[er] ? 1 : 0) + ((e != r && w[re]) ? 1 : 0);
+            if (cnt) acc += cnt * ((double)dre * dre + (double)dim * dim);
+        }
     }
     if (den_part) {
         __shared__ double sred[256];
