@@ -13,9 +13,12 @@
 // holding for each of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 the coefficients
 // (a, b, c, d) of its bilinear interpolant a + b u + c v + d u v over the cell
 // (u, v in [0, 1]), from the corner values q00 = (i0, j0), q10, q01, q11:
-// a = q00, b = q10 - q00, c = q01 - q00, d = q11 - q10 - q01 + q00; seven
-// float4 (+1 pad).  A ray that enters a cell loads one aligned 128-byte line and
-// keeps it in registers until it leaves the cell.
+// a = q00, b = q10 - q00, c = q01 - q00, d = q11 - q10 - q01 + q00.  The fields go
+// in pairs (c, c_x), (c_y, c_xx), (c_xy, c_yy), two float4 per pair:
+// {a_F, a_G, b_F, b_G}, {c_F, c_G, d_F, d_G}, so that the sampler evaluates a pair
+// with packed two-lane FMAs; then alpha0's {a, b, c, d} and a pad.  A ray that enters
+// a cell loads one aligned 128-byte line and keeps it in registers until it leaves
+// the cell.
 #include "rb_internal.cuh"
 
 __global__ void k_elem_positions(GeoDev G, float4* xy) {
@@ -70,12 +73,13 @@ __global__ void k_fields(GeoDev G, const float* __restrict__ c, const float* __r
     auto coef = [](float q00, float q10, float q01, float q11) {
         return make_float4(q00, q10 - q00, q01 - q00, (q11 - q10) - (q01 - q00));
     };
-    o[0] = coef(q[0].c, q[1].c, q[2].c, q[3].c);
-    o[1] = coef(q[0].cx, q[1].cx, q[2].cx, q[3].cx);
-    o[2] = coef(q[0].cy, q[1].cy, q[2].cy, q[3].cy);
-    o[3] = coef(q[0].cxx, q[1].cxx, q[2].cxx, q[3].cxx);
-    o[4] = coef(q[0].cxy, q[1].cxy, q[2].cxy, q[3].cxy);
-    o[5] = coef(q[0].cyy, q[1].cyy, q[2].cyy, q[3].cyy);
+    auto pair = [&](float4* dst, float4 f, float4 g) {
+        dst[0] = make_float4(f.x, g.x, f.y, g.y);
+        dst[1] = make_float4(f.z, g.z, f.w, g.w);
+    };
+    pair(o + 0, coef(q[0].c, q[1].c, q[2].c, q[3].c), coef(q[0].cx, q[1].cx, q[2].cx, q[3].cx));
+    pair(o + 2, coef(q[0].cy, q[1].cy, q[2].cy, q[3].cy), coef(q[0].cxx, q[1].cxx, q[2].cxx, q[3].cxx));
+    pair(o + 4, coef(q[0].cxy, q[1].cxy, q[2].cxy, q[3].cxy), coef(q[0].cyy, q[1].cyy, q[2].cyy, q[3].cyy));
     o[6] = coef(a[0], a[1], a[2], a[3]);
     o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }

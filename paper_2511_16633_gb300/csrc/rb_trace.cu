@@ -39,17 +39,19 @@ namespace {
 
 struct Cache {
     float fi, fj;   // cell indices of the cached record (as floats; -1 = none)
-    float4 c, cx, cy, cxx, cxy, cyy, a0;
+    float4 r[7];    // field pairs (c, c_x), (c_y, c_xx), (c_xy, c_yy) as {a, a', b, b'}, {c, c', d, d'}; alpha0
 };
 
 struct Deriv { float x, y, th, t, q, p, l; };
 
 struct Vtx { float xh, xl, yh, yl, t, q, l; int k; };
 
-// Bilinear samples of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 at (px, py).  Each cell
-// record holds per field the coefficients (a, b, c, d) of a + b u + c v + d u v over
-// the cell's unit square; the cell indices stay floats (floorf), and the record is
-// reloaded only when the ray changes cell.
+// Bilinear samples of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 at (px, py).  The cell
+// record holds per field the coefficients (a, b, c, d) of a + b u + c v + d u v over the
+// cell's unit square, paired fields side by side (rb_fields.cu), so each pair takes three
+// packed two-lane FMAs (same operations and rounding as three scalar ones per field).
+// The cell indices stay floats (floorf), and the record is reloaded only when the ray
+// changes cell.
 __device__ __forceinline__ void sample(const GeoDev& G, const float4* __restrict__ cells, Cache& cc, float px, float py,
                                        float f[7]) {
     const float u = fminf(fmaxf(fmaf(px, G.inv_h, G.cxg), 0.f), G.fxmax);
@@ -58,26 +60,24 @@ __device__ __forceinline__ void sample(const GeoDev& G, const float4* __restrict
     const float fu = u - fi, fv = v - fj;
     if (fi != cc.fi || fj != cc.fj) {
         const float4* p = cells + ((size_t)(int)fj * (size_t)(G.nx - 1) + (size_t)(int)fi) * 8;
-        cc.c = __ldg(p + 0);
-        cc.cx = __ldg(p + 1);
-        cc.cy = __ldg(p + 2);
-        cc.cxx = __ldg(p + 3);
-        cc.cxy = __ldg(p + 4);
-        cc.cyy = __ldg(p + 5);
-        cc.a0 = __ldg(p + 6);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) cc.r[k] = __ldg(p + k);
         cc.fi = fi;
         cc.fj = fj;
     }
     const float uv = fu * fv;
-#define RB_BL(q) fmaf((q).w, uv, fmaf((q).z, fv, fmaf((q).y, fu, (q).x)))
-    f[0] = RB_BL(cc.c);
-    f[1] = RB_BL(cc.cx);
-    f[2] = RB_BL(cc.cy);
-    f[3] = RB_BL(cc.cxx);
-    f[4] = RB_BL(cc.cxy);
-    f[5] = RB_BL(cc.cyy);
-    f[6] = RB_BL(cc.a0);
-#undef RB_BL
+    const float2 u2 = make_float2(fu, fu), v2 = make_float2(fv, fv), w2 = make_float2(uv, uv);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 ab = cc.r[2 * k], cd = cc.r[2 * k + 1];
+        const float2 s = __ffma2_rn(make_float2(cd.z, cd.w), w2,
+                                    __ffma2_rn(make_float2(cd.x, cd.y), v2,
+                                               __ffma2_rn(make_float2(ab.z, ab.w), u2, make_float2(ab.x, ab.y))));
+        f[2 * k] = s.x;
+        f[2 * k + 1] = s.y;
+    }
+    const float4 q = cc.r[6];
+    f[6] = fmaf(q.w, uv, fmaf(q.z, fv, fmaf(q.y, fu, q.x)));
 }
 
 // sin and cos of a ray angle (|x| < 1e4 rad), inline and branch-light: Cody-Waite
