@@ -390,3 +390,40 @@ def test_born_forward_bf16x3(dev, case):
         e = rel_l2(d.cpu().numpy(), do)
         print(f"bf16x3 forward {case} f={f:.3g}: rel L2 {e:.3g}")
         assert e <= 1e-4, e
+
+
+# Mixed precision at the other supported ring sizes, on grids whose pixel count is not a
+# multiple of the 128-pixel tile: n_elem = 128 (one N-block of U) and 192 (two N-blocks
+# of 96 elements, 8-row TMA boxes in the forward).
+@pytest.mark.parametrize("n_elem,nx,ny", [(128, 70, 66), (192, 66, 70)])
+def test_bf16x3_ring_sizes_ragged(dev, n_elem, nx, ny):
+    cfg = rbgen.tiny(n_elem=n_elem, nx=nx, ny=ny, n_rays=48)
+    inp = rbgen.make_inputs(rbgen.tiny(nx=nx, ny=ny, seed=cfg.seed))
+    c = inp.c_true
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    assert g.npix % 128 != 0
+    tab, _ = gpu_tables(geom, c, inp.alpha0, dev)
+    ot = ogrid.grid(g, c, inp.alpha0)
+    rng = np.random.default_rng(7)
+    R = (rng.standard_normal((g.n_elem, g.n_elem)) + 1j * rng.standard_normal((g.n_elem, g.n_elem))).astype(np.complex64)
+    W = (rng.uniform(size=(g.n_elem, g.n_elem)) > 0.25).astype(np.uint8)
+    m = rng.standard_normal(g.npix).astype(np.float32) * 1e-9
+    ws = rb.workspace(geom, 1, rb.RB_PREC_BF16X3, dev)
+    ct = _t(c, dev)
+    f = cfg.freqs_hz[-1]
+    Go = ogreen.green(g, ot, c, f)
+    gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
+    hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+    rb.rb_born_adjoint(geom, tab, ct, f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev), gg, ws, hh,
+                       prec=rb.RB_PREC_BF16X3)
+    d = torch.empty((g.n_elem, g.n_elem), dtype=torch.complex64, device=dev)
+    rb.rb_born_forward(geom, tab, ct, f, _t(m, dev), d, ws, prec=rb.RB_PREC_BF16X3)
+    torch.cuda.synchronize()
+    eg = rel_l2(gg.cpu().numpy(), oborn.born_adjoint(Go, W * R.astype(np.complex128), f))
+    eh = rel_l2(hh.cpu().numpy(), oborn.hess_diag(Go, W, f))
+    ed = rel_l2(d.cpu().numpy(), oborn.born_forward(Go, m.astype(np.float64), f))
+    print(f"bf16x3 n={n_elem} {nx}x{ny}: gradient {eg:.3g}, Hessian diagonal {eh:.3g}, forward {ed:.3g}")
+    assert eg <= 1e-4, eg
+    assert eh <= 1e-4, eh
+    assert ed <= 1e-4, ed
