@@ -11,5 +11,6 @@ The acquisition shapes follow the ring-array experiments of the paper
 consecutive frequencies swept from low to high); the phantoms are stand-ins
 for the in-vitro and in-vivo datasets, which are not available here.
 """
-from .configs import Config, config_by_name, tiny, breast256, breast512, CONFIGS  # noqa: F401
+from .configs import (Config, config_by_name, tiny, breast256, breast512, CONFIGS, ring, batch_mix,  # noqa: F401
+                      poisson_requests)
 from .phantom import Inputs, make_inputs, ellipse_phantom, breast_phantom, initial_guess, noise_draws  # noqa: F401

@@ -8,6 +8,8 @@ Three workloads, named for what they are:
                   256 rays per emitter, 12 frequencies 0.3-1.0 MHz in 4 sets of 3.
 * ``breast512`` — same ring, 512x512 grid at 0.45 mm, 256 rays per emitter,
                   20 frequencies 0.3-1.25 MHz in 5 sets of 4.
+* ``ring`` / ``batch_mix`` / ``poisson_requests`` — workloads of uneven sizes on the
+                  same 110 mm ring (batched reconstructions and a request stream).
 
 The ring of 256 elements with an 11 cm radius, the 1480 m/s water speed and
 the low-to-high sweep over sets of consecutive frequencies are the paper's
@@ -97,3 +99,49 @@ CONFIGS = {"tiny": tiny, "breast256": breast256, "breast512": breast512}
 
 def config_by_name(name: str, **kw) -> Config:
     return CONFIGS[name](**kw)
+
+
+def ring(n_elem: int, n_grid: int, n_freq: int, per_set: int = 4, f_lo_mhz: float = 0.3, f_hi_mhz: float = 1.25,
+         n_rays: int = 256, seed: int = 20251116 + 3, name: str = "ring", **kw) -> Config:
+    """A breast-phantom workload on the 110 mm ring with n_elem elements and an n_grid^2
+    grid whose half-width is 5 % beyond the ring; n_freq frequencies in sets of per_set."""
+    R = 0.110
+    h = 2.0 * 1.05 * R / (n_grid - 1)
+    f = _linspace_hz(f_lo_mhz, f_hi_mhz, n_freq)
+    base = dict(name=name, n_elem=n_elem, ring_radius=R, nx=n_grid, ny=n_grid, h=h, n_rays=n_rays, freqs_hz=f,
+                sets=_sets(n_freq, per_set), power_y=1.1, seed=seed, kind="breast")
+    base.update(kw)
+    return Config(**base)
+
+
+def batch_mix(n: int = 16, rings=(128, 256, 512), grids=(256, 512, 768), freqs=(8, 24), seed: int = 20251116 + 4,
+              **kw) -> List[Config]:
+    """n reconstructions of uneven sizes: ring sizes and grid sizes drawn from the given
+    lists, frequency counts uniform in [freqs[0], freqs[1]] rounded to whole sets of 4."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        ne = int(rng.choice(rings))
+        ng = int(rng.choice(grids))
+        nf = int(rng.integers(freqs[0] // 4, freqs[1] // 4 + 1)) * 4
+        out.append(ring(ne, ng, nf, seed=seed + 1 + k, name=f"mix{k}_{ne}el_{ng}px_{nf}f", **kw))
+    return out
+
+
+def poisson_requests(rate_hz: float, count: int, rings=(128, 256, 512), grids=(256, 512, 768, 1024), sets=(3, 6),
+                     per_set: int = 4, seed: int = 20251116 + 5, **kw) -> List[Tuple[float, Config]]:
+    """count requests with exponential inter-arrival times of mean 1 / rate_hz seconds;
+    ring and grid sizes drawn from the lists, 3-6 frequency sets of per_set."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate_hz))
+        ne = int(rng.choice(rings))
+        ng = int(rng.choice(grids))
+        ns = int(rng.integers(sets[0], sets[1] + 1))
+        out.append((t, ring(ne, ng, ns * per_set, per_set=per_set, seed=seed + 1 + k,
+                            name=f"req{k}_{ne}el_{ng}px_{ns}sets", **kw)))
+    return out

@@ -1,0 +1,51 @@
+"""Admission logic of the batched / served runner (host only, no GPU)."""
+import pytest
+
+from paper_2511_16633_gb300.serve import Job, Scheduler
+
+
+def _jobs(spec):
+    # spec: (arrival, footprint) per job
+    return [Job(k, None, a, 0, f) for k, (a, f) in enumerate(spec)]
+
+
+def test_admits_in_arrival_order_within_budget_and_slots():
+    s = Scheduler(_jobs([(0.0, 4), (0.0, 4), (0.0, 4), (1.0, 1)]), budget=10, max_slots=8)
+    first = s.admit(0.0)
+    assert [j.jid for j in first] == [0, 1]          # the third does not fit (12 > 10)
+    assert s.used == 8
+    assert s.admit(0.5) == []                        # nothing new fits or has arrived
+    s.finish(first[0], 0.7)
+    assert [j.jid for j in s.admit(0.8)] == [2]      # freed memory goes to the next in line
+    assert [j.jid for j in s.admit(1.0)] == [3]      # the later arrival fits beside them
+    assert s.used == 9
+
+
+def test_first_come_first_served_no_overtaking():
+    s = Scheduler(_jobs([(0.0, 6), (0.1, 6), (0.2, 1)]), budget=10, max_slots=8)
+    assert [j.jid for j in s.admit(0.0)] == [0]
+    # job 1 does not fit; job 2 would, but must wait behind job 1
+    assert s.admit(0.3) == []
+    s.finish(s.active[0], 0.4)
+    assert [j.jid for j in s.admit(0.5)] == [1, 2]
+
+
+def test_slot_limit_and_rejection_of_oversized_jobs():
+    s = Scheduler(_jobs([(0.0, 1)] * 5 + [(0.0, 100)]), budget=50, max_slots=3)
+    assert len(s.admit(0.0)) == 3
+    assert [j.jid for j in s.rejected] == [5]
+    for j in list(s.active.values()):
+        s.finish(j, 1.0)
+    assert len(s.admit(1.0)) == 2
+    for j in list(s.active.values()):
+        s.finish(j, 2.0)
+    assert s.idle()
+    assert [j.jid for j in s.started] == [0, 1, 2, 3, 4]
+    assert all(j.done is not None for j in s.started)
+
+
+def test_next_arrival_and_idle():
+    s = Scheduler(_jobs([(2.5, 1), (1.5, 1)]), budget=10, max_slots=2)
+    assert s.next_arrival() == pytest.approx(1.5)
+    assert s.admit(1.0) == [] and not s.idle()
+    assert [j.jid for j in s.admit(3.0)] == [1, 0]
