@@ -28,6 +28,11 @@ weights to its reference [Javaherian 2022], so these are readings:
   m_true = -2 h^2 (c_true - c0)/c0^3 on the support, noise =
   level * rms_masked |p_obs_w| * (n1 + i n2)/sqrt(2) with the seeded draws.
 
+* CG variant (``cg_solve``, ``cg_update``): the same linearised objective solved by
+  conjugate gradients instead of the diagonal Hessian (readings beside the code);
+  pinned by Krylov optimality, finite termination, the first iteration equal to the
+  one-step update, and a decreasing objective.
+
 Parity unpinned against the paper for ``sweep`` (the paper prints no values,
 its figures are absent); the one-step solve is pinned by a least-squares
 check on a single-pixel support.
@@ -157,3 +162,91 @@ def synth_data(g: Geom, c0: np.ndarray, c_true: np.ndarray, alpha0: np.ndarray, 
             p = p + level * rms * (noise_re[j] + 1j * noise_im[j]) / math.sqrt(2.0)
         out.append(p)
     return np.stack(out)
+
+
+# ---------------------------------------------------------------------------
+# CG variant (Sec. 3: the linear equation of Eq. 10 solved iteratively, as in
+# the earlier ray-Born method the paper contrasts with; 10-15 iterations).
+#
+# Readings: the linearised objective is the one of ``hf_update``,
+#   phi(dm) = 1/2 sum_w sum_{e,r} W |R_w + B_w dm|^2  over real dm on the support,
+# whose normal equations are  A dm = b,  A = sum_w Re(B_w^H W B_w),  b = -sum_w Re g_w.
+# The paper does not say whether its CG is preconditioned; ``precond`` selects the
+# plain method (M = I) or the diagonal-Hessian preconditioner M^-1 = 1/(sum_w H_w + eps)
+# on the support (the one-step update's solution-space weight), under which a single
+# iteration is exactly the one-step update with the exact step.  The iteration is
+# Hestenes and Stiefel's conjugate gradients (1952) with a preconditioner, started at 0.
+# ---------------------------------------------------------------------------
+def cg_solve(apply_A, b: np.ndarray, minv: np.ndarray | None, iters: int):
+    """Preconditioned conjugate gradients for A x = b from x = 0.
+
+    apply_A(p) returns A p; minv is the diagonal of M^-1 (None: M = I).  Returns x after
+    ``iters`` iterations and the list rho_k = <r_k, M^-1 r_k>, k = 0..iters.  An iteration
+    whose curvature <p, A p> is not positive leaves x unchanged from then on."""
+    x = np.zeros_like(b, dtype=np.float64)
+    r = np.array(b, dtype=np.float64)
+    z = r * minv if minv is not None else r.copy()
+    p = z.copy()
+    rho = float(r @ z)
+    hist = [rho]
+    for _ in range(iters):
+        q = apply_A(p)
+        curv = float(p @ q)
+        a = rho / curv if curv > 0.0 else 0.0
+        x = x + a * p
+        r = r - a * q
+        z = r * minv if minv is not None else r.copy()
+        rho_new = float(r @ z)
+        beta = rho_new / rho if rho != 0.0 else 0.0
+        p = z + beta * p
+        rho = rho_new
+        hist.append(rho)
+    return x, hist
+
+
+@dataclasses.dataclass
+class CGResult:
+    c_new: np.ndarray
+    dc: np.ndarray
+    dm: np.ndarray
+    dc_norm: float
+    rho: List[float]
+    phi: float            # the linearised objective at dm, minus its value at 0
+
+
+def cg_update(g: Geom, c: np.ndarray, alpha0: np.ndarray, freqs: Sequence[float], p_obs: np.ndarray, iters: int,
+              precond: bool = True, outlier_frac: float = 0.01, eps_rel: float = 1e-3) -> CGResult:
+    """One frequency-set update with dm from ``iters`` CG iterations on the normal equations
+    of the linearised objective (data, weights and eps exactly as in ``hf_update``)."""
+    c = np.asarray(c, dtype=np.float64).reshape(g.ny, g.nx)
+    F = fields(g, c, alpha0)
+    tabs = grid(g, c, alpha0, F)
+    E, nvert, lost = rays.trace_endpoints(g, c, alpha0, F)
+    lk = link.link(g, E, lost, c)
+    p_ray = np.stack([link.ray_data(g, lk, f) for f in freqs])
+    R = p_ray - p_obs
+    base = np.broadcast_to(receiver_mask(g) & lk.linked, R.shape)
+    W, _, _ = outlier_weights(base, R, outlier_frac)
+    Gs = [green.green(g, tabs, c, f) for f in freqs]
+    sup = support_mask(g).ravel()
+    g_sum = np.zeros(g.npix)
+    h_sum = np.zeros(g.npix)
+    for j, f in enumerate(freqs):
+        g_sum += np.real(born.born_adjoint(Gs[j], W[j] * R[j], f))
+        h_sum += born.hess_diag(Gs[j], W[j], f)
+    eps = eps_rel * float(np.mean(h_sum[sup]))
+
+    def apply_A(p):
+        q = np.zeros(g.npix)
+        for j, f in enumerate(freqs):
+            q += np.real(born.born_adjoint(Gs[j], W[j] * born.born_forward(Gs[j], p, f), f))
+        return np.where(sup, q, 0.0)
+
+    b = np.where(sup, -g_sum, 0.0)
+    minv = np.where(sup, 1.0 / (h_sum + eps), 0.0) if precond else None
+    dm, hist = cg_solve(apply_A, b, minv, iters)
+    phi = 0.5 * float(dm @ apply_A(dm)) - float(b @ dm)
+    cf = c.ravel()
+    dc = -dm * cf ** 3 / (2.0 * g.h * g.h)
+    return CGResult(c_new=(cf + dc).reshape(g.ny, g.nx), dc=dc.reshape(g.ny, g.nx), dm=dm,
+                    dc_norm=float(np.sqrt(np.sum(dc[sup] ** 2))), rho=hist, phi=phi)
