@@ -110,7 +110,7 @@ ADJ_ISSUE_RATIO = 2.8
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512
 # (ncu --metrics, 1 pass; profiles/k_adjoint_tc.md), None when not measured for the
 # kernel as built.
-ADJ_TRAFFIC_BYTES = 2309901312 + 1443407616
+ADJ_TRAFFIC_BYTES = 2153628928 + 856079360   # dram read + write of one k_adjoint_tc launch (ncu, breast512)
 
 
 def run_ours(args):
@@ -140,8 +140,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     nst = len(rb.STAGES)
 
-    def measure(prec_name, with_clocks):
+    def measure(prec_name, with_clocks, cg_iters=0, n_steps=None):
         prec = precs[prec_name]
+        n_steps = args.steps if n_steps is None else n_steps
         ws = rb.workspace(geom, nf, prec, dev)
         c = c0.clone()
         dc = torch.empty_like(c)
@@ -153,9 +154,16 @@ def run_ours(args):
 
         def step(k, events=None):
             j = k % nsets
-            if j == 0:
+            # the one-step update sweeps the sets from c_init; the CG variant starts every
+            # update from c_init (CG fits the Born data far more closely than the one-step
+            # update and a sweep on them leaves the range where they are valid)
+            if j == 0 or cg_iters:
                 c.copy_(c0)
             s = cfg.sets[j]
+            if cg_iters:
+                rb.rb_cg_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], p_obs[s[0]:s[-1] + 1], ws, cg_iters, True,
+                                0.01, 1e-3, prec, dc, None, diag, stream, events)
+                return
             rb.rb_hf_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], p_obs[s[0]:s[-1] + 1], ws, 0.01, 1e-3,
                             rb.RB_STEP_EXACT, prec, dc, diag, stream, events)
 
@@ -163,14 +171,14 @@ def run_ours(args):
             step(k)
         torch.cuda.synchronize()
         stage_ms = np.zeros(nst)
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
         clocks = ClockSampler(local) if with_clocks else None
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(n_steps):
             starts[k].record(stream)
             step(args.warmup + k, ev_arr)
             ends[k].record(stream)
@@ -183,17 +191,21 @@ def run_ours(args):
             torch.distributed.barrier()
         wall = time.perf_counter() - t0
         clk = clocks.stop() if clocks else None
-        per_step = np.array([starts[k].elapsed_time(ends[k]) for k in range(args.steps)])
+        per_step = np.array([starts[k].elapsed_time(ends[k]) for k in range(n_steps)])
         ms = float(np.sum(per_step))
         if world > 1:
             t = torch.tensor([ms], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
-        out = {"value": world * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+        out = {"value": world * n_steps / (ms / 1e3), "ms_per_step": ms / n_steps,
                "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
-               "stage_ms": {name: round(stage_ms[i] / args.steps, 4) for i, name in enumerate(rb.STAGES)},
+               "stage_ms": {name: round(stage_ms[i] / n_steps, 4) for i, name in enumerate(rb.STAGES)},
                "wall_s": wall, "clocks": clk, "diag": rb.decode_diag(diag)}
 
+        if cg_iters:
+            del ws
+            torch.cuda.empty_cache()
+            return out
         # end to end through the same call: pinned host data in, c and diagnostics out, every step
         host_p = torch.empty(p_obs.shape, dtype=p_obs.dtype, pin_memory=True)
         host_p.copy_(p_obs.cpu())
@@ -228,6 +240,19 @@ def run_ours(args):
     if not args.no_compare:
         runs[other] = measure(other, False)
     R = runs[head]
+    cg = None
+    if args.cg_iters > 0:
+        # the CG variant of the same update (the paper's comparison: 10-15 iterations per set)
+        o = measure(head, False, cg_iters=args.cg_iters, n_steps=max(3, min(args.steps, 20)))
+        cg = {"iters": args.cg_iters, "precond": "diagonal Hessian", "start": "c_init every update",
+              "updates_per_s": o["value"],
+              "ms_per_update": o["ms_per_step"], "stage_ms": o["stage_ms"],
+              "time_vs_one_step": o["ms_per_step"] / R["ms_per_step"],
+              # the gradient stages, 4 CG start kernels, per iteration a forward (+ reduce) and a
+              # B-image prep (mixed path) per frequency, one partial sum, the adjoint and 3 vector
+              # kernels, then 3 apply/norm kernels
+              "gpu_launches_per_update": (19 + nf + args.cg_iters * (3 * nf + 5) if head == "bf16x3"
+                                          else 18 + args.cg_iters * (2 * nf + 5))}
     peaks, peak_src = _peaks()
     work = algorithmic_work(cfg, nf)
     st = R["stage_ms"]
@@ -296,6 +321,8 @@ def run_ours(args):
         "gpu_launches": (20 + 3 * nf if tc else 19 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
+    if cg is not None:
+        line["cg_variant"] = cg
     if other in runs:
         o = runs[other]
         line["compare"] = {"precision": other, "value": o["value"], "ms_per_step": o["ms_per_step"],
@@ -381,6 +408,8 @@ def main():
     ap.add_argument("--cpu-fans", type=int, default=32)
     ap.add_argument("--cpu-pix", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cg-iters", type=int, default=12,
+                    help="also time the CG variant of the update with this many iterations (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -153,8 +153,10 @@ typedef struct rb_diag {
     uint32_t tc_timeouts;   /* tensor-core pipeline waits that ran out (0 unless the device misbehaves) */
 } rb_diag;                  /* 48 bytes */
 
-/* Largest n_freq per call to rb_green_grid / rb_ray_forward / rb_hf_update. */
+/* Largest n_freq per call to rb_green_grid / rb_ray_forward / rb_hf_update / rb_cg_update. */
 #define RB_MAX_FREQ 16
+/* Largest number of CG iterations per call to rb_cg_update (the paper cites 10-15). */
+#define RB_MAX_CG 24
 
 /*
  * Bytes of workspace every call below needs for this geometry, n_freq
@@ -227,6 +229,30 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
 rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alpha0, const double* freqs_hz,
                        int32_t n_freq, const float* p_obs, const rb_update_params* params, rb_precision prec,
                        float* dc_out, rb_diag* diag_out, void* ws, size_t ws_bytes, rb_stream stream);
+
+/*
+ * CG variant of the frequency-set update (Sec. 3: the linear equation of Eq. 10
+ * solved iteratively by conjugate gradients, 10-15 iterations per set, as in
+ * the earlier ray-Born method the one-step update replaces).  Everything up to
+ * the gradient is as in rb_hf_update (same rays, data weights and eps); then
+ * cg_iters iterations (1..RB_MAX_CG) of preconditioned conjugate gradients on
+ *   A dm = -sum_w Re g_w,   A = sum_w Re(B_w^H W B_w)   (support pixels, dm_0 = 0),
+ * each one Born forward per frequency and one adjoint over the set, with the
+ * operand images of the set built once and reused.  precond 1: M^-1 = 1/(sum_w
+ * H_w + eps) per pixel (one iteration then equals rb_hf_update's exact step);
+ * precond 0: plain CG (run with the scalar 1/(mean H + eps), which leaves the
+ * iterates unchanged).  Then dc = -dm c^3 / (2 h^2), c_inout += dc.
+ * params->step_mode must be valid and is otherwise ignored.  cg_hist_out
+ * (nullable, device, cg_iters + 1 doubles) receives rho_k / rho_0 with
+ * rho_k = <r_k, M^-1 r_k>.  diag_out as for rb_hf_update (alpha = 1).  Stage
+ * events: RB_STAGE_DIRECTION brackets the CG start, RB_STAGE_FORWARD all
+ * iterations.  Same workspace size as rb_hf_update.  Errors as rb_hf_update,
+ * plus RB_ERR_ARG for cg_iters or precond out of range.
+ */
+rb_status rb_cg_update(const rb_geometry* geom, float* c_inout, const float* alpha0, const double* freqs_hz,
+                       int32_t n_freq, const float* p_obs, const rb_update_params* params, int32_t cg_iters,
+                       int32_t precond, rb_precision prec, float* dc_out, double* cg_hist_out, rb_diag* diag_out,
+                       void* ws, size_t ws_bytes, rb_stream stream);
 
 /*
  * Born forward operator without a workspace (the paper has no counterpart:

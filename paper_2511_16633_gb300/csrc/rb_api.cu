@@ -127,6 +127,81 @@ int tc_ctas() {
         if ((x) != cudaSuccess) return RB_ERR_CUDA; \
     } while (0)
 
+// Stage events of the update entry points (none when the caller gave no array).
+struct Marks {
+    cudaEvent_t* ev;
+    cudaStream_t s;
+    cudaError_t operator()(int stage, int end) const { return ev ? cudaEventRecord(ev[2 * stage + end], s) : cudaSuccess; }
+};
+
+rb_status check_update(const rb_geometry* geom, const float* c, const float* alpha0, const double* freqs_hz,
+                       int n_freq, const float* p_obs, const rb_update_params* params, rb_precision prec,
+                       FreqSet* F) {
+    if (!geom || !c || !alpha0 || !p_obs || !params) return RB_ERR_ARG;
+    if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    if (!(params->outlier_frac >= 0.0 && params->outlier_frac < 1.0)) return RB_ERR_ARG;
+    if (!(params->eps_rel >= 0.0) || !isfinite(params->eps_rel)) return RB_ERR_ARG;
+    if (params->step_mode != RB_STEP_EXACT && params->step_mode != RB_STEP_DIAG) return RB_ERR_ARG;
+    if (!make_freqs(geom, freqs_hz, n_freq, F)) return RB_ERR_ARG;
+    if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
+    return RB_OK;
+}
+
+// The stages both updates share (Secs. 3-4): fields, rays and first-arrival tables,
+// linking, residuals and data weights, the operand images (mixed path), and the
+// gradient sum_w Re g_w -> gsum and Hessian diagonal sum_w H_w -> hsum.
+rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float* c, const float* alpha0,
+                          const float* p_obs, const rb_update_params* params, rb_precision prec, const Marks& mark,
+                          cudaStream_t s) {
+    const int n_freq = F.n;
+    const int ne2 = G.n_elem * G.n_elem;
+    float4* exy = W.at<float4>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    float4* cells = W.at<float4>(W.L.cells);
+    rb_cell* tables = W.at<rb_cell>(W.L.tables);
+    rb_ray_end* ends = W.at<rb_ray_end>(W.L.ends);
+    float2* R = W.at<float2>(W.L.pray);
+    uint8_t* linked = W.at<uint8_t>(W.L.linked);
+    uint8_t* wts = W.at<uint8_t>(W.L.wts);
+    uint64_t* keys = W.at<uint64_t>(W.L.keys);
+    const bool tc = prec == RB_PREC_BF16X3;
+    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4 + DBL_N * 8, s));
+    RB_CU(mark(RB_STAGE_FIELDS, 0));
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_fields(G, c, alpha0, cells, s));
+    RB_CU(mark(RB_STAGE_FIELDS, 1));
+    RB_CU(mark(RB_STAGE_TRACE_GRID, 0));
+    // the mixed path reads only the synthesis records, the plain path only the tables
+    float4* srec = tc ? W.at<float4>(W.L.srec) : nullptr;
+    RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), tc ? nullptr : tables, W.at<void>(W.L.verts), c,
+                       srec, cnt, s));
+    RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
+    RB_CU(mark(RB_STAGE_LINK, 0));
+    RB_CU(launch_link(G, c, ends, F, R, linked, s));
+    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, W.at<void>(W.L.sel), s));
+    RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, W.at<void>(W.L.sel), s));
+    RB_CU(mark(RB_STAGE_LINK, 1));
+    RB_CU(mark(RB_STAGE_IMAGES, 0));
+    if (tc) {
+        const size_t img = tc_b_images_bytes(G.n_elem);
+        for (int w = 0; w < n_freq; ++w)
+            RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
+        RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg), s));
+    }
+    RB_CU(mark(RB_STAGE_IMAGES, 1));
+    RB_CU(mark(RB_STAGE_ADJOINT, 0));
+    if (tc) {
+        RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
+                                nullptr, nullptr, W.at<float>(W.L.gsum), W.at<float>(W.L.hsum), cnt, s));
+    } else {
+        RB_CU(launch_adjoint_simt(G, tables, c, F, R, wts, nullptr, nullptr, W.at<float>(W.L.gsum),
+                                  W.at<float>(W.L.hsum), cnt, s));
+    }
+    RB_CU(mark(RB_STAGE_ADJOINT, 1));
+    return RB_OK;
+}
+
 }  // namespace
 
 GeoDev rb_make_geo(const rb_geometry* g, const float4* elem_xy) { return make_geo(g, elem_xy); }
@@ -162,6 +237,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
     L->srec = o; o = align256(o + (tcp ? ne * npix * 16 : 0));
     L->aimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_aimage_elems(g->n_elem, (int)npix) * 2 : 0));
+    L->cgv = o; o = align256(o + 4 * npix * 4);
     L->total = o;
     return o;
 }
@@ -314,74 +390,28 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
 rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alpha0, const double* freqs_hz,
                        int32_t n_freq, const float* p_obs, const rb_update_params* params, rb_precision prec,
                        float* dc_out, rb_diag* diag_out, void* ws, size_t ws_bytes, rb_stream stream) {
-    if (!geom || !c_inout || !alpha0 || !p_obs || !params) return RB_ERR_ARG;
-    if (prec != RB_PREC_FP32 && prec != RB_PREC_BF16X3) return RB_ERR_ARG;
-    if (!geom_ok(geom)) return RB_ERR_SHAPE;
-    if (!(params->outlier_frac >= 0.0 && params->outlier_frac < 1.0)) return RB_ERR_ARG;
-    if (!(params->eps_rel >= 0.0) || !isfinite(params->eps_rel)) return RB_ERR_ARG;
-    if (params->step_mode != RB_STEP_EXACT && params->step_mode != RB_STEP_DIAG) return RB_ERR_ARG;
     FreqSet F;
-    if (!make_freqs(geom, freqs_hz, n_freq, &F)) return RB_ERR_ARG;
-    if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
+    rb_status st = check_update(geom, c_inout, alpha0, freqs_hz, n_freq, p_obs, params, prec, &F);
+    if (st != RB_OK) return st;
     Ws W;
-    rb_status st = check_ws(geom, n_freq, prec, ws, ws_bytes, &W);
+    st = check_ws(geom, n_freq, prec, ws, ws_bytes, &W);
     if (st != RB_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    float4* exy = W.at<float4>(W.L.elem_xy);
+    const GeoDev G = make_geo(geom, W.at<float4>(W.L.elem_xy));
+    const Marks mark{(cudaEvent_t*)params->stage_events, s};
+    st = gradient_stages(G, F, W, c_inout, alpha0, p_obs, params, prec, mark, s);
+    if (st != RB_OK) return st;
+    const int ne2 = G.n_elem * G.n_elem;
     uint32_t* cnt = W.at<uint32_t>(W.L.counters);
     double* dbl = (double*)(cnt + CNT_N);
-    const GeoDev G = make_geo(geom, exy);
-    const int ne2 = G.n_elem * G.n_elem;
-    float4* cells = W.at<float4>(W.L.cells);
     rb_cell* tables = W.at<rb_cell>(W.L.tables);
-    rb_ray_end* ends = W.at<rb_ray_end>(W.L.ends);
-    float2* R = W.at<float2>(W.L.pray);
-    uint8_t* linked = W.at<uint8_t>(W.L.linked);
     uint8_t* wts = W.at<uint8_t>(W.L.wts);
-    uint64_t* keys = W.at<uint64_t>(W.L.keys);
     float* gsum = W.at<float>(W.L.gsum);
     float* hsum = W.at<float>(W.L.hsum);
     float* pdir = W.at<float>(W.L.pdir);
     double* part = W.at<double>(W.L.part);
     float2* fwd = W.at<float2>(W.L.fwd);
     const int nch = rb_fwd_chunks_for(G.npix);
-    cudaEvent_t* ev = (cudaEvent_t*)params->stage_events;
-    auto mark = [&](int stage, int end) -> cudaError_t {
-        return ev ? cudaEventRecord(ev[2 * stage + end], s) : cudaSuccess;
-    };
-
-    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4 + DBL_N * 8, s));
-    RB_CU(mark(RB_STAGE_FIELDS, 0));
-    RB_CU(launch_elem_positions(G, exy, s));
-    RB_CU(launch_fields(G, c_inout, alpha0, cells, s));
-    RB_CU(mark(RB_STAGE_FIELDS, 1));
-    RB_CU(mark(RB_STAGE_TRACE_GRID, 0));
-    // the mixed path reads only the synthesis records, the plain path only the tables
-    float4* srec = prec == RB_PREC_BF16X3 ? W.at<float4>(W.L.srec) : nullptr;
-    RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), prec == RB_PREC_BF16X3 ? nullptr : tables,
-                       W.at<void>(W.L.verts), c_inout, srec, cnt, s));
-    RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
-    RB_CU(mark(RB_STAGE_LINK, 0));
-    RB_CU(launch_link(G, c_inout, ends, F, R, linked, s));
-    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, W.at<void>(W.L.sel), s));
-    RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, W.at<void>(W.L.sel), s));
-    RB_CU(mark(RB_STAGE_LINK, 1));
-    RB_CU(mark(RB_STAGE_IMAGES, 0));
-    if (prec == RB_PREC_BF16X3) {
-        const size_t img = tc_b_images_bytes(G.n_elem);
-        for (int w = 0; w < n_freq; ++w)
-            RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
-        RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg), s));
-    }
-    RB_CU(mark(RB_STAGE_IMAGES, 1));
-    RB_CU(mark(RB_STAGE_ADJOINT, 0));
-    if (prec == RB_PREC_BF16X3) {
-        RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
-                                nullptr, nullptr, gsum, hsum, cnt, s));
-    } else {
-        RB_CU(launch_adjoint_simt(G, tables, c_inout, F, R, wts, nullptr, nullptr, gsum, hsum, cnt, s));
-    }
-    RB_CU(mark(RB_STAGE_ADJOINT, 1));
     RB_CU(mark(RB_STAGE_DIRECTION, 0));
     RB_CU(launch_update(G, c_inout, gsum, hsum, pdir, dc_out, part, dbl, cnt, diag_out, params->eps_rel,
                         params->step_mode, 0, s));
@@ -405,6 +435,78 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_APPLY, 0));
     RB_CU(launch_update(G, c_inout, gsum, hsum, pdir, dc_out, part + (size_t)RB_MAX_FREQ * 256, dbl, cnt, diag_out,
                         params->eps_rel, params->step_mode, 1, s));
+    RB_CU(mark(RB_STAGE_APPLY, 1));
+    return RB_OK;
+}
+
+rb_status rb_cg_update(const rb_geometry* geom, float* c_inout, const float* alpha0, const double* freqs_hz,
+                       int32_t n_freq, const float* p_obs, const rb_update_params* params, int32_t cg_iters,
+                       int32_t precond, rb_precision prec, float* dc_out, double* cg_hist_out, rb_diag* diag_out,
+                       void* ws, size_t ws_bytes, rb_stream stream) {
+    if (cg_iters < 1 || cg_iters > RB_MAX_CG || (precond != 0 && precond != 1)) return RB_ERR_ARG;
+    FreqSet F;
+    rb_status st = check_update(geom, c_inout, alpha0, freqs_hz, n_freq, p_obs, params, prec, &F);
+    if (st != RB_OK) return st;
+    Ws W;
+    st = check_ws(geom, n_freq, prec, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const GeoDev G = make_geo(geom, W.at<float4>(W.L.elem_xy));
+    const Marks mark{(cudaEvent_t*)params->stage_events, s};
+    st = gradient_stages(G, F, W, c_inout, alpha0, p_obs, params, prec, mark, s);
+    if (st != RB_OK) return st;
+    const int ne2 = G.n_elem * G.n_elem;
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    double* dbl = (double*)(cnt + CNT_N);
+    rb_cell* tables = W.at<rb_cell>(W.L.tables);
+    uint8_t* wts = W.at<uint8_t>(W.L.wts);
+    float* gsum = W.at<float>(W.L.gsum);
+    float* hsum = W.at<float>(W.L.hsum);
+    double* part = W.at<double>(W.L.part);
+    double* vpart = part + (size_t)RB_MAX_FREQ * 256;
+    float* x = W.at<float>(W.L.cgv);
+    float* r = x + G.npix;
+    float* p = r + G.npix;
+    float* q = p + G.npix;
+    // the residuals are consumed by the gradient: their buffer holds B_w p from here on
+    float2* d = W.at<float2>(W.L.pray);
+    const bool tc = prec == RB_PREC_BF16X3;
+    const size_t img = tc_b_images_bytes(G.n_elem);
+    const int nch = rb_fwd_chunks_for(G.npix);
+    RB_CU(mark(RB_STAGE_DIRECTION, 0));
+    RB_CU(launch_cg_init(G, gsum, hsum, precond, x, r, p, part, dbl, params->eps_rel, s));
+    RB_CU(mark(RB_STAGE_DIRECTION, 1));
+    RB_CU(mark(RB_STAGE_FORWARD, 0));
+    for (int k = 0; k < cg_iters; ++k) {
+        // B_w p for every frequency of the set, and sum_w sum W |B_w p|^2
+        for (int w = 0; w < n_freq; ++w) {
+            float2* dw = d + (size_t)w * ne2;
+            if (tc) {
+                RB_CU(launch_forward_tc(G, W.at<char>(W.L.aimg) + (size_t)w * tc_aimage_elems(G.n_elem, G.npix) * 2,
+                                        F.f[w], p, W.at<float>(W.L.tcfwd), tc_ctas(), dw, wts + (size_t)w * ne2,
+                                        part + (size_t)w * 256, cnt, s));
+                RB_CU(launch_prep_b(G.n_elem, dw, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
+            } else {
+                RB_CU(launch_forward_simt(G, tables, c_inout, F.f[w], p, W.at<float2>(W.L.fwd), nch, s));
+                RB_CU(launch_forward_reduce(G, F.f[w], W.at<float2>(W.L.fwd), nch, dw, wts + (size_t)w * ne2,
+                                            part + (size_t)w * 256, s));
+            }
+        }
+        RB_CU(launch_sum_partials(part, n_freq * 256, dbl, DBL_CG_PAP + k, 1.0, 0, s));
+        // q = sum_w Re B_w^H W B_w p
+        if (tc) {
+            RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr),
+                                    tc_ctas(), nullptr, nullptr, q, nullptr, cnt, s));
+        } else {
+            RB_CU(launch_adjoint_simt(G, tables, c_inout, F, d, wts, nullptr, nullptr, q, nullptr, cnt, s));
+        }
+        RB_CU(launch_cg_step(G, hsum, precond, k, x, r, p, q, vpart, dbl, s));
+    }
+    if (cg_hist_out) RB_CU(launch_cg_history(dbl, cg_iters, cg_hist_out, s));
+    RB_CU(mark(RB_STAGE_FORWARD, 1));
+    RB_CU(mark(RB_STAGE_APPLY, 0));
+    RB_CU(launch_update(G, c_inout, gsum, hsum, x, dc_out, vpart, dbl, cnt, diag_out, params->eps_rel, RB_STEP_DIAG,
+                        1, s));
     RB_CU(mark(RB_STAGE_APPLY, 1));
     return RB_OK;
 }

@@ -138,14 +138,6 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// One core-matrix row of a K = 16 slice: the 8 bf16 of K-group g of pixel row p, hi and lo.
-__device__ __forceinline__ void store_row16(unsigned char* a_hi, unsigned char* a_lo, uint32_t p, uint32_t g,
-                                            const uint32_t (&whi)[4], const uint32_t (&wlo)[4]) {
-    const uint32_t off = tc::tile16_offset(p, 8u * g);
-    *(uint4*)(a_hi + off) = make_uint4(whi[0], whi[1], whi[2], whi[3]);
-    *(uint4*)(a_lo + off) = make_uint4(wlo[0], wlo[1], wlo[2], wlo[3]);
-}
-
 // Producer work of one U slice (8 elements, K' = 16) for thread (p, h), h < 4: the
 // A slice in shared memory (two rows of the A image, see k_synth_images) holds, at
 // K' positions 4h .. 4h + 3 of row p, the bf16
@@ -283,6 +275,10 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
             int ql = 0, s = 0, j = 0, fw = 0, tile = blockIdx.x;
             uint32_t ph = 0, vrp = 0;
             bool err = false;
+            // the operand image streams through L2 once per launch: first out, so that it does
+            // not push the CTAs' G and |G|^2 scratch (rewritten every tile) out to DRAM
+            uint64_t stream_pol;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_pol));
             for (; ql < total; ++ql) {
                 // stage s = ql % NST with phase ph = (ql / NST) & 1; slice j of frequency fw of tile
                 if (ql >= NST && !tc::mbar_wait(tc::smem_u32(&s_empty[s]), ph ^ 1u, kMaxTries)) {
@@ -298,12 +294,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     // image rows 2j, 2j + 1 of the hi plane, then of the lo plane
                     const __nv_bfloat16* asrc =
                         A.aimg + (size_t)fw * A.aimg_stride + ((size_t)tile * 2 * (n2 / 8) + 2 * j) * 1024;
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 ::"r"(tc::smem_u32(stage(s))), "l"(asrc), "r"(abytes), "r"(mb)
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                                 " [%0], [%1], %2, [%3], %4;"
+                                 ::"r"(tc::smem_u32(stage(s))), "l"(asrc), "r"(abytes), "r"(mb), "l"(stream_pol)
                                  : "memory");
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                                 " [%0], [%1], %2, [%3], %4;"
                                  ::"r"(tc::smem_u32(stage(s) + ST_ALO)), "l"(asrc + (size_t)(n2 / 8) * 1024), "r"(abytes),
-                                 "r"(mb)
+                                 "r"(mb), "l"(stream_pol)
                                  : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                                  ::"r"(tc::smem_u32(stage(s) + ST_B)),

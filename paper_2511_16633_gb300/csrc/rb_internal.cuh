@@ -222,6 +222,7 @@ struct WsLayout {
     size_t tcfwd;      // tensor-core path: partial D blocks of the forward
     size_t aimg;       // tensor-core path: A operand images of the adjoint, [n_freq][...] bf16
     size_t srec;       // tensor-core path: synthesis records, [n_elem][npix] float4
+    size_t cgv;        // CG variant: x, r, p, q vectors, [4][npix] float
     size_t total;
 };
 
@@ -234,6 +235,10 @@ FreqC rb_make_freq(const rb_geometry* g, double f_hz);
 enum { CNT_LOST = 0, CNT_HOLES = 1, CNT_UNLINKED = 2, CNT_KEPT = 3, CNT_ZEROED = 4, CNT_TC_TIMEOUT = 6, CNT_N = 64 };
 // double scalars after the uint32 block
 enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_HMEAN = 5, DBL_N = 64 };
+// CG variant: rho_k = <r_k, M^-1 r_k> at DBL_CG_RHO + k (k = 0..RB_MAX_CG) and the curvature
+// <p_k, A p_k> at DBL_CG_PAP + k (k = 0..RB_MAX_CG-1)
+enum { DBL_CG_RHO = 8, DBL_CG_PAP = DBL_CG_RHO + RB_MAX_CG + 1 };
+static_assert(DBL_CG_PAP + RB_MAX_CG <= DBL_N, "CG scalars exceed the double block");
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files); all return cudaGetLastError().
@@ -279,6 +284,11 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
                               int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
                               cudaStream_t s);
 cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s);
+cudaError_t launch_cg_init(const GeoDev& G, const float* gsum, const float* hsum, int precond, float* x, float* r,
+                           float* p, double* part, double* dbl, double eps_rel, cudaStream_t s);
+cudaError_t launch_cg_step(const GeoDev& G, const float* hsum, int precond, int k, float* x, float* r, float* p,
+                           const float* q, double* part, double* dbl, cudaStream_t s);
+cudaError_t launch_cg_history(const double* dbl, int iters, double* hist, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);
 cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir,

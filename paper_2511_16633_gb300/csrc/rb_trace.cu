@@ -200,23 +200,6 @@ __device__ __forceinline__ float rel(float vh, float vl, float oh, float ol) {
     return __fadd_rn(__fsub_rn(vh, oh), __fsub_rn(vl, ol));
 }
 
-__device__ __forceinline__ Quad quad_of(const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1) {
-    Quad Q;
-    Q.b0x = rel(B0.xh, B0.xl, A0.xh, A0.xl);
-    Q.b0y = rel(B0.yh, B0.yl, A0.yh, A0.yl);
-    Q.b1x = rel(B1.xh, B1.xl, A0.xh, A0.xl);
-    Q.b1y = rel(B1.yh, B1.yl, A0.yh, A0.yl);
-    Q.a1x = rel(A1.xh, A1.xl, A0.xh, A0.xl);
-    Q.a1y = rel(A1.yh, A1.yl, A0.yh, A0.yl);
-    const float ar0 = __fsub_rn(__fmul_rn(Q.b0x, Q.b1y), __fmul_rn(Q.b0y, Q.b1x));
-    const float ar1 = __fsub_rn(__fmul_rn(Q.b1x, Q.a1y), __fmul_rn(Q.b1y, Q.a1x));
-    Q.t0 = ar0 != 0.f;
-    Q.t1 = ar1 != 0.f;
-    Q.i0 = Q.t0 ? __frcp_rn(ar0) : 0.f;
-    Q.i1 = Q.t1 ? __frcp_rn(ar1) : 0.f;
-    return Q;
-}
-
 // Barycentric weights of the point A0 + (dx, dy) in the triangle with edge vectors
 // (ux, uy), (vx, vy) from A0 and reciprocal doubled area inv: w = (wa, wb, wc) for
 // (A0, A0 + u, A0 + v).
@@ -267,7 +250,7 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
     const int iy1 = min(G.ny - 1, (int)floorf(fmaf(ymax, G.inv_h, va) + 1e-3f));
     if (bx0 > bx1 || iy0 > iy1) return;
     {
-        // as quad_of, with the hardware reciprocal: these weights only decide coverage and
+        // doubled areas of T0 and T1, with the hardware reciprocal: these weights only decide coverage and
         // the residual offered as the key; the table record's weights are formed exactly
         // by the resolve pass
         const float ar0 = __fsub_rn(__fmul_rn(Q.b0x, Q.b1y), __fmul_rn(Q.b0y, Q.b1x));
@@ -409,8 +392,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                     pfi = fi;
                     pfj = fj;
                     const float4* pc = cells + ((size_t)(int)fj * (size_t)(G.nx - 1) + (size_t)(int)fi) * 8;
-                    float dummy;
-                    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(dummy) : "l"(pc));
+                    asm volatile("{ .reg .f32 t; ld.global.nc.f32 t, [%0]; }" ::"l"(pc));
                 }
             }
             const Deriv z{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -624,7 +606,7 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
             const int i = min((int)qi, G.n_rays - 2), k1 = min((int)qk1 + 1, G.max_steps);
             const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
             // the winning triangle only: T0 = (A0, B0, B1), T1 = (A0, B1, A1); edge vectors,
-            // doubled area and weights as in quad_of / bary
+            // doubled area (rounded reciprocal) and weights as in bary
             const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
             const Vtx Vb = get_vtx(half ? verts + vidx(G, t, min(k1, lb), i + 1) : verts + vidx(G, t, min(k1 - 1, lb), i + 1));
             const Vtx Vc = get_vtx(half ? verts + vidx(G, t, min(k1, la), i) : verts + vidx(G, t, min(k1, lb), i + 1));

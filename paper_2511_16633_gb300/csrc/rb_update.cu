@@ -121,6 +121,68 @@ __global__ void __launch_bounds__(RT) k_apply(GeoDev G, float* __restrict__ c, c
     block_sum_store(acc, part + blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// CG variant: preconditioned conjugate gradients (Hestenes and Stiefel, 1952) on the
+// normal equations of the linearised objective of Eq. 10,
+//   A dm = b,  A = sum_w Re(B_w^H W B_w),  b = -sum_w Re g_w,  over the support, dm_0 = 0.
+// M^-1 = 1/(sum_w H_w + eps) per pixel (precond), or the scalar 1/(mean H + eps): a scalar
+// preconditioner leaves the CG iterates those of plain CG and keeps A p within FP32 range.
+// The curvature <p_k, A p_k> is taken as sum_w sum_{e,r} W |B_w p_k|^2 from the forward
+// reduction (equal in exact arithmetic, non-negative by construction).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float cg_minv(const float* __restrict__ hsum, int p, int precond, float eps, float hm) {
+    return precond ? 1.0f / (hsum[p] + eps) : 1.0f / (hm + eps);
+}
+
+__global__ void __launch_bounds__(RT) k_cg_init(GeoDev G, const float* __restrict__ gsum, const float* __restrict__ hsum,
+                                                const double* __restrict__ dbl, int precond, float* __restrict__ x,
+                                                float* __restrict__ r, float* __restrict__ pv, double* __restrict__ part) {
+    const float eps = (float)dbl[DBL_EPS], hm = (float)dbl[DBL_HMEAN];
+    double acc = 0.0;
+    for (int p = blockIdx.x * RT + threadIdx.x; p < G.npix; p += RB * RT) {
+        float rv = 0.f, zv = 0.f;
+        if (in_support(G, p)) {
+            rv = -gsum[p];
+            zv = cg_minv(hsum, p, precond, eps, hm) * rv;
+            acc += (double)rv * (double)zv;
+        }
+        x[p] = 0.f;
+        r[p] = rv;
+        pv[p] = zv;
+    }
+    block_sum_store(acc, part + blockIdx.x);
+}
+
+// x += alpha p, r -= alpha q (alpha = rho_k / <p_k, A p_k>, 0 when the curvature is not
+// positive); partials of rho_{k+1} = <r, M^-1 r>
+__global__ void __launch_bounds__(RT) k_cg_xr(GeoDev G, const float* __restrict__ hsum, const double* __restrict__ dbl,
+                                              int precond, int k, float* __restrict__ x, float* __restrict__ r,
+                                              const float* __restrict__ pv, const float* __restrict__ q,
+                                              double* __restrict__ part) {
+    const float eps = (float)dbl[DBL_EPS], hm = (float)dbl[DBL_HMEAN];
+    const double pap = dbl[DBL_CG_PAP + k];
+    const float a = pap > 0.0 ? (float)(dbl[DBL_CG_RHO + k] / pap) : 0.f;
+    double acc = 0.0;
+    for (int p = blockIdx.x * RT + threadIdx.x; p < G.npix; p += RB * RT) {
+        if (!in_support(G, p)) continue;
+        x[p] = fmaf(a, pv[p], x[p]);
+        const float rv = fmaf(-a, q[p], r[p]);
+        r[p] = rv;
+        acc += (double)rv * (double)(cg_minv(hsum, p, precond, eps, hm) * rv);
+    }
+    block_sum_store(acc, part + blockIdx.x);
+}
+
+// p = M^-1 r + beta p,  beta = rho_{k+1} / rho_k
+__global__ void __launch_bounds__(RT) k_cg_p(GeoDev G, const float* __restrict__ hsum, const double* __restrict__ dbl,
+                                             int precond, int k, const float* __restrict__ r, float* __restrict__ pv) {
+    const float eps = (float)dbl[DBL_EPS], hm = (float)dbl[DBL_HMEAN];
+    const double rho = dbl[DBL_CG_RHO + k];
+    const float beta = rho != 0.0 ? (float)(dbl[DBL_CG_RHO + k + 1] / rho) : 0.f;
+    for (int p = blockIdx.x * RT + threadIdx.x; p < G.npix; p += RB * RT)
+        if (in_support(G, p)) pv[p] = fmaf(beta, pv[p], cg_minv(hsum, p, precond, eps, hm) * r[p]);
+}
+
 __global__ void k_finish(const double* __restrict__ dbl, const uint32_t* __restrict__ cnt, rb_diag* __restrict__ diag) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     rb_diag d;
@@ -159,6 +221,35 @@ cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const fl
         default:
             return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init(const GeoDev& G, const float* gsum, const float* hsum, int precond, float* x, float* r,
+                           float* p, double* part, double* dbl, double eps_rel, cudaStream_t s) {
+    k_hsum_part<<<RB, RT, 0, s>>>(G, hsum, part);
+    k_eps<<<1, RT, 0, s>>>(part, eps_rel, dbl);
+    k_cg_init<<<RB, RT, 0, s>>>(G, gsum, hsum, dbl, precond, x, r, p, part);
+    k_sum_part<<<1, RT, 0, s>>>(part, RB, dbl, DBL_CG_RHO, 1.0, 0);
+    return cudaGetLastError();
+}
+
+// after <p_k, A p_k> is in DBL_CG_PAP + k: x, r, rho_{k+1}, then p_{k+1}
+cudaError_t launch_cg_step(const GeoDev& G, const float* hsum, int precond, int k, float* x, float* r, float* p,
+                           const float* q, double* part, double* dbl, cudaStream_t s) {
+    k_cg_xr<<<RB, RT, 0, s>>>(G, hsum, dbl, precond, k, x, r, p, q, part);
+    k_sum_part<<<1, RT, 0, s>>>(part, RB, dbl, DBL_CG_RHO + k + 1, 1.0, 0);
+    k_cg_p<<<RB, RT, 0, s>>>(G, hsum, dbl, precond, k, r, p);
+    return cudaGetLastError();
+}
+
+__global__ void k_cg_history(const double* __restrict__ dbl, int iters, double* __restrict__ hist) {
+    const int k = threadIdx.x;
+    const double rho0 = dbl[DBL_CG_RHO];
+    if (k <= iters) hist[k] = rho0 != 0.0 ? dbl[DBL_CG_RHO + k] / rho0 : 0.0;
+}
+
+cudaError_t launch_cg_history(const double* dbl, int iters, double* hist, cudaStream_t s) {
+    k_cg_history<<<1, 32, 0, s>>>(dbl, iters, hist);
     return cudaGetLastError();
 }
 

@@ -19,10 +19,11 @@ RB_OK, RB_ERR_ARG, RB_ERR_SHAPE, RB_ERR_WORKSPACE, RB_ERR_CUDA, RB_ERR_LIMIT, RB
 RB_PREC_FP32, RB_PREC_BF16X3 = 0, 1
 RB_STEP_EXACT, RB_STEP_DIAG = 0, 1
 RB_MAX_FREQ = 16
+RB_MAX_CG = 24
 RB_HOLE = 0xFFFFFFFF
 
 EXPORTS = ("rb_workspace_size", "rb_trace_rays", "rb_green_grid", "rb_ray_forward", "rb_born_forward",
-           "rb_born_adjoint", "rb_hf_update", "rb_born_forward_noalloc", "rb_status_string")
+           "rb_born_adjoint", "rb_hf_update", "rb_cg_update", "rb_born_forward_noalloc", "rb_status_string")
 
 
 class RbError(RuntimeError):
@@ -84,6 +85,8 @@ def load(build_if_missing: bool = True):
     L.rb_born_adjoint.argtypes = [G, P, P, ctypes.c_double, P, P, P, P, ctypes.c_int, P, ctypes.c_size_t, P]
     L.rb_hf_update.argtypes = [G, P, P, P, ctypes.c_int32, P, ctypes.POINTER(rb_update_params), ctypes.c_int, P, P,
                                P, ctypes.c_size_t, P]
+    L.rb_cg_update.argtypes = [G, P, P, P, ctypes.c_int32, P, ctypes.POINTER(rb_update_params), ctypes.c_int32,
+                               ctypes.c_int32, ctypes.c_int, P, P, P, P, ctypes.c_size_t, P]
     L.rb_born_forward_noalloc.argtypes = [G, P, P, ctypes.c_double, P, P, P]
     L.rb_status_string.argtypes = [ctypes.c_int]
     L.rb_status_string.restype = ctypes.c_char_p
@@ -210,6 +213,18 @@ def rb_hf_update(geom, c_inout, alpha0, freqs, p_obs, ws, outlier_frac=0.01, eps
     code = load().rb_hf_update(ctypes.byref(geom), _ptr(c_inout), _ptr(alpha0), fa, nf, _ptr(p_obs), ctypes.byref(prm),
                                int(prec), _ptr(dc_out), _ptr(diag_out), _ptr(ws), ws.numel(), _stream(stream))
     _check("rb_hf_update", code)
+
+
+def rb_cg_update(geom, c_inout, alpha0, freqs, p_obs, ws, cg_iters, precond=True, outlier_frac=0.01, eps_rel=1e-3,
+                 prec=RB_PREC_FP32, dc_out=None, hist_out=None, diag_out=None, stream=None, stage_events=None):
+    """CG variant of the update; hist_out: None or a float64 device tensor of cg_iters + 1."""
+    fa, nf = _freqs(freqs)
+    prm = rb_update_params(float(outlier_frac), float(eps_rel), RB_STEP_EXACT, 0,
+                           ctypes.cast(stage_events, ctypes.c_void_p) if stage_events is not None else None)
+    code = load().rb_cg_update(ctypes.byref(geom), _ptr(c_inout), _ptr(alpha0), fa, nf, _ptr(p_obs), ctypes.byref(prm),
+                               int(cg_iters), 1 if precond else 0, int(prec), _ptr(dc_out), _ptr(hist_out),
+                               _ptr(diag_out), _ptr(ws), ws.numel(), _stream(stream))
+    _check("rb_cg_update", code)
 
 
 # ---------------------------------------------------------------------------

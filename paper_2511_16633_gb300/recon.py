@@ -1,8 +1,10 @@
 """Device-resident driver for sweeps of ray-Born updates (marshalling only).
 
 ``Reconstruction`` owns the device buffers of one problem (sound speed,
-absorption, measured data, workspace) and calls ``rb_hf_update`` once per
-frequency set, low to high, leaving c(x) resident between sets.  ``synth_data``
+absorption, measured data, workspace) and calls ``rb_hf_update`` (or, for the
+CG variant, ``rb_cg_update``) once per frequency set, low to high, leaving c(x)
+resident between sets.  ``compare_solvers`` (``python -m
+paper_2511_16633_gb300.recon``) runs the one-step update against CG updates.  ``synth_data``
 builds synthetic measurements on the device through the library's own
 forward entry points (ray data plus Born-scattered data about a background
 model, plus seeded noise); it is input preparation for benchmarks and demos.
@@ -70,12 +72,15 @@ class Reconstruction:
     """One problem resident on the device; update(j) runs frequency set j."""
 
     def __init__(self, cfg, c_init, alpha0, p_obs, prec=rb.RB_PREC_FP32, outlier_frac=0.01, eps_rel=1e-3,
-                 step_mode=rb.RB_STEP_EXACT, device="cuda"):
+                 step_mode=rb.RB_STEP_EXACT, device="cuda", cg_iters=0, cg_precond=True):
+        """cg_iters > 0 solves each set's linear equation by that many CG iterations
+        (rb_cg_update) instead of the one-step update."""
         import torch
         self.cfg = cfg
         self.geom = rb.geometry_from_config(cfg)
         self.prec = prec
         self.outlier_frac, self.eps_rel, self.step_mode = outlier_frac, eps_rel, step_mode
+        self.cg_iters, self.cg_precond = int(cg_iters), bool(cg_precond)
         self.device = torch.device(device)
         self.c = torch.as_tensor(np.asarray(c_init, dtype=np.float32), device=self.device).contiguous().clone()
         self.alpha0 = torch.as_tensor(np.asarray(alpha0, dtype=np.float32), device=self.device).contiguous()
@@ -92,8 +97,13 @@ class Reconstruction:
         lo, hi = s[0], s[-1] + 1
         if list(s) != list(range(lo, hi)):
             raise ValueError("frequency sets must be consecutive")
-        rb.rb_hf_update(self.geom, self.c, self.alpha0, freqs, self.p_obs[lo:hi], self.ws, self.outlier_frac,
-                        self.eps_rel, self.step_mode, self.prec, self.dc, self.diag, stream)
+        if self.cg_iters > 0:
+            rb.rb_cg_update(self.geom, self.c, self.alpha0, freqs, self.p_obs[lo:hi], self.ws, self.cg_iters,
+                            self.cg_precond, self.outlier_frac, self.eps_rel, self.prec, self.dc, None, self.diag,
+                            stream)
+        else:
+            rb.rb_hf_update(self.geom, self.c, self.alpha0, freqs, self.p_obs[lo:hi], self.ws, self.outlier_frac,
+                            self.eps_rel, self.step_mode, self.prec, self.dc, self.diag, stream)
 
     def diagnostics(self) -> dict:
         return rb.decode_diag(self.diag)
@@ -104,3 +114,75 @@ class Reconstruction:
             self.update(j)
             self.norms.append(self.diagnostics()["dc_norm"])
         return self.c
+
+
+def compare_solvers(cfg, variants: Sequence[int], prec=rb.RB_PREC_BF16X3, device="cuda", precond=True,
+                    data: str = "born") -> dict:
+    """Full sweeps of one synthetic problem with the one-step update (variant 0) and with
+    CG updates of k iterations (variant k): per variant the RMS error of c against the
+    true phantom over the support after every set, and the device time of the sweep.
+    data "born": ray data about c_init plus the Born-scattered data of the contrast (as
+    ``synth_data``); "ray": the ray-model data of the true medium (no scattering term)."""
+    import torch
+
+    import rbgen
+    dev = torch.device(device)
+    inp = rbgen.make_inputs(cfg)
+    geom = rb.geometry_from_config(cfg)
+    c0 = torch.as_tensor(inp.c_init, device=dev).contiguous()
+    a0 = torch.as_tensor(inp.alpha0, device=dev).contiguous()
+    ct = torch.as_tensor(inp.c_true, device=dev).contiguous()
+    if data == "born":
+        p = synth_data(geom, c0, ct, a0, list(cfg.freqs_hz), inp.noise_re, inp.noise_im, 0.01, prec)
+    elif data == "ray":
+        p = synth_data(geom, ct, ct, a0, list(cfg.freqs_hz), inp.noise_re, inp.noise_im, 0.01, prec)
+    else:
+        raise ValueError(data)
+    sup = _support_mask(geom, dev)
+
+    def rms():
+        return float(torch.sqrt(torch.mean((rec.c - ct)[sup].double() ** 2)))
+
+    out = {"workload": cfg.name, "data": data, "precond": precond, "n_sets": len(cfg.sets), "rms_init": float(torch.sqrt(torch.mean((c0 - ct)[sup].double() ** 2))),
+           "variants": []}
+    for k in variants:
+        rec = Reconstruction(cfg, inp.c_init, inp.alpha0, p, prec=prec, device=dev, cg_iters=k, cg_precond=precond)
+        rec.update(0)   # warm-up (and first-use setup) on set 0, then the timed sweep from c_init
+        rec.c.copy_(c0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        errs = []
+        ms = 0.0
+        for j in range(len(cfg.sets)):
+            e0.record()
+            rec.update(j)
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            errs.append(rms())
+        out["variants"].append({"solver": "one-step" if k == 0 else f"cg{k}", "sweep_ms": ms, "rms_after_set": errs})
+        del rec
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    import argparse
+    import json
+
+    import rbgen
+    ap = argparse.ArgumentParser(description="one-step update against CG updates over a full sweep")
+    ap.add_argument("--workload", default="breast512", choices=sorted(rbgen.CONFIGS))
+    ap.add_argument("--cg", default="0,4,12", help="comma-separated CG iteration counts (0: one-step update)")
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"])
+    ap.add_argument("--plain-cg", action="store_true", help="CG without the diagonal preconditioner")
+    ap.add_argument("--data", default="born", choices=["born", "ray"])
+    a = ap.parse_args()
+    prec = rb.RB_PREC_BF16X3 if a.prec == "bf16x3" else rb.RB_PREC_FP32
+    res = compare_solvers(rbgen.config_by_name(a.workload), [int(x) for x in a.cg.split(",")], prec,
+                          precond=not a.plain_cg, data=a.data)
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

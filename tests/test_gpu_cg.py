@@ -1,0 +1,126 @@
+"""GPU parity of the CG variant (rb_cg_update) against the oracle's cg_update.
+
+Same seeded inputs on both sides.  Tolerances: dc within 1 % relative L2 and ||dc||
+within 0.5 % after 4 iterations (the FP32 path's operator matches the oracle's to about
+1e-4; CG amplifies that mildly over a few iterations), and the history rho_k / rho_0
+within 2 % (1e-3 absolute for entries below 0.05).  One iteration with the diagonal
+preconditioner is the one-step update, so on the GPU it matches rb_hf_update's
+exact step to rounding.
+"""
+import numpy as np
+import pytest
+
+import rbgen
+from oracle import geometry as ogeom
+from oracle import update as oupd
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_16633_gb300 import rb  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rb.load()
+    return torch.device("cuda:0")
+
+
+def _t(a, dev):
+    return torch.as_tensor(np.ascontiguousarray(a), device=dev).to(torch.float32).contiguous()
+
+
+def _problem(cfg, nf=1):
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    freqs = list(cfg.freqs_hz[1:1 + nf])
+    p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, freqs, inp.noise_re, inp.noise_im)
+    return g, inp, freqs, p_obs
+
+
+def _gpu_cg(cfg, inp, freqs, p_obs, dev, iters, pre, prec):
+    geom = rb.geometry_from_config(cfg)
+    c = _t(inp.c_init, dev)
+    dc = torch.empty_like(c)
+    hist = torch.zeros(iters + 1, dtype=torch.float64, device=dev)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    ws = rb.workspace(geom, len(freqs), prec, dev)
+    rb.rb_cg_update(geom, c, _t(inp.alpha0, dev), freqs, torch.as_tensor(p_obs.astype(np.complex64), device=dev), ws,
+                    iters, pre, prec=prec, dc_out=dc, hist_out=hist, diag_out=diag)
+    torch.cuda.synchronize()
+    return c.cpu().numpy(), dc.cpu().numpy(), hist.cpu().numpy(), rb.decode_diag(diag)
+
+
+def _check(g, ref, dc, hist, d, label):
+    sup = ogeom.support_mask(g)
+    e = np.linalg.norm((dc - ref.dc)[sup]) / np.linalg.norm(ref.dc[sup])
+    rh = np.asarray(ref.rho) / ref.rho[0]
+    print(f"{label}: dc rel L2 {e:.3g}, norm {d['dc_norm']:.6g} vs {ref.dc_norm:.6g}, "
+          f"hist {np.array2string(hist, precision=4)} vs {np.array2string(rh, precision=4)}")
+    assert d["tc_timeouts"] == 0 and d["lost_rays"] == 0
+    assert e <= 1e-2, e
+    assert abs(d["dc_norm"] - ref.dc_norm) <= 5e-3 * ref.dc_norm
+    assert np.all(np.abs(hist - rh) <= np.maximum(2e-2 * rh, 1e-3)), (hist, rh)
+
+
+@pytest.mark.parametrize("prec", [rb.RB_PREC_FP32, rb.RB_PREC_BF16X3], ids=["fp32", "bf16x3"])
+@pytest.mark.parametrize("pre", [True, False], ids=["precond", "plain"])
+def test_cg_tiny(dev, prec, pre):
+    cfg = rbgen.tiny()
+    g, inp, freqs, p_obs = _problem(cfg, nf=2)
+    ref = oupd.cg_update(g, inp.c_init, inp.alpha0, freqs, p_obs, 4, precond=pre)
+    c, dc, hist, d = _gpu_cg(cfg, inp, freqs, p_obs, dev, 4, pre, prec)
+    _check(g, ref, dc, hist, d, f"tiny prec={prec} pre={pre}")
+    assert np.allclose(c, inp.c_init.astype(np.float32) + dc, rtol=0, atol=1e-3)
+
+
+@pytest.mark.parametrize("prec", [rb.RB_PREC_FP32, rb.RB_PREC_BF16X3], ids=["fp32", "bf16x3"])
+def test_cg_ragged_128(dev, prec):
+    cfg = rbgen.tiny(n_elem=128, nx=70, ny=66, n_rays=48)
+    g, inp, freqs, p_obs = _problem(cfg, nf=1)
+    assert g.npix % 128 != 0
+    ref = oupd.cg_update(g, inp.c_init, inp.alpha0, freqs, p_obs, 3, precond=True)
+    c, dc, hist, d = _gpu_cg(cfg, inp, freqs, p_obs, dev, 3, True, prec)
+    _check(g, ref, dc, hist, d, f"ragged128 prec={prec}")
+
+
+@pytest.mark.parametrize("prec", [rb.RB_PREC_FP32, rb.RB_PREC_BF16X3], ids=["fp32", "bf16x3"])
+def test_cg_one_iteration_is_hf_update(dev, prec):
+    cfg = rbgen.tiny()
+    g, inp, freqs, p_obs = _problem(cfg, nf=1)
+    geom = rb.geometry_from_config(cfg)
+    _, dc_cg, _, d_cg = _gpu_cg(cfg, inp, freqs, p_obs, dev, 1, True, prec)
+    c = _t(inp.c_init, dev)
+    dc = torch.empty_like(c)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    ws = rb.workspace(geom, 1, prec, dev)
+    rb.rb_hf_update(geom, c, _t(inp.alpha0, dev), freqs, torch.as_tensor(p_obs.astype(np.complex64), device=dev), ws,
+                    prec=prec, dc_out=dc, diag_out=diag)
+    torch.cuda.synchronize()
+    dc = dc.cpu().numpy()
+    assert np.linalg.norm(dc_cg - dc) <= 1e-4 * np.linalg.norm(dc)
+
+
+def test_cg_sweep_tiny(dev):
+    """A whole sweep with 4 CG iterations per set: the sound-speed map after the last set
+    within 0.05 m/s RMS of the oracle's, and ||dc|| per set within 0.5 %."""
+    cfg = rbgen.tiny()
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, cfg.freqs_hz, inp.noise_re, inp.noise_im)
+    c = np.asarray(inp.c_init, dtype=np.float64)
+    norms = []
+    for s in cfg.sets:
+        r = oupd.cg_update(g, c, inp.alpha0, [cfg.freqs_hz[i] for i in s], p_obs[list(s)], 4)
+        c = r.c_new
+        norms.append(r.dc_norm)
+    from paper_2511_16633_gb300.recon import Reconstruction
+    rec = Reconstruction(cfg, inp.c_init, inp.alpha0, p_obs.astype(np.complex64), device=dev, cg_iters=4)
+    c_gpu = rec.sweep().cpu().numpy()
+    sup = ogeom.support_mask(g)
+    rms = np.sqrt(np.mean((c_gpu - c)[sup] ** 2))
+    print(f"CG sweep: c RMS difference {rms:.3g} m/s; norms {rec.norms} vs {norms}")
+    assert rms <= 0.05, rms
+    assert np.allclose(rec.norms, norms, rtol=5e-3)
