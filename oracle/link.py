@@ -36,6 +36,8 @@ class Links:
     L: np.ndarray
     kappa: np.ndarray
     c_rx: np.ndarray    # [r] sound speed sampled at each receiver
+    best: np.ndarray    # [e, r] winning interval i (rays i, i + 1); -1 if unlinked
+    lam: np.ndarray     # [e, r] its interpolation weight of ray i + 1
 
 
 def link(g: Geom, E: np.ndarray, lost: np.ndarray, c: np.ndarray) -> Links:
@@ -48,6 +50,8 @@ def link(g: Geom, E: np.ndarray, lost: np.ndarray, c: np.ndarray) -> Links:
     Q = np.zeros((n, n))
     L = np.zeros((n, n))
     K = np.zeros((n, n), dtype=np.int64)
+    BI = np.full((n, n), -1, dtype=np.int64)
+    LM = np.zeros((n, n))
     two_pi = 2.0 * math.pi
     for e in range(n):
         ex, ey = E[e, :, VX], E[e, :, VY]
@@ -76,8 +80,10 @@ def link(g: Geom, E: np.ndarray, lost: np.ndarray, c: np.ndarray) -> Links:
         Q[e] = np.where(has, (1 - lb) * q0 + lb * q1, 0.0)
         L[e] = np.where(has, (1 - lb) * l0 + lb * l1, 0.0)
         K[e] = np.where(has, np.where(lb <= 0.5, k0, k1), 0).astype(np.int64)
+        BI[e] = np.where(has, best, -1)
+        LM[e] = np.where(has, lb, 0.0)
     c_rx = bilinear(g, c2, xe, ye)
-    return Links(linked, T, Q, L, K, c_rx)
+    return Links(linked, T, Q, L, K, c_rx, BI, LM)
 
 
 def ray_data(g: Geom, links: Links, f_hz: float) -> np.ndarray:
