@@ -255,6 +255,34 @@ rb_status rb_cg_update(const rb_geometry* geom, float* c_inout, const float* alp
                        void* ws, size_t ws_bytes, rb_stream stream);
 
 /*
+ * Times of flight along rays (Sec. 4, the measured quantity of the time-of-flight
+ * initial guess): the first-arrival traveltime of the ray linking of every pair,
+ * as in rb_ray_forward, through c[ny*nx].  t_out[n_elem][n_elem] double (device,
+ * 0 where unlinked); linked_out[n_elem][n_elem] (nullable) 1 where linked.
+ */
+rb_status rb_tof_times(const rb_geometry* geom, const float* c, const float* alpha0, double* t_out,
+                       uint8_t* linked_out, void* ws, size_t ws_bytes, rb_stream stream);
+
+/* Largest n_iter of rb_tof_invert. */
+#define RB_MAX_TOF_ITERS 16
+
+/*
+ * Time-of-flight initial guess (Sec. 4: a few linearisations of a reconstruction
+ * that fits measured times of flight with times along rays; the paper uses three).
+ * Each linearisation traces the fans through c_inout, links them, and takes one
+ * SIRT step in slowness along the rays (ds = D_col^-1 L^T D_row^-1 (t_obs - T(c))
+ * with L the ray-path operator of the linked times; rows: the opposite ~75 % of
+ * the ring, linked in the data (obs_linked) and in c); c_inout <- 1/(1/c + ds) on
+ * the support.  t_obs, obs_linked [n_elem][n_elem] device (e.g. from
+ * rb_tof_times).  resid_out (nullable, device, n_iter + 1 doubles): RMS ToF
+ * misfit of the rows before each linearisation and after the last.  n_iter in
+ * 1..RB_MAX_TOF_ITERS.  Workspace as rb_workspace_size(geom, 1, RB_PREC_FP32).
+ */
+rb_status rb_tof_invert(const rb_geometry* geom, float* c_inout, const float* alpha0, const double* t_obs,
+                        const uint8_t* obs_linked, int32_t n_iter, double* resid_out, void* ws, size_t ws_bytes,
+                        rb_stream stream);
+
+/*
  * Born forward operator without a workspace (the paper has no counterpart:
  * this is a calling convention of the library).  For callers that cannot
  * give the library device scratch memory, such as plugins of a host

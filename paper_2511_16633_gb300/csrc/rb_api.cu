@@ -238,6 +238,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->srec = o; o = align256(o + (tcp ? ne * npix * 16 : 0));
     L->aimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_aimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->cgv = o; o = align256(o + 4 * npix * 4);
+    L->tof = o; o = align256(o + tof_ws_bytes(g->n_elem, g->n_rays, (int)npix));
     L->total = o;
     return o;
 }
@@ -508,6 +509,59 @@ rb_status rb_cg_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(launch_update(G, c_inout, gsum, hsum, x, dc_out, vpart, dbl, cnt, diag_out, params->eps_rel, RB_STEP_DIAG,
                         1, s));
     RB_CU(mark(RB_STAGE_APPLY, 1));
+    return RB_OK;
+}
+
+rb_status rb_tof_times(const rb_geometry* geom, const float* c, const float* alpha0, double* t_out,
+                       uint8_t* linked_out, void* ws, size_t ws_bytes, rb_stream stream) {
+    if (!geom || !c || !alpha0 || !t_out) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    Ws W;
+    rb_status st = check_ws(geom, 1, RB_PREC_FP32, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    float4* exy = W.at<float4>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    const GeoDev G = make_geo(geom, exy);
+    rb_ray_end* ends = W.at<rb_ray_end>(W.L.ends);
+    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), ends, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cnt, s));
+    RB_CU(launch_tof_link(G, c, ends, W.at<void>(W.L.tof), linked_out, s));
+    RB_CU(launch_tof_times_out(G, W.at<void>(W.L.tof), t_out, s));
+    return RB_OK;
+}
+
+rb_status rb_tof_invert(const rb_geometry* geom, float* c_inout, const float* alpha0, const double* t_obs,
+                        const uint8_t* obs_linked, int32_t n_iter, double* resid_out, void* ws, size_t ws_bytes,
+                        rb_stream stream) {
+    if (!geom || !c_inout || !alpha0 || !t_obs || !obs_linked) return RB_ERR_ARG;
+    if (n_iter < 1 || n_iter > RB_MAX_TOF_ITERS) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    Ws W;
+    rb_status st = check_ws(geom, 1, RB_PREC_FP32, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    float4* exy = W.at<float4>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    const GeoDev G = make_geo(geom, exy);
+    rb_ray_end* ends = W.at<rb_ray_end>(W.L.ends);
+    float4* cells = W.at<float4>(W.L.cells);
+    void* tw = W.at<void>(W.L.tof);
+    Vtx* verts = W.at<Vtx>(W.L.verts);
+    double* part = W.at<double>(W.L.part);
+    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
+    RB_CU(launch_elem_positions(G, exy, s));
+    for (int k = 0; k <= n_iter; ++k) {
+        const bool last = k == n_iter;
+        RB_CU(launch_fields(G, c_inout, alpha0, cells, s));
+        RB_CU(launch_trace(G, cells, ends, nullptr, nullptr, nullptr, last ? nullptr : (void*)verts, nullptr, nullptr,
+                           cnt, s));
+        RB_CU(launch_tof_link(G, c_inout, ends, tw, nullptr, s));
+        if (resid_out) RB_CU(launch_tof_resid(G, tw, t_obs, obs_linked, part, resid_out + k, s));
+        if (!last) RB_CU(launch_tof_step(G, verts, ends, tw, t_obs, obs_linked, c_inout, s));
+    }
     return RB_OK;
 }
 

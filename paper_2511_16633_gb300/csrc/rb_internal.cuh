@@ -223,6 +223,7 @@ struct WsLayout {
     size_t aimg;       // tensor-core path: A operand images of the adjoint, [n_freq][...] bf16
     size_t srec;       // tensor-core path: synthesis records, [n_elem][npix] float4
     size_t cgv;        // CG variant: x, r, p, q vectors, [4][npix] float
+    size_t tof;        // time-of-flight guess: link records, ray lengths and coefficients, pixel sums
     size_t total;
 };
 
@@ -240,6 +241,23 @@ enum { DBL_EPS = 0, DBL_NUM = 1, DBL_DEN = 2, DBL_ALPHA = 3, DBL_NORM2 = 4, DBL_
 enum { DBL_CG_RHO = 8, DBL_CG_PAP = DBL_CG_RHO + RB_MAX_CG + 1 };
 static_assert(DBL_CG_PAP + RB_MAX_CG <= DBL_N, "CG scalars exceed the double block");
 
+// One ray vertex in the vertex stream (written by the ray tracer when a buffer is
+// given): position as float pairs, traveltime, q, l and the KMAH count (32 bytes).
+struct Vtx { float xh, xl, yh, yl, t, q, l; int k; };
+
+// Vertex k of ray i of fan t in the vertex stream: [fan][step][ray].
+__device__ __forceinline__ size_t vtx_index(const GeoDev& G, int t, int k, int i) {
+    return ((size_t)t * (size_t)(G.max_steps + 1) + (size_t)k) * (size_t)G.n_rays + (size_t)i;
+}
+
+// First-arrival link of one (emitter, receiver) pair: the traveltime, the winning
+// interval (rays i, i + 1; -1 if unlinked) and the interpolation weight of ray i + 1.
+struct LinkRec {
+    double T;
+    int32_t i;
+    float lam;
+};
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files); all return cudaGetLastError().
 // ---------------------------------------------------------------------------
@@ -254,7 +272,7 @@ size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);
 cudaError_t launch_link(const GeoDev& G, const float* c, const rb_ray_end* ends, const FreqSet& F,
-                        float2* p_out, uint8_t* linked, cudaStream_t s);
+                        float2* p_out, uint8_t* linked, cudaStream_t s, LinkRec* lrec = nullptr);
 // outlier selection: histogram, scalars and candidates (rb_sel_bytes) in sel_ws
 size_t rb_sel_bytes();
 cudaError_t launch_residual_keys(const GeoDev& G, int n_freq, const float2* p_obs, float2* r_inout,
@@ -288,6 +306,14 @@ cudaError_t launch_cg_init(const GeoDev& G, const float* gsum, const float* hsum
                            float* p, double* part, double* dbl, double eps_rel, cudaStream_t s);
 cudaError_t launch_cg_step(const GeoDev& G, const float* hsum, int precond, int k, float* x, float* r, float* p,
                            const float* q, double* part, double* dbl, cudaStream_t s);
+size_t tof_ws_bytes(int n_elem, int n_rays, int npix);
+cudaError_t launch_tof_link(const GeoDev& G, const float* c, const rb_ray_end* ends, void* tof_ws, uint8_t* linked,
+                            cudaStream_t s);
+cudaError_t launch_tof_times_out(const GeoDev& G, void* tof_ws, double* t_out, cudaStream_t s);
+cudaError_t launch_tof_resid(const GeoDev& G, void* tof_ws, const double* t_obs, const uint8_t* obs_linked,
+                             double* part, double* out, cudaStream_t s);
+cudaError_t launch_tof_step(const GeoDev& G, const Vtx* verts, const rb_ray_end* ends, void* tof_ws, const double* t_obs,
+                            const uint8_t* obs_linked, float* c, cudaStream_t s);
 cudaError_t launch_cg_history(const double* dbl, int iters, double* hist, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);

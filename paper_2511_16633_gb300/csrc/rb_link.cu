@@ -54,7 +54,8 @@ __device__ __forceinline__ unsigned long long d2key(double v) {
 // smallest interval index in a second pass, which reproduces a sequential scan
 // over i that keeps the first strictly smaller T.
 __global__ void __launch_bounds__(256) k_link(GeoDev G, const float* __restrict__ c, const rb_ray_end* __restrict__ ends,
-                                              FreqSet F, float2* __restrict__ p_out, uint8_t* __restrict__ linked) {
+                                              FreqSet F, float2* __restrict__ p_out, uint8_t* __restrict__ linked,
+                                              LinkRec* __restrict__ lrec) {
     extern __shared__ unsigned char smem[];
     const int n = G.n_rays, N = G.n_elem;
     double* th = (double*)smem;                             // [n]
@@ -124,12 +125,15 @@ __global__ void __launch_bounds__(256) k_link(GeoDev G, const float* __restrict_
         const int bsel = bi[dr];
         if (linked) linked[o] = bsel != 0x7fffffff ? 1 : 0;
         if (bsel == 0x7fffffff) {
+            if (lrec) lrec[o] = LinkRec{0.0, -1, 0.f};
             for (int w = 0; w < F.n; ++w) p_out[(size_t)w * N * N + o] = make_float2(0.f, 0.f);
             continue;
         }
         const double thr = two_pi * (double)dr / (double)N;
         double bestLam;
         const double bestT = bracket_T(cht[dr], th[bsel], th[bsel + 1], thr, tr[bsel], tr[bsel + 1], &bestLam);
+        if (lrec) lrec[o] = LinkRec{bestT, bsel, (float)bestLam};
+        if (F.n == 0) continue;
         double xr, yr;
         sincos(two_pi * (double)r / (double)N, &yr, &xr);
         xr *= G.R_d;
@@ -376,14 +380,14 @@ __global__ void k_sel_write(int n_total, const uint64_t* __restrict__ keys, cons
 }  // namespace
 
 cudaError_t launch_link(const GeoDev& G, const float* c, const rb_ray_end* ends, const FreqSet& F, float2* p_out,
-                        uint8_t* linked, cudaStream_t s) {
+                        uint8_t* linked, cudaStream_t s, LinkRec* lrec) {
     if (G.n_rays > LINK_MAX_RAYS) return cudaErrorInvalidValue;
     const size_t sm = (size_t)G.n_rays * (8 + 8 + 4 + 4 + 4 + 4) + (size_t)G.n_elem * (8 + 8 + 4);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_link, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_link<<<G.n_elem, 256, sm, s>>>(G, c, ends, F, p_out, linked);
+    k_link<<<G.n_elem, 256, sm, s>>>(G, c, ends, F, p_out, linked, lrec);
     return cudaGetLastError();
 }
 

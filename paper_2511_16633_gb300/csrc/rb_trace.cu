@@ -44,8 +44,6 @@ struct Cache {
 
 struct Deriv { float x, y, th, t, q, p, l; };
 
-struct Vtx { float xh, xl, yh, yl, t, q, l; int k; };
-
 // Bilinear samples of c, c_x, c_y, c_xx, c_xy, c_yy, alpha0 at (px, py).  The cell
 // record holds per field the coefficients (a, b, c, d) of a + b u + c v + d u v over the
 // cell's unit square, paired fields side by side (rb_fields.cu), so each pair takes three
@@ -312,10 +310,7 @@ __device__ __forceinline__ void udivmod(uint32_t q, uint32_t d, uint32_t m, uint
     rem = r;
 }
 
-// Vertex k of ray i of fan t in the vertex stream: [fan][step][ray], 32 bytes each.
-__device__ __forceinline__ size_t vidx(const GeoDev& G, int t, int k, int i) {
-    return ((size_t)t * (size_t)(G.max_steps + 1) + (size_t)k) * (size_t)G.n_rays + (size_t)i;
-}
+__device__ __forceinline__ size_t vidx(const GeoDev& G, int t, int k, int i) { return vtx_index(G, t, k, i); }
 
 __device__ __forceinline__ void put_vtx(Vtx* dst, const Vtx& v) {
     float4* d = reinterpret_cast<float4*>(dst);
@@ -650,8 +645,9 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
         S = *samples;
         ws = 1;
     }
+    // vertices are stored whenever a buffer is given; gridding needs them and the keys
     const bool grid = keys != nullptr;
-    Vtx* V = grid ? (Vtx*)verts : nullptr;
+    Vtx* V = (Vtx*)verts;
     if (grid && (!V || (!tables && !srec))) return cudaErrorInvalidValue;
     unsigned long long* K = (unsigned long long*)keys;
     if (grid) {

@@ -20,10 +20,12 @@ RB_PREC_FP32, RB_PREC_BF16X3 = 0, 1
 RB_STEP_EXACT, RB_STEP_DIAG = 0, 1
 RB_MAX_FREQ = 16
 RB_MAX_CG = 24
+RB_MAX_TOF_ITERS = 16
 RB_HOLE = 0xFFFFFFFF
 
 EXPORTS = ("rb_workspace_size", "rb_trace_rays", "rb_green_grid", "rb_ray_forward", "rb_born_forward",
-           "rb_born_adjoint", "rb_hf_update", "rb_cg_update", "rb_born_forward_noalloc", "rb_status_string")
+           "rb_born_adjoint", "rb_hf_update", "rb_cg_update", "rb_tof_times", "rb_tof_invert", "rb_born_forward_noalloc",
+           "rb_status_string")
 
 
 class RbError(RuntimeError):
@@ -87,6 +89,8 @@ def load(build_if_missing: bool = True):
                                P, ctypes.c_size_t, P]
     L.rb_cg_update.argtypes = [G, P, P, P, ctypes.c_int32, P, ctypes.POINTER(rb_update_params), ctypes.c_int32,
                                ctypes.c_int32, ctypes.c_int, P, P, P, P, ctypes.c_size_t, P]
+    L.rb_tof_times.argtypes = [G, P, P, P, P, P, ctypes.c_size_t, P]
+    L.rb_tof_invert.argtypes = [G, P, P, P, P, ctypes.c_int32, P, P, ctypes.c_size_t, P]
     L.rb_born_forward_noalloc.argtypes = [G, P, P, ctypes.c_double, P, P, P]
     L.rb_status_string.argtypes = [ctypes.c_int]
     L.rb_status_string.restype = ctypes.c_char_p
@@ -225,6 +229,20 @@ def rb_cg_update(geom, c_inout, alpha0, freqs, p_obs, ws, cg_iters, precond=True
                                int(cg_iters), 1 if precond else 0, int(prec), _ptr(dc_out), _ptr(hist_out),
                                _ptr(diag_out), _ptr(ws), ws.numel(), _stream(stream))
     _check("rb_cg_update", code)
+
+
+def rb_tof_times(geom, c, alpha0, t_out, ws, linked_out=None, stream=None):
+    """Linked first-arrival times of flight: t_out [n_elem, n_elem] float64 device tensor."""
+    code = load().rb_tof_times(ctypes.byref(geom), _ptr(c), _ptr(alpha0), _ptr(t_out), _ptr(linked_out), _ptr(ws),
+                               ws.numel(), _stream(stream))
+    _check("rb_tof_times", code)
+
+
+def rb_tof_invert(geom, c_inout, alpha0, t_obs, obs_linked, ws, n_iter=3, resid_out=None, stream=None):
+    """Time-of-flight initial guess: n_iter linearisations in place on c_inout."""
+    code = load().rb_tof_invert(ctypes.byref(geom), _ptr(c_inout), _ptr(alpha0), _ptr(t_obs), _ptr(obs_linked),
+                                int(n_iter), _ptr(resid_out), _ptr(ws), ws.numel(), _stream(stream))
+    _check("rb_tof_invert", code)
 
 
 # ---------------------------------------------------------------------------

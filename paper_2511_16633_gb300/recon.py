@@ -116,6 +116,40 @@ class Reconstruction:
         return self.c
 
 
+def tof_guess(cfg, n_iter: int = 3, device="cuda", noise_s: float = 0.0, c_start=None):
+    """The time-of-flight initial guess: times of flight through the true phantom
+    (rb_tof_times; plus noise_s seconds times the seeded normal draws, as picking
+    jitter), then n_iter linearisations (rb_tof_invert) from water (or c_start).
+    Returns (c [device], RMS misfit history [s], device milliseconds of the inversion)."""
+    import torch
+
+    import rbgen
+    dev = torch.device(device)
+    inp = rbgen.make_inputs(cfg)
+    geom = rb.geometry_from_config(cfg)
+    n = cfg.n_elem
+    ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    a0 = torch.as_tensor(inp.alpha0, device=dev, dtype=torch.float32).contiguous()
+    ct = torch.as_tensor(inp.c_true, device=dev, dtype=torch.float32).contiguous()
+    T = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    lk = torch.zeros((n, n), dtype=torch.uint8, device=dev)
+    rb.rb_tof_times(geom, ct, a0, T, ws, lk)
+    if noise_s > 0:
+        T += noise_s * torch.as_tensor(inp.noise_re[0], device=dev, dtype=torch.float64)
+    if c_start is None:
+        c = torch.full((cfg.ny, cfg.nx), float(cfg.c_water), device=dev, dtype=torch.float32)
+    else:
+        c = torch.as_tensor(np.asarray(c_start, dtype=np.float32), device=dev).contiguous().clone()
+    hist = torch.zeros(n_iter + 1, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    rb.rb_tof_invert(geom, c, a0, T, lk, ws, n_iter, hist)
+    e1.record()
+    e1.synchronize()
+    return c, hist.cpu().numpy().tolist(), e0.elapsed_time(e1)
+
+
 def compare_solvers(cfg, variants: Sequence[int], prec=rb.RB_PREC_BF16X3, device="cuda", precond=True,
                     data: str = "born") -> dict:
     """Full sweeps of one synthetic problem with the one-step update (variant 0) and with
@@ -177,7 +211,26 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"])
     ap.add_argument("--plain-cg", action="store_true", help="CG without the diagonal preconditioner")
     ap.add_argument("--data", default="born", choices=["born", "ray"])
+    ap.add_argument("--tof", type=int, default=0,
+                    help="only the time-of-flight initial guess with this many linearisations (timing and error)")
     a = ap.parse_args()
+    if a.tof > 0:
+        import torch
+        cfg = rbgen.config_by_name(a.workload)
+        inp = rbgen.make_inputs(cfg)
+        tof_guess(cfg, a.tof)   # warm-up
+        out = {"workload": cfg.name, "tof_iters": a.tof}
+        for noise in (0.0, 20e-9):
+            c, hist, ms = tof_guess(cfg, a.tof, noise_s=noise)
+            sup = _support_mask(rb.geometry_from_config(cfg), c.device)
+            ct = torch.as_tensor(inp.c_true, device=c.device, dtype=torch.float32)
+            water = torch.full_like(ct, float(cfg.c_water))
+            ci = torch.as_tensor(inp.c_init, device=c.device, dtype=torch.float32)
+            rms = lambda x: float(torch.sqrt(torch.mean((x - ct)[sup].double() ** 2)))
+            out[f"noise_{noise * 1e9:.0f}ns"] = {"ms": ms, "misfit_s": hist, "rms_water": rms(water),
+                                                "rms_tof": rms(c), "rms_smooth_stand_in": rms(ci)}
+        print(json.dumps(out), flush=True)
+        return
     prec = rb.RB_PREC_BF16X3 if a.prec == "bf16x3" else rb.RB_PREC_FP32
     res = compare_solvers(rbgen.config_by_name(a.workload), [int(x) for x in a.cg.split(",")], prec,
                           precond=not a.plain_cg, data=a.data)

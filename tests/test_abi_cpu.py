@@ -112,6 +112,12 @@ def test_argument_errors_are_synchronous(lib):
                                 None, fake, 1 << 30, None) == rb.RB_ERR_ARG
     assert lib.rb_cg_update(ctypes.byref(g), fake, fake, f1, 1, fake, ctypes.byref(prm), 4, 1, 0, None, None, None,
                             fake, 1024, None) == rb.RB_ERR_WORKSPACE
+    for iters in (0, rb.RB_MAX_TOF_ITERS + 1):
+        assert lib.rb_tof_invert(ctypes.byref(g), fake, fake, fake, fake, iters, None, fake, 1 << 30,
+                                 None) == rb.RB_ERR_ARG
+    assert lib.rb_tof_invert(ctypes.byref(g), fake, fake, None, fake, 3, None, fake, 1 << 30, None) == rb.RB_ERR_ARG
+    assert lib.rb_tof_times(ctypes.byref(g), fake, fake, None, None, fake, 1 << 30, None) == rb.RB_ERR_ARG
+    assert lib.rb_tof_times(ctypes.byref(g), fake, fake, fake, None, fake, 1024, None) == rb.RB_ERR_WORKSPACE
     misaligned_tab = P(0x10004)
     assert lib.rb_green_grid(ctypes.byref(g), fake, fake, misaligned_tab, None, 0, None, fake, 1 << 30,
                              None) == rb.RB_ERR_ARG
