@@ -330,20 +330,20 @@ def run_ours(args):
                            "e2e": o["e2e"]["value"]}
         line["speedup_mixed_vs_plain"] = (R["value"] / o["value"]) if tc else (o["value"] / R["value"])
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
-        line["cpu_baseline"] = cpu_baseline(sample_fans=args.cpu_fans, sample_pix=args.cpu_pix)
+        line["cpu_baseline"] = cpu_baseline(sample_fans=256, sample_pix=args.cpu_pix_baseline, n_freq=4)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline(sample_fans=32, sample_pix=32768, seed=0):
+def cpu_baseline(sample_fans=32, sample_pix=32768, seed=0, n_freq=1):
     """The FP64 oracle, as it stands, on a bounded sample of one breast512 update, scaled to updates/s.
 
     Sample: (a) rays + gridding of `sample_fans` of the 256 fans (an element subset of the same ring
     and grid, same work per fan), scaled by 256/sample_fans; (b) Green's functions, Born adjoint,
-    Hessian diagonal and Born forward at one frequency on `sample_pix` of the 262144 pixels, scaled by
-    the pixel ratio and the 4 frequencies of a set."""
+    Hessian diagonal and Born forward at `n_freq` of the set's 4 frequencies on `sample_pix` of the
+    262144 pixels, scaled by the pixel and frequency ratios."""
     from oracle import born, geometry, green, grid
     cfg = rbgen.breast512()
     inp = rbgen.make_inputs(cfg)
@@ -357,21 +357,22 @@ def cpu_baseline(sample_fans=32, sample_pix=32768, seed=0):
     pix = np.sort(rng.choice(sup, sample_pix, replace=False))
     # tables at the sampled pixels for all fans (not timed: it repeats the timed ray work above)
     tabs = grid.grid_pixels(g, inp.c_init, inp.alpha0, pix)
-    f = cfg.freqs_hz[10]
     S = rng.standard_normal((g.n_elem, g.n_elem)) + 1j * rng.standard_normal((g.n_elem, g.n_elem))
     W = (rng.uniform(size=S.shape) > 0.25).astype(np.uint8)
-    t1 = time.perf_counter()
-    G = green.green(g, tabs, inp.c_init, f, pix=pix)
-    born.born_adjoint(G, W * S, f)
-    born.hess_diag(G, W, f)
-    born.born_forward(G, rng.standard_normal(pix.size), f)
-    t_born = time.perf_counter() - t1
     nf = len(cfg.sets[0])
-    per_update = t_rays * (cfg.n_elem / sample_fans) + t_born * (g.npix / sample_pix) * nf
+    n_freq = max(1, min(n_freq, nf))
+    t1 = time.perf_counter()
+    for f in [cfg.freqs_hz[i] for i in cfg.sets[2][:n_freq]]:
+        G = green.green(g, tabs, inp.c_init, f, pix=pix)
+        born.born_adjoint(G, W * S, f)
+        born.hess_diag(G, W, f)
+        born.born_forward(G, rng.standard_normal(pix.size), f)
+    t_born = time.perf_counter() - t1
+    per_update = t_rays * (cfg.n_elem / sample_fans) + t_born * (g.npix / sample_pix) * (nf / n_freq)
     return {"value": 1.0 / per_update, "unit": "updates/s", "cores": _cores(), "kind": "oracle",
             "sample": f"rays+gridding of {sample_fans}/256 fans ({t_rays:.2f} s) and G+adjoint+Hessian+forward on "
-                      f"{sample_pix}/262144 pixels at 1 of 4 frequencies ({t_born:.2f} s), scaled to one update",
-            "seconds_per_update_est": per_update}
+                      f"{sample_pix}/262144 pixels at {n_freq} of 4 frequencies ({t_born:.2f} s), scaled to one "
+                      f"update", "seconds_per_update_est": per_update}
 
 
 def run_reference(args):
@@ -406,7 +407,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=["breast512", "breast256", "tiny"],
                     help="the timed workload is breast512; smaller ones are for profiling captures")
     ap.add_argument("--cpu-fans", type=int, default=32)
-    ap.add_argument("--cpu-pix", type=int, default=32768)
+    ap.add_argument("--cpu-pix", type=int, default=32768, help="reference arm: pixels sampled per step")
+    ap.add_argument("--cpu-pix-baseline", type=int, default=160000,
+                    help="cpu_baseline of the GPU arm's line: pixels sampled (all fans, all 4 frequencies)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cg-iters", type=int, default=12,
                     help="also time the CG variant of the update with this many iterations (0: skip)")

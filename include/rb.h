@@ -51,9 +51,11 @@ typedef enum {
 } rb_status;
 
 typedef enum {
-    RB_PREC_FP32 = 0,       /* plain FP32 CUDA-core contractions */
-    RB_PREC_BF16X3 = 1      /* tcgen05 BF16 tensor cores, 3-term split products, FP32 accumulation */
-} rb_precision;
+    RB_PREC_FP32 = 0,       /* plain FP32 CUDA-core contractions (the adjoint, and so rb_born_adjoint,
+                               rb_hf_update and rb_cg_update, for rings of up to 512 elements) */
+    RB_PREC_BF16X3 = 1      /* tcgen05 BF16 tensor cores, 3-term split products, FP32 accumulation
+                               (rings of 64..256 elements in multiples of 64) */
+} rb_precision;             /* other ring sizes return RB_ERR_UNSUPPORTED before any work */
 
 typedef enum {
     RB_STEP_EXACT = 0,      /* diagonal-Hessian direction, scaled by the exact line minimum of Eq. 10 */

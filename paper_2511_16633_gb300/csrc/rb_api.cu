@@ -145,6 +145,7 @@ rb_status check_update(const rb_geometry* geom, const float* c, const float* alp
     if (params->step_mode != RB_STEP_EXACT && params->step_mode != RB_STEP_DIAG) return RB_ERR_ARG;
     if (!make_freqs(geom, freqs_hz, n_freq, F)) return RB_ERR_ARG;
     if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
+    if (prec == RB_PREC_FP32 && !simt_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
     return RB_OK;
 }
 
@@ -363,6 +364,7 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
     if (!geom_ok(geom)) return RB_ERR_SHAPE;
     if (!(f_hz > 0.0) || !isfinite(f_hz)) return RB_ERR_ARG;
     if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
+    if (prec == RB_PREC_FP32 && !simt_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
     Ws W;
     rb_status st = check_ws(geom, 1, prec, ws, ws_bytes, &W);
     if (st != RB_OK) return st;

@@ -339,6 +339,10 @@ cudaError_t launch_adjoint_simt(const GeoDev& G, const rb_cell* tables, const fl
     return cudaGetLastError();
 }
 
+// the adjoint holds a 32-pixel tile of G for every element in shared memory and gives
+// each lane at most 16 elements: rings of up to 512 elements
+bool simt_adjoint_supported(int n_elem) { return n_elem >= 2 && (n_elem + 31) / 32 <= 16; }
+
 int rb_fwd_chunks_for(int npix) {
     int ch = (npix + 2047) / 2048;
     if (ch < 1) ch = 1;

@@ -288,6 +288,7 @@ cudaError_t launch_forward_simt(const GeoDev& G, const rb_cell* tables, const fl
 cudaError_t launch_forward_reduce(const GeoDev& G, const FreqC& F, const float2* partial, int n_chunks,
                                   float2* d_out, const uint8_t* w, double* den_part, cudaStream_t s);
 int rb_fwd_chunks_for(int npix);
+bool simt_adjoint_supported(int n_elem);
 bool tc_adjoint_supported(int n_elem);
 size_t tc_b_images_bytes(int n_elem);
 cudaError_t launch_prep_b(int n, const float2* R, const uint8_t* W, void* img, cudaStream_t s);

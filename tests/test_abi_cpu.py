@@ -118,6 +118,21 @@ def test_argument_errors_are_synchronous(lib):
     assert lib.rb_tof_invert(ctypes.byref(g), fake, fake, None, fake, 3, None, fake, 1 << 30, None) == rb.RB_ERR_ARG
     assert lib.rb_tof_times(ctypes.byref(g), fake, fake, None, None, fake, 1 << 30, None) == rb.RB_ERR_ARG
     assert lib.rb_tof_times(ctypes.byref(g), fake, fake, fake, None, fake, 1024, None) == rb.RB_ERR_WORKSPACE
+    f0 = (ctypes.c_double * 1)(3e5)
+    assert lib.rb_hf_update(ctypes.byref(g), fake, fake, f0, 0, fake, ctypes.byref(prm), 0, None, None, fake, 1 << 30,
+                            None) == rb.RB_ERR_ARG
+    # the tensor-core path takes rings of 64..256 elements in multiples of 64
+    for n_bad in (96, 320, 512):
+        gb = rb.geometry_from_config(rbgen.tiny(), n_elem=n_bad)
+        assert lib.rb_hf_update(ctypes.byref(gb), fake, fake, f1, 1, fake, ctypes.byref(prm), rb.RB_PREC_BF16X3, None,
+                                None, fake, 1 << 30, None) == rb.RB_ERR_UNSUPPORTED
+        assert lib.rb_cg_update(ctypes.byref(gb), fake, fake, f1, 1, fake, ctypes.byref(prm), 4, 1, rb.RB_PREC_BF16X3,
+                                None, None, None, fake, 1 << 30, None) == rb.RB_ERR_UNSUPPORTED
+    g640 = rb.geometry_from_config(rbgen.tiny(), n_elem=640)
+    assert lib.rb_hf_update(ctypes.byref(g640), fake, fake, f1, 1, fake, ctypes.byref(prm), rb.RB_PREC_FP32, None,
+                            None, fake, 1 << 30, None) == rb.RB_ERR_UNSUPPORTED
+    assert lib.rb_born_adjoint(ctypes.byref(g640), fake, fake, ctypes.c_double(3e5), fake, fake, fake, None,
+                               rb.RB_PREC_FP32, fake, 1 << 30, None) == rb.RB_ERR_UNSUPPORTED
     misaligned_tab = P(0x10004)
     assert lib.rb_green_grid(ctypes.byref(g), fake, fake, misaligned_tab, None, 0, None, fake, 1 << 30,
                              None) == rb.RB_ERR_ARG
