@@ -39,8 +39,10 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
         const int ep = (int)(j / n2), kp = (int)(j % n2);
         const int r = kp >> 1, part = kp & 1;
         // rows e' in N-blocks of nb columns (the adjoint's MMA width), each holding the
-        // Re U rows then the Im U rows of nb / 2 consecutive elements
-        const int nb = n2 > 256 ? n2 / 2 : n2, eb = nb / 2;
+        // Re U rows then the Im U rows of nb / 2 consecutive elements; a pass of the
+        // adjoint takes ne2 = 2 min(n, 256) rows in one or two N-blocks
+        const int ne2 = n2 < 512 ? n2 : 512;
+        const int nb = ne2 > 256 ? ne2 / 2 : ne2, eb = nb / 2;
         const int blk = ep / nb, w = ep % nb;
         const int e = blk * eb + w % eb, im = w / eb;
         float2 s = make_float2(0.f, 0.f);
@@ -84,6 +86,7 @@ struct TcArgs {
     uint32_t* counters;
     int n_tiles;
     uint32_t tmem_cols;
+    int n_e, npass;            // elements per pass (N of the MMAs: 2 n_e and n_e), passes = n / n_e
 };
 
 // Synthesis records of every element and pixel from the tables.
@@ -234,6 +237,9 @@ __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __
 // drain (MMA completion on the error path).  Every wait is bounded; a timeout
 // raises a shared flag that ends all loops.
 // ---------------------------------------------------------------------------
+// NP: passes over the elements (1 for rings up to 256 elements, 2 for 512), fixed at
+// compile time so that the one-pass kernel carries no pass bookkeeping.
+template <int NP>
 __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_full[NST], s_empty[NST], s_acc_full, s_acc_empty, s_acc_low, s_vready, s_drain;
@@ -242,6 +248,10 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     __shared__ float s_red[3][3][TP];             // partial sums of quarters 1..3: Re g, Im g, H
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
+    // the elements e of U and V are taken in passes of ne (the accumulators of one pass
+    // fit TMEM); the contractions run over all r in every pass
+    const int ne = A.n_e, ne2 = 2 * ne;
+    constexpr int npass = NP;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nU = n2 / 16, nV = n / 32, per = nU + nV;
     if (tid == 0) {
@@ -265,14 +275,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     const int my_tiles = (int)blockIdx.x < A.n_tiles ? (A.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // slices of this CTA (a few thousand: 32-bit counters, stage and phase advanced
     // incrementally, no divisions in the loops)
-    const int total = my_tiles * A.F.n * per;
+    const int total = my_tiles * A.F.n * npass * per;
     const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 32;  // bf16 per hi (or lo) / W image slice
     auto stage = [&](int s) { return smem + (size_t)s * ST_BYTES; };
 
     if (warp == NPROD / 32 + 1) {
         // ------------------------------ loader ------------------------------
         if (lane == 0) {
-            int ql = 0, s = 0, j = 0, fw = 0, tile = blockIdx.x;
+            int ql = 0, s = 0, j = 0, fw = 0, pass = 0, tile = blockIdx.x;
             uint32_t ph = 0, vrp = 0;
             bool err = false;
             // the operand image streams through L2 once per launch: first out, so that it does
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 if (s_err) break;
                 const uint32_t mb = tc::smem_u32(&s_full[s]);
                 if (j < nU) {
-                    const uint32_t abytes = TP * 16 * 2, bbytes = (uint32_t)(n2 * 64);
+                    const uint32_t abytes = TP * 16 * 2, bbytes = (uint32_t)(ne2 * 64);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * abytes + bbytes)
                                  : "memory");
                     // image rows 2j, 2j + 1 of the hi plane, then of the lo plane
@@ -303,10 +313,22 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                                  ::"r"(tc::smem_u32(stage(s) + ST_ALO)), "l"(asrc + (size_t)(n2 / 8) * 1024), "r"(abytes),
                                  "r"(mb), "l"(stream_pol)
                                  : "memory");
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 ::"r"(tc::smem_u32(stage(s) + ST_B)),
-                                 "l"(A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u), "r"(bbytes), "r"(mb)
-                                 : "memory");
+                    // B: rows e' of this pass (contiguous in each plane), hi then lo; with one
+                    // pass the two planes are adjacent and go in one copy
+                    const __nv_bfloat16* bsrc = A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u + (size_t)pass * ne2 * 16;
+                    if (NP == 1) {
+                        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                     ::"r"(tc::smem_u32(stage(s) + ST_B)), "l"(bsrc), "r"(bbytes), "r"(mb)
+                                     : "memory");
+                    } else {
+                        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                     ::"r"(tc::smem_u32(stage(s) + ST_B)), "l"(bsrc), "r"(bbytes / 2), "r"(mb)
+                                     : "memory");
+                        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                     ::"r"(tc::smem_u32(stage(s) + ST_B + bbytes / 2)), "l"(bsrc + img_u), "r"(bbytes / 2),
+                                     "r"(mb)
+                                     : "memory");
+                    }
                 } else {
                     if (j == nU) {
                         // this (tile, frequency)'s |G|^2 slices are written by the producers
@@ -316,12 +338,13 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                         }
                         ++vrp;
                     }
-                    const uint32_t wbytes = (uint32_t)(n * 64), abytes = 2u * TP * 32 * 2;
+                    const uint32_t wbytes = (uint32_t)(ne * 64), abytes = 2u * TP * 32 * 2;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(wbytes + abytes)
                                  : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                                  ::"r"(tc::smem_u32(stage(s) + ST_VB)),
-                                 "l"(A.bw + (size_t)fw * A.bw_stride + (size_t)(j - nU) * img_w), "r"(wbytes), "r"(mb)
+                                 "l"(A.bw + (size_t)fw * A.bw_stride + (size_t)(j - nU) * img_w + (size_t)pass * ne * 32),
+                                 "r"(wbytes), "r"(mb)
                                  : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                                  ::"r"(tc::smem_u32(stage(s))), "l"(vimg + (size_t)(j - nU) * (2 * TP * 32)), "r"(abytes),
@@ -331,7 +354,10 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 if (++s == NST) { s = 0; ph ^= 1u; }
                 if (++j == per) {
                     j = 0;
-                    if (++fw == A.F.n) { fw = 0; tile += gridDim.x; }
+                    if (++pass == npass) {
+                        pass = 0;
+                        if (++fw == A.F.n) { fw = 0; tile += gridDim.x; }
+                    }
                 }
             }
             if (err || s_err) {
@@ -345,10 +371,10 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     } else if (warp == NPROD / 32) {
         // ------------------------------ MMA issuer ------------------------------
         if (lane == 0) {
-            const int nbk = n2 > 256 ? 2 : 1;
-            const int nb_u = n2 / nbk;
+            const int nbk = ne2 > 256 ? 2 : 1;
+            const int nb_u = ne2 / nbk;
             const uint32_t id_u = tc::idesc_bf16_f32(128, (uint32_t)nb_u);
-            const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)n);
+            const uint32_t id_v = tc::idesc_bf16_f32(128, (uint32_t)ne);
             int s = 0, j = 0;
             uint32_t acce = 0, accl = 0, ph = 0;
             bool err = false, issued = false;
@@ -375,7 +401,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     for (int nb = 0; nb < nbk; ++nb) {
                         const uint32_t boff = (uint32_t)(nb * nb_u / 8) * 256u;
                         const uint64_t dbh = tc::sdesc(sb + boff, 128, 256);
-                        const uint64_t dbl = tc::sdesc(sb + (uint32_t)(n2 * 32) + boff, 128, 256);
+                        const uint64_t dbl = tc::sdesc(sb + (uint32_t)(ne2 * 32) + boff, 128, 256);
                         const uint32_t d = tmem + (uint32_t)(nb * nb_u);
                         tc::mma_bf16(d, dah, dbh, id_u, acc);
                         tc::mma_bf16(d, dah, dbl, id_u, 1u);
@@ -446,6 +472,9 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
             float acc_g = 0.f, acc_h = 0.f;
             for (int fw = 0; fw < A.F.n; ++fw) {
                 const FreqC fc = A.F.f[fw];
+                float fg_r = 0.f, fg_i = 0.f, fh = 0.f;   // this frequency's g and H, summed over the passes
+                for (int pass = 0; pass < npass; ++pass) {
+                const int eb0 = pass * ne;                 // first element of this pass
                 // ---- U slices: exact-enough G for the epilogue and the |G|^2 slices ----
                 for (int j = 0; j < nU; ++j)
                     slice([&](const unsigned char* ahi, const unsigned char* alo) {
@@ -463,14 +492,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 // and its Im U ebu columns further (N-blocks of nbu columns, ebu = nbu / 2
                 // elements each); G of the next chunk is loaded while the current one is used,
                 // the first before the accumulator wait ----
-                const int nch = 4 * ((n / 32 - (int)h + 3) / 4);
-                const int nbu = n2 > 256 ? n2 / 2 : n2, ebu = nbu / 2;
+                const int nch = 4 * ((ne / 32 - (int)h + 3) / 4);
+                const int nbu = ne2 > 256 ? ne2 / 2 : ne2, ebu = nbu / 2;
                 auto ce0 = [&](int k) { return 32 * ((int)h + 4 * (k >> 2)) + 8 * (k & 3); };
                 auto recol = [&](int e) { return (e / ebu) * nbu + e % ebu; };
                 auto gload = [&](int k, float2 (&g)[8]) {
                     const int e0 = ce0(k);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) g[i] = gs[(size_t)(e0 + i) * TP + p];
+                    for (int i = 0; i < 8; ++i) g[i] = gs[(size_t)(eb0 + e0 + i) * TP + p];
                 };
                 auto gchunk = [&](int k, const float2 (&g)[8], float& ar, float& ai) {
                     const int e0 = ce0(k);
@@ -513,10 +542,8 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
                 if (h == 0) {
-                    gr = (gr + s_red[0][0][p] + s_red[0][1][p] + s_red[0][2][p]) * fc.w2;
-                    gi = (gi + s_red[1][0][p] + s_red[1][1][p] + s_red[1][2][p]) * fc.w2;
-                    if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(gr, gi);
-                    acc_g += gr;
+                    fg_r += (gr + s_red[0][0][p] + s_red[0][1][p] + s_red[0][2][p]) * fc.w2;
+                    fg_i += (gi + s_red[1][0][p] + s_red[1][1][p] + s_red[1][2][p]) * fc.w2;
                 }
                 // ---- V slices: A and B come by bulk copy; the producers only pass the
                 // stage barriers, which keeps every stage's phases in step with its uses ----
@@ -543,10 +570,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 if (h > 0) s_red[2][h - 1][p] = hh;
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
+                if (h == 0) fh += (hh + s_red[2][0][p] + s_red[2][1][p] + s_red[2][2][p]) * fc.w4;
+                }   // passes
+                if (err) break;
                 if (h == 0) {
-                    hh = (hh + s_red[2][0][p] + s_red[2][1][p] + s_red[2][2][p]) * fc.w4;
-                    if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = hh;
-                    acc_h += hh;
+                    if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(fg_r, fg_i);
+                    if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = fh;
+                    acc_g += fg_r;
+                    acc_h += fh;
                 }
             }
             if (err) break;
@@ -562,7 +593,9 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
 }
 }  // namespace
 
-bool tc_adjoint_supported(int n_elem) { return n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0; }
+// rings of 64..256 elements in multiples of 64 in one pass over the elements of U and V,
+// and 512 elements in two passes of 256
+bool tc_adjoint_supported(int n_elem) { return (n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0) || n_elem == 512; }
 
 cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s) {
     const long long total = (long long)G.n_elem * G.npix;
@@ -619,15 +652,24 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
     A.hsum = hsum;
     A.counters = counters;
     A.n_tiles = (G.npix + TP - 1) / TP;
+    A.n_e = n < 256 ? n : 256;
+    A.npass = n / A.n_e;
     uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * n)) cols <<= 1;
+    while (cols < (uint32_t)(2 * A.n_e)) cols <<= 1;
     A.tmem_cols = cols;
     // NST stages of 40 KB: most of the SM's shared memory, so one CTA (one TMEM owner) per SM
     const int sm = NST * (int)ST_BYTES;
-    cudaError_t e = cudaFuncSetAttribute(k_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
     const int grid = n_ctas < A.n_tiles ? n_ctas : A.n_tiles;
-    k_adjoint_tc<<<grid, NTHR_A, sm, s>>>(A);
+    cudaError_t e;
+    if (A.npass == 1) {
+        e = cudaFuncSetAttribute(k_adjoint_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        k_adjoint_tc<1><<<grid, NTHR_A, sm, s>>>(A);
+    } else {
+        e = cudaFuncSetAttribute(k_adjoint_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        k_adjoint_tc<2><<<grid, NTHR_A, sm, s>>>(A);
+    }
     return cudaGetLastError();
 }
 
@@ -646,7 +688,8 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
 // ===========================================================================
 namespace {
 
-constexpr int FMAXB = 8;   // max row blocks (2n / 128, n <= 256 -> 4)
+constexpr int FMAXB = 8;   // max row blocks (2n / 128, n <= 512)
+constexpr int FMAXP = 16;  // max (row block, column group) pairs
 constexpr int FBOX_MAX = 32;   // rows (of 8 r') per TMA box, at most
 constexpr uint32_t ST_FB = 8192u;   // forward stage: A hi (4 KB), A lo (4 KB), then B hi and B lo
 
@@ -657,11 +700,16 @@ struct FwdArgs {
     float* partial;            // [cta][128][2n] fp32 (only needed columns written)
     int n_mb;                  // row blocks
     int nbn, nb;               // column blocks and their width
-    int splits[FMAXB];         // splits per row block
-    int cta0[FMAXB + 1];       // first CTA of each row block
+    // work pairs: row block p_i with the column blocks [p_jb, p_je) (at most two, so the
+    // accumulators fit TMEM), each split over pixel ranges
+    int n_pairs;
+    int p_i[FMAXP], p_jb[FMAXP], p_je[FMAXP];
+    int splits[FMAXP];         // splits per pair
+    int cta0[FMAXP + 1];       // first CTA of each pair
+    int pidx[FMAXB][2];        // pair of (row block, column group of two blocks)
     uint32_t tmem_cols;
     uint32_t* counters;
-    int fbox;                  // rows per TMA box: divides the rows loaded by every row block
+    int fbox;                  // rows per TMA box: divides every pair's loaded rows (and 16)
 };
 
 __host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i) / nb; }
@@ -672,6 +720,9 @@ __host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i
 //               re-split into hi / lo, once the slice's B has landed; then the epilogue;
 //   warp 8      MMA issuer; warp 9 loader (TMA boxes of the rows [col0, 2n) of the
 //               slice, hi and lo planes).
+// SEP: some pairs load their row block's own rows separately (rings above 256 elements);
+// without it every pair finds them among its B rows and the test compiles away.
+template <bool SEP>
 __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full;
@@ -680,15 +731,19 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
     const GeoDev& G = A.G;
     const int n = G.n_elem, n2 = 2 * n;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int i = 0;
-    while (i + 1 < A.n_mb && (int)blockIdx.x >= A.cta0[i + 1]) ++i;
-    const int sp = (int)blockIdx.x - A.cta0[i];
-    const int S = A.splits[i];
-    const int jmin = jmin_of(i, A.nb);
-    const int col0 = jmin * A.nb;                       // first needed column (= first B row loaded)
+    int pq = 0;
+    while (pq + 1 < A.n_pairs && (int)blockIdx.x >= A.cta0[pq + 1]) ++pq;
+    const int i = A.p_i[pq], jb = A.p_jb[pq], je = A.p_je[pq];
+    const int sp = (int)blockIdx.x - A.cta0[pq];
+    const int S = A.splits[pq];
+    const int col0 = jb * A.nb, col1 = je * A.nb;       // needed columns (= B rows loaded)
     const int rcn = n2 / 8, rc0 = col0 / 8;             // rows of 8 r' per plane; first one loaded
-    const int nrow = rcn - rc0;                         // rows loaded per plane (a multiple of fbox)
+    const int nrow = (col1 - col0) / 8;                 // rows loaded per plane (a multiple of fbox)
     const uint32_t plane_bytes = (uint32_t)nrow * 256u;
+    // the row block's own 16 rows (the A operand before scaling by m): inside the loaded B
+    // rows, or loaded separately into the A area of the stage
+    const bool own_in = !SEP || (16 * i >= rc0 && 16 * i + 16 <= rc0 + nrow);
+    const uint32_t tx_bytes = 2u * plane_bytes + (own_in ? 0u : 2u * 16u * 256u);
     const int n_tiles = (G.npix + TP - 1) / TP;
     const int nsl_all = n_tiles * 8;
     const int cps = (nsl_all + S - 1) / S;
@@ -725,9 +780,9 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
                 if (s_err) break;
                 const int sg = sbeg + ql, t = sg >> 3, x = (sg & 7) * 128;
                 const uint32_t mb = tc::smem_u32(&s_full_b[k]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * plane_bytes)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx_bytes)
                              : "memory");
-                for (int hl = 0; hl < 2; ++hl)
+                for (int hl = 0; hl < 2; ++hl) {
                     for (int b = 0; b < nrow / A.fbox; ++b) {
                         const uint32_t dst = tc::smem_u32(stage(k) + ST_FB + hl * plane_bytes + (uint32_t)(b * A.fbox) * 256u);
                         const int y = (t * 2 + hl) * rcn + rc0 + b * A.fbox;
@@ -736,6 +791,16 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
                             ::"r"(dst), "l"(tm), "r"(x), "r"(y), "r"(mb)
                             : "memory");
                     }
+                    if (!own_in)
+                        for (int b = 0; b < 16 / A.fbox; ++b) {
+                            const uint32_t dst = tc::smem_u32(stage(k) + hl * ST_ALO + (uint32_t)(b * A.fbox) * 256u);
+                            const int y = (t * 2 + hl) * rcn + 16 * i + b * A.fbox;
+                            asm volatile(
+                                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                                ::"r"(dst), "l"(tm), "r"(x), "r"(y), "r"(mb)
+                                : "memory");
+                        }
+                }
             }
             if (err || s_err) {
                 s_err = 1;
@@ -761,11 +826,11 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
                 tc::fence_after();
                 const uint32_t sa = tc::smem_u32(stage(k)), sb = sa + ST_FB;
                 const uint64_t dah = tc::sdesc(sa, 128, 256), dal = tc::sdesc(sa + ST_ALO, 128, 256);
-                for (int j = jmin; j < A.nbn; ++j) {
+                for (int j = jb; j < je; ++j) {
                     const uint32_t boff = (uint32_t)((j * A.nb) / 8 - rc0) * 256u;
                     const uint64_t dbh = tc::sdesc(sb + boff, 128, 256);
                     const uint64_t dbl = tc::sdesc(sb + plane_bytes + boff, 128, 256);
-                    const uint32_t d = tmem + (uint32_t)(j * A.nb);
+                    const uint32_t d = tmem + (uint32_t)((j - jb) * A.nb);
                     tc::mma_bf16(d, dah, dbh, id, q > 0 ? 1u : 0u);
                     tc::mma_bf16(d, dah, dbl, id, 1u);
                     tc::mma_bf16(d, dal, dbh, id, 1u);
@@ -786,8 +851,10 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
         // thread tid: row rl = tid / 16 of 8 r' (of the row block's 16), K core pc = (tid / 8) % 2,
         // pixel row x8 = tid % 8 of that core
         const int rl = tid >> 4, pc = (tid >> 3) & 1, x8 = tid & 7;
-        const uint32_t boff = (uint32_t)((16 * i - rc0 + rl) * 256 + pc * 128 + x8 * 16);
         const uint32_t aoff = (uint32_t)(rl * 256 + pc * 128 + x8 * 16);
+        // source of this thread's 16 bytes: the B rows, or the A area itself (scaled in place)
+        const uint32_t soff = own_in ? ST_FB + (uint32_t)((16 * i - rc0 + rl) * 256 + pc * 128 + x8 * 16) : aoff;
+        const uint32_t slo = own_in ? plane_bytes : ST_ALO;
         bool err = false;
         auto load_m = [&](int q) -> float {
             if (q >= nq) return 0.f;
@@ -804,8 +871,8 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
             if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_full_b[k]), ph, kMaxTries);
             err = __any_sync(0xffffffffu, err || s_err != 0);
             if (!err) {
-                const unsigned char* b_hi = stage(k) + ST_FB;
-                const uint4 vh = *(const uint4*)(b_hi + boff), vl = *(const uint4*)(b_hi + plane_bytes + boff);
+                const unsigned char* src = stage(k) + soff;
+                const uint4 vh = *(const uint4*)src, vl = *(const uint4*)(src + slo);
                 const uint32_t hw[4] = {vh.x, vh.y, vh.z, vh.w}, lw[4] = {vl.x, vl.y, vl.z, vl.w};
                 uint32_t oh[4], ol[4];
 #pragma unroll
@@ -836,11 +903,11 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
             const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
             float* out = A.partial + ((size_t)blockIdx.x * 128 + row) * n2;
             int cnum = 0;
-            for (int cb = col0; cb < n2; cb += 32, ++cnum) {
+            for (int cb = col0; cb < col1; cb += 32, ++cnum) {
                 if ((cnum & 1) != g) continue;
                 float v[32];
                 if (nq > 0) {
-                    tc::tmem_ld32(tmem + lane_off + (uint32_t)cb, v);
+                    tc::tmem_ld32(tmem + lane_off + (uint32_t)(cb - col0), v);
                 } else {
 #pragma unroll
                     for (int t = 0; t < 32; ++t) v[t] = 0.f;
@@ -871,9 +938,10 @@ __global__ void k_forward_tc_reduce(FwdArgs A, float2* __restrict__ d_out, const
         const int e = (int)(jj / n), r = (int)(jj % n);
         if (e > r) continue;
         const int i = (2 * e) >> 7, row = (2 * e) & 127;
+        const int pq = A.pidx[i][((2 * r) / A.nb) >> 1];
         float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);   // D[2e][2r..2r+1], D[2e+1][2r..2r+1]
-        for (int sp = 0; sp < A.splits[i]; ++sp) {
-            const float* blk = A.partial + ((size_t)(A.cta0[i] + sp) * 128 + row) * n2 + 2 * r;
+        for (int sp = 0; sp < A.splits[pq]; ++sp) {
+            const float* blk = A.partial + ((size_t)(A.cta0[pq] + sp) * 128 + row) * n2 + 2 * r;
             const float2 a0 = *(const float2*)blk, a1 = *(const float2*)(blk + n2);
             d0.x += a0.x;
             d0.y += a0.y;
@@ -918,39 +986,52 @@ FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const float* m, float* pa
     A.n_mb = n2 / 128;
     A.nbn = (n2 + 255) / 256;
     A.nb = n2 / A.nbn;
+    // pairs (row block i, column blocks [jb, je)): blocks from the diagonal one on, in
+    // groups of two (group g holds blocks 2g and 2g + 1)
+    A.n_pairs = 0;
+    for (int i = 0; i < A.n_mb; ++i) {
+        A.pidx[i][0] = A.pidx[i][1] = -1;
+        const int jmin = jmin_of(i, A.nb);
+        for (int g = jmin / 2; 2 * g < A.nbn; ++g) {
+            const int q = A.n_pairs++;
+            A.p_i[q] = i;
+            A.p_jb[q] = 2 * g > jmin ? 2 * g : jmin;
+            A.p_je[q] = 2 * g + 2 < A.nbn ? 2 * g + 2 : A.nbn;
+            A.pidx[i][g] = q;
+        }
+    }
+    // TMEM: the widest pair, two blocks (one when there is only one)
     uint32_t cols = 32;
-    while (cols < (uint32_t)n2) cols <<= 1;
+    while (cols < (uint32_t)((A.nbn > 1 ? 2 : 1) * A.nb)) cols <<= 1;
     A.tmem_cols = cols;
-    // splits per row block: equal.  A pixel slice costs about the same on every row
-    // block, whether it issues MMAs for one column block or two (the operand delivery
-    // and producer work per slice, not the tensor pipe, set the pace), so splits in
-    // proportion to the column blocks left the lower row blocks twice as long.
-    int wsum = 0, wts[FMAXB];
-    for (int i = 0; i < A.n_mb; ++i) {
-        wts[i] = 1;
-        wsum += wts[i];
-    }
+    // splits per pair: equal.  A pixel slice costs about the same on every pair, whether
+    // it issues MMAs for one column block or two (the operand delivery and producer work
+    // per slice, not the tensor pipe, set the pace), so splits in proportion to the
+    // column blocks left the pairs with one block idle half the time.
     int c0 = 0;
-    for (int i = 0; i < A.n_mb; ++i) {
-        int s = (int)((long long)n_ctas * wts[i] / wsum);
-        if (s < 1) s = 1;
-        A.splits[i] = s;
-        A.cta0[i] = c0;
-        c0 += s;
+    for (int q = 0; q < A.n_pairs; ++q) {
+        int sq = n_ctas / A.n_pairs;
+        if (sq < 1) sq = 1;
+        A.splits[q] = sq;
+        A.cta0[q] = c0;
+        c0 += sq;
     }
-    A.cta0[A.n_mb] = c0;
-    // TMA box height: the largest power of two up to FBOX_MAX dividing every row block's
-    // loaded rows (2n - col0) / 8
+    A.cta0[A.n_pairs] = c0;
+    // TMA box height: the largest power of two up to FBOX_MAX dividing every pair's loaded
+    // rows, and 16 where a pair loads its row block's own rows separately
     A.fbox = FBOX_MAX;
-    for (int i = 0; i < A.n_mb; ++i)
-        while ((n2 / 8 - (jmin_of(i, A.nb) * A.nb) / 8) % A.fbox != 0) A.fbox >>= 1;
+    for (int q = 0; q < A.n_pairs; ++q) {
+        const int rc0 = A.p_jb[q] * A.nb / 8, nrow = (A.p_je[q] - A.p_jb[q]) * A.nb / 8;
+        const bool own_in = 16 * A.p_i[q] >= rc0 && 16 * A.p_i[q] + 16 <= rc0 + nrow;
+        while (nrow % A.fbox != 0 || (!own_in && 16 % A.fbox != 0)) A.fbox >>= 1;
+    }
     return A;
 }
 
 }  // namespace
 
 size_t tc_forward_partial_bytes(int n_elem, int n_ctas) {
-    return (size_t)(n_ctas + FMAXB) * 128 * (2 * (size_t)n_elem) * sizeof(float);
+    return (size_t)(n_ctas + FMAXP) * 128 * (2 * (size_t)n_elem) * sizeof(float);
 }
 
 cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F, const float* m, float* partial,
@@ -966,9 +1047,21 @@ cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F,
     if (A.fbox < 1 || !tc::encode_tmap_2d(&tmap, aimg, 1024, (uint64_t)n_tiles * 2 * rcn, 2048, 128, (uint32_t)A.fbox))
         return cudaErrorUnknown;
     const int sm = NST * (int)ST_BYTES;
-    cudaError_t e = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    k_forward_tc<<<A.cta0[A.n_mb], NTHR_F, sm, s>>>(A, tmap);
+    bool sep = false;
+    for (int q = 0; q < A.n_pairs; ++q) {
+        const int rc0 = A.p_jb[q] * A.nb / 8, nrow = (A.p_je[q] - A.p_jb[q]) * A.nb / 8;
+        sep = sep || !(16 * A.p_i[q] >= rc0 && 16 * A.p_i[q] + 16 <= rc0 + nrow);
+    }
+    cudaError_t e;
+    if (sep) {
+        e = cudaFuncSetAttribute(k_forward_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        k_forward_tc<true><<<A.cta0[A.n_pairs], NTHR_F, sm, s>>>(A, tmap);
+    } else {
+        e = cudaFuncSetAttribute(k_forward_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        k_forward_tc<false><<<A.cta0[A.n_pairs], NTHR_F, sm, s>>>(A, tmap);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_forward_tc_reduce<<<256, 256, 0, s>>>(A, d_out, w, den_part);

@@ -35,11 +35,10 @@ from . import rb
 
 def precision_for(cfg, policy: str) -> int:
     """The contraction precision of a request: the tensor-core path (BF16 x3) where the
-    ring size allows it (multiples of 64 up to 256 elements), else plain FP32."""
+    ring size allows it (multiples of 64 up to 256 elements, and 512), else plain FP32."""
     if policy == "plain":
         return rb.RB_PREC_FP32
-    ok = 64 <= cfg.n_elem <= 256 and cfg.n_elem % 64 == 0
-    return rb.RB_PREC_BF16X3 if ok else rb.RB_PREC_FP32
+    return rb.RB_PREC_BF16X3 if rb.tc_supported(cfg.n_elem) else rb.RB_PREC_FP32
 
 
 def footprint_bytes(cfg, prec: int) -> int:

@@ -8,6 +8,8 @@ Three workloads, named for what they are:
                   256 rays per emitter, 12 frequencies 0.3-1.0 MHz in 4 sets of 3.
 * ``breast512`` — same ring, 512x512 grid at 0.45 mm, 256 rays per emitter,
                   20 frequencies 0.3-1.25 MHz in 5 sets of 4.
+* ``invivo512`` — 512 elements on the same ring (the in-vivo transducer count),
+                  256x256 grid at 0.9 mm, 512 rays per emitter, 5 sets of 4.
 * ``ring`` / ``batch_mix`` / ``poisson_requests`` — workloads of uneven sizes on the
                   same 110 mm ring (batched reconstructions and a request stream).
 
@@ -94,7 +96,16 @@ def breast512(**kw) -> Config:
     return Config(**base)
 
 
-CONFIGS = {"tiny": tiny, "breast256": breast256, "breast512": breast512}
+def invivo512(**kw) -> Config:
+    """The paper's in-vivo acquisition size (Sec. 4.2: 512 transducers, images on a ~1 mm
+    grid): 512 elements on the 110 mm ring, 256 x 256 pixels at 0.9 mm, 512 rays per
+    emitter, 20 frequencies 0.3-1.25 MHz in 5 sets of 4."""
+    base = dict(name="invivo512", n_elem=512, n_rays=512, seed=20251116 + 6)
+    base.update(kw)
+    return ring(512, 256, 20, **{k: v for k, v in base.items() if k not in ("n_elem",)})
+
+
+CONFIGS = {"tiny": tiny, "breast256": breast256, "breast512": breast512, "invivo512": invivo512}
 
 
 def config_by_name(name: str, **kw) -> Config:

@@ -128,3 +128,26 @@ def test_fan_of_4096_rays_linking(dev):
     assert np.mean((linked.cpu().numpy() == 1)[mask] == lk.linked[mask]) >= 0.999
     po = olink.ray_data(g, lk, f)
     assert _rel(p.cpu().numpy()[0][mask], po[mask]) <= 1e-4
+
+
+def test_ring_of_512_elements_bf16x3_update(dev):
+    cfg = rbgen.tiny(n_elem=512, n_rays=64)
+    inp = rbgen.make_inputs(cfg)
+    g = ogeom.from_config(cfg)
+    freqs = list(cfg.freqs_hz[1:3])
+    p_obs = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, freqs, inp.noise_re, inp.noise_im)
+    ref = oupd.hf_update(g, inp.c_init, inp.alpha0, freqs, p_obs)
+    geom = rb.geometry_from_config(cfg)
+    c = _t(inp.c_init, dev)
+    dc = torch.empty_like(c)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    ws = rb.workspace(geom, 2, rb.RB_PREC_BF16X3, dev)
+    rb.rb_hf_update(geom, c, _t(inp.alpha0, dev), freqs, torch.as_tensor(p_obs.astype(np.complex64), device=dev), ws,
+                    prec=rb.RB_PREC_BF16X3, dc_out=dc, diag_out=diag)
+    torch.cuda.synchronize()
+    d = rb.decode_diag(diag)
+    e = _rel(dc.cpu().numpy(), ref.dc)
+    print(f"512 elements bf16x3: dc rel L2 {e:.3g}, alpha {d['alpha']:.6g} vs {ref.alpha:.6g}")
+    assert d["tc_timeouts"] == 0
+    assert d["kept"] == ref.n_kept and d["zeroed"] == ref.n_zeroed
+    assert e <= 1e-3

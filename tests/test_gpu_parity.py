@@ -427,3 +427,36 @@ def test_bf16x3_ring_sizes_ragged(dev, n_elem, nx, ny):
     assert eg <= 1e-4, eg
     assert eh <= 1e-4, eh
     assert ed <= 1e-4, ed
+
+
+# A ring of 512 elements (the in-vivo transducer count of the paper's Sec. 4) on the
+# tensor cores: the adjoint in two passes of 256 elements, the forward in (row block,
+# column group) pairs, some of which load their row block's own rows separately.
+def test_bf16x3_ring_512(dev):
+    cfg = rbgen.tiny(n_elem=512, n_rays=64)
+    inp = rbgen.make_inputs(cfg)
+    c = inp.c_true
+    g = ogeom.from_config(cfg)
+    geom = rb.geometry_from_config(cfg)
+    tab, _ = gpu_tables(geom, c, inp.alpha0, dev)
+    ot = ogrid.grid(g, c, inp.alpha0)
+    rng = np.random.default_rng(9)
+    R = (rng.standard_normal((g.n_elem, g.n_elem)) + 1j * rng.standard_normal((g.n_elem, g.n_elem))).astype(np.complex64)
+    W = (rng.uniform(size=(g.n_elem, g.n_elem)) > 0.25).astype(np.uint8)
+    m = rng.standard_normal(g.npix).astype(np.float32) * 1e-9
+    ws = rb.workspace(geom, 1, rb.RB_PREC_BF16X3, dev)
+    ct = _t(c, dev)
+    f = cfg.freqs_hz[-1]
+    Go = ogreen.green(g, ot, c, f)
+    gg = torch.empty(g.npix, dtype=torch.complex64, device=dev)
+    hh = torch.empty(g.npix, dtype=torch.float32, device=dev)
+    rb.rb_born_adjoint(geom, tab, ct, f, torch.as_tensor(R, device=dev), torch.as_tensor(W, device=dev), gg, ws, hh,
+                       prec=rb.RB_PREC_BF16X3)
+    d = torch.empty((g.n_elem, g.n_elem), dtype=torch.complex64, device=dev)
+    rb.rb_born_forward(geom, tab, ct, f, _t(m, dev), d, ws, prec=rb.RB_PREC_BF16X3)
+    torch.cuda.synchronize()
+    eg = rel_l2(gg.cpu().numpy(), oborn.born_adjoint(Go, W * R.astype(np.complex128), f))
+    eh = rel_l2(hh.cpu().numpy(), oborn.hess_diag(Go, W, f))
+    ef = rel_l2(d.cpu().numpy(), oborn.born_forward(Go, m.astype(np.float64), f))
+    print(f"bf16x3 n=512: gradient {eg:.3g}, Hessian diagonal {eh:.3g}, forward {ef:.3g}")
+    assert eg <= 1e-4 and eh <= 1e-4 and ef <= 1e-4
