@@ -286,8 +286,8 @@ def run_ours(args):
     roof_fwd = contraction_roof("forward", work["forward_flop"], "k_forward_tc" if tc else "k_forward_simt", fwd_ratio)
     # the dominant kernel: the adjoint contraction (one launch per update, alone in its stage)
     roof = dict(roof_adj)
-    if tc:
-        roof["traffic"] = ADJ_TRAFFIC_BYTES
+    if tc and args.workload == WORKLOAD:
+        roof["traffic"] = ADJ_TRAFFIC_BYTES   # captured on the default workload only
     # the operand-image synthesis (mixed path): HBM-bound; algorithmic bytes = the synthesis
     # records read once and the operand image (bf16 hi and lo of 2n x npix) of every
     # frequency of the set written once
