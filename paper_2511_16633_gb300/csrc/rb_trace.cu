@@ -505,11 +505,14 @@ __device__ __forceinline__ Vtx get_vtx(const Vtx* __restrict__ src) {
     return Vtx{a.x, a.y, a.z, a.w, b.x, b.y, b.z, __float_as_int(b.w)};
 }
 
-// Rasteriser: thread (t, i, kb) rasterises the quads k in [KB kb + 1, KB kb + KB] of
-// tube (i, i + 1) of fan t from the vertex stream, up to the later of the two rays'
-// last vertices (beyond it both triangles are degenerate).  Consecutive threads take
-// consecutive tubes, so the vertex loads of a warp are contiguous.
-constexpr int KB = 8;
+// Rasteriser: warp (t, i, kc) rasterises the quads k = 32 kc + 1 .. 32 kc + 32 of tube
+// (i, i + 1) of fan t from the vertex stream, one per lane, up to the later of the two
+// rays' last vertices (beyond it both triangles are degenerate).  Neighbouring quads
+// along a tube are alike in size, so the lanes' pixel loops are of similar length (32
+// tubes at the same step, the other way round, differ far more where the medium bends
+// the rays); each lane's four vertices are 32-byte loads, shared with the next lane
+// through L1.
+constexpr int KW = 32;
 
 // Columns [lo, hi] of row iy inside the support disc (2 ix - (nx - 1))^2 +
 // (2 iy - (ny - 1))^2 <= r2max, exact in integers; lo > hi for an empty row.
@@ -531,28 +534,24 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
     for (int iy = threadIdx.x; iy < G.ny; iy += blockDim.x) s_supp[iy] = support_row(G, iy);
     __syncthreads();
     const int NT = G.n_rays - 1;
-    const int nkb = (G.max_steps + KB - 1) / KB;
+    const int nkc = (G.max_steps + KW - 1) / KW;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
-    const int per_fan = nkb * NT;   // < 2^31 (the triangle ids fit 24 bits)
-    // fans t = blockIdx.y + k gridDim.y; within a fan, item = kb NT + i
+    const int per_fan = nkc * NT;   // warp items per fan, < 2^31 (the triangle ids fit 24 bits)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    // fans t = blockIdx.y + j gridDim.y; within a fan, warp item = kc NT + i
     for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y)
-    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < per_fan; item += gridDim.x * blockDim.x) {
-        uint32_t ukb, ui;
-        udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukb, ui);
-        const int i = (int)ui, kb = (int)ukb;
+    for (int item = blockIdx.x * wpb + wib; item < per_fan; item += gridDim.x * wpb) {
+        uint32_t ukc, ui;
+        udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukc, ui);
+        const int i = (int)ui;
         const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
-        const int k0 = kb * KB + 1, k1 = min(k0 + KB - 1, max(la, lb));
-        if (k0 > k1) continue;
-        unsigned long long* tab = keys + (size_t)t * G.npix;
-        Vtx A0 = get_vtx(verts + vidx(G, t, min(k0 - 1, la), i));
-        Vtx B0 = get_vtx(verts + vidx(G, t, min(k0 - 1, lb), i + 1));
-        for (int k = k0; k <= k1; ++k) {
-            const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
-            const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
-            raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, tab, s_supp);
-            A0 = A1;
-            B0 = B1;
-        }
+        const int k = (int)ukc * KW + lane + 1;
+        if (k > max(la, lb)) continue;
+        const Vtx A0 = get_vtx(verts + vidx(G, t, min(k - 1, la), i));
+        const Vtx B0 = get_vtx(verts + vidx(G, t, min(k - 1, lb), i + 1));
+        const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
+        const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
+        raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, keys + (size_t)t * G.npix, s_supp);
     }
 }
 
