@@ -2,6 +2,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "rb_internal.cuh"
 
 namespace {
@@ -127,6 +129,32 @@ int tc_ctas() {
         if ((x) != cudaSuccess) return RB_ERR_CUDA; \
     } while (0)
 
+// A side stream per device for the work of an update that does not wait for the
+// gridding (linking, residuals, data weights, B images), forked after the ray trace and
+// joined before the adjoint.  Created on first use and kept for the process; the mutex
+// keeps each call's fork and join events together when several host threads call.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mutex;
+SideStream g_side[64];
+
+cudaError_t side_stream(SideStream** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    SideStream& ss = g_side[dev];
+    if (!ss.s) {
+        if ((e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    *out = &ss;
+    return cudaSuccess;
+}
+
 // Stage events of the update entry points (none when the caller gave no array).
 struct Marks {
     cudaEvent_t* ev;
@@ -167,6 +195,11 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     uint8_t* wts = W.at<uint8_t>(W.L.wts);
     uint64_t* keys = W.at<uint64_t>(W.L.keys);
     const bool tc = prec == RB_PREC_BF16X3;
+    std::lock_guard<std::mutex> lock(g_side_mutex);
+    SideStream* ss = nullptr;
+    RB_CU(side_stream(&ss));
+    const cudaStream_t s2 = ss->s;
+    const Marks mark2{mark.ev, s2};   // stage events of the side branch
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4 + DBL_N * 8, s));
     RB_CU(mark(RB_STAGE_FIELDS, 0));
     RB_CU(launch_elem_positions(G, exy, s));
@@ -176,21 +209,27 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     // the mixed path reads only the synthesis records, the plain path only the tables
     float4* srec = tc ? W.at<float4>(W.L.srec) : nullptr;
     RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), tc ? nullptr : tables, W.at<void>(W.L.verts), c,
-                       srec, cnt, s));
-    RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
-    RB_CU(mark(RB_STAGE_LINK, 0));
-    RB_CU(launch_link(G, c, ends, F, R, linked, s));
-    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, W.at<void>(W.L.sel), s));
-    RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, W.at<void>(W.L.sel), s));
-    RB_CU(mark(RB_STAGE_LINK, 1));
-    RB_CU(mark(RB_STAGE_IMAGES, 0));
+                       srec, cnt, s, ss->fork));
+    // side branch (needs the end records only): links, residuals, weights, B images
+    RB_CU(cudaStreamWaitEvent(s2, ss->fork, 0));
+    RB_CU(mark2(RB_STAGE_LINK, 0));
+    RB_CU(launch_link(G, c, ends, F, R, linked, s2));
+    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, keys, cnt, W.at<void>(W.L.sel), s2));
+    RB_CU(launch_outlier_select(n_freq * ne2, params->outlier_frac, keys, cnt, wts, W.at<void>(W.L.sel), s2));
     if (tc) {
         const size_t img = tc_b_images_bytes(G.n_elem);
         for (int w = 0; w < n_freq; ++w)
-            RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img, s));
-        RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg), s));
+            RB_CU(launch_prep_b(G.n_elem, R + (size_t)w * ne2, wts + (size_t)w * ne2, W.at<char>(W.L.tcimg) + w * img,
+                                s2));
     }
+    RB_CU(mark2(RB_STAGE_LINK, 1));
+    RB_CU(cudaEventRecord(ss->join, s2));
+    // main branch: rasteriser and resolve (in launch_trace), the operand images
+    RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
+    RB_CU(mark(RB_STAGE_IMAGES, 0));
+    if (tc) RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg), s));
     RB_CU(mark(RB_STAGE_IMAGES, 1));
+    RB_CU(cudaStreamWaitEvent(s, ss->join, 0));
     RB_CU(mark(RB_STAGE_ADJOINT, 0));
     if (tc) {
         RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),

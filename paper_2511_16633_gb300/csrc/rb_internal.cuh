@@ -265,9 +265,11 @@ cudaError_t launch_elem_positions(const GeoDev& G, float4* elem_xy, cudaStream_t
 cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s);
 // Rays; with keys set also the gridding: keys are reset here, tables and/or srec are
 // written for every (element, pixel).
+// traced (nullable): recorded on s once the rays' end records are written, before the
+// rasteriser and the resolve pass
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
-                         cudaStream_t s);
+                         cudaStream_t s, cudaEvent_t traced = nullptr);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);

@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
-                         cudaStream_t s) {
+                         cudaStream_t s, cudaEvent_t traced) {
     rb_rays S{};
     int ws = 0;
     if (samples && samples->vx) {
@@ -656,6 +656,7 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     const long long rays = (long long)G.n_elem * G.n_rays;
     k_trace<<<(int)((rays + 127) / 128), 128, 0, s>>>(G, cells, ends, S, ws, V, counters);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && traced) e = cudaEventRecord(traced, s);   // the end records are complete
     if (e != cudaSuccess || !grid) return e;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
