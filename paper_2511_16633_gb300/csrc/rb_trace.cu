@@ -123,10 +123,6 @@ __device__ __forceinline__ void rotate(float C0, float S0, float th_hi, float d,
     }
 }
 
-struct RayCtx {
-    float xs_hi, xs_lo, ys_hi, ys_lo;  // source position
-};
-
 __device__ __forceinline__ Deriv eval_stage(const GeoDev& G, const float4* __restrict__ cells, Cache& cc,
                                             float xh, float xl, float yh, float yl, float Ca, float Sa, float tha,
                                             float dth, float q, float p,

@@ -124,3 +124,36 @@ def test_cg_sweep_tiny(dev):
     print(f"CG sweep: c RMS difference {rms:.3g} m/s; norms {rec.norms} vs {norms}")
     assert rms <= 0.05, rms
     assert np.allclose(rec.norms, norms, rtol=5e-3)
+
+
+def test_breast256_cg_mixed_against_plain(dev):
+    """Full size (256 elements, 256 x 256 pixels, 3 frequencies), where the oracle is too slow
+    for a CG solve: 6 iterations on the tensor-core path agree with the FP32 path (dc within
+    1e-3 relative L2, the residual history within 1 %), and the preconditioned residual falls."""
+    cfg = rbgen.breast256()
+    inp = rbgen.make_inputs(cfg)
+    geom = rb.geometry_from_config(cfg)
+    from paper_2511_16633_gb300.recon import synth_data
+    c0 = _t(inp.c_init, dev)
+    a0 = _t(inp.alpha0, dev)
+    s = cfg.sets[1]
+    freqs = [cfg.freqs_hz[i] for i in s]
+    p = synth_data(geom, c0, _t(inp.c_true, dev), a0, freqs, inp.noise_re[list(s)], inp.noise_im[list(s)], 0.01)
+    out = {}
+    for prec in (rb.RB_PREC_FP32, rb.RB_PREC_BF16X3):
+        c = c0.clone()
+        dc = torch.empty_like(c)
+        hist = torch.zeros(7, dtype=torch.float64, device=dev)
+        diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+        ws = rb.workspace(geom, len(freqs), prec, dev)
+        rb.rb_cg_update(geom, c, a0, freqs, p, ws, 6, True, prec=prec, dc_out=dc, hist_out=hist, diag_out=diag)
+        torch.cuda.synchronize()
+        assert rb.decode_diag(diag)["tc_timeouts"] == 0
+        out[prec] = (dc.cpu().numpy(), hist.cpu().numpy())
+        del ws
+    (d32, h32), (d16, h16) = out[rb.RB_PREC_FP32], out[rb.RB_PREC_BF16X3]
+    e = float(np.linalg.norm(d16 - d32) / np.linalg.norm(d32))
+    print(f"breast256 CG 6: mixed vs plain dc rel L2 {e:.3g}; history {h16} vs {h32}")
+    assert e <= 1e-3
+    assert np.allclose(h16, h32, rtol=1e-2, atol=1e-4)
+    assert h32[6] < 0.5 * h32[0]

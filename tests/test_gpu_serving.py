@@ -24,7 +24,8 @@ def _cfgs():
     return [rbgen.tiny(),
             rbgen.tiny(n_elem=128, nx=70, ny=66, n_rays=48, seed=20251116 + 11),
             rbgen.tiny(n_elem=40, nx=66, ny=70, n_rays=45, seed=20251116 + 12),
-            rbgen.tiny(n_elem=192, nx=64, ny=64, n_rays=64, seed=20251116 + 13)]
+            rbgen.tiny(n_elem=192, nx=64, ny=64, n_rays=64, seed=20251116 + 13),
+            rbgen.tiny(n_elem=512, nx=64, ny=64, n_rays=64, seed=20251116 + 14)]
 
 
 def _run(cfgs, problems, dev, policy, budget, slots, arrivals=None, realtime=False):
@@ -56,9 +57,9 @@ def test_poisson_stream_under_a_tight_budget(dev):
     problems = {k: serve.make_problem(c, dev) for k, c in enumerate(cfgs)}
     fps = [serve.footprint_bytes(c, serve.precision_for(c, "mixed")) for c in cfgs]
     budget = max(fps) + min(fps)            # at most two of them resident at once
-    arrivals = [0.0, 0.01, 0.02, 0.03]
+    arrivals = [0.01 * k for k in range(len(cfgs))]
     out, res = _run(cfgs, problems, dev, "mixed", budget, slots=4, arrivals=arrivals, realtime=True)
-    assert sorted(out) == [0, 1, 2, 3]
+    assert sorted(out) == list(range(len(cfgs)))
     assert res["peak_footprint_gb"] * 1e9 <= budget
     assert res["p99_s"] >= res["p50_s"] > 0
     for j in res["jobs"]:
