@@ -94,6 +94,20 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+def combine_ranks(ms_local, steps, world, device=None):
+    """Whole-job throughput of `world` replicas: the slowest rank's time for the timed
+    steps (all-reduce max; every rank gets it) and the updates of all ranks over that
+    time.  Returns (ms, updates/s)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
+
+
 def algorithmic_work(cfg, n_freq):
     """Per-update algorithmic work of the contractions (FLOP), as defined in the design doc section 6."""
     ne, npix = cfg.n_elem, cfg.nx * cfg.ny
@@ -192,12 +206,8 @@ def run_ours(args):
         wall = time.perf_counter() - t0
         clk = clocks.stop() if clocks else None
         per_step = np.array([starts[k].elapsed_time(ends[k]) for k in range(n_steps)])
-        ms = float(np.sum(per_step))
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        out = {"value": world * n_steps / (ms / 1e3), "ms_per_step": ms / n_steps,
+        ms, value = combine_ranks(float(np.sum(per_step)), n_steps, world, dev)
+        out = {"value": value, "ms_per_step": ms / n_steps,
                "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
                "stage_ms": {name: round(stage_ms[i] / n_steps, 4) for i, name in enumerate(rb.STAGES)},
                "wall_s": wall, "clocks": clk, "diag": rb.decode_diag(diag)}
