@@ -15,9 +15,14 @@
  *     ring sits at angle 2 pi t / n_elem.  Complex values are interleaved
  *     (re, im) float pairs.  Units are SI (m, s, Hz); alpha0 is in
  *     dB / (MHz^y cm).
- *   - The library allocates nothing, frees nothing and never synchronises
- *     the device: all scratch comes from the caller's workspace, sized by
- *     rb_workspace_size().  Calls are asynchronous and stream-ordered.
+ *   - The library allocates no device memory, frees nothing and never
+ *     synchronises the device: all scratch comes from the caller's workspace,
+ *     sized by rb_workspace_size() (rb_born_forward_noalloc excepted, see
+ *     there).  Calls are asynchronous and stream-ordered.  rb_hf_update and
+ *     rb_cg_update run part of their work on a library stream of the current
+ *     device (created with two events on the first such call and kept for the
+ *     process), forked from and joined back into the caller's stream inside the
+ *     call, so their results are ordered on the caller's stream as usual.
  *   - Argument and shape errors are detected on the host before any launch
  *     and returned synchronously; a failed launch returns RB_ERR_CUDA.
  *     Data-dependent conditions found on the device (a ray that does not
