@@ -135,7 +135,7 @@ int tc_ctas() {
 // keeps each call's fork and join events together when several host threads call.
 struct SideStream {
     cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t start = nullptr, keys = nullptr, fork = nullptr, join = nullptr;
 };
 std::mutex g_side_mutex;
 SideStream g_side[64];
@@ -148,6 +148,8 @@ cudaError_t side_stream(SideStream** out) {
     SideStream& ss = g_side[dev];
     if (!ss.s) {
         if ((e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ss.start, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ss.keys, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return e;
     }
@@ -201,6 +203,11 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     const cudaStream_t s2 = ss->s;
     const Marks mark2{mark.ev, s2};   // stage events of the side branch
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4 + DBL_N * 8, s));
+    // side branch 1: the first-arrival keys reset (all ones) while the fields and rays run
+    RB_CU(cudaEventRecord(ss->start, s));
+    RB_CU(cudaStreamWaitEvent(s2, ss->start, 0));
+    RB_CU(cudaMemsetAsync(W.at<void>(W.L.gkeys), 0xff, (size_t)G.n_elem * G.npix * sizeof(unsigned long long), s2));
+    RB_CU(cudaEventRecord(ss->keys, s2));
     RB_CU(mark(RB_STAGE_FIELDS, 0));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, cells, s));
@@ -209,8 +216,8 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     // the mixed path reads only the synthesis records, the plain path only the tables
     float4* srec = tc ? W.at<float4>(W.L.srec) : nullptr;
     RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), tc ? nullptr : tables, W.at<void>(W.L.verts), c,
-                       srec, cnt, s, ss->fork));
-    // side branch (needs the end records only): links, residuals, weights, B images
+                       srec, cnt, s, ss->fork, ss->keys));
+    // side branch 2 (needs the end records only): links, residuals, weights, B images
     RB_CU(cudaStreamWaitEvent(s2, ss->fork, 0));
     RB_CU(mark2(RB_STAGE_LINK, 0));
     RB_CU(launch_link(G, c, ends, F, R, linked, s2));

@@ -266,10 +266,12 @@ cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, 
 // Rays; with keys set also the gridding: keys are reset here, tables and/or srec are
 // written for every (element, pixel).
 // traced (nullable): recorded on s once the rays' end records are written, before the
-// rasteriser and the resolve pass
+// rasteriser and the resolve pass.  keys_ready (nullable): the caller resets the keys
+// (all ones) on another stream and records this event; s waits for it before the
+// rasteriser instead of resetting them itself
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
-                         cudaStream_t s, cudaEvent_t traced = nullptr);
+                         cudaStream_t s, cudaEvent_t traced = nullptr, cudaEvent_t keys_ready = nullptr);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);

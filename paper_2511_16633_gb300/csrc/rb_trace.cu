@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
-                         cudaStream_t s, cudaEvent_t traced) {
+                         cudaStream_t s, cudaEvent_t traced, cudaEvent_t keys_ready) {
     rb_rays S{};
     int ws = 0;
     if (samples && samples->vx) {
@@ -645,7 +645,7 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     Vtx* V = (Vtx*)verts;
     if (grid && (!V || (!tables && !srec))) return cudaErrorInvalidValue;
     unsigned long long* K = (unsigned long long*)keys;
-    if (grid) {
+    if (grid && !keys_ready) {
         cudaError_t e = cudaMemsetAsync(K, 0xff, (size_t)G.n_elem * G.npix * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
@@ -654,6 +654,7 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && traced) e = cudaEventRecord(traced, s);   // the end records are complete
     if (e != cudaSuccess || !grid) return e;
+    if (keys_ready && (e = cudaStreamWaitEvent(s, keys_ready, 0)) != cudaSuccess) return e;   // keys reset elsewhere
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         nsm = 148;
