@@ -238,6 +238,9 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
     const float va = fmaf(A0.yh, G.inv_h, G.cyg) + A0.yl * G.inv_h;
     const float xmin = fminf(fminf(0.f, Q.b0x), fminf(Q.b1x, Q.a1x)), xmax = fmaxf(fmaxf(0.f, Q.b0x), fmaxf(Q.b1x, Q.a1x));
     const float ymin = fminf(fminf(0.f, Q.b0y), fminf(Q.b1y, Q.a1y)), ymax = fmaxf(fmaxf(0.f, Q.b0y), fmaxf(Q.b1y, Q.a1y));
+    // a non-finite vertex (only from a non-physical sound speed, e.g. zero or infinite) would
+    // give a box over the whole grid: such a quad covers nothing
+    if (!isfinite(ua + va + xmin + xmax + ymin + ymax)) return;
     const int bx0 = max(0, (int)ceilf(fmaf(xmin, G.inv_h, ua) - 1e-3f));
     const int bx1 = min(G.nx - 1, (int)floorf(fmaf(xmax, G.inv_h, ua) + 1e-3f));
     const int iy0 = max(0, (int)ceilf(fmaf(ymin, G.inv_h, va) - 1e-3f));
