@@ -414,7 +414,7 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "bf16x3"],
                     help="headline precision; the other one is measured beside it unless --no-compare")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["breast512", "breast256", "invivo512", "tiny"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["breast512", "breast256", "invivo512", "fullring1024", "tiny"],
                     help="the timed workload is breast512; smaller ones are for profiling captures")
     ap.add_argument("--cpu-fans", type=int, default=32)
     ap.add_argument("--cpu-pix", type=int, default=32768, help="reference arm: pixels sampled per step")

@@ -59,7 +59,8 @@ typedef enum {
     RB_PREC_FP32 = 0,       /* plain FP32 CUDA-core contractions (the adjoint, and so rb_born_adjoint,
                                rb_hf_update and rb_cg_update, for rings of up to 512 elements) */
     RB_PREC_BF16X3 = 1      /* tcgen05 BF16 tensor cores, 3-term split products, FP32 accumulation
-                               (rings of 64..256 elements in multiples of 64, and of 512) */
+                               (rings of 64..256 elements in multiples of 64, and of 512, 768
+                               and 1024) */
 } rb_precision;             /* other ring sizes return RB_ERR_UNSUPPORTED before any work */
 
 typedef enum {

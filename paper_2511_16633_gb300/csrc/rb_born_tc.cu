@@ -237,9 +237,9 @@ __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __
 // drain (MMA completion on the error path).  Every wait is bounded; a timeout
 // raises a shared flag that ends all loops.
 // ---------------------------------------------------------------------------
-// NP: passes over the elements (1 for rings up to 256 elements, 2 for 512), fixed at
-// compile time so that the one-pass kernel carries no pass bookkeeping.
-template <int NP>
+// MULTI: more than one pass over the elements (rings above 256 elements, passes of 256);
+// the one-pass kernel is compiled without the pass bookkeeping.
+template <bool MULTI>
 __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_full[NST], s_empty[NST], s_acc_full, s_acc_empty, s_acc_low, s_vready, s_drain;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     // the elements e of U and V are taken in passes of ne (the accumulators of one pass
     // fit TMEM); the contractions run over all r in every pass
     const int ne = A.n_e, ne2 = 2 * ne;
-    constexpr int npass = NP;
+    const int npass = MULTI ? A.npass : 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nU = n2 / 16, nV = n / 32, per = nU + nV;
     if (tid == 0) {
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     // B: rows e' of this pass (contiguous in each plane), hi then lo; with one
                     // pass the two planes are adjacent and go in one copy
                     const __nv_bfloat16* bsrc = A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u + (size_t)pass * ne2 * 16;
-                    if (NP == 1) {
+                    if (!MULTI) {
                         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                                      ::"r"(tc::smem_u32(stage(s) + ST_B)), "l"(bsrc), "r"(bbytes), "r"(mb)
                                      : "memory");
@@ -594,8 +594,10 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
 }  // namespace
 
 // rings of 64..256 elements in multiples of 64 in one pass over the elements of U and V,
-// and 512 elements in two passes of 256
-bool tc_adjoint_supported(int n_elem) { return (n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0) || n_elem == 512; }
+// and of 512, 768 and 1024 elements in passes of 256
+bool tc_adjoint_supported(int n_elem) {
+    return (n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0) || (n_elem % 256 == 0 && n_elem >= 512 && n_elem <= 1024);
+}
 
 cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s) {
     const long long total = (long long)G.n_elem * G.npix;
@@ -662,13 +664,13 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
     const int grid = n_ctas < A.n_tiles ? n_ctas : A.n_tiles;
     cudaError_t e;
     if (A.npass == 1) {
-        e = cudaFuncSetAttribute(k_adjoint_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        e = cudaFuncSetAttribute(k_adjoint_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        k_adjoint_tc<1><<<grid, NTHR_A, sm, s>>>(A);
+        k_adjoint_tc<false><<<grid, NTHR_A, sm, s>>>(A);
     } else {
-        e = cudaFuncSetAttribute(k_adjoint_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        e = cudaFuncSetAttribute(k_adjoint_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        k_adjoint_tc<2><<<grid, NTHR_A, sm, s>>>(A);
+        k_adjoint_tc<true><<<grid, NTHR_A, sm, s>>>(A);
     }
     return cudaGetLastError();
 }
@@ -688,8 +690,9 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
 // ===========================================================================
 namespace {
 
-constexpr int FMAXB = 8;   // max row blocks (2n / 128, n <= 512)
-constexpr int FMAXP = 16;  // max (row block, column group) pairs
+constexpr int FMAXB = 16;  // max row blocks (2n / 128, n <= 1024)
+constexpr int FMAXG = 4;   // max column groups of two 256-column blocks (2n / 512)
+constexpr int FMAXP = 40;  // max (row block, column group) pairs (40 for n = 1024)
 constexpr int FBOX_MAX = 32;   // rows (of 8 r') per TMA box, at most
 constexpr uint32_t ST_FB = 8192u;   // forward stage: A hi (4 KB), A lo (4 KB), then B hi and B lo
 
@@ -706,7 +709,7 @@ struct FwdArgs {
     int p_i[FMAXP], p_jb[FMAXP], p_je[FMAXP];
     int splits[FMAXP];         // splits per pair
     int cta0[FMAXP + 1];       // first CTA of each pair
-    int pidx[FMAXB][2];        // pair of (row block, column group of two blocks)
+    int pidx[FMAXB][FMAXG];    // pair of (row block, column group of two blocks)
     uint32_t tmem_cols;
     uint32_t* counters;
     int fbox;                  // rows per TMA box: divides every pair's loaded rows (and 16)
@@ -990,7 +993,7 @@ FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const float* m, float* pa
     // groups of two (group g holds blocks 2g and 2g + 1)
     A.n_pairs = 0;
     for (int i = 0; i < A.n_mb; ++i) {
-        A.pidx[i][0] = A.pidx[i][1] = -1;
+        for (int g = 0; g < FMAXG; ++g) A.pidx[i][g] = -1;
         const int jmin = jmin_of(i, A.nb);
         for (int g = jmin / 2; 2 * g < A.nbn; ++g) {
             const int q = A.n_pairs++;

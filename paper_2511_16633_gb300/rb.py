@@ -144,7 +144,7 @@ def _freqs(freqs):
 
 def tc_supported(n_elem: int) -> bool:
     """Ring sizes the tensor-core (RB_PREC_BF16X3) contractions take."""
-    return (64 <= n_elem <= 256 and n_elem % 64 == 0) or n_elem == 512
+    return (64 <= n_elem <= 256 and n_elem % 64 == 0) or (n_elem % 256 == 0 and 512 <= n_elem <= 1024)
 
 
 def rb_workspace_size(geom: rb_geometry, n_freq: int = 1, prec: int = RB_PREC_FP32) -> int:

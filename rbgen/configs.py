@@ -10,6 +10,7 @@ Three workloads, named for what they are:
                   20 frequencies 0.3-1.25 MHz in 5 sets of 4.
 * ``invivo512`` — 512 elements on the same ring (the in-vivo transducer count),
                   256x256 grid at 0.9 mm, 512 rays per emitter, 5 sets of 4.
+* ``fullring1024`` — the same with all 1024 elements of the array.
 * ``ring`` / ``batch_mix`` / ``poisson_requests`` — workloads of uneven sizes on the
                   same 110 mm ring (batched reconstructions and a request stream).
 
@@ -105,7 +106,17 @@ def invivo512(**kw) -> Config:
     return ring(512, 256, 20, **{k: v for k, v in base.items() if k not in ("n_elem",)})
 
 
-CONFIGS = {"tiny": tiny, "breast256": breast256, "breast512": breast512, "invivo512": invivo512}
+def fullring1024(**kw) -> Config:
+    """The full 1024-element array the in-vivo data come from (Sec. 4.2 uses half of it):
+    1024 elements on the 110 mm ring, 256 x 256 pixels at 0.9 mm, 512 rays per emitter,
+    5 sets of 4 frequencies 0.3-1.25 MHz."""
+    base = dict(name="fullring1024", n_rays=512, seed=20251116 + 7)
+    base.update(kw)
+    return ring(1024, 256, 20, **base)
+
+
+CONFIGS = {"tiny": tiny, "breast256": breast256, "breast512": breast512, "invivo512": invivo512,
+           "fullring1024": fullring1024}
 
 
 def config_by_name(name: str, **kw) -> Config:

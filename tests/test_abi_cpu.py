@@ -121,8 +121,8 @@ def test_argument_errors_are_synchronous(lib):
     f0 = (ctypes.c_double * 1)(3e5)
     assert lib.rb_hf_update(ctypes.byref(g), fake, fake, f0, 0, fake, ctypes.byref(prm), 0, None, None, fake, 1 << 30,
                             None) == rb.RB_ERR_ARG
-    # the tensor-core path takes rings of 64..256 elements in multiples of 64, and 512
-    for n_bad in (96, 320, 768):
+    # the tensor-core path takes rings of 64..256 elements in multiples of 64, and 512, 768, 1024
+    for n_bad in (96, 320, 640):
         gb = rb.geometry_from_config(rbgen.tiny(), n_elem=n_bad)
         assert lib.rb_hf_update(ctypes.byref(gb), fake, fake, f1, 1, fake, ctypes.byref(prm), rb.RB_PREC_BF16X3, None,
                                 None, fake, 1 << 30, None) == rb.RB_ERR_UNSUPPORTED

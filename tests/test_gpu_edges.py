@@ -130,8 +130,9 @@ def test_fan_of_4096_rays_linking(dev):
     assert _rel(p.cpu().numpy()[0][mask], po[mask]) <= 1e-4
 
 
-def test_ring_of_512_elements_bf16x3_update(dev):
-    cfg = rbgen.tiny(n_elem=512, n_rays=64)
+@pytest.mark.parametrize("n_elem", [512, 1024])
+def test_ring_of_512_elements_bf16x3_update(dev, n_elem):
+    cfg = rbgen.tiny(n_elem=n_elem, n_rays=64)
     inp = rbgen.make_inputs(cfg)
     g = ogeom.from_config(cfg)
     freqs = list(cfg.freqs_hz[1:3])
@@ -147,7 +148,7 @@ def test_ring_of_512_elements_bf16x3_update(dev):
     torch.cuda.synchronize()
     d = rb.decode_diag(diag)
     e = _rel(dc.cpu().numpy(), ref.dc)
-    print(f"512 elements bf16x3: dc rel L2 {e:.3g}, alpha {d['alpha']:.6g} vs {ref.alpha:.6g}")
+    print(f"{n_elem} elements bf16x3: dc rel L2 {e:.3g}, alpha {d['alpha']:.6g} vs {ref.alpha:.6g}")
     assert d["tc_timeouts"] == 0
     assert d["kept"] == ref.n_kept and d["zeroed"] == ref.n_zeroed
     assert e <= 1e-3

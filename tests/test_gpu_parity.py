@@ -429,11 +429,13 @@ def test_bf16x3_ring_sizes_ragged(dev, n_elem, nx, ny):
     assert ed <= 1e-4, ed
 
 
-# A ring of 512 elements (the in-vivo transducer count of the paper's Sec. 4) on the
-# tensor cores: the adjoint in two passes of 256 elements, the forward in (row block,
-# column group) pairs, some of which load their row block's own rows separately.
-def test_bf16x3_ring_512(dev):
-    cfg = rbgen.tiny(n_elem=512, n_rays=64)
+# Rings of 512 elements (the in-vivo transducer count of the paper's Sec. 4) and 1024 (the
+# full array it was taken from) on the tensor cores: the adjoint in passes of 256
+# elements, the forward in (row block, column group) pairs, some of which load their row
+# block's own rows separately.
+@pytest.mark.parametrize("n_elem", [512, 1024])
+def test_bf16x3_ring_512(dev, n_elem):
+    cfg = rbgen.tiny(n_elem=n_elem, n_rays=64)
     inp = rbgen.make_inputs(cfg)
     c = inp.c_true
     g = ogeom.from_config(cfg)
@@ -458,5 +460,5 @@ def test_bf16x3_ring_512(dev):
     eg = rel_l2(gg.cpu().numpy(), oborn.born_adjoint(Go, W * R.astype(np.complex128), f))
     eh = rel_l2(hh.cpu().numpy(), oborn.hess_diag(Go, W, f))
     ef = rel_l2(d.cpu().numpy(), oborn.born_forward(Go, m.astype(np.float64), f))
-    print(f"bf16x3 n=512: gradient {eg:.3g}, Hessian diagonal {eh:.3g}, forward {ef:.3g}")
+    print(f"bf16x3 n={n_elem}: gradient {eg:.3g}, Hessian diagonal {eh:.3g}, forward {ef:.3g}")
     assert eg <= 1e-4 and eh <= 1e-4 and ef <= 1e-4
