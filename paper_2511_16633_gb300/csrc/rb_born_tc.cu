@@ -439,6 +439,10 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
         // -------------------------------- producers --------------------------------
         const uint32_t p = (uint32_t)(tid & (TP - 1)), h = (uint32_t)(tid / TP);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        // the U slices' (pixel, quarter) items go 8 pixels x 4 quarters to a warp: the A reads
+        // then fall on distinct shared-memory banks and the |G|^2 stores on 128 contiguous
+        // bytes (the epilogues keep p = the TMEM lane)
+        const uint32_t cp = (uint32_t)((lane & 7) + 8 * warp), ch = (uint32_t)(lane >> 3);
         float2* gs = A.gscr + (size_t)blockIdx.x * n * TP;
         bool err = false;
         int qs = 0;                // stage of the next slice
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 // ---- U slices: exact-enough G for the epilogue and the |G|^2 slices ----
                 for (int j = 0; j < nU; ++j)
                     slice([&](const unsigned char* ahi, const unsigned char* alo) {
-                        consume_u(j * 8, p, h, ahi, alo, gs, vimg);
+                        consume_u(j * 8, cp, ch, ahi, alo, gs, vimg);
                     });
                 // the |G|^2 slices (read next by the bulk copies of the loader) are complete
                 asm volatile("fence.proxy.async.global;" ::: "memory");
