@@ -109,7 +109,10 @@ def combine_ranks(ms_local, steps, world, device=None):
 
 
 def algorithmic_work(cfg, n_freq):
-    """Per-update algorithmic work of the contractions (FLOP), as defined in the design doc section 6."""
+    """Per-update algorithmic work of the contractions (FLOP), complex products written out
+    in real arithmetic: per frequency the adjoint's U = S conj(G) (8 n^2 npix), its Hessian
+    contraction W |G|^2 (2 n^2 npix) and the two epilogues (10 n npix); the forward's
+    G diag(m) G^T (8 n^2 npix)."""
     ne, npix = cfg.n_elem, cfg.nx * cfg.ny
     adj_flop = n_freq * (8.0 * ne * ne * npix + 2.0 * ne * ne * npix + 10.0 * ne * npix)
     fwd_flop = n_freq * 8.0 * ne * ne * npix
@@ -122,7 +125,7 @@ def algorithmic_work(cfg, n_freq):
 # contraction (2 n^2 npix) two (W is exact in bf16): (3 x 8 + 2 x 2) / (8 + 2).
 ADJ_ISSUE_RATIO = 2.8
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512
-# (ncu --metrics, 1 pass; profiles/k_adjoint_tc.md), None when not measured for the
+# (ncu --metrics, one pass), None when not measured for the
 # kernel as built.
 ADJ_TRAFFIC_BYTES = 2152357376 + 1045066752   # dram read + write of one k_adjoint_tc launch (ncu, breast512)
 
