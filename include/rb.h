@@ -52,7 +52,7 @@ typedef enum {
     RB_ERR_WORKSPACE = 3,   /* workspace missing, too small or misaligned */
     RB_ERR_CUDA = 4,        /* a CUDA launch or call failed */
     RB_ERR_LIMIT = 5,       /* reserved for device-side limits reported by later calls */
-    RB_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    RB_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
 } rb_status;
 
 typedef enum {

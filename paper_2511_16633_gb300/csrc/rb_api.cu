@@ -306,7 +306,7 @@ const char* rb_status_string(rb_status s) {
         case RB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
         case RB_ERR_CUDA: return "CUDA launch or call failed";
         case RB_ERR_LIMIT: return "device-side limit reached";
-        case RB_ERR_UNSUPPORTED: return "not supported by this build";
+        case RB_ERR_UNSUPPORTED: return "not supported by the library";
     }
     return "unknown status";
 }
