@@ -87,6 +87,7 @@ struct TcArgs {
     int n_tiles;
     uint32_t tmem_cols;
     int n_e, npass;            // elements per pass (N of the MMAs: 2 n_e and n_e), passes = n / n_e
+    int want_h;                // the Hessian contraction is wanted (h_out or hsum set)
 };
 
 // Synthesis records of every element and pixel from the tables.
@@ -148,7 +149,7 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
 // G to ~2^-17 relative for the epilogue (gs), and |G|^2 (hi / lo) goes to the V
 // slice r0 / 16 of this CTA.
 __device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const unsigned char* a_hi,
-                                          const unsigned char* a_lo, float2* gs, __nv_bfloat16* vimg) {
+                                          const unsigned char* a_lo, float2* gs, __nv_bfloat16* vimg, bool want_h) {
     // A slice = two image rows (K cores) of 2 KB: K core h / 2, pixel core p / 8, row p % 8
     const uint32_t off = (h >> 1) * 2048u + (p >> 3) * 128u + (p & 7u) * 16u + 8u * (h & 1u);
     const uint2 wh = *(const uint2*)(a_hi + off), wl = *(const uint2*)(a_lo + off);
@@ -163,6 +164,7 @@ __device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const 
         gs[(size_t)(r0 + 2 * (int)h + j) * TP + p] = make_float2(re, -mim);
         tc::split_bf16(re * re + mim * mim, vh[j], vl[j]);
     }
+    if (!want_h) return;
     __nv_bfloat16* vs = vimg + (size_t)(r0 >> 5) * (2 * TP * 32);
     const uint32_t voff = tc::chunk_offset(p, (uint32_t)(r0 & 31) + 2u * h) / 2;
     *(uint32_t*)(vs + voff) = pack2(vh[0], vh[1]);
@@ -253,7 +255,9 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     const int ne = A.n_e, ne2 = 2 * ne;
     const int npass = MULTI ? A.npass : 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nU = n2 / 16, nV = n / 32, per = nU + nV;
+    // U slices, then (when the Hessian diagonal is wanted) V slices
+    const bool want_h = A.want_h != 0;
+    const int nU = n2 / 16, nV = want_h ? n / 32 : 0, per = nU + nV;
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             tc::mbar_init(tc::smem_u32(&s_full[s]), 1);
@@ -482,12 +486,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 // ---- U slices: exact-enough G for the epilogue and the |G|^2 slices ----
                 for (int j = 0; j < nU; ++j)
                     slice([&](const unsigned char* ahi, const unsigned char* alo) {
-                        consume_u(j * 8, cp, ch, ahi, alo, gs, vimg);
+                        consume_u(j * 8, cp, ch, ahi, alo, gs, vimg, want_h);
                     });
                 // the |G|^2 slices (read next by the bulk copies of the loader) are complete
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                __syncwarp();
-                if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_vready));
+                if (want_h) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_vready));
+                }
                 // gs (G of the tile) is complete
                 err = tc::named_or(1, NPROD, err);
                 if (err) break;
@@ -548,6 +554,11 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 if (h == 0) {
                     fg_r += (gr + s_red[0][0][p] + s_red[0][1][p] + s_red[0][2][p]) * fc.w2;
                     fg_i += (gi + s_red[1][0][p] + s_red[1][1][p] + s_red[1][2][p]) * fc.w2;
+                }
+                if (!want_h) {
+                    // no V phase: the accumulator is free for the next U phase
+                    acc_release();
+                    continue;
                 }
                 // ---- V slices: A and B come by bulk copy; the producers only pass the
                 // stage barriers, which keeps every stage's phases in step with its uses ----
@@ -659,6 +670,7 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
     A.counters = counters;
     A.n_tiles = (G.npix + TP - 1) / TP;
     A.n_e = n < 256 ? n : 256;
+    A.want_h = (h_out || hsum) ? 1 : 0;
     A.npass = n / A.n_e;
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * A.n_e)) cols <<= 1;
