@@ -728,7 +728,7 @@ struct FwdArgs {
     int pidx[FMAXB][FMAXG];    // pair of (row block, column group of two blocks)
     uint32_t tmem_cols;
     uint32_t* counters;
-    int fbox;                  // rows per TMA box: divides every pair's loaded rows (and 16)
+    int fbox;                  // rows per TMA box of the B rows: divides every pair's loaded rows
 };
 
 __host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i) / nb; }
@@ -742,7 +742,8 @@ __host__ __device__ __forceinline__ int jmin_of(int i, int nb) { return (128 * i
 // SEP: some pairs load their row block's own rows separately (rings above 256 elements);
 // without it every pair finds them among its B rows and the test compiles away.
 template <bool SEP>
-__global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __grid_constant__ CUtensorMap tmap,
+                                                         const __grid_constant__ CUtensorMap tmap16) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_full_a[NST], s_full_b[NST], s_empty[NST], s_acc_full;
     __shared__ uint32_t s_tmem;
@@ -790,6 +791,7 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
             int ql = 0;
             bool err = false;
             const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
+            const uint64_t tm16 = reinterpret_cast<uint64_t>(&tmap16);   // 16-row boxes: a row block's own rows
             for (; ql < nq; ++ql) {
                 const int k = ql % NST;
                 if (ql >= NST && !tc::mbar_wait(tc::smem_u32(&s_empty[k]), (uint32_t)((ql / NST) - 1) & 1u, kMaxTries)) {
@@ -810,15 +812,14 @@ __global__ void __launch_bounds__(NTHR_F, 1) k_forward_tc(FwdArgs A, const __gri
                             ::"r"(dst), "l"(tm), "r"(x), "r"(y), "r"(mb)
                             : "memory");
                     }
-                    if (!own_in)
-                        for (int b = 0; b < 16 / A.fbox; ++b) {
-                            const uint32_t dst = tc::smem_u32(stage(k) + hl * ST_ALO + (uint32_t)(b * A.fbox) * 256u);
-                            const int y = (t * 2 + hl) * rcn + 16 * i + b * A.fbox;
-                            asm volatile(
-                                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                                ::"r"(dst), "l"(tm), "r"(x), "r"(y), "r"(mb)
-                                : "memory");
-                        }
+                    if (!own_in) {
+                        const uint32_t dst = tc::smem_u32(stage(k) + hl * ST_ALO);
+                        const int y = (t * 2 + hl) * rcn + 16 * i;
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                            ::"r"(dst), "l"(tm16), "r"(x), "r"(y), "r"(mb)
+                            : "memory");
+                    }
                 }
             }
             if (err || s_err) {
@@ -1036,13 +1037,12 @@ FwdArgs make_fwd_args(const GeoDev& G, const FreqC& F, const float* m, float* pa
         c0 += sq;
     }
     A.cta0[A.n_pairs] = c0;
-    // TMA box height: the largest power of two up to FBOX_MAX dividing every pair's loaded
-    // rows, and 16 where a pair loads its row block's own rows separately
+    // TMA box height of the B rows: the largest power of two up to FBOX_MAX dividing every
+    // pair's loaded rows (a row block's own 16 rows, where loaded apart, use 16-row boxes)
     A.fbox = FBOX_MAX;
     for (int q = 0; q < A.n_pairs; ++q) {
-        const int rc0 = A.p_jb[q] * A.nb / 8, nrow = (A.p_je[q] - A.p_jb[q]) * A.nb / 8;
-        const bool own_in = 16 * A.p_i[q] >= rc0 && 16 * A.p_i[q] + 16 <= rc0 + nrow;
-        while (nrow % A.fbox != 0 || (!own_in && 16 % A.fbox != 0)) A.fbox >>= 1;
+        const int nrow = (A.p_je[q] - A.p_jb[q]) * A.nb / 8;
+        while (nrow % A.fbox != 0) A.fbox >>= 1;
     }
     return A;
 }
@@ -1062,9 +1062,10 @@ cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F,
     // (tile, plane, row) major; boxes of 128 elements (one 16-pixel slice) x fbox rows
     const int rcn = 2 * G.n_elem / 8;
     const int n_tiles = (G.npix + TP - 1) / TP;
-    CUtensorMap tmap;
+    CUtensorMap tmap, tmap16;
     if (A.fbox < 1 || !tc::encode_tmap_2d(&tmap, aimg, 1024, (uint64_t)n_tiles * 2 * rcn, 2048, 128, (uint32_t)A.fbox))
         return cudaErrorUnknown;
+    if (!tc::encode_tmap_2d(&tmap16, aimg, 1024, (uint64_t)n_tiles * 2 * rcn, 2048, 128, 16u)) return cudaErrorUnknown;
     const int sm = NST * (int)ST_BYTES;
     bool sep = false;
     for (int q = 0; q < A.n_pairs; ++q) {
@@ -1075,11 +1076,11 @@ cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F,
     if (sep) {
         e = cudaFuncSetAttribute(k_forward_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        k_forward_tc<true><<<A.cta0[A.n_pairs], NTHR_F, sm, s>>>(A, tmap);
+        k_forward_tc<true><<<A.cta0[A.n_pairs], NTHR_F, sm, s>>>(A, tmap, tmap16);
     } else {
         e = cudaFuncSetAttribute(k_forward_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
-        k_forward_tc<false><<<A.cta0[A.n_pairs], NTHR_F, sm, s>>>(A, tmap);
+        k_forward_tc<false><<<A.cta0[A.n_pairs], NTHR_F, sm, s>>>(A, tmap, tmap16);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
