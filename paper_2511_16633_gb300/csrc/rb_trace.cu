@@ -512,6 +512,10 @@ __device__ __forceinline__ Vtx get_vtx(const Vtx* __restrict__ src) {
 // the rays); each lane's four vertices are 32-byte loads, shared with the next lane
 // through L1.
 constexpr int KW = 32;
+constexpr int KB = 8;   // quads per thread of the tube-major mapping
+#ifndef RASTER_ALONG_K_MIN_PX
+#define RASTER_ALONG_K_MIN_PX 4.0   // tube width (pixels, across the ring) from which warps run along the tubes
+#endif
 
 // Columns [lo, hi] of row iy inside the support disc (2 ix - (nx - 1))^2 +
 // (2 iy - (ny - 1))^2 <= r2max, exact in integers; lo > hi for an empty row.
@@ -526,6 +530,12 @@ __device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
     return make_short2((short)lo, (short)hi);
 }
 
+// ALONG_K: a warp takes 32 consecutive quads of one tube (one per lane) -- for fans whose
+// tubes span several pixels, where neighbouring quads of a tube are alike in size.
+// Otherwise a thread takes 8 consecutive quads of one tube and a warp 32 neighbouring
+// tubes at the same steps -- for fans finer than the grid, whose quads mostly cover at
+// most one pixel, where the vertex loads (contiguous across tubes) set the pace.
+template <bool ALONG_K>
 __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict__ verts,
                                                 const rb_ray_end* __restrict__ ends, unsigned long long* __restrict__ keys,
                                                 uint32_t nt_magic) {
@@ -533,24 +543,50 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
     for (int iy = threadIdx.x; iy < G.ny; iy += blockDim.x) s_supp[iy] = support_row(G, iy);
     __syncthreads();
     const int NT = G.n_rays - 1;
-    const int nkc = (G.max_steps + KW - 1) / KW;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
-    const int per_fan = nkc * NT;   // warp items per fan, < 2^31 (the triangle ids fit 24 bits)
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    // fans t = blockIdx.y + j gridDim.y; within a fan, warp item = kc NT + i
-    for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y)
-    for (int item = blockIdx.x * wpb + wib; item < per_fan; item += gridDim.x * wpb) {
-        uint32_t ukc, ui;
-        udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukc, ui);
-        const int i = (int)ui;
-        const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
-        const int k = (int)ukc * KW + lane + 1;
-        if (k > max(la, lb)) continue;
-        const Vtx A0 = get_vtx(verts + vidx(G, t, min(k - 1, la), i));
-        const Vtx B0 = get_vtx(verts + vidx(G, t, min(k - 1, lb), i + 1));
-        const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
-        const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
-        raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, keys + (size_t)t * G.npix, s_supp);
+    if (ALONG_K) {
+        const int nkc = (G.max_steps + KW - 1) / KW;
+        const int per_fan = nkc * NT;   // warp items per fan, < 2^31 (the triangle ids fit 24 bits)
+        const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+        // fans t = blockIdx.y + j gridDim.y; within a fan, warp item = kc NT + i
+        for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y)
+        for (int item = blockIdx.x * wpb + wib; item < per_fan; item += gridDim.x * wpb) {
+            uint32_t ukc, ui;
+            udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukc, ui);
+            const int i = (int)ui;
+            const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+            const int k = (int)ukc * KW + lane + 1;
+            if (k > max(la, lb)) continue;
+            const Vtx A0 = get_vtx(verts + vidx(G, t, min(k - 1, la), i));
+            const Vtx B0 = get_vtx(verts + vidx(G, t, min(k - 1, lb), i + 1));
+            const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
+            const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
+            raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, keys + (size_t)t * G.npix,
+                        s_supp);
+        }
+    } else {
+        const int nkb = (G.max_steps + KB - 1) / KB;
+        const int per_fan = nkb * NT;
+        // fans t = blockIdx.y + j gridDim.y; within a fan, thread item = kb NT + i
+        for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y)
+        for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < per_fan; item += gridDim.x * blockDim.x) {
+            uint32_t ukb, ui;
+            udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukb, ui);
+            const int i = (int)ui, kb = (int)ukb;
+            const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+            const int k0 = kb * KB + 1, k1 = min(k0 + KB - 1, max(la, lb));
+            if (k0 > k1) continue;
+            unsigned long long* tab = keys + (size_t)t * G.npix;
+            Vtx A0 = get_vtx(verts + vidx(G, t, min(k0 - 1, la), i));
+            Vtx B0 = get_vtx(verts + vidx(G, t, min(k0 - 1, lb), i + 1));
+            for (int k = k0; k <= k1; ++k) {
+                const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
+                const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
+                raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, tab, s_supp);
+                A0 = A1;
+                B0 = B1;
+            }
+        }
     }
 }
 
@@ -662,8 +698,15 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         nsm = 148;
     const int ry = G.n_elem < 16 ? G.n_elem : 16;
-    k_raster<<<dim3(nsm * 16 / ry, ry), 256, (size_t)G.ny * sizeof(short2), s>>>(
-        G, V, ends, K, (uint32_t)(0x100000000ull / (uint32_t)(G.n_rays - 1)));
+    // tube width in pixels where the fan is widest (across the ring): the ray spacing
+    // 2 R pi / n_rays over h
+    const double tube_px = 2.0 * G.R_d * RB_PI_D / (double)G.n_rays / G.h_d;
+    const uint32_t ntm = (uint32_t)(0x100000000ull / (uint32_t)(G.n_rays - 1));
+    const size_t ssm = (size_t)G.ny * sizeof(short2);
+    if (tube_px >= RASTER_ALONG_K_MIN_PX)
+        k_raster<true><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, ntm);
+    else
+        k_raster<false><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, ntm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
