@@ -200,6 +200,43 @@ def compare_solvers(cfg, variants: Sequence[int], prec=rb.RB_PREC_BF16X3, device
     return out
 
 
+def pipeline(cfg, tof_iters: int = 3, prec=rb.RB_PREC_BF16X3, device="cuda") -> dict:
+    """The paper's workflow on one synthetic problem: the time-of-flight guess from water
+    (tof_iters linearisations), then the one-step ray-Born sweep from that image over the
+    frequency sets, low to high.  Data: the ray-model data of the true medium plus 1 %
+    noise, and its linked times of flight.  Returns the RMS error of c against the phantom
+    over the support after each stage and the device times."""
+    import torch
+
+    import rbgen
+    dev = torch.device(device)
+    inp = rbgen.make_inputs(cfg)
+    geom = rb.geometry_from_config(cfg)
+    ct = torch.as_tensor(inp.c_true, device=dev, dtype=torch.float32).contiguous()
+    a0 = torch.as_tensor(inp.alpha0, device=dev, dtype=torch.float32).contiguous()
+    p = synth_data(geom, ct, ct, a0, list(cfg.freqs_hz), inp.noise_re, inp.noise_im, 0.01, prec)
+    sup = _support_mask(geom, dev)
+
+    def rms(c):
+        return float(torch.sqrt(torch.mean((c - ct)[sup].double() ** 2)))
+
+    c_tof, hist, tof_ms = tof_guess(cfg, tof_iters, device)
+    out = {"workload": cfg.name, "rms_water": rms(torch.full_like(ct, float(cfg.c_water))), "rms_tof": rms(c_tof),
+           "tof_ms": tof_ms, "tof_misfit_s": hist}
+    rec = Reconstruction(cfg, c_tof.cpu().numpy(), inp.alpha0, p, prec=prec, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    errs, ms = [], 0.0
+    for j in range(len(cfg.sets)):
+        e0.record()
+        rec.update(j)
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        errs.append(rms(rec.c))
+    out.update(sweep_ms=ms, rms_after_set=errs)
+    return out
+
+
 def main():
     import argparse
     import json
@@ -213,7 +250,13 @@ def main():
     ap.add_argument("--data", default="born", choices=["born", "ray"])
     ap.add_argument("--tof", type=int, default=0,
                     help="only the time-of-flight initial guess with this many linearisations (timing and error)")
+    ap.add_argument("--pipeline", action="store_true",
+                    help="time-of-flight guess, then the one-step sweep from it, on ray data of the true medium")
     a = ap.parse_args()
+    if a.pipeline:
+        prec = rb.RB_PREC_BF16X3 if a.prec == "bf16x3" else rb.RB_PREC_FP32
+        print(json.dumps(pipeline(rbgen.config_by_name(a.workload), 3, prec)), flush=True)
+        return
     if a.tof > 0:
         import torch
         cfg = rbgen.config_by_name(a.workload)
