@@ -118,3 +118,13 @@ def test_tof_breast256_properties(dev):
     e3 = math.sqrt(float(np.mean((c1 - inp.c_true)[sup] ** 2)))
     print(f"breast256 ToF: misfit {h1}, c error {e0:.3f} -> {e3:.3f} m/s")
     assert e3 < 0.9 * e0
+
+
+def test_pipeline_tof_then_sweep_reduces_error(dev):
+    """The workflow end to end on the tiny phantom: the time-of-flight guess improves on
+    water and the ray-Born sweep from it improves on the guess."""
+    from paper_2511_16633_gb300.recon import pipeline
+    out = pipeline(rbgen.tiny(), 3, rb.RB_PREC_BF16X3, dev)
+    print(f"pipeline tiny: water {out['rms_water']:.3f}, ToF {out['rms_tof']:.3f}, sweep {out['rms_after_set']}")
+    assert out["rms_tof"] < out["rms_water"]
+    assert out["rms_after_set"][-1] < out["rms_tof"]

@@ -49,3 +49,14 @@ def test_next_arrival_and_idle():
     assert s.next_arrival() == pytest.approx(1.5)
     assert s.admit(1.0) == [] and not s.idle()
     assert [j.jid for j in s.admit(3.0)] == [1, 0]
+
+
+def test_precision_policy_covers_the_tensor_core_ring_sizes():
+    import rbgen
+    from paper_2511_16633_gb300 import rb, serve
+    for n, tc in ((64, True), (96, False), (192, True), (256, True), (320, False), (512, True), (768, True),
+                  (1024, True)):
+        cfg = rbgen.ring(n, 128, 4)
+        assert rb.tc_supported(n) == tc
+        assert serve.precision_for(cfg, "mixed") == (rb.RB_PREC_BF16X3 if tc else rb.RB_PREC_FP32)
+        assert serve.precision_for(cfg, "plain") == rb.RB_PREC_FP32
