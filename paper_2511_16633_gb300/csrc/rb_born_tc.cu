@@ -108,26 +108,7 @@ __global__ void k_srec(GeoDev G, const rb_cell* __restrict__ tables, const float
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// Adjoint kernel: warp-specialised, NST-stage pipeline of K = 16 slices.
-//   warps 0..15 producers: pixel p = tid % 128 (TMEM lane), quarter h = tid / 128;
-//               they synthesise the U slices from the synthesis records, write
-//               the forward images and the |G|^2 slices of V, and run the
-//               epilogues (TMEM -> registers);
-//   warp 16     MMA issuer (lane 0): waits for a stage's A and B, issues its MMAs
-//               and commits their completion; it never waits on a commit except
-//               at the start of an accumulation phase;
-//   warp 17     B loader (lane 0): bulk-copies B slices (and, for V, the |G|^2 A
-//               slices) into stages as soon as the MMAs that read the stage's
-//               previous contents are done.
-// Per (tile, frequency) the slice sequence is U (2n / 16 slices of K = 16) then V
-// (n / 32 slices of K = 32).
-// Barriers: full_a[s] (16 producer-warp arrivals), full_b[s] (bulk-copy bytes),
-// empty[s] (MMAs that read stage s done), acc_full (last MMA of a phase done),
-// acc_empty (16 producer-warp arrivals: the epilogue has read the accumulator),
-// vready (16 producer-warp arrivals: the |G|^2 slices of this tile are written).
-// Every wait is bounded; a timeout raises a shared flag that ends all loops.
-// ---------------------------------------------------------------------------
+// Pipeline shapes of the tensor-core kernels.
 constexpr int NPROD = 512;                   // adjoint producer threads: four per pixel row
 constexpr int NTHR_A = NPROD + 64;           // + MMA warp + B-loader warp
 constexpr int NPROD_F = 256;                 // forward producer threads: two per A row
@@ -221,17 +202,20 @@ __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __
 
 // ---------------------------------------------------------------------------
 // Adjoint kernel: warp-specialised, NST-stage pipeline of K = 16 slices.
-//   warps 0..15 producers: pixel p = tid % 128 (TMEM lane), quarter h = tid / 128;
-//               from each U slice's A (in shared memory) they keep G for the
-//               epilogue (gs) and write the |G|^2 A slices of V; then the
-//               epilogues (TMEM -> registers);
+//   warps 0..15 producers: from each U slice's A (in shared memory, items of 8
+//               pixels x 4 K quarters per warp) they keep G for the epilogue (gs)
+//               and write the |G|^2 A slices of V; then the epilogues (TMEM ->
+//               registers; thread = pixel p = tid % 128, the TMEM lane, and quarter
+//               h = tid / 128 of the elements);
 //   warp 16     MMA issuer (lane 0): waits for a stage, issues its MMAs and
 //               commits their completion to the stage's "empty" barrier;
 //   warp 17     loader (lane 0): bulk-copies A and B of each slice (U: the A image
 //               and S; V: the |G|^2 slices and W) into a stage as soon as the
 //               stage's previous contents have been used.
-// Per (tile, frequency) the slice sequence is U (2n / 16 slices of K = 16) then V
-// (n / 32 slices of K = 32).
+// Per (tile, frequency, pass over the elements) the slice sequence is U (2n / 16
+// slices of K = 16) then, when the Hessian diagonal is wanted, V (n / 32 slices of
+// K = 32); a pass covers 256 elements of e (all of them up to 256 elements), the
+// contractions always run over all of r.
 // Barriers: full[s] (bulk-copy bytes), empty[s] (the MMAs that read stage s done,
 // plus 16 producer-warp arrivals: A read), acc_full (last MMA of a phase done),
 // acc_empty (16 producer-warp arrivals: the epilogue has read the accumulator),
