@@ -225,3 +225,32 @@ def test_breast256_whole_update_against_the_oracle(dev, breast256_update_ref, pr
     assert abs(d["alpha"] - ref.alpha) <= 1e-3 * abs(ref.alpha)
     assert abs(d["dc_norm"] - ref.dc_norm) <= 1e-3 * ref.dc_norm
     assert e <= 1e-3, e
+
+
+@pytest.mark.parametrize("prec", [rb.RB_PREC_FP32, rb.RB_PREC_BF16X3], ids=["fp32", "bf16x3"])
+def test_breast256_cg_update_against_the_oracle(dev, breast256_update_ref, prec):
+    """The CG variant (3 preconditioned iterations) at 256 elements x 256^2 pixels x 3
+    frequencies against the oracle's: dc within 1e-3 relative L2, ||dc|| within 1e-3 and
+    the residual history rho_k / rho_0 within 1 %."""
+    from oracle import update as oupd
+    cfg, inp, freqs, p_obs, _ = breast256_update_ref
+    g = ogeom.from_config(cfg)
+    ref = oupd.cg_update(g, inp.c_init, inp.alpha0, freqs, p_obs, 3, precond=True)
+    geom = rb.geometry_from_config(cfg)
+    c = _t(inp.c_init, dev)
+    dc = torch.empty_like(c)
+    hist = torch.zeros(4, dtype=torch.float64, device=dev)
+    diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+    ws = rb.workspace(geom, len(freqs), prec, dev)
+    rb.rb_cg_update(geom, c, _t(inp.alpha0, dev), freqs, torch.as_tensor(p_obs.astype(np.complex64), device=dev), ws,
+                    3, True, prec=prec, dc_out=dc, hist_out=hist, diag_out=diag)
+    torch.cuda.synchronize()
+    d = rb.decode_diag(diag)
+    e = rel_l2(dc.cpu().numpy(), ref.dc)
+    h = hist.cpu().numpy()
+    rh = np.asarray(ref.rho) / ref.rho[0]
+    print(f"breast256 CG3 prec={prec}: dc rel L2 {e:.3g}, norm {d['dc_norm']:.6g} vs {ref.dc_norm:.6g}, hist {h} vs {rh}")
+    assert d["tc_timeouts"] == 0
+    assert e <= 1e-3, e
+    assert abs(d["dc_norm"] - ref.dc_norm) <= 1e-3 * ref.dc_norm
+    assert np.allclose(h, rh, rtol=1e-2, atol=1e-4)
