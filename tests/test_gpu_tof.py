@@ -94,8 +94,8 @@ def test_tof_invert(dev, case):
 
 def test_tof_breast256_properties(dev):
     """Full size (256 elements, 256 x 256 pixels, 256 rays): three linearisations from water
-    lower the ToF misfit at every step and the sound-speed error against the phantom, and
-    two runs agree bit for bit."""
+    lower the ToF misfit at every step and the sound-speed error against the phantom, two
+    runs agree bit for bit, and the map and misfit history match the oracle's."""
     cfg = rbgen.breast256()
     inp = rbgen.make_inputs(cfg)
     g = ogeom.from_config(cfg)
@@ -118,6 +118,13 @@ def test_tof_breast256_properties(dev):
     e3 = math.sqrt(float(np.mean((c1 - inp.c_true)[sup] ** 2)))
     print(f"breast256 ToF: misfit {h1}, c error {e0:.3f} -> {e3:.3f} m/s")
     assert e3 < 0.9 * e0
+    # and against the oracle at this size (about 40 s of CPU)
+    To, lo = otof.tof_times(g, inp.c_true, inp.alpha0)
+    c_ref, hist_ref = otof.tof_invert(g, c0, inp.alpha0, To, lo, 3)
+    rms = math.sqrt(float(np.mean((c1 - c_ref)[sup] ** 2)))
+    print(f"breast256 ToF against the oracle: c RMS {rms:.3g} m/s, misfit {h1} vs {np.array(hist_ref)}")
+    assert rms <= 0.05, rms
+    assert np.allclose(h1, hist_ref, rtol=1e-3)
 
 
 def test_pipeline_tof_then_sweep_reduces_error(dev):
