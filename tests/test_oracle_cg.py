@@ -85,3 +85,15 @@ def test_cg_objective_decreases():
         phis = [oupd.cg_update(g, inp.c_init, inp.alpha0, freqs, p_obs, k, precond=pre).phi for k in (1, 2, 4)]
         assert phis[0] < 0.0
         assert phis[1] < phis[0] and phis[2] < phis[1], (pre, phis)
+
+
+def test_scalar_preconditioner_leaves_the_iterates_unchanged():
+    """Plain CG on the GPU runs with the scalar preconditioner 1/(mean H + eps) to keep A p
+    inside the FP32 range; a scalar M scales r, z and p but not the iterates x_k, so it is
+    plain CG.  (Checked on a well-conditioned system, where rounding stays small.)"""
+    A, b, _ = _normal_system(48, 20, 13)
+    for k in (1, 3, 6):
+        x_plain, h_plain = oupd.cg_solve(lambda p: A @ p, b, None, k)
+        x_scal, h_scal = oupd.cg_solve(lambda p: A @ p, b, np.full(len(b), 3.7e-9), k)
+        assert np.allclose(x_scal, x_plain, rtol=1e-9, atol=0), k
+        assert np.allclose(np.array(h_scal) / h_scal[0], np.array(h_plain) / h_plain[0], rtol=1e-9)
