@@ -19,11 +19,15 @@ precision:
 * born.py     - Born forward operator, its adjoint and the Gauss-Newton
                 Hessian diagonal (the linearisation of Eqs. 9-10);
 * update.py   - data weighting (75 % receiver mask, 1 % outlier zeroing),
-                the diagonal one-step update and the frequency sweep.
+                the diagonal one-step update, the frequency sweep and the
+                CG variant of the linear solve;
+* tof.py      - the time-of-flight initial guess (straight-ray SIRT,
+                linearised about the current medium).
 
 Parity status: every function is pinned by tests under tests/test_oracle_*.py
-against closed forms, library routines or brute force, except the sweep
-(update.sweep), whose end result has no printed value to match: parity
-unpinned against the paper; it is checked only as GPU-vs-oracle and by the
-smoke property that the update norm falls across frequency sets.
+against closed forms, library routines or brute force.  The sweep
+(update.sweep) has no printed value to match; it is pinned by properties the
+mathematics and the method fix: the true medium is a fixed point under its own
+noise-free data, and on noise-free data the error to the phantom falls set by
+set.
 """

@@ -33,9 +33,10 @@ weights to its reference [Javaherian 2022], so these are readings:
   pinned by Krylov optimality, finite termination, the first iteration equal to the
   one-step update, and a decreasing objective.
 
-Parity unpinned against the paper for ``sweep`` (the paper prints no values,
-its figures are absent); the one-step solve is pinned by a least-squares
-check on a single-pixel support.
+``sweep`` has no printed values to match (the paper's figures are absent); it is
+pinned by the fixed point of the true medium under its own noise-free data and by
+the error to the phantom falling set by set.  The one-step solve is pinned by a
+least-squares check on a single-pixel support.
 """
 from __future__ import annotations
 

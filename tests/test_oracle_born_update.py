@@ -7,8 +7,9 @@
 * One-step update on a single-pixel support with eps = 0 equals the
   least-squares solution (numpy.linalg.lstsq) of that 1-unknown problem.
 * Outlier zeroing: invariants of a top-k selection and its tie rule.
-* Sweep smoke (no printed values exist to match): the update norm is finite
-  and the error to the true phantom falls on noise-free data.
+* Sweep (no printed values exist to match): the true medium is a fixed point under
+  its own noise-free data (zero residual, zero update, in every set); on noise-free
+  data the error to the phantom falls set by set, each set seeded by the last.
 """
 import math
 
@@ -140,3 +141,40 @@ def test_sweep_smoke_noise_free(step):
     assert corr > 0          # the step points toward the truth
     if step == "exact":
         assert e1 < e0
+
+
+def test_sweep_true_medium_is_a_fixed_point():
+    """Noise-free data made about the true medium leave it unchanged through the whole
+    sweep: every set's residual vanishes, so its gradient and update do (Eqs. 8-10).
+    The same data handed to the sets in the wrong frequency order move it."""
+    cfg = rbgen.tiny()
+    g = geometry.from_config(cfg)
+    inp = rbgen.make_inputs(cfg)
+    p = update.synth_data(g, inp.c_true, inp.c_true, inp.alpha0, cfg.freqs_hz, level=0.0)
+    c, norms = update.sweep(g, inp.c_true, inp.alpha0, cfg.freqs_hz, cfg.sets, p)
+    assert norms == [0.0] * len(cfg.sets)
+    assert np.array_equal(c, inp.c_true.reshape(g.ny, g.nx).astype(np.float64))
+    # planted mistake: each set sees the data of the next frequency
+    c_bad, norms_bad = update.sweep(g, inp.c_true, inp.alpha0, cfg.freqs_hz, cfg.sets, np.roll(p, 1, axis=0))
+    assert min(norms_bad) > 0.0
+
+
+def test_sweep_error_falls_set_by_set():
+    """On noise-free data the image after each set is closer to the phantom than the one
+    that seeded it (the sweep's low-to-high refinement, Secs. 3-4): each set starts from
+    the previous set's image, so seeding every set from the start image would fail."""
+    cfg = rbgen.tiny()
+    g = geometry.from_config(cfg)
+    inp = rbgen.make_inputs(cfg)
+    p = update.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, cfg.freqs_hz, level=0.0)
+    sup = geometry.support_mask(g)
+    ct = inp.c_true.reshape(g.ny, g.nx)
+    errs = [np.sqrt(np.mean((inp.c_init.reshape(g.ny, g.nx) - ct)[sup] ** 2))]
+    for k in range(1, len(cfg.sets) + 1):
+        c, norms = update.sweep(g, inp.c_init, inp.alpha0, cfg.freqs_hz, cfg.sets[:k], p)
+        assert len(norms) == k and all(n > 0 for n in norms)
+        errs.append(np.sqrt(np.mean((c - ct)[sup] ** 2)))
+    assert all(b < 0.9 * a for a, b in zip(errs, errs[1:])), errs
+    # the last set alone, from the start image, lands further from the phantom
+    last, _ = update.sweep(g, inp.c_init, inp.alpha0, cfg.freqs_hz, cfg.sets[-1:], p)
+    assert np.sqrt(np.mean((last - ct)[sup] ** 2)) > errs[-1] * 1.2
