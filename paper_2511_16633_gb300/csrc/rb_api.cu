@@ -147,11 +147,18 @@ cudaError_t side_stream(SideStream** out) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     SideStream& ss = g_side[dev];
     if (!ss.s) {
-        if ((e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
-        if ((e = cudaEventCreateWithFlags(&ss.start, cudaEventDisableTiming)) != cudaSuccess) return e;
-        if ((e = cudaEventCreateWithFlags(&ss.keys, cudaEventDisableTiming)) != cudaSuccess) return e;
-        if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-        if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        // built aside and published whole, so a failed creation leaves no half-made entry
+        SideStream n;
+        cudaEvent_t* evs[4] = {&n.start, &n.keys, &n.fork, &n.join};
+        e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (int k = 0; k < 4; ++k)
+                if (*evs[k]) cudaEventDestroy(*evs[k]);
+            if (n.s) cudaStreamDestroy(n.s);
+            return e;
+        }
+        ss = n;
     }
     *out = &ss;
     return cudaSuccess;
