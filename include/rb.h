@@ -20,7 +20,7 @@
  *     sized by rb_workspace_size() (rb_born_forward_noalloc excepted, see
  *     there).  Calls are asynchronous and stream-ordered.  rb_hf_update and
  *     rb_cg_update run part of their work on a library stream of the current
- *     device (created with two events on the first such call and kept for the
+ *     device (created with four events on the first such call and kept for the
  *     process), forked from and joined back into the caller's stream inside the
  *     call, so their results are ordered on the caller's stream as usual.
  *   - Argument and shape errors are detected on the host before any launch
@@ -29,8 +29,10 @@
  *     reach the ring within max_steps, uncovered pixels, unlinked pairs) are
  *     counted in an rb_diag record the caller can read afterwards; no kernel
  *     traps and every device loop is bounded.
- *   - Calls are reentrant given distinct workspaces.  There is no global
- *     state besides the constant status strings.
+ *   - Calls are reentrant given distinct workspaces.  The only global state is
+ *     that library stream with its events per device (a mutex orders the host
+ *     threads that fork and join it), the fixed scratch array of
+ *     rb_born_forward_noalloc, and the constant status strings.
  */
 #ifndef RB_H
 #define RB_H
