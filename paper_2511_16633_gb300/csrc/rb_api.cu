@@ -147,11 +147,16 @@ cudaError_t side_stream(SideStream** out) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     SideStream& ss = g_side[dev];
     if (!ss.s) {
-        // built aside and published whole, so a failed creation leaves no half-made entry
+        // built aside and published whole, so a failed creation leaves no half-made entry;
+        // the first call may come inside a stream capture, so this thread's capture mode is
+        // relaxed around the creation and restored after it
         SideStream n;
         cudaEvent_t* evs[4] = {&n.start, &n.keys, &n.fork, &n.join};
+        cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+        if ((e = cudaThreadExchangeStreamCaptureMode(&mode)) != cudaSuccess) return e;
         e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
         for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+        cudaThreadExchangeStreamCaptureMode(&mode);
         if (e != cudaSuccess) {
             for (int k = 0; k < 4; ++k)
                 if (*evs[k]) cudaEventDestroy(*evs[k]);

@@ -143,9 +143,15 @@ def make_problem(cfg, device, data_prec: Optional[int] = None) -> Problem:
 
 class _Running:
     """An admitted job on its stream: the resident reconstruction, the next set, and
-    the event that marks the end of the update in flight."""
+    the event that marks the end of the work in flight.
 
-    def __init__(self, job: Job, prob: Problem, device):
+    With ``graphs`` the job's whole sweep (every set's update, in order) is captured
+    into one CUDA graph on its stream at admission and replayed once: its 20-40
+    launches per set leave the host as a single graph launch, and the library's
+    side-stream fork and join become edges inside the graph, so the sweeps of
+    different jobs share no stream.  Without it, one set is issued at a time."""
+
+    def __init__(self, job: Job, prob: Problem, device, graphs: bool = False):
         import torch
 
         from .recon import Reconstruction
@@ -154,14 +160,34 @@ class _Running:
         with torch.cuda.stream(self.stream):
             self.rec = Reconstruction(job.cfg, prob.c_init, prob.alpha0, prob.p_obs, prec=job.prec, device=device)
         self.next_set = 0
+        self.in_flight = 0
         self.event = None
+        self.graph = None
+        if graphs:
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(self.stream):
+                self.graph.capture_begin()
+                try:
+                    for j in range(len(job.cfg.sets)):
+                        self.rec.update(j, self.stream)
+                finally:
+                    self.graph.capture_end()
 
     def launch(self):
+        """Issue the next set (or, with a graph, the whole sweep); returns the number of
+        updates issued."""
         import torch
-        self.rec.update(self.next_set, self.stream)
-        self.next_set += 1
+        if self.graph is not None:
+            with torch.cuda.stream(self.stream):
+                self.graph.replay()
+            self.in_flight = len(self.job.cfg.sets) - self.next_set
+        else:
+            self.rec.update(self.next_set, self.stream)
+            self.in_flight = 1
+        self.next_set += self.in_flight
         self.event = torch.cuda.Event()
         self.event.record(self.stream)
+        return self.in_flight
 
     def finished_set(self) -> bool:
         return self.event is not None and self.event.query()
@@ -171,11 +197,13 @@ class _Running:
 
 
 def run(jobs: Sequence[Job], problems: Dict[int, Problem], budget: int, max_slots: int, device="cuda",
-        keep: Optional[Callable[[Job, object], None]] = None, realtime: bool = True) -> dict:
+        keep: Optional[Callable[[Job, object], None]] = None, realtime: bool = True, graphs: bool = False) -> dict:
     """Run the jobs under the scheduler; arrival times are honoured on the host clock
     (``realtime``) or ignored (every job available at once).  ``keep(job, c)`` receives
     each finished job's sound-speed map (a device tensor) before its buffers go.
-    Returns per-job times and the totals."""
+    ``graphs``: each job's sweep is captured into one CUDA graph at admission and
+    replayed (the capture counts in the job's latency).  Returns per-job times and the
+    totals."""
     import torch
     sched = Scheduler([dataclasses.replace(j, arrival=j.arrival if realtime else 0.0) for j in jobs], budget,
                       max_slots)
@@ -186,7 +214,7 @@ def run(jobs: Sequence[Job], problems: Dict[int, Problem], budget: int, max_slot
     while not sched.idle():
         now = time.perf_counter() - t0
         for j in sched.admit(now):
-            r = _Running(j, problems[j.jid], device)
+            r = _Running(j, problems[j.jid], device, graphs)
             running[j.jid] = r
             r.launch()
         peak_used = max(peak_used, sched.used)
@@ -196,8 +224,8 @@ def run(jobs: Sequence[Job], problems: Dict[int, Problem], budget: int, max_slot
             if not r.finished_set():
                 continue
             progressed = True
-            r.job.updates += 1
-            n_updates += 1
+            r.job.updates += r.in_flight
+            n_updates += r.in_flight
             if r.more():
                 r.launch()
             else:
@@ -214,7 +242,7 @@ def run(jobs: Sequence[Job], problems: Dict[int, Problem], budget: int, max_slot
     span = time.perf_counter() - t0
     done = [j for j in sched.started if j.done is not None]
     lat = np.array([j.done - j.arrival for j in done]) if done else np.zeros(1)
-    return {"updates": n_updates, "seconds": span, "updates_per_s": n_updates / span if span > 0 else 0.0,
+    return {"updates": n_updates, "seconds": span, "graphs": bool(graphs), "updates_per_s": n_updates / span if span > 0 else 0.0,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "rejected": [j.cfg.name for j in sched.rejected], "peak_footprint_gb": peak_used / 1e9,
             "jobs": [{"name": j.cfg.name, "prec": "bf16x3" if j.prec == rb.RB_PREC_BF16X3 else "fp32",
@@ -238,6 +266,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=0.0, help="0: free device memory minus 8 GB")
     ap.add_argument("--prec", choices=["mixed", "plain", "both"], default="both")
     ap.add_argument("--seed", type=int, default=20251116 + 4)
+    ap.add_argument("--graphs", choices=["off", "on", "both"], default="off",
+                    help="capture each request's sweep into one CUDA graph (both: measure each way)")
     args = ap.parse_args()
     dev = torch.device("cuda:0")
     rings = tuple(int(x) for x in args.rings.split(","))
@@ -257,11 +287,12 @@ def main():
     out = {"mode": args.mode, "n": args.n, "budget_gb": budget / 1e9, "slots": args.slots,
            "workload": [c.name for _, c in items]}
     for pol in (["mixed", "plain"] if args.prec == "both" else [args.prec]):
-        jobs = [Job(k, cfg, t, precision_for(cfg, pol), footprint_bytes(cfg, precision_for(cfg, pol)))
-                for k, (t, cfg) in enumerate(items)]
-        res = run(jobs, problems, budget, args.slots, dev, realtime=(args.mode == "serve"))
-        out[pol] = res
-        torch.cuda.empty_cache()
+        for gr in ([False, True] if args.graphs == "both" else [args.graphs == "on"]):
+            jobs = [Job(k, cfg, t, precision_for(cfg, pol), footprint_bytes(cfg, precision_for(cfg, pol)))
+                    for k, (t, cfg) in enumerate(items)]
+            res = run(jobs, problems, budget, args.slots, dev, realtime=(args.mode == "serve"), graphs=gr)
+            out[pol + ("_graphs" if gr and args.graphs == "both" else "")] = res
+            torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
 
 

@@ -61,3 +61,51 @@ def test_update_replayed_from_a_cuda_graph(dev, prec, cg):
     assert torch.equal(c1, c2)
     assert torch.equal(dc1, dc2)
     assert rb.decode_diag(d1) == rb.decode_diag(d2)
+
+
+_FIRST_CALL_IN_CAPTURE = r"""
+import sys
+import torch
+import rbgen
+from paper_2511_16633_gb300 import rb, serve
+from paper_2511_16633_gb300.recon import Reconstruction
+dev = torch.device("cuda:0")
+rb.load()
+cfg = rbgen.tiny()
+prob = serve.make_problem(cfg, dev)
+s = torch.cuda.Stream()
+with torch.cuda.stream(s):
+    rec = Reconstruction(cfg, prob.c_init, prob.alpha0, prob.p_obs, prec=rb.RB_PREC_BF16X3, device=dev)
+    c0 = rec.c.clone()
+    g = torch.cuda.CUDAGraph()
+    g.capture_begin()
+    for j in range(len(cfg.sets)):
+        rec.update(j, s)
+    g.capture_end()
+    g.replay()
+s.synchronize()
+c_graph = rec.c.clone()
+with torch.cuda.stream(s):
+    rec.c.copy_(c0)
+    for j in range(len(cfg.sets)):
+        rec.update(j, s)
+s.synchronize()
+assert torch.equal(c_graph, rec.c)
+assert not torch.equal(c_graph, c0)
+print("first update call inside a capture: ok")
+"""
+
+
+def test_first_update_call_inside_a_capture(dev):
+    """A fresh process whose first update call is made inside a CUDA-graph capture (the
+    library then creates its side stream during the capture): the captured sweep of all
+    sets replays to the eager sweep's result."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL_IN_CAPTURE], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    assert "ok" in r.stdout

@@ -28,12 +28,13 @@ def _cfgs():
             rbgen.tiny(n_elem=512, nx=64, ny=64, n_rays=64, seed=20251116 + 14)]
 
 
-def _run(cfgs, problems, dev, policy, budget, slots, arrivals=None, realtime=False):
+def _run(cfgs, problems, dev, policy, budget, slots, arrivals=None, realtime=False, graphs=False):
     jobs = [serve.Job(k, c, 0.0 if arrivals is None else arrivals[k], serve.precision_for(c, policy),
                       serve.footprint_bytes(c, serve.precision_for(c, policy))) for k, c in enumerate(cfgs)]
     out = {}
     res = serve.run(jobs, {j.jid: problems[j.jid] for j in jobs}, budget, slots, dev,
-                    keep=lambda job, c: out.__setitem__(job.jid, c.cpu().numpy().copy()), realtime=realtime)
+                    keep=lambda job, c: out.__setitem__(job.jid, c.cpu().numpy().copy()), realtime=realtime,
+                    graphs=graphs)
     return out, res
 
 
@@ -64,3 +65,16 @@ def test_poisson_stream_under_a_tight_budget(dev):
     assert res["p99_s"] >= res["p50_s"] > 0
     for j in res["jobs"]:
         assert j["admitted_s"] >= j["arrival_s"] and j["done_s"] > j["admitted_s"]
+
+
+def test_graph_mode_gives_the_eager_results(dev):
+    """Each job's sweep captured into one CUDA graph and replayed, all jobs at once: the
+    same maps, bit for bit, as the eager runner's."""
+    cfgs = _cfgs()
+    problems = {k: serve.make_problem(c, dev) for k, c in enumerate(cfgs)}
+    eager, _ = _run(cfgs, problems, dev, "mixed", budget=1 << 40, slots=len(cfgs))
+    graphed, res = _run(cfgs, problems, dev, "mixed", budget=1 << 40, slots=len(cfgs), graphs=True)
+    assert res["graphs"] and res["updates"] == sum(len(c.sets) for c in cfgs)
+    assert sorted(j["updates"] for j in res["jobs"]) == sorted(len(c.sets) for c in cfgs)
+    for k in range(len(cfgs)):
+        assert np.array_equal(graphed[k], eager[k]), k
