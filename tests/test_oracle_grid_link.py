@@ -9,6 +9,9 @@
   fan geometry is mirror-symmetric), the linked traveltime equal to the chord
   time, and in a heterogeneous medium a reciprocity error that falls as the
   fans are refined.
+* Ray data in water: the linked p[e,r] against SciPy's exact 2-D Green's function
+  (i/4) H0^(1)(k r) over the chord, within its leading asymptotic error, and the
+  uniform-absorption decay along the chord.
 * The receiver mask keeps the "opposite 75 %" of the ring the paper uses
   (Sec. 4.1), with the paper's element counts read from tests/golden.
 """
@@ -17,6 +20,7 @@ import math
 import os
 
 import numpy as np
+import pytest
 
 import rbgen
 from oracle import geometry, grid, link, rays
@@ -151,3 +155,34 @@ def test_receiver_mask_matches_paper_fraction():
         assert np.all(frac == frac[0])
         assert abs(frac[0] - facts[key]["receiver_fraction_kept"]) < 0.01
         assert np.array_equal(m, m.T)
+
+
+@pytest.mark.parametrize("f", [0.3e6, 0.8e6])
+def test_ray_data_in_water_is_the_hankel_green_function(f):
+    """The linked ray data between two elements in homogeneous water must approach the
+    exact 2-D Green's function (i/4) H0^(1)(k r) over the chord (SciPy's Hankel routine),
+    within the leading asymptotic error 1/(8 k r); with uniform absorption its modulus
+    falls by exp(-K_a alpha0 f^y r) along the chord."""
+    from scipy.special import hankel1
+
+    from oracle import green
+    cfg = rbgen.tiny(n_rays=256)
+    g = geometry.from_config(cfg)
+    c = np.full((g.ny, g.nx), g.c_ref)
+    mask = geometry.receiver_mask(g)
+    xe, ye = geometry.element_positions(g)
+    chord = np.hypot(xe[:, None] - xe[None, :], ye[:, None] - ye[None, :])
+    k = 2 * math.pi * f / g.c_ref
+    out = {}
+    for a0 in (0.0, 0.5):
+        al = np.full((g.ny, g.nx), a0)
+        E, nv, lost = rays.trace_endpoints(g, c, al)
+        lk = link.link(g, E, lost, c)
+        assert lk.linked[mask].all()
+        out[a0] = link.ray_data(g, lk, f)
+    ex = 0.25j * hankel1(0, k * chord[mask])
+    rel = np.abs(out[0.0][mask] / ex - 1.0)
+    assert np.all(rel <= 1.0 / (8 * k * chord[mask]) + 2e-3), float(np.max(rel))
+    ratio = np.abs(out[0.5][mask]) / np.abs(out[0.0][mask])
+    expect = np.exp(-green.K_A * 0.5 * (f / 1e6) ** g.power_y * chord[mask])
+    assert np.max(np.abs(ratio / expect - 1.0)) < 2e-3
