@@ -142,3 +142,13 @@ def test_status_strings(lib):
     for code in range(7):
         assert len(rb.status_string(code)) > 0
     assert rb.status_string(99) == "unknown status"
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the compiled library the binding raises instead of computing
+    anything another way."""
+    from paper_2511_16633_gb300 import _build, rb
+    monkeypatch.setattr(rb, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "librb.so"))
+    with pytest.raises(RuntimeError, match="librb.so not found"):
+        rb.load(build_if_missing=False)
