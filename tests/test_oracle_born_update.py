@@ -6,8 +6,9 @@
   gradient equals central finite differences of 1/2 ||W^(1/2)(B m + R)||^2.
 * The Born data of a weak smooth perturbation equal the first-order change of the
   linked ray data (central difference of p(c) at c0 +- dc) to 2 %.
-* One-step update on a single-pixel support with eps = 0 equals the
-  least-squares solution (numpy.linalg.lstsq) of that 1-unknown problem.
+* One-step update on a support of a few pixels equals, pixel by pixel, the
+  least-squares solution (numpy.linalg.lstsq) of that 1-unknown problem, damped by
+  H_j / (H_j + eps) with eps from the mean of H over the support (eps_rel 0 and 0.5).
 * Outlier zeroing: invariants of a top-k selection and its tie rule.
 * Sweep (no printed values exist to match): the true medium is a fixed point under
   its own noise-free data (zero residual, zero update, in every set); on noise-free
@@ -80,19 +81,26 @@ def test_brute_force_columns_hessian_and_gradient():
         assert abs(fd - gr[j]) <= 1e-7 * (abs(gr[j]) + 1e-30) + 1e-9 * np.max(np.abs(gr))
 
 
-def test_one_step_single_pixel_equals_least_squares():
+@pytest.mark.parametrize("eps_rel", [0.0, 0.5])
+def test_one_step_single_pixel_equals_least_squares(eps_rel):
+    """On a support of a few pixels the diagonal step of each pixel is that pixel's own
+    least-squares solution (numpy.linalg.lstsq over its brute-force Born column), damped
+    by the solution-space weight's eps: dm_j = dm_ls_j H_j / (H_j + eps), with
+    H_j = ||W^(1/2) b_j||^2 from the same column and eps = eps_rel x the mean of H over
+    the support pixels (not over the whole grid, where H is zero outside the support)."""
     cfg = rbgen.tiny()
     # margin so large that the support holds the 4 central pixels only
     g = geometry.from_config(cfg, support_margin=cfg.ring_radius - 1.2 * cfg.h)
     sup = geometry.support_mask(g).ravel()
-    assert 1 <= sup.sum() <= 4
+    assert 2 <= sup.sum() <= 4
     inp = rbgen.make_inputs(cfg)
     rng = np.random.default_rng(5)
     fr = [0.3e6, 0.35e6]
     p_obs = 0.01 * (rng.standard_normal((2, g.n_elem, g.n_elem)) + 1j * rng.standard_normal((2, g.n_elem, g.n_elem)))
-    r = update.hf_update(g, inp.c_init, inp.alpha0, fr, p_obs, outlier_frac=0.0, eps_rel=0.0, step="diag")
+    r = update.hf_update(g, inp.c_init, inp.alpha0, fr, p_obs, outlier_frac=0.0, eps_rel=eps_rel, step="diag")
     # least squares for each support pixel alone: min_dm sum_w ||W^(1/2) (R_w + b_w dm)||^2
     tabs = grid.grid(g, inp.c_init, inp.alpha0)
+    dm_ls, hj = {}, {}
     for j in np.flatnonzero(sup):
         rows, rhs = [], []
         for k, f in enumerate(fr):
@@ -103,11 +111,15 @@ def test_one_step_single_pixel_equals_least_squares():
             rhs += [-(sw * r.R[k]).real.ravel(), -(sw * r.R[k]).imag.ravel()]
         A = np.concatenate(rows)[:, None]
         y = np.concatenate(rhs)
-        dm_ls = np.linalg.lstsq(A, y, rcond=None)[0][0]
+        dm_ls[j] = np.linalg.lstsq(A, y, rcond=None)[0][0]
+        hj[j] = float(A[:, 0] @ A[:, 0])
+    eps = eps_rel * np.mean(list(hj.values()))
+    for j in dm_ls:
         dm = r.dc.ravel()[j] * (-2 * g.h * g.h) / np.asarray(inp.c_init, float).ravel()[j] ** 3
         # with several support pixels the diagonal step for pixel j is still that pixel's
         # own least-squares solution (off-diagonal couplings are ignored by construction)
-        assert abs(dm - dm_ls) <= 1e-10 * abs(dm_ls)
+        expect = dm_ls[j] * hj[j] / (hj[j] + eps)
+        assert abs(dm - expect) <= 1e-10 * abs(expect)
 
 
 def test_outlier_selection_invariants_and_ties():
