@@ -19,10 +19,12 @@
  *     synchronises the device: all scratch comes from the caller's workspace,
  *     sized by rb_workspace_size() (rb_born_forward_noalloc excepted, see
  *     there).  Calls are asynchronous and stream-ordered.  rb_hf_update and
- *     rb_cg_update run part of their work on a library stream of the current
- *     device (created with four events on the first such call and kept for the
- *     process), forked from and joined back into the caller's stream inside the
- *     call, so their results are ordered on the caller's stream as usual.
+ *     rb_cg_update run part of their work on a library stream kept for the
+ *     caller's stream on the current device (created with four events on the
+ *     first such call from that stream and kept for the process; past 256 such
+ *     streams callers share them), forked from and joined back into the
+ *     caller's stream inside the call, so their results are ordered on the
+ *     caller's stream as usual.
  *   - Argument and shape errors are detected on the host before any launch
  *     and returned synchronously; a failed launch returns RB_ERR_CUDA.
  *     Data-dependent conditions found on the device (a ray that does not
@@ -30,8 +32,8 @@
  *     counted in an rb_diag record the caller can read afterwards; no kernel
  *     traps and every device loop is bounded.
  *   - Calls are reentrant given distinct workspaces.  The only global state is
- *     that library stream with its events per device (a mutex orders the host
- *     threads that fork and join it), the fixed scratch array of
+ *     those library streams with their events (a mutex orders the host
+ *     threads that fork and join them), the fixed scratch array of
  *     rb_born_forward_noalloc, and the constant status strings.
  */
 #ifndef RB_H
@@ -207,6 +209,22 @@ rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* al
 rb_status rb_ray_forward(const rb_geometry* geom, const float* c, const rb_ray_end* ends,
                          const double* freqs_hz, int32_t n_freq, float* p_out, uint8_t* linked_out,
                          rb_stream stream);
+
+/*
+ * Residuals and data-space weights of one frequency set (Eq. 8 and Sec. 4.1),
+ * the data side of rb_hf_update on its own: rays through c[ny*nx], ray-model
+ * data by ray linking, R = p_ray - p_obs, and the weights W: 1 for receivers
+ * on the opposite ~75 % of the ring (circular index distance >= ceil(n_elem/8))
+ * that a ray interval links, then the floor(outlier_frac * kept) kept entries
+ * of largest |R| over the whole set zeroed (ties to the smallest flat index
+ * (w, e, r)).  p_obs, resid_out [n_freq][n_elem][n_elem] complex;
+ * w_out [n_freq][n_elem][n_elem] bytes (0 or 1); freqs_hz host array, n_freq
+ * in 1..RB_MAX_FREQ; outlier_frac in [0, 1).  Workspace as
+ * rb_workspace_size(geom, n_freq, RB_PREC_FP32).
+ */
+rb_status rb_data_weights(const rb_geometry* geom, const float* c, const float* alpha0, const double* freqs_hz,
+                          int32_t n_freq, const float* p_obs, double outlier_frac, float* resid_out, uint8_t* w_out,
+                          void* ws, size_t ws_bytes, rb_stream stream);
 
 /*
  * Born forward operator (the linearisation of Eq. 10 in Born form):

@@ -25,7 +25,10 @@ precision:
                 linearised about the current medium).
 
 Parity status: every function is pinned by tests under tests/test_oracle_*.py
-against closed forms, library routines or brute force.  The sweep
+against closed forms, library routines or brute force.  The KMAH phase shift of
+green.py and the KMAH index of the rays and the gridding are pinned past a caustic
+against an independent finite-difference solution of the Helmholtz equation
+(tests/test_oracle_kmah.py).  The sweep
 (update.sweep) has no printed value to match; it is pinned by properties the
 mathematics and the method fix: the true medium is a fixed point under its own
 noise-free data, and on noise-free data the error to the phantom falls set by

@@ -129,43 +129,62 @@ int tc_ctas() {
         if ((x) != cudaSuccess) return RB_ERR_CUDA; \
     } while (0)
 
-// A side stream per device for the work of an update that does not wait for the
-// gridding (linking, residuals, data weights, B images), forked after the ray trace and
-// joined before the adjoint.  Created on first use and kept for the process; the mutex
+// A side stream per (device, caller stream) for the work of an update that does not wait
+// for the gridding (linking, residuals, data weights, B images), forked after the ray
+// trace and joined before the adjoint, so that updates issued on different streams (the
+// requests of a server) do not queue behind one another's side work.  Created on first
+// use and kept for the process (at most kMaxSide; beyond that, callers share the entries
+// of their device, which stays correct and only serialises their side work); the mutex
 // keeps each call's fork and join events together when several host threads call.
 struct SideStream {
+    int dev = -1;
+    cudaStream_t caller = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t start = nullptr, keys = nullptr, fork = nullptr, join = nullptr;
 };
+constexpr int kMaxSide = 256;
 std::mutex g_side_mutex;
-SideStream g_side[64];
+SideStream g_side[kMaxSide];
+int g_side_n = 0;
 
-cudaError_t side_stream(SideStream** out) {
+cudaError_t side_stream(cudaStream_t caller, SideStream** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    SideStream& ss = g_side[dev];
-    if (!ss.s) {
-        // built aside and published whole, so a failed creation leaves no half-made entry;
-        // the first call may come inside a stream capture, so this thread's capture mode is
-        // relaxed around the creation and restored after it
-        SideStream n;
-        cudaEvent_t* evs[4] = {&n.start, &n.keys, &n.fork, &n.join};
-        cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
-        if ((e = cudaThreadExchangeStreamCaptureMode(&mode)) != cudaSuccess) return e;
-        e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
-        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
-        cudaThreadExchangeStreamCaptureMode(&mode);
-        if (e != cudaSuccess) {
-            for (int k = 0; k < 4; ++k)
-                if (*evs[k]) cudaEventDestroy(*evs[k]);
-            if (n.s) cudaStreamDestroy(n.s);
-            return e;
+    int any = -1;
+    for (int k = 0; k < g_side_n; ++k) {
+        if (g_side[k].dev != dev) continue;
+        if (g_side[k].caller == caller) {
+            *out = &g_side[k];
+            return cudaSuccess;
         }
-        ss = n;
+        if (any < 0) any = k;
     }
-    *out = &ss;
+    if (g_side_n == kMaxSide) {
+        if (any < 0) return cudaErrorInvalidDevice;
+        *out = &g_side[any];   // table full: share an entry of this device
+        return cudaSuccess;
+    }
+    // built aside and published whole, so a failed creation leaves no half-made entry;
+    // the first call may come inside a stream capture, so this thread's capture mode is
+    // relaxed around the creation and restored after it
+    SideStream n;
+    n.dev = dev;
+    n.caller = caller;
+    cudaEvent_t* evs[4] = {&n.start, &n.keys, &n.fork, &n.join};
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    if ((e = cudaThreadExchangeStreamCaptureMode(&mode)) != cudaSuccess) return e;
+    e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    if (e != cudaSuccess) {
+        for (int k = 0; k < 4; ++k)
+            if (*evs[k]) cudaEventDestroy(*evs[k]);
+        if (n.s) cudaStreamDestroy(n.s);
+        return e;
+    }
+    g_side[g_side_n] = n;
+    *out = &g_side[g_side_n++];
     return cudaSuccess;
 }
 
@@ -211,7 +230,7 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     const bool tc = prec == RB_PREC_BF16X3;
     std::lock_guard<std::mutex> lock(g_side_mutex);
     SideStream* ss = nullptr;
-    RB_CU(side_stream(&ss));
+    RB_CU(side_stream(s, &ss));
     const cudaStream_t s2 = ss->s;
     const Marks mark2{mark.ev, s2};   // stage events of the side branch
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4 + DBL_N * 8, s));
@@ -225,10 +244,10 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     RB_CU(launch_fields(G, c, alpha0, cells, s));
     RB_CU(mark(RB_STAGE_FIELDS, 1));
     RB_CU(mark(RB_STAGE_TRACE_GRID, 0));
-    // the mixed path reads only the synthesis records, the plain path only the tables
-    float4* srec = tc ? W.at<float4>(W.L.srec) : nullptr;
+    // the plain path reads the tables; on the mixed path the resolve pass writes the
+    // operand images of the set itself
     RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), tc ? nullptr : tables, W.at<void>(W.L.verts), c,
-                       srec, cnt, s, ss->fork, ss->keys));
+                       nullptr, cnt, s, ss->fork, ss->keys, tc ? &F : nullptr, tc ? W.at<void>(W.L.aimg) : nullptr));
     // side branch 2 (needs the end records only): links, residuals, weights, B images
     RB_CU(cudaStreamWaitEvent(s2, ss->fork, 0));
     RB_CU(mark2(RB_STAGE_LINK, 0));
@@ -243,10 +262,10 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     }
     RB_CU(mark2(RB_STAGE_LINK, 1));
     RB_CU(cudaEventRecord(ss->join, s2));
-    // main branch: rasteriser and resolve (in launch_trace), the operand images
+    // main branch: rasteriser and resolve (in launch_trace; on the mixed path with the
+    // operand images, so the images stage is empty)
     RB_CU(mark(RB_STAGE_TRACE_GRID, 1));
     RB_CU(mark(RB_STAGE_IMAGES, 0));
-    if (tc) RB_CU(launch_synth_images(G, srec, F, W.at<void>(W.L.aimg), s));
     RB_CU(mark(RB_STAGE_IMAGES, 1));
     RB_CU(cudaStreamWaitEvent(s, ss->join, 0));
     RB_CU(mark(RB_STAGE_ADJOINT, 0));
@@ -378,6 +397,36 @@ rb_status rb_ray_forward(const rb_geometry* geom, const float* c, const rb_ray_e
     if (!make_freqs(geom, freqs_hz, n_freq, &F)) return RB_ERR_ARG;
     const GeoDev G = make_geo(geom, nullptr);
     RB_CU(launch_link(G, c, ends, F, (float2*)p_out, linked_out, (cudaStream_t)stream));
+    return RB_OK;
+}
+
+rb_status rb_data_weights(const rb_geometry* geom, const float* c, const float* alpha0, const double* freqs_hz,
+                          int32_t n_freq, const float* p_obs, double outlier_frac, float* resid_out, uint8_t* w_out,
+                          void* ws, size_t ws_bytes, rb_stream stream) {
+    if (!geom || !c || !alpha0 || !p_obs || !resid_out || !w_out) return RB_ERR_ARG;
+    if (!geom_ok(geom)) return RB_ERR_SHAPE;
+    if (!(outlier_frac >= 0.0 && outlier_frac < 1.0)) return RB_ERR_ARG;
+    FreqSet F;
+    if (!make_freqs(geom, freqs_hz, n_freq, &F)) return RB_ERR_ARG;
+    Ws W;
+    rb_status st = check_ws(geom, n_freq, RB_PREC_FP32, ws, ws_bytes, &W);
+    if (st != RB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    float4* exy = W.at<float4>(W.L.elem_xy);
+    uint32_t* cnt = W.at<uint32_t>(W.L.counters);
+    const GeoDev G = make_geo(geom, exy);
+    rb_ray_end* ends = W.at<rb_ray_end>(W.L.ends);
+    uint8_t* linked = W.at<uint8_t>(W.L.linked);
+    float2* R = (float2*)resid_out;
+    RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
+    RB_CU(launch_elem_positions(G, exy, s));
+    RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), ends, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cnt, s));
+    RB_CU(launch_link(G, c, ends, F, R, linked, s));
+    RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, W.at<uint64_t>(W.L.keys), cnt,
+                               W.at<void>(W.L.sel), s));
+    RB_CU(launch_outlier_select(n_freq * G.n_elem * G.n_elem, outlier_frac, W.at<uint64_t>(W.L.keys), cnt, w_out,
+                                W.at<void>(W.L.sel), s));
     return RB_OK;
 }
 

@@ -20,7 +20,7 @@
 
 namespace {
 
-constexpr int TP = 128;                 // pixels per tile = MMA M
+constexpr int TP = RB_TP;               // pixels per tile = MMA M
 constexpr uint32_t kMaxTries = 1u << 22; // mbarrier polls before giving up (each poll suspends briefly)
 
 // ---------------------------------------------------------------------------
@@ -153,16 +153,15 @@ __device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const 
 }
 
 // ---------------------------------------------------------------------------
-// Operand image of one frequency set, synthesised once at full occupancy from the
-// synthesis records.  Per frequency, tile of 128 pixels and plane (bf16 hi, lo):
-// n / 4 rows, row rc holding r' = 8 rc .. 8 rc + 7 (r' = 2r + {0: Re G_r, 1: -Im G_r})
-// for the 128 pixels as 16 core matrices of 8 pixels x 16 bytes:
-//   element (rc, x, r') at rc * 1024 + (x / 8) * 64 + (x % 8) * 8 + r' % 8.
-// The adjoint reads it K-major (a K = 16 slice is two rows: one 4 KB bulk copy per
-// plane), the forward MN-major (a 16-pixel slice of every row is one 2-D TMA box).
-// CTA (tile, element block of 16): thread (p, half) synthesises elements
-// 16 eb + 8 half + k (k < 8) at pixel p for every frequency and writes rows
-// 4 eb + 2 half + {0, 1} of the pixel's core row (coalesced: 128 threads, 2 KB).
+// Operand image of one frequency set (layout: aimg_put4 in rb_internal.cuh),
+// synthesised once at full occupancy from the synthesis records; the update itself
+// writes it from the resolve pass (k_resolve_images, rb_trace.cu), this kernel serves
+// the single-operator entry points.  The adjoint reads it K-major (a K = 16 slice is
+// two rows: one 4 KB bulk copy per plane), the forward MN-major (a 16-pixel slice of
+// every row is one 2-D TMA box).  CTA (tile, element block of 16): thread (p, half)
+// synthesises elements 16 eb + 8 half + k (k < 8) at pixel p for every frequency and
+// writes rows 4 eb + 2 half + {0, 1} of the pixel's core row (coalesced: 128 threads,
+// 2 KB).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __restrict__ srec, FreqSet F,
                                                       __nv_bfloat16* __restrict__ aimg, size_t a_stride) {
@@ -177,25 +176,15 @@ __global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         sr[k] = valid ? __ldg(srec + (size_t)(e0 + k) * G.npix + px) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const size_t pix_off = (size_t)(p >> 3) * 64 + (size_t)(p & 7) * 8;
     for (int fw = 0; fw < F.n; ++fw) {
         const FreqC& fc = F.f[fw];
         __nv_bfloat16* plane = aimg + (size_t)fw * a_stride + (size_t)tile * 2 * rcn * 1024;
 #pragma unroll
         for (int kg = 0; kg < 2; ++kg) {
-            uint32_t ah[4], al[4];   // 8 r' (4 elements) of this pixel, hi / lo
+            float2 g[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 g = green_srec(sr[4 * kg + q], fc);
-                __nv_bfloat16 h0, l0, h1, l1;
-                tc::split_bf16(g.x, h0, l0);
-                tc::split_bf16(-g.y, h1, l1);
-                ah[q] = pack2(h0, h1);
-                al[q] = pack2(l0, l1);
-            }
-            const int rc = 4 * eb + 2 * half + kg;
-            *(uint4*)(plane + (size_t)rc * 1024 + pix_off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
-            *(uint4*)(plane + (size_t)(rcn + rc) * 1024 + pix_off) = make_uint4(al[0], al[1], al[2], al[3]);
+            for (int q = 0; q < 4; ++q) g[q] = green_srec(sr[4 * kg + q], fc);
+            aimg_put4(plane, rcn, 4 * eb + 2 * half + kg, p, g);
         }
     }
 }

@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of librb.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -179,6 +180,43 @@ __device__ __forceinline__ float2 green_srec(float4 sr, const FreqC& F) {
     return make_float2(amp * re, amp * im);
 }
 
+// ---------------------------------------------------------------------------
+// Operand image of the tensor-core contractions, one frequency: per tile of
+// RB_TP pixels and plane (bf16 hi, lo), 2n / 8 rows of 1024 bf16, row rc holding
+// r' = 8 rc .. 8 rc + 7 (r' = 2r + {0: Re G_r, 1: -Im G_r}) of the tile's pixels as
+// 16 core matrices of 8 pixels x 16 bytes:
+//   element (rc, x, r') at rc * 1024 + (x / 8) * 64 + (x % 8) * 8 + r' % 8.
+// The adjoint reads it K-major, the forward MN-major (rb_born_tc.cu).
+// ---------------------------------------------------------------------------
+constexpr int RB_TP = 128;
+
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi): x to ~2^-17 relative.
+__device__ __forceinline__ void bf16_split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t bf16_pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Pixel p's 16 bytes of image row rc (elements 4 rc .. 4 rc + 3) in both planes of a
+// tile (tile_img: the tile's hi plane; its lo plane follows after rcn rows).
+__device__ __forceinline__ void aimg_put4(__nv_bfloat16* tile_img, int rcn, int rc, int p, const float2 g[4]) {
+    uint32_t ah[4], al[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        bf16_split(g[q].x, h0, l0);
+        bf16_split(-g[q].y, h1, l1);
+        ah[q] = bf16_pack2(h0, h1);
+        al[q] = bf16_pack2(l0, l1);
+    }
+    const size_t off = (size_t)(p >> 3) * 64 + (size_t)(p & 7) * 8;
+    *(uint4*)(tile_img + (size_t)rc * 1024 + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+    *(uint4*)(tile_img + (size_t)(rcn + rc) * 1024 + off) = make_uint4(al[0], al[1], al[2], al[3]);
+}
+
 // Element t's position as float pairs.
 __device__ __forceinline__ void elem_pos(const GeoDev& G, int t, DF& ex, DF& ey) {
     const float4 e = G.elem_xy[t];
@@ -269,9 +307,12 @@ cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, 
 // rasteriser and the resolve pass.  keys_ready (nullable): the caller resets the keys
 // (all ones) on another stream and records this event; s waits for it before the
 // rasteriser instead of resetting them itself
+// images (nullable, with F): the mixed path's operand images of every frequency of F,
+// written by the resolve pass itself (tables and srec then unused).
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
-                         cudaStream_t s, cudaEvent_t traced = nullptr, cudaEvent_t keys_ready = nullptr);
+                         cudaStream_t s, cudaEvent_t traced = nullptr, cudaEvent_t keys_ready = nullptr,
+                         const FreqSet* F = nullptr, void* images = nullptr);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);

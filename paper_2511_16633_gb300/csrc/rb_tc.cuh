@@ -104,6 +104,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
+// `count` arrivals at once (on behalf of threads that do not take part in this use).
+__device__ __forceinline__ void mbar_arrive_cnt(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
 // Barrier over the first `nthreads` threads of the CTA (a multiple of 32) on hardware barrier `id`.
 __device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");

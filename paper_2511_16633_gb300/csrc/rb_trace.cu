@@ -590,18 +590,56 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
     }
 }
 
-// Completes every hit record: from the winning triangle id in the tag, its vertices
-// and the pixel, the barycentric weights (bit-identical to the rasteriser's), then
-// Q, L and the KMAH index of the heaviest vertex.  Holes stay all ones.  Thread =
-// pixel (its coordinates and support test computed once), looping over the
-// elements t = blockIdx.y, blockIdx.y + gridDim.y, ...; consecutive threads take
-// consecutive pixels, so every key load and record store is coalesced.
+// The table record of entry (t, pix) from its first-arrival key: from the winning
+// triangle id in the tag, its vertices and the pixel (X, Y), the barycentric weights
+// (bit-identical to the rasteriser's), then Q, L and the KMAH index of the heaviest
+// vertex.  Returns false for a hole (no triangle covered the pixel).
+__device__ __forceinline__ bool resolve_entry(const GeoDev& G, const Vtx* __restrict__ verts,
+                                              const rb_ray_end* __restrict__ ends, unsigned long long key, int t,
+                                              const DF& X, const DF& Y, uint32_t kq_magic, rb_cell& rec) {
+    const uint32_t KQ = (uint32_t)(G.max_steps + 1);
+    const uint2 kv = make_uint2((uint32_t)key, (uint32_t)(key >> 32));   // {tag, tkey}
+    if (kv.y == RB_HOLE) return false;
+    const uint32_t id = kv.x >> 8;
+    const int half = (int)(id & 1u);
+    uint32_t qi, qk1;
+    udivmod(id >> 1, KQ, kq_magic, qi, qk1);
+    // ids come from the rasteriser (i + 1 < n_rays, 1 <= k1 <= max_steps); clamped all the same
+    const int i = min((int)qi, G.n_rays - 2), k1 = min((int)qk1 + 1, G.max_steps);
+    const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+    // the winning triangle only: T0 = (A0, B0, B1), T1 = (A0, B1, A1); edge vectors,
+    // doubled area (rounded reciprocal) and weights as in bary
+    const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
+    const Vtx Vb = get_vtx(half ? verts + vidx(G, t, min(k1, lb), i + 1) : verts + vidx(G, t, min(k1 - 1, lb), i + 1));
+    const Vtx Vc = get_vtx(half ? verts + vidx(G, t, min(k1, la), i) : verts + vidx(G, t, min(k1, lb), i + 1));
+    const float ux = rel(Vb.xh, Vb.xl, A0.xh, A0.xl), uy = rel(Vb.yh, Vb.yl, A0.yh, A0.yl);
+    const float vx = rel(Vc.xh, Vc.xl, A0.xh, A0.xl), vy = rel(Vc.yh, Vc.yl, A0.yh, A0.yl);
+    const float ar = __fsub_rn(__fmul_rn(ux, vy), __fmul_rn(uy, vx));
+    const float inv = ar != 0.f ? __frcp_rn(ar) : 0.f;
+    const float dx = rel(X.hi, X.lo, A0.xh, A0.xl), dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
+    float wa, wb, wc;
+    bary(ux, uy, vx, vy, inv, dx, dy, wa, wb, wc);
+    int kap = A0.k;
+    float wbest = wa;
+    if (wb > wbest) { kap = Vb.k; wbest = wb; }
+    if (wc > wbest) kap = Vc.k;
+    rec.tag = (id << 8) | (uint32_t)min(kap, 255);
+    rec.tkey = kv.y;
+    rec.q = interp(wa, wb, wc, A0.q, Vb.q, Vc.q);
+    rec.l = interp(wa, wb, wc, A0.l, Vb.l, Vc.l);
+    return true;
+}
+
+// Completes every table record (plain path) and/or synthesis record from the keys.
+// Holes stay all ones.  Thread = pixel (its coordinates and support test computed
+// once), looping over the elements t = blockIdx.y, blockIdx.y + gridDim.y, ...;
+// consecutive threads take consecutive pixels, so every key load and record store is
+// coalesced.
 __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict__ verts,
                                                  const rb_ray_end* __restrict__ ends,
                                                  const unsigned long long* __restrict__ keys, rb_cell* __restrict__ tables,
                                                  const float* __restrict__ c, float4* __restrict__ srec,
                                                  uint32_t* __restrict__ counters, uint32_t kq_magic) {
-    const uint32_t KQ = (uint32_t)(G.max_steps + 1);
     uint32_t holes = 0;   // support pixels that no triangle of the fan covered
     for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < G.npix; pix += gridDim.x * blockDim.x) {
         const int iy = pix / G.nx, ix = pix - iy * G.nx;
@@ -612,9 +650,8 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
         const float c_px = srec ? __ldg(c + pix) : 0.f;
         for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y) {
             const size_t u = (size_t)t * G.npix + pix;
-            const unsigned long long key = keys[u];
-            const uint2 kv = make_uint2((uint32_t)key, (uint32_t)(key >> 32));   // {tag, tkey}
-            if (kv.y == RB_HOLE) {
+            rb_cell rec;
+            if (!resolve_entry(G, verts, ends, keys[u], t, X, Y, kq_magic, rec)) {
                 if (tables) {
                     rb_cell hole;
                     hole.tag = RB_HOLE;
@@ -627,34 +664,6 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
                 if (in_support) ++holes;
                 continue;
             }
-            const uint32_t id = kv.x >> 8;
-            const int half = (int)(id & 1u);
-            uint32_t qi, qk1;
-            udivmod(id >> 1, KQ, kq_magic, qi, qk1);
-            // ids come from the rasteriser (i + 1 < n_rays, 1 <= k1 <= max_steps); clamped all the same
-            const int i = min((int)qi, G.n_rays - 2), k1 = min((int)qk1 + 1, G.max_steps);
-            const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
-            // the winning triangle only: T0 = (A0, B0, B1), T1 = (A0, B1, A1); edge vectors,
-            // doubled area (rounded reciprocal) and weights as in bary
-            const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
-            const Vtx Vb = get_vtx(half ? verts + vidx(G, t, min(k1, lb), i + 1) : verts + vidx(G, t, min(k1 - 1, lb), i + 1));
-            const Vtx Vc = get_vtx(half ? verts + vidx(G, t, min(k1, la), i) : verts + vidx(G, t, min(k1, lb), i + 1));
-            const float ux = rel(Vb.xh, Vb.xl, A0.xh, A0.xl), uy = rel(Vb.yh, Vb.yl, A0.yh, A0.yl);
-            const float vx = rel(Vc.xh, Vc.xl, A0.xh, A0.xl), vy = rel(Vc.yh, Vc.yl, A0.yh, A0.yl);
-            const float ar = __fsub_rn(__fmul_rn(ux, vy), __fmul_rn(uy, vx));
-            const float inv = ar != 0.f ? __frcp_rn(ar) : 0.f;
-            const float dx = rel(X.hi, X.lo, A0.xh, A0.xl), dy = rel(Y.hi, Y.lo, A0.yh, A0.yl);
-            float wa, wb, wc;
-            bary(ux, uy, vx, vy, inv, dx, dy, wa, wb, wc);
-            int kap = A0.k;
-            float wbest = wa;
-            if (wb > wbest) { kap = Vb.k; wbest = wb; }
-            if (wc > wbest) kap = Vc.k;
-            rb_cell rec;
-            rec.tag = (id << 8) | (uint32_t)min(kap, 255);
-            rec.tkey = kv.y;
-            rec.q = interp(wa, wb, wc, A0.q, Vb.q, Vc.q);
-            rec.l = interp(wa, wb, wc, A0.l, Vb.l, Vc.l);
             if (tables) tables[u] = rec;
             if (srec) {
                 DF ex, ey;
@@ -668,11 +677,71 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
     if ((threadIdx.x & 31) == 0 && holes) atomicAdd(counters + CNT_HOLES, holes);
 }
 
+// Mixed path: the resolve pass fused with the synthesis of the operand images, so the
+// per-(element, pixel) record never goes to memory.  CTA (tile of RB_TP pixels,
+// element block of 16): thread (p, half) resolves elements 16 eb + 8 half + k (k < 8)
+// at pixel p of the tile, keeps their synthesis records in registers, and writes for
+// every frequency of the set the Green's functions of Eqs. 4-5 into rows
+// 4 eb + 2 half + {0, 1} of the pixel's core row in both bf16 planes (the same values
+// as the separate record and image passes: the same record, the same formulas).
+__global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __restrict__ verts,
+                                                        const rb_ray_end* __restrict__ ends,
+                                                        const unsigned long long* __restrict__ keys,
+                                                        const float* __restrict__ c, FreqSet F,
+                                                        __nv_bfloat16* __restrict__ aimg, size_t a_stride,
+                                                        uint32_t* __restrict__ counters, uint32_t kq_magic) {
+    const int n = G.n_elem, rcn = 2 * n / 8, neb = n / 16;
+    const int tile = (int)blockIdx.x / neb, eb = (int)blockIdx.x % neb;
+    const int p = (int)threadIdx.x & (RB_TP - 1), half = (int)threadIdx.x >> 7;
+    const int pix = tile * RB_TP + p;
+    const int e0 = 16 * eb + 8 * half;
+    float4 sr[8];
+    uint32_t holes = 0;
+    if (pix < G.npix) {
+        const int iy = pix / G.nx, ix = pix - iy * G.nx;
+        const DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
+        const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
+        const long long jx = 2LL * ix - (G.nx - 1), jy = 2LL * iy - (G.ny - 1);
+        const bool in_support = jx * jx + jy * jy <= G.r2max;
+        const float c_px = __ldg(c + pix);
+        unsigned long long key[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) key[k] = keys[(size_t)(e0 + k) * G.npix + pix];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            rb_cell rec;
+            if (!resolve_entry(G, verts, ends, key[k], e0 + k, X, Y, kq_magic, rec)) {
+                sr[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (in_support) ++holes;
+                continue;
+            }
+            DF ex, ey;
+            elem_pos(G, e0 + k, ex, ey);
+            sr[k] = synth_record(rec, c_px, pixel_elem_dist(G, ix, iy, ex, ey), G.inv_cref, G.inv_cref_lo, G.j_floor);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sr[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int fw = 0; fw < F.n; ++fw) {
+        __nv_bfloat16* plane = aimg + (size_t)fw * a_stride + (size_t)tile * 2 * rcn * 1024;
+#pragma unroll
+        for (int kg = 0; kg < 2; ++kg) {
+            float2 g[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[q] = green_srec(sr[4 * kg + q], F.f[fw]);
+            aimg_put4(plane, rcn, 4 * eb + 2 * half + kg, p, g);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) holes += __shfl_down_sync(0xffffffffu, holes, o);
+    if ((threadIdx.x & 31) == 0 && holes) atomicAdd(counters + CNT_HOLES, holes);
+}
+
 }  // namespace
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
-                         cudaStream_t s, cudaEvent_t traced, cudaEvent_t keys_ready) {
+                         cudaStream_t s, cudaEvent_t traced, cudaEvent_t keys_ready, const FreqSet* F, void* images) {
     rb_rays S{};
     int ws = 0;
     if (samples && samples->vx) {
@@ -682,7 +751,9 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     // vertices are stored whenever a buffer is given; gridding needs them and the keys
     const bool grid = keys != nullptr;
     Vtx* V = (Vtx*)verts;
-    if (grid && (!V || (!tables && !srec))) return cudaErrorInvalidValue;
+    const bool fused = images != nullptr;
+    if (fused && (!F || F->n < 1 || !c || (G.n_elem % 16) != 0)) return cudaErrorInvalidValue;
+    if (grid && (!V || (!tables && !srec && !fused))) return cudaErrorInvalidValue;
     unsigned long long* K = (unsigned long long*)keys;
     if (grid && !keys_ready) {
         cudaError_t e = cudaMemsetAsync(K, 0xff, (size_t)G.n_elem * G.npix * sizeof(unsigned long long), s);
@@ -711,6 +782,13 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     if (e != cudaSuccess) return e;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
     const uint32_t kq_magic = (uint32_t)(0x100000000ull / KQ);
+    if (fused) {
+        const long long blocks = (long long)((G.npix + RB_TP - 1) / RB_TP) * (G.n_elem / 16);
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        k_resolve_images<<<(int)blocks, 256, 0, s>>>(G, V, ends, K, c, *F, (__nv_bfloat16*)images,
+                                                     tc_aimage_elems(G.n_elem, G.npix), counters, kq_magic);
+        return cudaGetLastError();
+    }
     int bx = (G.npix + 255) / 256;
     int by = 1;
     while (by < 16 && by * 2 <= G.n_elem && (long long)bx * by < (long long)nsm * 16) by *= 2;

@@ -23,7 +23,7 @@ RB_MAX_CG = 24
 RB_MAX_TOF_ITERS = 16
 RB_HOLE = 0xFFFFFFFF
 
-EXPORTS = ("rb_workspace_size", "rb_trace_rays", "rb_green_grid", "rb_ray_forward", "rb_born_forward",
+EXPORTS = ("rb_workspace_size", "rb_trace_rays", "rb_green_grid", "rb_ray_forward", "rb_data_weights", "rb_born_forward",
            "rb_born_adjoint", "rb_hf_update", "rb_cg_update", "rb_tof_times", "rb_tof_invert", "rb_born_forward_noalloc",
            "rb_status_string")
 
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
     L.rb_trace_rays.argtypes = [G, P, P, ctypes.POINTER(rb_rays), P, ctypes.c_size_t, P]
     L.rb_green_grid.argtypes = [G, P, P, P, P, ctypes.c_int32, P, P, ctypes.c_size_t, P]
     L.rb_ray_forward.argtypes = [G, P, P, P, ctypes.c_int32, P, P, P]
+    L.rb_data_weights.argtypes = [G, P, P, P, ctypes.c_int32, P, ctypes.c_double, P, P, P, ctypes.c_size_t, P]
     L.rb_born_forward.argtypes = [G, P, P, ctypes.c_double, P, P, ctypes.c_int, P, ctypes.c_size_t, P]
     L.rb_born_adjoint.argtypes = [G, P, P, ctypes.c_double, P, P, P, P, ctypes.c_int, P, ctypes.c_size_t, P]
     L.rb_hf_update.argtypes = [G, P, P, P, ctypes.c_int32, P, ctypes.POINTER(rb_update_params), ctypes.c_int, P, P,
@@ -186,6 +187,15 @@ def rb_ray_forward(geom, c, ends, freqs, p_out, linked_out=None, stream=None):
     code = load().rb_ray_forward(ctypes.byref(geom), _ptr(c), _ptr(ends), fa, nf, _ptr(p_out), _ptr(linked_out),
                                  _stream(stream))
     _check("rb_ray_forward", code)
+
+
+def rb_data_weights(geom, c, alpha0, freqs, p_obs, resid_out, w_out, ws, outlier_frac=0.01, stream=None):
+    """Residuals R = p_ray - p_obs and data weights W of one set: resid_out complex64 and w_out uint8,
+    both [n_freq, n_elem, n_elem]; ws from workspace(geom, n_freq, RB_PREC_FP32)."""
+    fa, nf = _freqs(freqs)
+    code = load().rb_data_weights(ctypes.byref(geom), _ptr(c), _ptr(alpha0), fa, nf, _ptr(p_obs), float(outlier_frac),
+                                  _ptr(resid_out), _ptr(w_out), _ptr(ws), ws.numel(), _stream(stream))
+    _check("rb_data_weights", code)
 
 
 def rb_born_forward(geom, tables, c, f_hz, m, d_out, ws, prec=RB_PREC_FP32, stream=None):

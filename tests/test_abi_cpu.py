@@ -133,6 +133,33 @@ def test_argument_errors_are_synchronous(lib):
                             None, fake, 1 << 30, None) == rb.RB_ERR_UNSUPPORTED
     assert lib.rb_born_adjoint(ctypes.byref(g640), fake, fake, ctypes.c_double(3e5), fake, fake, fake, None,
                                rb.RB_PREC_FP32, fake, 1 << 30, None) == rb.RB_ERR_UNSUPPORTED
+    # residuals and data weights of one set
+    assert lib.rb_data_weights(ctypes.byref(g), fake, fake, f1, 1, fake, ctypes.c_double(0.01), None, fake, fake,
+                               1 << 30, None) == rb.RB_ERR_ARG
+    assert lib.rb_data_weights(ctypes.byref(g), fake, fake, f1, 1, fake, ctypes.c_double(1.0), fake, fake, fake,
+                               1 << 30, None) == rb.RB_ERR_ARG
+    assert lib.rb_data_weights(ctypes.byref(g), fake, fake, f17, 17, fake, ctypes.c_double(0.01), fake, fake, fake,
+                               1 << 30, None) == rb.RB_ERR_ARG
+    assert lib.rb_data_weights(ctypes.byref(g), fake, fake, fneg, 1, fake, ctypes.c_double(0.01), fake, fake, fake,
+                               1 << 30, None) == rb.RB_ERR_ARG
+    assert lib.rb_data_weights(ctypes.byref(bad), fake, fake, f1, 1, fake, ctypes.c_double(0.01), fake, fake, fake,
+                               1 << 30, None) == rb.RB_ERR_SHAPE
+    assert lib.rb_data_weights(ctypes.byref(g), fake, fake, f1, 1, fake, ctypes.c_double(0.01), fake, fake, fake,
+                               1024, None) == rb.RB_ERR_WORKSPACE
+    # the Born forward without a workspace: null pointers, bad frequency, rejected geometry,
+    # all before its scratch array is looked up (no CUDA call)
+    for args in ((None, fake, fake, fake), (fake, None, fake, fake), (fake, fake, None, fake), (fake, fake, fake, None)):
+        tab, cc, mm, dd = args
+        assert lib.rb_born_forward_noalloc(ctypes.byref(g), tab, cc, ctypes.c_double(3e5), mm, dd,
+                                           None) == rb.RB_ERR_ARG
+    for fbad in (0.0, -3e5, float("nan"), float("inf")):
+        assert lib.rb_born_forward_noalloc(ctypes.byref(g), fake, fake, ctypes.c_double(fbad), fake, fake,
+                                           None) == rb.RB_ERR_ARG
+    assert lib.rb_born_forward_noalloc(None, fake, fake, ctypes.c_double(3e5), fake, fake, None) == rb.RB_ERR_ARG
+    for gbad in (bad, rb.geometry_from_config(rbgen.tiny(), nx=2),
+                 rb.geometry_from_config(rbgen.tiny(), ring_radius=0.06)):
+        assert lib.rb_born_forward_noalloc(ctypes.byref(gbad), fake, fake, ctypes.c_double(3e5), fake, fake,
+                                           None) == rb.RB_ERR_SHAPE
     misaligned_tab = P(0x10004)
     assert lib.rb_green_grid(ctypes.byref(g), fake, fake, misaligned_tab, None, 0, None, fake, 1 << 30,
                              None) == rb.RB_ERR_ARG

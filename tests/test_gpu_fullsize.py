@@ -5,8 +5,10 @@
 * 512x512 grid (the benchmarked workload, same launch configuration): every
   ray endpoint against the oracle; tables, Born adjoint and Hessian diagonal
   at a seeded sample of support pixels (the oracle grids every fan but keeps
-  only those pixels); one full rb_hf_update checked by properties that hold
-  at any size (counts, the outlier rule, the update norm, finiteness).
+  only those pixels); the Born forward on every pixel against the oracle; one
+  full rb_hf_update checked by properties that hold at any size (counts, the
+  outlier rule, the update norm, finiteness).  Whole updates and sweeps at this
+  size against the oracle are in test_gpu_sweep_oracle.py.
 """
 import math
 
@@ -167,6 +169,29 @@ def test_breast512_update_properties(dev, big, prec):
     assert dd["alpha"] > 0
     # the step lowers the linearised objective: c moved by dc exactly
     assert np.allclose(c.cpu().numpy(), inp.c_init + dc.cpu().numpy(), rtol=0, atol=1e-3)
+
+
+@pytest.mark.slow
+def test_breast512_forward_against_the_oracle(dev, big):
+    """rb_born_forward at the benchmarked size (256 elements, 512^2 pixels, the launch
+    configuration the update's line search uses) against oracle.born.born_forward on the
+    oracle's own full tables, both paths, 1e-4 relative L2."""
+    cfg, inp, g, geom = big
+    tab, _ = _tables(geom, inp.c_init, inp.alpha0, dev)
+    ot = ogrid.grid(g, inp.c_init, inp.alpha0)
+    rng = np.random.default_rng(16)
+    sup = ogeom.support_mask(g).ravel()
+    m = np.where(sup, rng.standard_normal(g.npix), 0.0) * 1e-9
+    f = cfg.freqs_hz[3]
+    do = oborn.born_forward(ogreen.green(g, ot, inp.c_init, f), m, f)
+    del ot
+    for prec in (rb.RB_PREC_FP32, rb.RB_PREC_BF16X3):
+        ws = rb.workspace(geom, 1, prec, dev)
+        d = torch.empty((g.n_elem, g.n_elem), dtype=torch.complex64, device=dev)
+        rb.rb_born_forward(geom, tab, _t(inp.c_init, dev), f, _t(m, dev), d, ws, prec=prec)
+        e = rel_l2(d.cpu().numpy(), do)
+        print(f"breast512 forward prec={prec}: rel L2 {e:.3g}")
+        assert e <= 1e-4, (prec, e)
 
 
 def test_breast256_forward_bf16x3(dev):
