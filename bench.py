@@ -124,10 +124,32 @@ def algorithmic_work(cfg, n_freq):
 # (8 n^2 npix per frequency) takes three bf16 products (hi.hi, hi.lo, lo.hi), the Hessian
 # contraction (2 n^2 npix) two (W is exact in bf16): (3 x 8 + 2 x 2) / (8 + 2).
 ADJ_ISSUE_RATIO = 2.8
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512
-# (ncu --metrics, one pass), None when not measured for the
-# kernel as built.
-ADJ_TRAFFIC_BYTES = 2152406016 + 1040590080   # dram read + write of one k_adjoint_tc launch (ncu, breast512)
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512 from
+# one ncu capture (--metrics, one pass) of the kernel as it stands in ADJ_TRAFFIC_SOURCE;
+# set to None whenever the kernel changes until it is captured again.
+ADJ_TRAFFIC_BYTES = 2152406016 + 1040590080
+ADJ_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one k_adjoint_tc launch on "
+                      "breast512, kernel as of commit 8eec6b4 (profiles/k_adjoint_tc.md)")
+
+
+def rays_grid_bytes(cfg, n_vertices):
+    """Algorithmic HBM bytes of the ray and gridding stage of one update: every ray vertex
+    (x, y, T, Q, L, kappa: 24 bytes) written once by the tracer and read once by the
+    gridding, the per-(element, pixel) first-arrival record (16 bytes) written once, its
+    64-bit first-arrival key written and read once (16 bytes), and the 7 field grids read
+    once."""
+    ne, npix = cfg.n_elem, cfg.nx * cfg.ny
+    return 48.0 * n_vertices + 16.0 * ne * npix + 16.0 * ne * npix + 28.0 * npix
+
+
+def workload_config(workload, head, world):
+    """The config object of the JSON line, the same for both arms."""
+    cfg = rbgen.config_by_name(workload)
+    return {"workload": workload, "n_elem": cfg.n_elem, "grid": [cfg.nx, cfg.ny], "h_m": cfg.h,
+            "n_rays": cfg.n_rays, "freqs_per_set": max(len(s) for s in cfg.sets), "n_sets": len(cfg.sets),
+            "precision": head, "step_mode": "exact",
+            "l2": "per-update working set (1.1 GB tables) larger than L2, no flush",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def run_ours(args):
@@ -155,6 +177,12 @@ def run_ours(args):
     nsets = len(cfg.sets)
     nf = max(len(s) for s in cfg.sets)
     stream = torch.cuda.current_stream()
+    # vertices of the rays through c_init (the algorithmic bytes of the ray and gridding stage)
+    ends_u8 = torch.empty((cfg.n_elem, cfg.n_rays, 56), dtype=torch.uint8, device=dev)
+    ws1 = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+    rb.rb_trace_rays(geom, c0, a0, ends_u8, ws1)
+    n_vertices = int(np.maximum(rb.decode_ends(ends_u8)["n_vert"], 0).sum())
+    del ws1, ends_u8
     nst = len(rb.STAGES)
 
     def measure(prec_name, with_clocks, cg_iters=0, n_steps=None):
@@ -264,24 +292,26 @@ def run_ours(args):
               # the gradient stages, 4 CG start kernels, per iteration a forward (+ reduce) and a
               # B-image prep (mixed path) per frequency, one partial sum, the adjoint and 3 vector
               # kernels, then 3 apply/norm kernels
-              "gpu_launches_per_update": (19 + nf + args.cg_iters * (3 * nf + 5) if head == "bf16x3"
+              "gpu_launches_per_update": (18 + nf + args.cg_iters * (3 * nf + 5) if head == "bf16x3"
                                           else 18 + args.cg_iters * (2 * nf + 5))}
     peaks, peak_src = _peaks()
     work = algorithmic_work(cfg, nf)
     st = R["stage_ms"]
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    bf16_peak = peaks.get("bf16_tflops_sustained", 1735.5)
+    bf16_burst = peaks.get("bf16_tflops", 1900.0)
 
     def contraction_roof(stage, flop, kern, issue_ratio):
         t = st[stage] / 1e3
         ach = flop / t / 1e12
         if head == "bf16x3":
-            peak = bf16_peak / issue_ratio
-            return {"kernel": kern, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
-                    "tensor_issued_tflops": ach * issue_ratio, "frac_of_bf16_sustained": ach * issue_ratio / bf16_peak,
-                    "peak_source": f"measured bf16 sustained (MEASURED_PEAKS.json, {bf16_peak} TFLOP/s) / "
-                                   f"{issue_ratio:.2f} bf16 tensor FLOPs issued per algorithmic FLOP (3-product split)"}
+            # algorithmic FLOP/s against the measured bf16 burst rate (a kernel of ~1 ms);
+            # the 3-product split's extra tensor work is reported apart as issue utilisation
+            return {"kernel": kern, "bound": "tensor", "achieved": ach, "peak": bf16_burst, "unit": "TFLOP/s",
+                    "frac": ach / bf16_burst, "traffic": None,
+                    "tensor_issued_tflops": ach * issue_ratio, "tensor_issue_frac": ach * issue_ratio / bf16_burst,
+                    "issue_ratio": issue_ratio,
+                    "peak_source": f"{peak_src} bf16 burst (MEASURED_PEAKS.json bf16_tflops, {bf16_burst} TFLOP/s); "
+                                   f"algorithmic FLOP only, split-precision extras excluded"}
         return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak, "traffic": None,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max SM clock"}
@@ -299,17 +329,28 @@ def run_ours(args):
     roof_fwd = contraction_roof("forward", work["forward_flop"], "k_forward_tc" if tc else "k_forward_simt", fwd_ratio)
     # the dominant kernel: the adjoint contraction (one launch per update, alone in its stage)
     roof = dict(roof_adj)
-    if tc and args.workload == WORKLOAD:
+    if tc and args.workload == WORKLOAD and ADJ_TRAFFIC_BYTES is not None:
         roof["traffic"] = ADJ_TRAFFIC_BYTES   # captured on the default workload only
+        roof["traffic_source"] = ADJ_TRAFFIC_SOURCE
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # the ray and gridding stage against the HBM roofline (its algorithmic bytes / stage time)
+    rg_bytes = rays_grid_bytes(cfg, n_vertices)
+    rg_ach = rg_bytes / (st["trace_grid"] / 1e3) / 1e9
+    roof_rg = {"kernels": ["k_trace", "k_raster", "k_resolve"], "bound": "hbm", "achieved": rg_ach, "peak": hbm,
+               "unit": "GB/s", "frac": rg_ach / hbm, "bytes_per_update": rg_bytes, "vertices": n_vertices,
+               "traffic": None,
+               "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+               "note": "algorithmic bytes: 24 B per ray vertex written and read, 16 B first-arrival record "
+                       "written, 16 B key written and read per (element, pixel), field grids read; vertex "
+                       "count of the rays through c_init"}
     # the operand-image synthesis (mixed path): HBM-bound; algorithmic bytes = the synthesis
     # records read once and the operand image (bf16 hi and lo of 2n x npix) of every
     # frequency of the set written once
     roof_img = None
-    if tc and st.get("images", 0.0) > 0:
+    if tc and st.get("images", 0.0) > 0.05:   # a separate synthesis pass (not the fused resolve)
         npix = cfg.nx * cfg.ny
         img_bytes = cfg.n_elem * npix * 16.0 + nf * (2 * cfg.n_elem) * npix * 2 * 2.0
         ach = img_bytes / (st["images"] / 1e3) / 1e9
-        hbm = peaks.get("hbm_gbs", 6800.0)
         roof_img = {"kernel": "k_synth_images", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                     "frac": ach / hbm, "traffic": None, "bytes_per_launch": img_bytes,
                     "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback"}
@@ -319,19 +360,16 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3 split products, f32 accumulate" if tc else "f32",
         "data": "synthetic (seeded breast phantom; data from the library's own ray-Born forward model + 1% noise)",
-        "config": {"workload": args.workload, "n_elem": cfg.n_elem, "grid": [cfg.nx, cfg.ny], "h_m": cfg.h,
-                   "n_rays": cfg.n_rays, "freqs_per_set": nf, "n_sets": nsets, "precision": head,
-                   "step_mode": "exact", "l2": "per-update working set (1.1 GB tables) larger than L2, no flush",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(args.workload, head, world),
         "p50_ms": R["p50_ms"], "p99_ms": R["p99_ms"], "stage_ms": st, "wall_s": R["wall_s"],
         "roofline": roof, "roofline_contractions": {"adjoint": roof_adj, "forward": roof_fwd},
-        "roofline_images": roof_img,
+        "roofline_images": roof_img, "roofline_rays_grid": roof_rg,
         "clocks": R["clocks"], "e2e": R["e2e"],
-        # launches per update: positions, fields, trace/raster/resolve, link, residual keys and
-        # the three selection passes, adjoint (+ the operand-image synthesis and one B-image
-        # prep per frequency on the mixed
-        # path), 4 direction kernels, forward + reduce per frequency, 4 apply/norm kernels
-        "gpu_launches": (20 + 3 * nf if tc else 19 + 2 * nf) * args.steps,
+        # launches per update: positions, fields, trace/raster/resolve (the resolve pass writes
+        # the operand images on the mixed path), link, residual keys and the three selection
+        # passes, adjoint (+ one B-image prep per frequency on the mixed path), 4 direction
+        # kernels, forward + reduce per frequency, 4 apply/norm kernels
+        "gpu_launches": (19 + 3 * nf) * args.steps if tc else (19 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
     if cg is not None:
@@ -392,26 +430,36 @@ def cpu_baseline(sample_fans=32, sample_pix=32768, seed=0, n_freq=1, cache=None)
     return {"value": 1.0 / per_update, "unit": "updates/s", "cores": _cores(), "kind": "oracle",
             "sample": f"rays+gridding of {sample_fans}/256 fans ({t_rays:.2f} s) and G+adjoint+Hessian+forward on "
                       f"{sample_pix}/262144 pixels at {n_freq} of 4 frequencies ({t_born:.2f} s), scaled to one "
-                      f"update", "seconds_per_update_est": per_update}
+                      f"update", "seconds_per_update_est": per_update, "t_rays": t_rays, "t_born": t_born}
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on the host cores.  A step is a fixed eighth of one
+    breast512 update: rays and gridding of 32 of the 256 fans, and the Green's functions,
+    Born adjoint, Hessian diagonal and Born forward at all 4 frequencies of a set on 32768
+    of the 262144 pixels.  ms_per_step is the measured time of such a step; value (updates/s)
+    is the eighth of an update it did over that time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
+    frac = args.cpu_fans / 256.0
+    pix = int(round(262144 * frac))
+    times = []
     cache = {}   # one pixel sample for every step: its tables are built once, untimed
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(sample_fans=args.cpu_fans, sample_pix=args.cpu_pix, seed=0, cache=cache)
+        cb = cpu_baseline(sample_fans=args.cpu_fans, sample_pix=pix, seed=0, n_freq=4, cache=cache)
         if k >= args.warmup:
-            vals.append(cb["seconds_per_update_est"])
-    v = 1.0 / float(np.mean(vals))
+            times.append(cb["t_rays"] + cb["t_born"])
+    t_step = float(np.mean(times))
+    v = frac / t_step
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_elem": 256, "grid": [512, 512]},
+            "config": workload_config(WORKLOAD, args.prec, 1),
             "cpu_baseline": {"value": v, "unit": "updates/s", "cores": _cores(), "kind": "oracle",
-                             "sample": cb["sample"]},
+                             "sample": f"each step {frac:g} of one update: " + cb["sample"].replace(
+                                 ", scaled to one update", ""),
+                             "update_fraction_per_step": frac},
             "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -427,8 +475,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=["breast512", "breast256", "invivo512", "fullring1024", "tiny"],
                     help="the timed workload is breast512; smaller ones are for profiling captures")
-    ap.add_argument("--cpu-fans", type=int, default=32)
-    ap.add_argument("--cpu-pix", type=int, default=32768, help="reference arm: pixels sampled per step")
+    ap.add_argument("--cpu-fans", type=int, default=32,
+                    help="reference arm: fans per step; the step does that fraction of an update (pixels alike)")
     ap.add_argument("--cpu-pix-baseline", type=int, default=160000,
                     help="cpu_baseline of the GPU arm's line: pixels sampled (all fans, all 4 frequencies)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

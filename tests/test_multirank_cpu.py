@@ -58,28 +58,32 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     import bench
     monkeypatch.setenv("RANK", "1")
-    args = argparse.Namespace(steps=1, warmup=0, cpu_fans=2, cpu_pix=16)
+    args = argparse.Namespace(steps=1, warmup=0, cpu_fans=2, prec="bf16x3")
     assert bench.run_reference(args) is None
     assert capsys.readouterr().out == ""
 
 
 def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
     """Rank 0 times the oracle on a bounded sample and prints one line in the bench's
-    format: the same metric and unit, a cpu_baseline that describes the run, and an
-    e2e object with no host-device traffic."""
+    format: the same metric, unit and config as the GPU arm, a cpu_baseline that
+    describes the run (each step a fixed fraction of an update, fans and pixels alike),
+    and an e2e object with no host-device traffic."""
     import argparse
     import json
 
     import bench
     monkeypatch.setenv("RANK", "0")
-    bench.run_reference(argparse.Namespace(steps=1, warmup=0, cpu_fans=2, cpu_pix=64))
+    bench.run_reference(argparse.Namespace(steps=1, warmup=0, cpu_fans=2, prec="bf16x3"))
     lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "updates/s"
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    frac = 2 / 256
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 * frac / d["value"]) < 1e-6 * d["ms_per_step"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "2/256 fans" in cb["sample"]
+    assert cb["update_fraction_per_step"] == frac and "2048/262144 pixels" in cb["sample"]
+    assert d["config"] == bench.workload_config(bench.WORKLOAD, "bf16x3", 1)
     assert d["e2e"] == {"value": d["value"], "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == bench.WORKLOAD
