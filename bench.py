@@ -185,9 +185,23 @@ def run_ours(args):
     del ws1, ends_u8
     nst = len(rb.STAGES)
 
+    tuned = {}
+
+    def tune_for(prec):
+        # the kernel-shape choice measured fastest on this problem (tune.py), before any timing
+        if args.tune == "off":
+            return rb.RB_TUNE_RULE
+        if prec not in tuned:
+            from paper_2511_16633_gb300.tune import tune_update
+            s0 = cfg.sets[0]
+            tuned[prec] = tune_update(geom, c0, a0, [cfg.freqs_hz[i] for i in s0], p_obs[s0[0]:s0[-1] + 1], prec)
+            torch.cuda.empty_cache()
+        return tuned[prec][0]
+
     def measure(prec_name, with_clocks, cg_iters=0, n_steps=None):
         prec = precs[prec_name]
         n_steps = args.steps if n_steps is None else n_steps
+        tch = tune_for(prec)
         ws = rb.workspace(geom, nf, prec, dev)
         c = c0.clone()
         dc = torch.empty_like(c)
@@ -207,10 +221,10 @@ def run_ours(args):
             s = cfg.sets[j]
             if cg_iters:
                 rb.rb_cg_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], p_obs[s[0]:s[-1] + 1], ws, cg_iters, True,
-                                0.01, 1e-3, prec, dc, None, diag, stream, events)
+                                0.01, 1e-3, prec, dc, None, diag, stream, events, tune=tch)
                 return
             rb.rb_hf_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], p_obs[s[0]:s[-1] + 1], ws, 0.01, 1e-3,
-                            rb.RB_STEP_EXACT, prec, dc, diag, stream, events)
+                            rb.RB_STEP_EXACT, prec, dc, diag, stream, events, tune=tch)
 
         for k in range(args.warmup):
             step(k)
@@ -263,7 +277,7 @@ def run_ours(args):
             s = cfg.sets[j]
             dev_p[:len(s)].copy_(host_p[s[0]:s[-1] + 1], non_blocking=True)
             rb.rb_hf_update(geom, c, a0, [cfg.freqs_hz[i] for i in s], dev_p[:len(s)], ws, 0.01, 1e-3,
-                            rb.RB_STEP_EXACT, prec, dc, diag, stream)
+                            rb.RB_STEP_EXACT, prec, dc, diag, stream, tune=tch)
             host_c.copy_(c, non_blocking=True)
             host_diag.copy_(diag, non_blocking=True)
             stream.synchronize()
@@ -372,6 +386,8 @@ def run_ours(args):
         "gpu_launches": (19 + 3 * nf) * args.steps if tc else (19 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
+    if tuned:
+        line["tune"] = {("bf16x3" if p == rb.RB_PREC_BF16X3 else "fp32"): v[1] for p, v in tuned.items()}
     if cg is not None:
         line["cg_variant"] = cg
     if other in runs:
@@ -480,6 +496,9 @@ def main():
     ap.add_argument("--cpu-pix-baseline", type=int, default=160000,
                     help="cpu_baseline of the GPU arm's line: pixels sampled (all fans, all 4 frequencies)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", choices=["on", "off"], default="on",
+                    help="run with the kernel-shape choice the tuner measures fastest on this problem (tuned before "
+                         "the warm-up; off: the library's rule)")
     ap.add_argument("--cg-iters", type=int, default=12,
                     help="also time the CG variant of the update with this many iterations (0: skip)")
     args = ap.parse_args()

@@ -30,10 +30,15 @@
  *     Data-dependent conditions found on the device (a ray that does not
  *     reach the ring within max_steps, uncovered pixels, unlinked pairs) are
  *     counted in an rb_diag record the caller can read afterwards; no kernel
- *     traps and every device loop is bounded.
+ *     traps and every device loop is bounded.  Lost rays are also reported
+ *     without synchronisation: an update that lost rays sets a host-mapped word
+ *     kept for its stream, and the next rb_hf_update or rb_cg_update from that
+ *     stream and workspace that finds the word set (the lossy update has
+ *     completed by then) clears it and returns RB_ERR_LIMIT before launching
+ *     anything (a call with another workspace discards the pending report).
  *   - Calls are reentrant given distinct workspaces.  The only global state is
- *     those library streams with their events (a mutex orders the host
- *     threads that fork and join them), the fixed scratch array of
+ *     those library streams with their events and limit words (a mutex orders
+ *     the host threads that fork and join them), the fixed scratch array of
  *     rb_born_forward_noalloc, and the constant status strings.
  */
 #ifndef RB_H
@@ -55,7 +60,9 @@ typedef enum {
     RB_ERR_SHAPE = 2,       /* sizes outside the supported ranges */
     RB_ERR_WORKSPACE = 3,   /* workspace missing, too small or misaligned */
     RB_ERR_CUDA = 4,        /* a CUDA launch or call failed */
-    RB_ERR_LIMIT = 5,       /* reserved for device-side limits reported by later calls */
+    RB_ERR_LIMIT = 5,       /* an earlier rb_hf_update / rb_cg_update from the same stream and workspace lost rays
+                               (a ray still inside the ring after max_steps): reported once by the next
+                               such call that finds it, which then launches nothing */
     RB_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
 } rb_status;
 
@@ -146,7 +153,13 @@ typedef struct rb_update_params {
     double outlier_frac;    /* fraction of kept data zeroed by largest |residual| (0.01) */
     double eps_rel;         /* eps = eps_rel * mean over the support of sum_w H_w (1e-3) */
     int32_t step_mode;      /* rb_step_mode */
-    int32_t pad;
+    int32_t tune;           /* kernel-shape choices, 0 = the library's rules (a caller may time the
+                               alternatives and pass the fastest; the results do not change):
+                               bits 0-1 the rasteriser's work mapping, 1 = warps along the ray tubes,
+                               2 = warps across them (rule: along from tubes of 4 pixels at the ring);
+                               bits 2-3 the tensor-core adjoint, 1 = CTA pairs (cta_group::2 MMAs),
+                               2 = one CTA per pixel tile (the rule); other bits 0; a field of 3
+                               returns RB_ERR_ARG */
     void* stage_events;     /* NULL, or a caller-created array of 2 * RB_STAGE_COUNT cudaEvent_t:
                                events [2s] and [2s+1] are recorded on the stream before and after
                                stage s (no events are created or destroyed by the library) */

@@ -136,16 +136,44 @@ int tc_ctas() {
 // use and kept for the process (at most kMaxSide; beyond that, callers share the entries
 // of their device, which stays correct and only serialises their side work); the mutex
 // keeps each call's fork and join events together when several host threads call.
+// With each entry goes a word of host-mapped memory: the update that loses rays writes
+// its lost-ray count there from the device, and the next update call from the same
+// stream with the same workspace that finds it set clears it and returns RB_ERR_LIMIT
+// without launching anything (no synchronisation: the word is seen once the lossy update
+// has completed).  A call with another workspace (a new problem on a reused stream)
+// discards a pending report that belonged to the previous one.
 struct SideStream {
     int dev = -1;
     cudaStream_t caller = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t start = nullptr, keys = nullptr, fork = nullptr, join = nullptr;
+    uint32_t* lim_host = nullptr;   // null when host-mapped memory is unavailable
+    uint32_t* lim_dev = nullptr;
+    const void* last_ws = nullptr;  // workspace of the stream's last update
 };
 constexpr int kMaxSide = 256;
+constexpr int kLimitStride = 16;   // one 64-byte line per entry
 std::mutex g_side_mutex;
 SideStream g_side[kMaxSide];
 int g_side_n = 0;
+alignas(4096) uint32_t g_limit_words[kMaxSide * kLimitStride];
+int g_limit_state = 0;   // 0: not registered yet, 1: registered (mapped, portable), -1: unavailable
+
+// The device address of limit word k on the current device (null if unavailable).
+uint32_t* limit_word_dev(int k) {
+    if (g_limit_state == 0) {
+        g_limit_state = cudaHostRegister(g_limit_words, sizeof(g_limit_words),
+                                         cudaHostRegisterMapped | cudaHostRegisterPortable) == cudaSuccess ? 1 : -1;
+        if (g_limit_state < 0) cudaGetLastError();
+    }
+    if (g_limit_state < 0) return nullptr;
+    void* p = nullptr;
+    if (cudaHostGetDevicePointer(&p, g_limit_words, 0) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (uint32_t*)p + (size_t)k * kLimitStride;
+}
 
 cudaError_t side_stream(cudaStream_t caller, SideStream** out) {
     int dev = 0;
@@ -176,6 +204,13 @@ cudaError_t side_stream(cudaStream_t caller, SideStream** out) {
     if ((e = cudaThreadExchangeStreamCaptureMode(&mode)) != cudaSuccess) return e;
     e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        n.lim_dev = limit_word_dev(g_side_n);
+        if (n.lim_dev) {
+            n.lim_host = g_limit_words + (size_t)g_side_n * kLimitStride;
+            __atomic_store_n(n.lim_host, 0u, __ATOMIC_RELEASE);
+        }
+    }
     cudaThreadExchangeStreamCaptureMode(&mode);
     if (e != cudaSuccess) {
         for (int k = 0; k < 4; ++k)
@@ -204,6 +239,7 @@ rb_status check_update(const rb_geometry* geom, const float* c, const float* alp
     if (!(params->outlier_frac >= 0.0 && params->outlier_frac < 1.0)) return RB_ERR_ARG;
     if (!(params->eps_rel >= 0.0) || !isfinite(params->eps_rel)) return RB_ERR_ARG;
     if (params->step_mode != RB_STEP_EXACT && params->step_mode != RB_STEP_DIAG) return RB_ERR_ARG;
+    if ((params->tune & ~15) != 0 || (params->tune & 3) == 3 || ((params->tune >> 2) & 3) == 3) return RB_ERR_ARG;
     if (!make_freqs(geom, freqs_hz, n_freq, F)) return RB_ERR_ARG;
     if (prec == RB_PREC_BF16X3 && !tc_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
     if (prec == RB_PREC_FP32 && !simt_adjoint_supported(geom->n_elem)) return RB_ERR_UNSUPPORTED;
@@ -215,7 +251,7 @@ rb_status check_update(const rb_geometry* geom, const float* c, const float* alp
 // gradient sum_w Re g_w -> gsum and Hessian diagonal sum_w H_w -> hsum.
 rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float* c, const float* alpha0,
                           const float* p_obs, const rb_update_params* params, rb_precision prec, const Marks& mark,
-                          cudaStream_t s) {
+                          cudaStream_t s, uint32_t** limit_word) {
     const int n_freq = F.n;
     const int ne2 = G.n_elem * G.n_elem;
     float4* exy = W.at<float4>(W.L.elem_xy);
@@ -231,6 +267,13 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     std::lock_guard<std::mutex> lock(g_side_mutex);
     SideStream* ss = nullptr;
     RB_CU(side_stream(s, &ss));
+    // an earlier update from this stream and workspace lost rays: report it once, launching nothing
+    if (ss->lim_host) {
+        const bool same = ss->last_ws == (const void*)W.base;
+        ss->last_ws = (const void*)W.base;
+        if (__atomic_exchange_n(ss->lim_host, 0u, __ATOMIC_ACQ_REL) != 0 && same) return RB_ERR_LIMIT;
+    }
+    *limit_word = ss->lim_dev;
     const cudaStream_t s2 = ss->s;
     const Marks mark2{mark.ev, s2};   // stage events of the side branch
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4 + DBL_N * 8, s));
@@ -247,7 +290,8 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     // the plain path reads the tables; on the mixed path the resolve pass writes the
     // operand images of the set itself
     RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), tc ? nullptr : tables, W.at<void>(W.L.verts), c,
-                       nullptr, cnt, s, ss->fork, ss->keys, tc ? &F : nullptr, tc ? W.at<void>(W.L.aimg) : nullptr));
+                       cnt, s, ss->fork, ss->keys, tc ? &F : nullptr, tc ? W.at<void>(W.L.aimg) : nullptr,
+                       params->tune & 3));
     // side branch 2 (needs the end records only): links, residuals, weights, B images
     RB_CU(cudaStreamWaitEvent(s2, ss->fork, 0));
     RB_CU(mark2(RB_STAGE_LINK, 0));
@@ -271,7 +315,8 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     RB_CU(mark(RB_STAGE_ADJOINT, 0));
     if (tc) {
         RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
-                                nullptr, nullptr, W.at<float>(W.L.gsum), W.at<float>(W.L.hsum), cnt, s));
+                                nullptr, nullptr, W.at<float>(W.L.gsum), W.at<float>(W.L.hsum), cnt, s,
+                                (params->tune >> 2) & 3));
     } else {
         RB_CU(launch_adjoint_simt(G, tables, c, F, R, wts, nullptr, nullptr, W.at<float>(W.L.gsum),
                                   W.at<float>(W.L.hsum), cnt, s));
@@ -295,7 +340,9 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->counters = o; o = align256(o + CNT_N * 4 + DBL_N * 8);
     L->elem_xy = o; o = align256(o + ne * 16);
     L->cells = o; o = align256(o + ncell * 128);
-    L->tables = o; o = align256(o + ne * npix * sizeof(rb_cell));
+    // the plain path's tables and forward partials; the mixed path keeps neither (its
+    // resolve pass writes the operand images)
+    L->tables = o; o = align256(o + (tcp ? 0 : ne * npix * sizeof(rb_cell)));
     L->verts = o; o = align256(o + rb_verts_bytes(g->n_elem, g->n_rays, g->max_steps));
     L->gkeys = o; o = align256(o + ne * npix * 8);
     L->ends = o; o = align256(o + ne * (size_t)g->n_rays * sizeof(rb_ray_end));
@@ -308,15 +355,21 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->hsum = o; o = align256(o + npix * 4);
     L->pdir = o; o = align256(o + npix * 4);
     L->part = o; o = align256(o + (size_t)(RB_MAX_FREQ + 2) * 256 * 8);
-    L->fwd = o; o = align256(o + (size_t)rb_fwd_chunks_for((int)npix) * ne * ne * 8);
+    L->fwd = o; o = align256(o + (tcp ? 0 : (size_t)rb_fwd_chunks_for((int)npix) * ne * ne * 8));
     L->tcimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_b_images_bytes(g->n_elem) : 0));
     // exact G per persistent CTA, then its |G|^2 A slices (bf16 hi and lo)
     L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * (8 + 4) : 0));
     L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
-    L->srec = o; o = align256(o + (tcp ? ne * npix * 16 : 0));
     L->aimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_aimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->cgv = o; o = align256(o + 4 * npix * 4);
     L->tof = o; o = align256(o + tof_ws_bytes(g->n_elem, g->n_rays, (int)npix));
+    // one size fits every entry point: the single-precision calls (rays, gridding, data
+    // weights, times of flight) lay the same workspace out as the FP32 path does
+    if (tcp) {
+        WsLayout L32;
+        const size_t o32 = rb_ws_layout(g, n_freq, RB_PREC_FP32, &L32);
+        if (o32 > o) o = o32;
+    }
     L->total = o;
     return o;
 }
@@ -359,8 +412,7 @@ rb_status rb_trace_rays(const rb_geometry* geom, const float* c, const float* al
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, nullptr, nullptr, nullptr, nullptr, cnt,
-                       s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), out->ends, out, nullptr, nullptr, nullptr, nullptr, cnt, s));
     return RB_OK;
 }
 
@@ -384,7 +436,7 @@ rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* al
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
     RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, W.at<void>(W.L.gkeys), tables,
-                       W.at<void>(W.L.verts), nullptr, nullptr, cnt, s));
+                       W.at<void>(W.L.verts), nullptr, cnt, s));
     if (g_out) RB_CU(launch_green_out(G, tables, c, F, (float2*)g_out, s));
     return RB_OK;
 }
@@ -421,7 +473,7 @@ rb_status rb_data_weights(const rb_geometry* geom, const float* c, const float* 
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), ends, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cnt, s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), ends, nullptr, nullptr, nullptr, nullptr, nullptr, cnt, s));
     RB_CU(launch_link(G, c, ends, F, R, linked, s));
     RB_CU(launch_residual_keys(G, n_freq, (const float2*)p_obs, R, linked, W.at<uint64_t>(W.L.keys), cnt,
                                W.at<void>(W.L.sel), s));
@@ -452,8 +504,7 @@ rb_status rb_born_forward(const rb_geometry* geom, const rb_cell* tables, const 
         FreqSet F1;
         F1.n = 1;
         F1.f[0] = F;
-        RB_CU(launch_srec(G, tables, c, W.at<float4>(W.L.srec), s));
-        RB_CU(launch_synth_images(G, W.at<float4>(W.L.srec), F1, W.at<void>(W.L.aimg), s));
+        RB_CU(launch_tables_images(G, tables, c, F1, W.at<void>(W.L.aimg), s));
         RB_CU(launch_forward_tc(G, W.at<void>(W.L.aimg), F, m, W.at<float>(W.L.tcfwd), tc_ctas(), (float2*)d_out,
                                 nullptr, nullptr, cnt, s));
     } else {
@@ -486,8 +537,7 @@ rb_status rb_born_adjoint(const rb_geometry* geom, const rb_cell* tables, const 
     if (prec == RB_PREC_BF16X3) {
         RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
         RB_CU(launch_prep_b(G.n_elem, (const float2*)resid, w, W.at<void>(W.L.tcimg), s));
-        RB_CU(launch_srec(G, tables, c, W.at<float4>(W.L.srec), s));
-        RB_CU(launch_synth_images(G, W.at<float4>(W.L.srec), F, W.at<void>(W.L.aimg), s));
+        RB_CU(launch_tables_images(G, tables, c, F, W.at<void>(W.L.aimg), s));
         RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr), tc_ctas(),
                                 (float2*)g_out, hdiag_out, nullptr, nullptr, cnt, s));
     } else {
@@ -509,7 +559,8 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     cudaStream_t s = (cudaStream_t)stream;
     const GeoDev G = make_geo(geom, W.at<float4>(W.L.elem_xy));
     const Marks mark{(cudaEvent_t*)params->stage_events, s};
-    st = gradient_stages(G, F, W, c_inout, alpha0, p_obs, params, prec, mark, s);
+    uint32_t* limit_word = nullptr;
+    st = gradient_stages(G, F, W, c_inout, alpha0, p_obs, params, prec, mark, s, &limit_word);
     if (st != RB_OK) return st;
     const int ne2 = G.n_elem * G.n_elem;
     uint32_t* cnt = W.at<uint32_t>(W.L.counters);
@@ -544,7 +595,7 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_FORWARD, 1));
     RB_CU(mark(RB_STAGE_APPLY, 0));
     RB_CU(launch_update(G, c_inout, gsum, hsum, pdir, dc_out, part + (size_t)RB_MAX_FREQ * 256, dbl, cnt, diag_out,
-                        params->eps_rel, params->step_mode, 1, s));
+                        params->eps_rel, params->step_mode, 1, s, limit_word));
     RB_CU(mark(RB_STAGE_APPLY, 1));
     return RB_OK;
 }
@@ -563,7 +614,8 @@ rb_status rb_cg_update(const rb_geometry* geom, float* c_inout, const float* alp
     cudaStream_t s = (cudaStream_t)stream;
     const GeoDev G = make_geo(geom, W.at<float4>(W.L.elem_xy));
     const Marks mark{(cudaEvent_t*)params->stage_events, s};
-    st = gradient_stages(G, F, W, c_inout, alpha0, p_obs, params, prec, mark, s);
+    uint32_t* limit_word = nullptr;
+    st = gradient_stages(G, F, W, c_inout, alpha0, p_obs, params, prec, mark, s, &limit_word);
     if (st != RB_OK) return st;
     const int ne2 = G.n_elem * G.n_elem;
     uint32_t* cnt = W.at<uint32_t>(W.L.counters);
@@ -606,7 +658,7 @@ rb_status rb_cg_update(const rb_geometry* geom, float* c_inout, const float* alp
         // q = sum_w Re B_w^H W B_w p
         if (tc) {
             RB_CU(launch_adjoint_tc(G, W.at<void>(W.L.aimg), F, W.at<void>(W.L.tcimg), W.at<float2>(W.L.gscr),
-                                    tc_ctas(), nullptr, nullptr, q, nullptr, cnt, s));
+                                    tc_ctas(), nullptr, nullptr, q, nullptr, cnt, s, (params->tune >> 2) & 3));
         } else {
             RB_CU(launch_adjoint_simt(G, tables, c_inout, F, d, wts, nullptr, nullptr, q, nullptr, cnt, s));
         }
@@ -616,7 +668,7 @@ rb_status rb_cg_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_FORWARD, 1));
     RB_CU(mark(RB_STAGE_APPLY, 0));
     RB_CU(launch_update(G, c_inout, gsum, hsum, x, dc_out, vpart, dbl, cnt, diag_out, params->eps_rel, RB_STEP_DIAG,
-                        1, s));
+                        1, s, limit_word));
     RB_CU(mark(RB_STAGE_APPLY, 1));
     return RB_OK;
 }
@@ -636,7 +688,7 @@ rb_status rb_tof_times(const rb_geometry* geom, const float* c, const float* alp
     RB_CU(cudaMemsetAsync(cnt, 0, CNT_N * 4, s));
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
-    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), ends, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, cnt, s));
+    RB_CU(launch_trace(G, W.at<float4>(W.L.cells), ends, nullptr, nullptr, nullptr, nullptr, nullptr, cnt, s));
     RB_CU(launch_tof_link(G, c, ends, W.at<void>(W.L.tof), linked_out, s));
     RB_CU(launch_tof_times_out(G, W.at<void>(W.L.tof), t_out, s));
     return RB_OK;
@@ -665,8 +717,7 @@ rb_status rb_tof_invert(const rb_geometry* geom, float* c_inout, const float* al
     for (int k = 0; k <= n_iter; ++k) {
         const bool last = k == n_iter;
         RB_CU(launch_fields(G, c_inout, alpha0, cells, s));
-        RB_CU(launch_trace(G, cells, ends, nullptr, nullptr, nullptr, last ? nullptr : (void*)verts, nullptr, nullptr,
-                           cnt, s));
+        RB_CU(launch_trace(G, cells, ends, nullptr, nullptr, nullptr, last ? nullptr : (void*)verts, nullptr, cnt, s));
         RB_CU(launch_tof_link(G, c_inout, ends, tw, nullptr, s));
         if (resid_out) RB_CU(launch_tof_resid(G, tw, t_obs, obs_linked, part, resid_out + k, s));
         if (!last) RB_CU(launch_tof_step(G, verts, ends, tw, t_obs, obs_linked, c_inout, s));

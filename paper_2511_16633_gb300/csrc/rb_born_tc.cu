@@ -90,20 +90,6 @@ struct TcArgs {
     int want_h;                // the Hessian contraction is wanted (h_out or hsum set)
 };
 
-// Synthesis records of every element and pixel from the tables.
-__global__ void k_srec(GeoDev G, const rb_cell* __restrict__ tables, const float* __restrict__ c,
-                       float4* __restrict__ srec) {
-    const long long total = (long long)G.n_elem * G.npix;
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(u / G.npix), pix = (int)(u % G.npix);
-        const rb_cell rec = tables[u];
-        DF ex, ey;
-        elem_pos(G, r, ex, ey);
-        srec[u] = synth_record(rec, __ldg(c + pix), pixel_elem_dist(G, pix % G.nx, pix / G.nx, ex, ey), G.inv_cref,
-                               G.inv_cref_lo, G.j_floor);
-    }
-}
-
 }  // namespace
 
 namespace {
@@ -153,29 +139,40 @@ __device__ __forceinline__ void consume_u(int r0, uint32_t p, uint32_t h, const 
 }
 
 // ---------------------------------------------------------------------------
-// Operand image of one frequency set (layout: aimg_put4 in rb_internal.cuh),
-// synthesised once at full occupancy from the synthesis records; the update itself
-// writes it from the resolve pass (k_resolve_images, rb_trace.cu), this kernel serves
-// the single-operator entry points.  The adjoint reads it K-major (a K = 16 slice is
-// two rows: one 4 KB bulk copy per plane), the forward MN-major (a 16-pixel slice of
-// every row is one 2-D TMA box).  CTA (tile, element block of 16): thread (p, half)
-// synthesises elements 16 eb + 8 half + k (k < 8) at pixel p for every frequency and
-// writes rows 4 eb + 2 half + {0, 1} of the pixel's core row (coalesced: 128 threads,
-// 2 KB).
+// Operand image of one frequency set (layout: aimg_put4 in rb_internal.cuh) from the
+// caller's tables, for the single-operator entry points (the update writes it from its
+// resolve pass: k_resolve_images, rb_trace.cu).  The synthesis record of each entry is
+// formed in registers from its table record, c at the pixel and the distance to the
+// element.  The adjoint reads the image K-major (a K = 16 slice is two rows: one 4 KB
+// bulk copy per plane), the forward MN-major (a 16-pixel slice of every row is one 2-D
+// TMA box).  CTA (tile, element block of 16): thread (p, half) synthesises elements
+// 16 eb + 8 half + k (k < 8) at pixel p for every frequency and writes rows
+// 4 eb + 2 half + {0, 1} of the pixel's core row (coalesced: 128 threads, 2 KB).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_synth_images(GeoDev G, const float4* __restrict__ srec, FreqSet F,
-                                                      __nv_bfloat16* __restrict__ aimg, size_t a_stride) {
+__global__ void __launch_bounds__(256) k_tables_images(GeoDev G, const rb_cell* __restrict__ tables,
+                                                       const float* __restrict__ c, FreqSet F,
+                                                       __nv_bfloat16* __restrict__ aimg, size_t a_stride) {
     const int n = G.n_elem, rcn = 2 * n / 8;
     const int neb = n / 16;
     const int tile = (int)blockIdx.x / neb, eb = (int)blockIdx.x % neb;
     const int tid = threadIdx.x, p = tid & (TP - 1), half = tid >> 7;
     const int px = tile * TP + p;
-    const bool valid = px < G.npix;
     const int e0 = 16 * eb + 8 * half;
     float4 sr[8];
+    if (px < G.npix) {
+        const float c_px = __ldg(c + px);
+        const int ix = px % G.nx, iy = px / G.nx;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        sr[k] = valid ? __ldg(srec + (size_t)(e0 + k) * G.npix + px) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < 8; ++k) {
+            DF ex, ey;
+            elem_pos(G, e0 + k, ex, ey);
+            sr[k] = synth_record(tables[(size_t)(e0 + k) * G.npix + px], c_px, pixel_elem_dist(G, ix, iy, ex, ey),
+                                 G.inv_cref, G.inv_cref_lo, G.j_floor);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sr[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     for (int fw = 0; fw < F.n; ++fw) {
         const FreqC& fc = F.f[fw];
         __nv_bfloat16* plane = aimg + (size_t)fw * a_stride + (size_t)tile * 2 * rcn * 1024;
@@ -579,6 +576,395 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, A.tmem_cols);
 }
+// ---------------------------------------------------------------------------
+// The same adjoint on CTA pairs (a cluster of two CTAs, cta_group::2 MMAs of M = 256).
+// The pair takes two 128-pixel tiles at a time, one per CTA (a pair with one tile left
+// takes the last tile twice and keeps one result), and each CTA stages only its own
+// half of every operand: its tile's A slices and half the rows of each N-block of S
+// (and of W).  The MMA over both CTAs' shared memory then reads half the S bytes per
+// CTA that the single-CTA kernel reads, and the stages (A 8 KB + S half 16 KB) are
+// 24 KB instead of 40, so eight of them fit.  Each CTA's TMEM holds its own tile's U
+// and V (128 lanes), so the producers and epilogues are those of the single-CTA
+// kernel.  Roles as there, plus:
+//   rank 0, warp 16: MMA issuer for the pair: waits for its own stage and for the
+//               peer's ("pfull", arrived on from the peer), issues the pair MMAs and
+//               commits them to the "empty" (and accumulator) barriers of both CTAs;
+//   rank 1, warp 16: relay: when a stage of its CTA is filled, arrives on the
+//               issuer's pfull for it;
+//   the accumulator barriers the issuer waits for (acc_empty, acc_low) take the
+//   arrivals of both CTAs' producer warps.
+// Every wait is bounded; both CTAs meet at a cluster barrier before they free TMEM
+// and exit, so no CTA leaves while its peer may still touch its shared memory.
+// ---------------------------------------------------------------------------
+constexpr int NST2 = 8;
+constexpr uint32_t ST2_BYTES = 24u * 1024u;
+// U stage: A hi (4 KB), A lo (4 KB), then this CTA's S rows of every N-block (hi for each
+// N-block, then lo); V stage: |G|^2 hi (8 KB), lo (8 KB), this CTA's W rows (<= 8 KB)
+constexpr uint32_t ST2_ALO = 4096u, ST2_B = 8192u, ST2_VALO = 8192u, ST2_VB = 16384u;
+
+template <bool MULTI>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHR_A, 1) k_adjoint_tc2(TcArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t s_full[NST2], s_pfull[NST2], s_empty[NST2], s_acc_full, s_acc_empty, s_acc_low, s_vready, s_drain;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_err;
+    __shared__ float s_red[3][3][TP];             // partial sums of quarters 1..3: Re g, Im g, H
+    const GeoDev& G = A.G;
+    const int n = G.n_elem, n2 = 2 * n;
+    const int ne = A.n_e, ne2 = 2 * ne;
+    const int npass = MULTI ? A.npass : 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = tc::cluster_ctarank();   // 0 issues the pair's MMAs
+    const bool want_h = A.want_h != 0;
+    const int nU = n2 / 16, nV = want_h ? n / 32 : 0, per = nU + nV;
+    // N-blocks of U (as in the single-CTA kernel) and this CTA's half of each
+    const int nbk = ne2 > 256 ? 2 : 1, nb_u = ne2 / nbk, hrow = nb_u / 2;
+    const uint32_t hb = (uint32_t)hrow * 32u;    // bytes of one plane of one N-block half
+    const int wrow = ne / 2;                     // this CTA's W rows
+    if (tid == 0) {
+        for (int s = 0; s < NST2; ++s) {
+            tc::mbar_init(tc::smem_u32(&s_full[s]), 1);
+            tc::mbar_init(tc::smem_u32(&s_pfull[s]), 1);
+            tc::mbar_init(tc::smem_u32(&s_empty[s]), 1 + NPROD / 32);
+        }
+        tc::mbar_init(tc::smem_u32(&s_acc_full), 1);
+        tc::mbar_init(tc::smem_u32(&s_acc_empty), 2 * NPROD / 32);
+        tc::mbar_init(tc::smem_u32(&s_acc_low), 2 * NPROD / 32);
+        tc::mbar_init(tc::smem_u32(&s_vready), NPROD / 32);
+        tc::mbar_init(tc::smem_u32(&s_drain), 1);
+        s_err = 0;
+    }
+    if (warp == 0) tc::tmem_alloc_pair(tc::smem_u32(&s_tmem), A.tmem_cols);
+    tc::fence_before();
+    tc::cluster_sync();   // both CTAs' barriers initialised before any cross-CTA arrival
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    __nv_bfloat16* vimg = A.vimg + (size_t)blockIdx.x * (size_t)(n / 32) * (2 * TP * 32);
+    const int n_pairs = (A.n_tiles + 1) / 2, q0 = (int)blockIdx.x >> 1, nq = (int)gridDim.x >> 1;
+    const int my_items = q0 < n_pairs ? (n_pairs - 1 - q0) / nq + 1 : 0;
+    const int total = my_items * A.F.n * npass * per;
+    const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 32;
+    auto stage = [&](int s) { return smem + (size_t)s * ST2_BYTES; };
+    // this CTA's tile of pair item q (the last tile again when the pair has only one)
+    auto tile_of = [&](int q) {
+        const int t = 2 * q + (int)rank;
+        return t < A.n_tiles ? t : A.n_tiles - 1;
+    };
+
+    if (warp == NPROD / 32 + 1) {
+        // ------------------------------ loader (both CTAs) ------------------------------
+        if (lane == 0) {
+            int ql = 0, s = 0, j = 0, fw = 0, pass = 0, q = q0;
+            uint32_t ph = 0, vrp = 0;
+            bool err = false;
+            uint64_t stream_pol;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_pol));
+            for (; ql < total; ++ql) {
+                if (ql >= NST2 && !tc::mbar_wait(tc::smem_u32(&s_empty[s]), ph ^ 1u, kMaxTries)) {
+                    err = true;
+                    break;
+                }
+                if (s_err) break;
+                const uint32_t mb = tc::smem_u32(&s_full[s]);
+                const int tile = tile_of(q);
+                if (j < nU) {
+                    const uint32_t abytes = TP * 16 * 2;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                                 "r"(2u * abytes + 2u * (uint32_t)nbk * hb)
+                                 : "memory");
+                    const __nv_bfloat16* asrc =
+                        A.aimg + (size_t)fw * A.aimg_stride + ((size_t)tile * 2 * (n2 / 8) + 2 * j) * 1024;
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                                 " [%0], [%1], %2, [%3], %4;"
+                                 ::"r"(tc::smem_u32(stage(s))), "l"(asrc), "r"(abytes), "r"(mb), "l"(stream_pol)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                                 " [%0], [%1], %2, [%3], %4;"
+                                 ::"r"(tc::smem_u32(stage(s) + ST2_ALO)), "l"(asrc + (size_t)(n2 / 8) * 1024),
+                                 "r"(abytes), "r"(mb), "l"(stream_pol)
+                                 : "memory");
+                    for (int nb = 0; nb < nbk; ++nb) {
+                        // rows pass ne2 + nb nb_u + rank hrow .. + hrow of both planes
+                        const __nv_bfloat16* bsrc = A.bu + (size_t)fw * A.bu_stride + (size_t)j * 2 * img_u +
+                                                    (size_t)(pass * ne2 + nb * nb_u + (int)rank * hrow) * 16;
+                        const uint32_t dh = tc::smem_u32(stage(s) + ST2_B + (uint32_t)nb * hb);
+                        const uint32_t dl = tc::smem_u32(stage(s) + ST2_B + (uint32_t)(nbk + nb) * hb);
+                        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                     ::"r"(dh), "l"(bsrc), "r"(hb), "r"(mb)
+                                     : "memory");
+                        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                     ::"r"(dl), "l"(bsrc + img_u), "r"(hb), "r"(mb)
+                                     : "memory");
+                    }
+                } else {
+                    if (j == nU) {
+                        // this CTA's |G|^2 slices of the item are written by its producers
+                        if (!tc::mbar_wait(tc::smem_u32(&s_vready), vrp & 1u, kMaxTries)) {
+                            err = true;
+                            break;
+                        }
+                        ++vrp;
+                    }
+                    const uint32_t wbytes = (uint32_t)wrow * 64u, abytes = 2u * TP * 32 * 2;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(wbytes + abytes)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc::smem_u32(stage(s) + ST2_VB)),
+                                 "l"(A.bw + (size_t)fw * A.bw_stride + (size_t)(j - nU) * img_w +
+                                     (size_t)(pass * ne + (int)rank * wrow) * 32),
+                                 "r"(wbytes), "r"(mb)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc::smem_u32(stage(s))), "l"(vimg + (size_t)(j - nU) * (2 * TP * 32)), "r"(abytes),
+                                 "r"(mb)
+                                 : "memory");
+                }
+                if (++s == NST2) { s = 0; ph ^= 1u; }
+                if (++j == per) {
+                    j = 0;
+                    if (++pass == npass) {
+                        pass = 0;
+                        if (++fw == A.F.n) { fw = 0; q += nq; }
+                    }
+                }
+            }
+            if (err || s_err) {
+                s_err = 1;
+                for (int x = (ql > NST2 ? ql - NST2 : 0); x < ql; ++x)
+                    tc::mbar_wait(tc::smem_u32(&s_full[x % NST2]), (uint32_t)(x / NST2) & 1u, kMaxTries);
+            }
+        }
+        __syncwarp();
+    } else if (warp == NPROD / 32 && rank != 0) {
+        // ------------------------------ relay (rank 1) ------------------------------
+        if (lane == 0) {
+            const uint32_t r_pfull = tc::mapa(tc::smem_u32(&s_pfull[0]), 0u);
+            int s = 0;
+            uint32_t ph = 0;
+            for (int ql = 0; ql < total; ++ql) {
+                if (!tc::mbar_wait(tc::smem_u32(&s_full[s]), ph, kMaxTries)) {
+                    s_err = 1;
+                    break;
+                }
+                if (s_err) break;
+                tc::mbar_arrive_remote(r_pfull + 8u * (uint32_t)s);
+                if (++s == NST2) { s = 0; ph ^= 1u; }
+            }
+        }
+        __syncwarp();
+    } else if (warp == NPROD / 32) {
+        // ------------------------------ MMA issuer (rank 0) ------------------------------
+        if (lane == 0) {
+            const uint32_t id_u = tc::idesc_bf16_f32(256, (uint32_t)nb_u);
+            const uint32_t id_v = tc::idesc_bf16_f32(256, (uint32_t)ne);
+            int s = 0, j = 0;
+            uint32_t acce = 0, accl = 0, ph = 0;
+            bool err = false, issued = false;
+            for (int q = 0; q < total && !err; ++q) {
+                if (j == nU) {
+                    // V overwrites the columns of the first N-block of U: both CTAs' part of the U
+                    // epilogue there must be done
+                    if (!tc::mbar_wait_cluster(tc::smem_u32(&s_acc_low), accl & 1u, kMaxTries)) { err = true; break; }
+                    ++accl;
+                } else if (j == 0 && q > 0) {
+                    // a new U phase: both CTAs' V (or U) epilogue must have read the accumulator
+                    if (!tc::mbar_wait_cluster(tc::smem_u32(&s_acc_empty), acce & 1u, kMaxTries)) { err = true; break; }
+                    ++acce;
+                }
+                if (!tc::mbar_wait(tc::smem_u32(&s_full[s]), ph, kMaxTries)) { err = true; break; }
+                if (!tc::mbar_wait_cluster(tc::smem_u32(&s_pfull[s]), ph, kMaxTries)) { err = true; break; }
+                if (s_err) { err = true; break; }
+                tc::fence_after();
+                const uint32_t sa = tc::smem_u32(stage(s)), sal = sa + ST2_ALO, sb = sa + ST2_B;
+                const uint64_t dah = tc::sdesc(sa, 2048, 128), dal = tc::sdesc(sal, 2048, 128);
+                if (j < nU) {
+                    const uint32_t acc = j > 0 ? 1u : 0u;
+                    for (int nb = 0; nb < nbk; ++nb) {
+                        const uint64_t dbh = tc::sdesc(sb + (uint32_t)nb * hb, 128, 256);
+                        const uint64_t dbl = tc::sdesc(sb + (uint32_t)(nbk + nb) * hb, 128, 256);
+                        const uint32_t d = tmem + (uint32_t)(nb * nb_u);
+                        tc::mma_bf16_pair(d, dah, dbh, id_u, acc);
+                        tc::mma_bf16_pair(d, dah, dbl, id_u, 1u);
+                        tc::mma_bf16_pair(d, dal, dbh, id_u, 1u);
+                    }
+                } else {
+#pragma unroll
+                    for (int kh = 0; kh < 2; ++kh) {
+                        const uint64_t vah = tc::sdesc(sa + 256u * kh, 128, 512);
+                        const uint64_t val = tc::sdesc(sa + ST2_VALO + 256u * kh, 128, 512);
+                        const uint64_t vb = tc::sdesc(sa + ST2_VB + 256u * kh, 128, 512);
+                        tc::mma_bf16_pair(tmem, vah, vb, id_v, (j > nU || kh > 0) ? 1u : 0u);
+                        tc::mma_bf16_pair(tmem, val, vb, id_v, 1u);
+                    }
+                }
+                issued = true;
+                tc::commit_pair(tc::smem_u32(&s_empty[s]));
+                if (j == nU - 1 || j == per - 1) tc::commit_pair(tc::smem_u32(&s_acc_full));
+                if (++s == NST2) { s = 0; ph ^= 1u; }
+                if (++j == per) j = 0;
+            }
+            if (err) {
+                s_err = 1;
+                atomicAdd(A.counters + CNT_TC_TIMEOUT, 1u);
+                if (issued) {
+                    tc::commit_pair_local(tc::smem_u32(&s_drain));
+                    tc::mbar_wait(tc::smem_u32(&s_drain), 0u, kMaxTries);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // -------------------------------- producers (both CTAs) --------------------------------
+        const uint32_t p = (uint32_t)(tid & (TP - 1)), h = (uint32_t)(tid / TP);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t cp = (uint32_t)((lane & 7) + 8 * warp), ch = (uint32_t)(lane >> 3);
+        float2* gs = A.gscr + (size_t)blockIdx.x * n * TP;
+        // the issuer's accumulator barriers (in rank 0), arrived on by both CTAs
+        const uint32_t r_acc_empty = tc::mapa(tc::smem_u32(&s_acc_empty), 0u);
+        const uint32_t r_acc_low = tc::mapa(tc::smem_u32(&s_acc_low), 0u);
+        bool err = false;
+        int qs = 0;
+        uint32_t qph = 0;
+        uint32_t accf = 0;
+        auto slice = [&](auto&& consume) {
+            const int s = qs;
+            if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_full[s]), qph, kMaxTries);
+            err = __any_sync(0xffffffffu, err || s_err != 0);
+            if (!err) consume(stage(s), stage(s) + ST2_ALO);
+            __syncwarp();
+            if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_empty[s]));
+            if (++qs == NST2) { qs = 0; qph ^= 1u; }
+        };
+        auto acc_wait = [&]() {
+            if (!err) err = !tc::mbar_wait(tc::smem_u32(&s_acc_full), accf & 1u, kMaxTries);
+            ++accf;
+            err = __any_sync(0xffffffffu, err);
+            tc::fence_after();
+        };
+        auto arrive_issuer = [&](uint32_t caddr) {
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0 && !err) tc::mbar_arrive_remote(caddr);
+        };
+        for (int q = q0; q < n_pairs; q += nq) {
+            const int tile = tile_of(q);
+            const int px = tile * TP + (int)p;
+            const bool valid = px < G.npix && 2 * q + (int)rank < A.n_tiles;
+            float acc_g = 0.f, acc_h = 0.f;
+            for (int fw = 0; fw < A.F.n; ++fw) {
+                const FreqC fc = A.F.f[fw];
+                float fg_r = 0.f, fg_i = 0.f, fh = 0.f;
+                for (int pass = 0; pass < npass; ++pass) {
+                const int eb0 = pass * ne;
+                for (int j = 0; j < nU; ++j)
+                    slice([&](const unsigned char* ahi, const unsigned char* alo) {
+                        consume_u(j * 8, cp, ch, ahi, alo, gs, vimg, want_h);
+                    });
+                if (want_h) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_vready));
+                }
+                err = tc::named_or(1, NPROD, err);
+                if (err) break;
+                const int nch = 4 * ((ne / 32 - (int)h + 3) / 4);
+                const int nbu = ne2 > 256 ? ne2 / 2 : ne2, ebu = nbu / 2;
+                auto ce0 = [&](int k) { return 32 * ((int)h + 4 * (k >> 2)) + 8 * (k & 3); };
+                auto recol = [&](int e) { return (e / ebu) * nbu + e % ebu; };
+                auto gload = [&](int k, float2 (&g)[8]) {
+                    const int e0 = ce0(k);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) g[i] = gs[(size_t)(eb0 + e0 + i) * TP + p];
+                };
+                auto gchunk = [&](int k, const float2 (&g)[8], float& ar, float& ai) {
+                    const int e0 = ce0(k);
+                    float vr[8], vi[8];
+                    tc::tmem_ld8(tmem + lane_off + (uint32_t)recol(e0), vr);
+                    tc::tmem_ld8(tmem + lane_off + (uint32_t)(recol(e0) + ebu), vi);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        ar = fmaf(g[i].x, vr[i], fmaf(g[i].y, vi[i], ar));
+                        ai = fmaf(g[i].x, vi[i], fmaf(-g[i].y, vr[i], ai));
+                    }
+                };
+                bool low = false;
+                auto release_low = [&]() {
+                    arrive_issuer(r_acc_low);
+                    low = true;
+                };
+                float2 ga[8], gb[8];
+                if (nch > 0) gload(0, ga);
+                acc_wait();
+                float gr = 0.f, gi = 0.f;
+                if (!err) {
+                    for (int k = 0; k < nch; k += 2) {
+                        if (!low && ce0(k) >= ebu) release_low();
+                        gload(k + 1, gb);
+                        gchunk(k, ga, gr, gi);
+                        if (k + 2 < nch) gload(k + 2, ga);
+                        gchunk(k + 1, gb, gr, gi);
+                    }
+                }
+                if (!low) release_low();
+                if (h > 0) {
+                    s_red[0][h - 1][p] = gr;
+                    s_red[1][h - 1][p] = gi;
+                }
+                err = tc::named_or(1, NPROD, err);
+                if (err) break;
+                if (h == 0) {
+                    fg_r += (gr + s_red[0][0][p] + s_red[0][1][p] + s_red[0][2][p]) * fc.w2;
+                    fg_i += (gi + s_red[1][0][p] + s_red[1][1][p] + s_red[1][2][p]) * fc.w2;
+                }
+                if (!want_h) {
+                    arrive_issuer(r_acc_empty);
+                    continue;
+                }
+                // V slices: the producers only pass the stage barriers (as in the single-CTA kernel)
+                for (int j = 0; j < nV; ++j) slice([&](const unsigned char*, const unsigned char*) {});
+                if (nch > 0) gload(0, ga);
+                acc_wait();
+                float hh = 0.f;
+                if (!err) {
+                    auto hchunk = [&](int k, const float2 (&g)[8]) {
+                        float v[8];
+                        tc::tmem_ld8(tmem + lane_off + (uint32_t)ce0(k), v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) hh = fmaf(g[i].x * g[i].x + g[i].y * g[i].y, v[i], hh);
+                    };
+                    for (int k = 0; k < nch; k += 2) {
+                        gload(k + 1, gb);
+                        hchunk(k, ga);
+                        if (k + 2 < nch) gload(k + 2, ga);
+                        hchunk(k + 1, gb);
+                    }
+                }
+                arrive_issuer(r_acc_empty);
+                if (h > 0) s_red[2][h - 1][p] = hh;
+                err = tc::named_or(1, NPROD, err);
+                if (err) break;
+                if (h == 0) fh += (hh + s_red[2][0][p] + s_red[2][1][p] + s_red[2][2][p]) * fc.w4;
+                }   // passes
+                if (err) break;
+                if (h == 0) {
+                    if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(fg_r, fg_i);
+                    if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = fh;
+                    acc_g += fg_r;
+                    acc_h += fh;
+                }
+            }
+            if (err) break;
+            if (valid && h == 0) {
+                if (A.gsum) A.gsum[px] = acc_g;
+                if (A.hsum) A.hsum[px] = acc_h;
+            }
+        }
+    }
+    tc::fence_before();
+    tc::cluster_sync();   // the peer is done with this CTA's shared memory and barriers
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc_pair(tmem, A.tmem_cols);
+}
 }  // namespace
 
 // rings of 64..256 elements in multiples of 64 in one pass over the elements of U and V,
@@ -587,13 +973,6 @@ bool tc_adjoint_supported(int n_elem) {
     return (n_elem >= 64 && n_elem <= 256 && n_elem % 64 == 0) || (n_elem % 256 == 0 && n_elem >= 512 && n_elem <= 1024);
 }
 
-cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s) {
-    const long long total = (long long)G.n_elem * G.npix;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 8192) blocks = 8192;
-    k_srec<<<(int)blocks, 256, 0, s>>>(G, tables, c, srec);
-    return cudaGetLastError();
-}
 
 size_t tc_b_images_bytes(int n_elem) {
     const size_t n = (size_t)n_elem;
@@ -611,18 +990,20 @@ size_t tc_aimage_elems(int n_elem, int npix) {
     return (size_t)((npix + TP - 1) / TP) * 2 * (size_t)(2 * n_elem / 8) * 1024;
 }
 
-cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, cudaStream_t s) {
-    if (!tc_adjoint_supported(G.n_elem) || !srec || !aimg) return cudaErrorInvalidValue;
+cudaError_t launch_tables_images(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F, void* aimg,
+                                 cudaStream_t s) {
+    if (!tc_adjoint_supported(G.n_elem) || !tables || !c || !aimg) return cudaErrorInvalidValue;
     const int n_tiles = (G.npix + TP - 1) / TP;
     const long long blocks = (long long)n_tiles * (G.n_elem / 16);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_synth_images<<<(int)blocks, 256, 0, s>>>(G, srec, F, (__nv_bfloat16*)aimg, tc_aimage_elems(G.n_elem, G.npix));
+    k_tables_images<<<(int)blocks, 256, 0, s>>>(G, tables, c, F, (__nv_bfloat16*)aimg,
+                                                tc_aimage_elems(G.n_elem, G.npix));
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& F, const void* images, float2* gscr,
                               int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
-                              cudaStream_t s) {
+                              cudaStream_t s, int variant) {
     const int n = G.n_elem;
     if (!tc_adjoint_supported(n) || !aimg) return cudaErrorInvalidValue;
     TcArgs A;
@@ -648,10 +1029,26 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * A.n_e)) cols <<= 1;
     A.tmem_cols = cols;
-    // NST stages of 40 KB: most of the SM's shared memory, so one CTA (one TMEM owner) per SM
+    cudaError_t e;
+    // variant 1: CTA pairs (8 stages of 24 KB); 0 and 2: one CTA per tile (5 stages of 40 KB);
+    // either way most of the SM's shared memory, so one CTA (one TMEM owner) per SM
+    const int n_pairs = (A.n_tiles + 1) / 2;
+    if (variant == 1 && n_ctas >= 2) {
+        const int sm2 = NST2 * (int)ST2_BYTES;
+        const int grid2 = 2 * (n_ctas / 2 < n_pairs ? n_ctas / 2 : n_pairs);
+        if (A.npass == 1) {
+            e = cudaFuncSetAttribute(k_adjoint_tc2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+            if (e != cudaSuccess) return e;
+            k_adjoint_tc2<false><<<grid2, NTHR_A, sm2, s>>>(A);
+        } else {
+            e = cudaFuncSetAttribute(k_adjoint_tc2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+            if (e != cudaSuccess) return e;
+            k_adjoint_tc2<true><<<grid2, NTHR_A, sm2, s>>>(A);
+        }
+        return cudaGetLastError();
+    }
     const int sm = NST * (int)ST_BYTES;
     const int grid = n_ctas < A.n_tiles ? n_ctas : A.n_tiles;
-    cudaError_t e;
     if (A.npass == 1) {
         e = cudaFuncSetAttribute(k_adjoint_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;

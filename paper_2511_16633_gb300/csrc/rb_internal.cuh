@@ -259,7 +259,6 @@ struct WsLayout {
     size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
     size_t tcfwd;      // tensor-core path: partial D blocks of the forward
     size_t aimg;       // tensor-core path: A operand images of the adjoint, [n_freq][...] bf16
-    size_t srec;       // tensor-core path: synthesis records, [n_elem][npix] float4
     size_t cgv;        // CG variant: x, r, p, q vectors, [4][npix] float
     size_t tof;        // time-of-flight guess: link records, ray lengths and coefficients, pixel sums
     size_t total;
@@ -301,18 +300,19 @@ struct LinkRec {
 // ---------------------------------------------------------------------------
 cudaError_t launch_elem_positions(const GeoDev& G, float4* elem_xy, cudaStream_t s);
 cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, float4* cells, cudaStream_t s);
-// Rays; with keys set also the gridding: keys are reset here, tables and/or srec are
-// written for every (element, pixel).
+// Rays; with keys set also the gridding: keys are reset here, and the tables (or, with
+// images, the operand images) are written for every (element, pixel).
 // traced (nullable): recorded on s once the rays' end records are written, before the
 // rasteriser and the resolve pass.  keys_ready (nullable): the caller resets the keys
 // (all ones) on another stream and records this event; s waits for it before the
 // rasteriser instead of resetting them itself
 // images (nullable, with F): the mixed path's operand images of every frequency of F,
-// written by the resolve pass itself (tables and srec then unused).
+// written by the resolve pass itself (tables then unused).  raster_mode: 0 the rule
+// (along the tubes from 4 pixels per tube at the ring), 1 along the tubes, 2 across.
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
+                         void* keys, rb_cell* tables, void* verts, const float* c, uint32_t* counters,
                          cudaStream_t s, cudaEvent_t traced = nullptr, cudaEvent_t keys_ready = nullptr,
-                         const FreqSet* F = nullptr, void* images = nullptr);
+                         const FreqSet* F = nullptr, void* images = nullptr, int raster_mode = 0);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);
@@ -343,11 +343,12 @@ cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F,
                               cudaStream_t s);
 // A images of the adjoint (and optionally the forward's G images) from the synthesis records
 size_t tc_aimage_elems(int n_elem, int npix);
-cudaError_t launch_synth_images(const GeoDev& G, const float4* srec, const FreqSet& F, void* aimg, cudaStream_t s);
+// operand images of F from the caller's tables (the single-operator entry points)
+cudaError_t launch_tables_images(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F, void* aimg,
+                                 cudaStream_t s);
 cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& F, const void* images, float2* gscr,
                               int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
-                              cudaStream_t s);
-cudaError_t launch_srec(const GeoDev& G, const rb_cell* tables, const float* c, float4* srec, cudaStream_t s);
+                              cudaStream_t s, int variant = 0);
 cudaError_t launch_cg_init(const GeoDev& G, const float* gsum, const float* hsum, int precond, float* x, float* r,
                            float* p, double* part, double* dbl, double eps_rel, cudaStream_t s);
 cudaError_t launch_cg_step(const GeoDev& G, const float* hsum, int precond, int k, float* x, float* r, float* p,
@@ -363,6 +364,7 @@ cudaError_t launch_tof_step(const GeoDev& G, const Vtx* verts, const rb_ray_end*
 cudaError_t launch_cg_history(const double* dbl, int iters, double* hist, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* part, int n, double* dbl, int slot, double scale, int accumulate,
                                 cudaStream_t s);
+// limit_word (nullable, host-mapped): set to the lost-ray count when the update lost rays
 cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir,
                           float* dc_out, double* part, double* dbl, uint32_t* counters, rb_diag* diag,
-                          double eps_rel, int step_mode, int phase, cudaStream_t s);
+                          double eps_rel, int step_mode, int phase, cudaStream_t s, uint32_t* limit_word = nullptr);

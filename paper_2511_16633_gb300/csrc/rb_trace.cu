@@ -630,15 +630,13 @@ __device__ __forceinline__ bool resolve_entry(const GeoDev& G, const Vtx* __rest
     return true;
 }
 
-// Completes every table record (plain path) and/or synthesis record from the keys.
-// Holes stay all ones.  Thread = pixel (its coordinates and support test computed
-// once), looping over the elements t = blockIdx.y, blockIdx.y + gridDim.y, ...;
-// consecutive threads take consecutive pixels, so every key load and record store is
-// coalesced.
+// Completes every table record (plain path) from the keys.  Holes stay all ones.
+// Thread = pixel (its coordinates and support test computed once), looping over the
+// elements t = blockIdx.y, blockIdx.y + gridDim.y, ...; consecutive threads take
+// consecutive pixels, so every key load and record store is coalesced.
 __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict__ verts,
                                                  const rb_ray_end* __restrict__ ends,
                                                  const unsigned long long* __restrict__ keys, rb_cell* __restrict__ tables,
-                                                 const float* __restrict__ c, float4* __restrict__ srec,
                                                  uint32_t* __restrict__ counters, uint32_t kq_magic) {
     uint32_t holes = 0;   // support pixels that no triangle of the fan covered
     for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < G.npix; pix += gridDim.x * blockDim.x) {
@@ -647,30 +645,17 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
         const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
         const long long jx = 2LL * ix - (G.nx - 1), jy = 2LL * iy - (G.ny - 1);
         const bool in_support = jx * jx + jy * jy <= G.r2max;
-        const float c_px = srec ? __ldg(c + pix) : 0.f;
         for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y) {
             const size_t u = (size_t)t * G.npix + pix;
             rb_cell rec;
             if (!resolve_entry(G, verts, ends, keys[u], t, X, Y, kq_magic, rec)) {
-                if (tables) {
-                    rb_cell hole;
-                    hole.tag = RB_HOLE;
-                    hole.tkey = RB_HOLE;
-                    hole.q = __uint_as_float(RB_HOLE);
-                    hole.l = __uint_as_float(RB_HOLE);
-                    tables[u] = hole;
-                }
-                if (srec) srec[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                rec.tag = RB_HOLE;
+                rec.tkey = RB_HOLE;
+                rec.q = __uint_as_float(RB_HOLE);
+                rec.l = __uint_as_float(RB_HOLE);
                 if (in_support) ++holes;
-                continue;
             }
-            if (tables) tables[u] = rec;
-            if (srec) {
-                DF ex, ey;
-                elem_pos(G, t, ex, ey);
-                srec[u] = synth_record(rec, c_px, pixel_elem_dist(G, ix, iy, ex, ey), G.inv_cref, G.inv_cref_lo,
-                                       G.j_floor);
-            }
+            tables[u] = rec;
         }
     }
     for (int o = 16; o > 0; o >>= 1) holes += __shfl_down_sync(0xffffffffu, holes, o);
@@ -740,8 +725,9 @@ __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __r
 }  // namespace
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
-                         void* keys, rb_cell* tables, void* verts, const float* c, float4* srec, uint32_t* counters,
-                         cudaStream_t s, cudaEvent_t traced, cudaEvent_t keys_ready, const FreqSet* F, void* images) {
+                         void* keys, rb_cell* tables, void* verts, const float* c, uint32_t* counters,
+                         cudaStream_t s, cudaEvent_t traced, cudaEvent_t keys_ready, const FreqSet* F, void* images,
+                         int raster_mode) {
     rb_rays S{};
     int ws = 0;
     if (samples && samples->vx) {
@@ -753,7 +739,7 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     Vtx* V = (Vtx*)verts;
     const bool fused = images != nullptr;
     if (fused && (!F || F->n < 1 || !c || (G.n_elem % 16) != 0)) return cudaErrorInvalidValue;
-    if (grid && (!V || (!tables && !srec && !fused))) return cudaErrorInvalidValue;
+    if (grid && (!V || (!tables && !fused))) return cudaErrorInvalidValue;
     unsigned long long* K = (unsigned long long*)keys;
     if (grid && !keys_ready) {
         cudaError_t e = cudaMemsetAsync(K, 0xff, (size_t)G.n_elem * G.npix * sizeof(unsigned long long), s);
@@ -774,7 +760,8 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     const double tube_px = 2.0 * G.R_d * RB_PI_D / (double)G.n_rays / G.h_d;
     const uint32_t ntm = (uint32_t)(0x100000000ull / (uint32_t)(G.n_rays - 1));
     const size_t ssm = (size_t)G.ny * sizeof(short2);
-    if (tube_px >= RASTER_ALONG_K_MIN_PX)
+    const bool along = raster_mode == 1 || (raster_mode == 0 && tube_px >= RASTER_ALONG_K_MIN_PX);
+    if (along)
         k_raster<true><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, ntm);
     else
         k_raster<false><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, ntm);
@@ -792,7 +779,7 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     int bx = (G.npix + 255) / 256;
     int by = 1;
     while (by < 16 && by * 2 <= G.n_elem && (long long)bx * by < (long long)nsm * 16) by *= 2;
-    k_resolve<<<dim3(bx, by), 256, 0, s>>>(G, V, ends, K, tables, c, srec, counters, kq_magic);
+    k_resolve<<<dim3(bx, by), 256, 0, s>>>(G, V, ends, K, tables, counters, kq_magic);
     return cudaGetLastError();
 }
 

@@ -183,8 +183,13 @@ __global__ void __launch_bounds__(RT) k_cg_p(GeoDev G, const float* __restrict__
         if (in_support(G, p)) pv[p] = fmaf(beta, pv[p], cg_minv(hsum, p, precond, eps, hm) * r[p]);
 }
 
-__global__ void k_finish(const double* __restrict__ dbl, const uint32_t* __restrict__ cnt, rb_diag* __restrict__ diag) {
+// The diagnostics record (when asked for), and the lost-ray count into the caller
+// stream's host-mapped limit word when rays were lost (read by the next update call).
+__global__ void k_finish(const double* __restrict__ dbl, const uint32_t* __restrict__ cnt, rb_diag* __restrict__ diag,
+                         uint32_t* __restrict__ limit_word) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (limit_word && cnt[CNT_LOST] > 0) *(volatile uint32_t*)limit_word = cnt[CNT_LOST];
+    if (!diag) return;
     rb_diag d;
     d.dc_norm = sqrt(dbl[DBL_NORM2]);
     d.alpha = dbl[DBL_ALPHA];
@@ -203,7 +208,7 @@ __global__ void k_finish(const double* __restrict__ dbl, const uint32_t* __restr
 // Launch sequence pieces used by rb_hf_update (rb_api.cu).
 cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const float* hsum, float* pdir, float* dc_out,
                           double* part, double* dbl, uint32_t* counters, rb_diag* diag, double eps_rel, int step_mode,
-                          int phase, cudaStream_t s) {
+                          int phase, cudaStream_t s, uint32_t* limit_word) {
     switch (phase) {
         case 0: {  // eps, direction, numerator
             k_hsum_part<<<RB, RT, 0, s>>>(G, hsum, part);
@@ -215,7 +220,7 @@ cudaError_t launch_update(const GeoDev& G, float* c, const float* gsum, const fl
         case 1: {  // apply the step and finish
             k_apply<<<RB, RT, 0, s>>>(G, c, pdir, dbl, step_mode, dc_out, part);
             k_sum_part<<<1, RT, 0, s>>>(part, RB, dbl, DBL_NORM2, 1.0, 0);
-            if (diag) k_finish<<<1, 32, 0, s>>>(dbl, counters, diag);
+            if (diag || limit_word) k_finish<<<1, 32, 0, s>>>(dbl, counters, diag, limit_word);
             break;
         }
         default:

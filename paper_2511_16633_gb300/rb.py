@@ -18,6 +18,8 @@ from . import _build
 RB_OK, RB_ERR_ARG, RB_ERR_SHAPE, RB_ERR_WORKSPACE, RB_ERR_CUDA, RB_ERR_LIMIT, RB_ERR_UNSUPPORTED = range(7)
 RB_PREC_FP32, RB_PREC_BF16X3 = 0, 1
 RB_STEP_EXACT, RB_STEP_DIAG = 0, 1
+RB_TUNE_RULE, RB_TUNE_RASTER_ALONG, RB_TUNE_RASTER_ACROSS = 0, 1, 2
+RB_TUNE_ADJ_PAIR, RB_TUNE_ADJ_SINGLE = 1 << 2, 2 << 2
 RB_MAX_FREQ = 16
 RB_MAX_CG = 24
 RB_MAX_TOF_ITERS = 16
@@ -48,7 +50,7 @@ class rb_rays(ctypes.Structure):
 
 class rb_update_params(ctypes.Structure):
     _fields_ = [("outlier_frac", ctypes.c_double), ("eps_rel", ctypes.c_double), ("step_mode", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("stage_events", ctypes.c_void_p)]
+                ("tune", ctypes.c_int32), ("stage_events", ctypes.c_void_p)]
 
 
 STAGES = ("fields", "trace_grid", "link", "images", "adjoint", "direction", "forward", "apply")
@@ -224,10 +226,11 @@ def stage_event_array(events):
 
 
 def rb_hf_update(geom, c_inout, alpha0, freqs, p_obs, ws, outlier_frac=0.01, eps_rel=1e-3, step_mode=RB_STEP_EXACT,
-                 prec=RB_PREC_FP32, dc_out=None, diag_out=None, stream=None, stage_events=None):
-    """stage_events: None or a ctypes array from stage_event_array (kept alive by the caller)."""
+                 prec=RB_PREC_FP32, dc_out=None, diag_out=None, stream=None, stage_events=None, tune=RB_TUNE_RULE):
+    """stage_events: None or a ctypes array from stage_event_array (kept alive by the caller);
+    tune: the rb_update_params.tune choice (tune.py picks it by timing)."""
     fa, nf = _freqs(freqs)
-    prm = rb_update_params(float(outlier_frac), float(eps_rel), int(step_mode), 0,
+    prm = rb_update_params(float(outlier_frac), float(eps_rel), int(step_mode), int(tune),
                            ctypes.cast(stage_events, ctypes.c_void_p) if stage_events is not None else None)
     code = load().rb_hf_update(ctypes.byref(geom), _ptr(c_inout), _ptr(alpha0), fa, nf, _ptr(p_obs), ctypes.byref(prm),
                                int(prec), _ptr(dc_out), _ptr(diag_out), _ptr(ws), ws.numel(), _stream(stream))
@@ -235,10 +238,11 @@ def rb_hf_update(geom, c_inout, alpha0, freqs, p_obs, ws, outlier_frac=0.01, eps
 
 
 def rb_cg_update(geom, c_inout, alpha0, freqs, p_obs, ws, cg_iters, precond=True, outlier_frac=0.01, eps_rel=1e-3,
-                 prec=RB_PREC_FP32, dc_out=None, hist_out=None, diag_out=None, stream=None, stage_events=None):
+                 prec=RB_PREC_FP32, dc_out=None, hist_out=None, diag_out=None, stream=None, stage_events=None,
+                 tune=RB_TUNE_RULE):
     """CG variant of the update; hist_out: None or a float64 device tensor of cg_iters + 1."""
     fa, nf = _freqs(freqs)
-    prm = rb_update_params(float(outlier_frac), float(eps_rel), RB_STEP_EXACT, 0,
+    prm = rb_update_params(float(outlier_frac), float(eps_rel), RB_STEP_EXACT, int(tune),
                            ctypes.cast(stage_events, ctypes.c_void_p) if stage_events is not None else None)
     code = load().rb_cg_update(ctypes.byref(geom), _ptr(c_inout), _ptr(alpha0), fa, nf, _ptr(p_obs), ctypes.byref(prm),
                                int(cg_iters), 1 if precond else 0, int(prec), _ptr(dc_out), _ptr(hist_out),

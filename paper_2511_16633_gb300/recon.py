@@ -72,9 +72,10 @@ class Reconstruction:
     """One problem resident on the device; update(j) runs frequency set j."""
 
     def __init__(self, cfg, c_init, alpha0, p_obs, prec=rb.RB_PREC_FP32, outlier_frac=0.01, eps_rel=1e-3,
-                 step_mode=rb.RB_STEP_EXACT, device="cuda", cg_iters=0, cg_precond=True):
+                 step_mode=rb.RB_STEP_EXACT, device="cuda", cg_iters=0, cg_precond=True, tune=rb.RB_TUNE_RULE):
         """cg_iters > 0 solves each set's linear equation by that many CG iterations
-        (rb_cg_update) instead of the one-step update."""
+        (rb_cg_update) instead of the one-step update.  tune: an rb_update_params.tune value,
+        or "auto" to time the choices on the first set (tune.py; cached per problem shape)."""
         import torch
         self.cfg = cfg
         self.geom = rb.geometry_from_config(cfg)
@@ -90,6 +91,13 @@ class Reconstruction:
         self.dc = torch.empty_like(self.c)
         self.diag = torch.zeros(48, dtype=torch.uint8, device=self.device)
         self.norms: List[float] = []
+        self.tune_info = None
+        if tune == "auto":
+            from .tune import tune_update
+            s = cfg.sets[0]
+            tune, self.tune_info = tune_update(self.geom, self.c, self.alpha0, [cfg.freqs_hz[i] for i in s],
+                                               self.p_obs[s[0]:s[-1] + 1], prec)
+        self.tune = int(tune)
 
     def update(self, j: int, stream=None):
         s = self.cfg.sets[j]
@@ -100,10 +108,10 @@ class Reconstruction:
         if self.cg_iters > 0:
             rb.rb_cg_update(self.geom, self.c, self.alpha0, freqs, self.p_obs[lo:hi], self.ws, self.cg_iters,
                             self.cg_precond, self.outlier_frac, self.eps_rel, self.prec, self.dc, None, self.diag,
-                            stream)
+                            stream, tune=self.tune)
         else:
             rb.rb_hf_update(self.geom, self.c, self.alpha0, freqs, self.p_obs[lo:hi], self.ws, self.outlier_frac,
-                            self.eps_rel, self.step_mode, self.prec, self.dc, self.diag, stream)
+                            self.eps_rel, self.step_mode, self.prec, self.dc, self.diag, stream, tune=self.tune)
 
     def diagnostics(self) -> dict:
         return rb.decode_diag(self.diag)

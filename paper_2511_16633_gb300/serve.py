@@ -151,14 +151,15 @@ class _Running:
     side-stream fork and join become edges inside the graph, so the sweeps of
     different jobs share no stream.  Without it, one set is issued at a time."""
 
-    def __init__(self, job: Job, prob: Problem, device, graphs: bool = False):
+    def __init__(self, job: Job, prob: Problem, device, graphs: bool = False, autotune: bool = False):
         import torch
 
         from .recon import Reconstruction
         self.job = job
         self.stream = torch.cuda.Stream(device=device)
         with torch.cuda.stream(self.stream):
-            self.rec = Reconstruction(job.cfg, prob.c_init, prob.alpha0, prob.p_obs, prec=job.prec, device=device)
+            self.rec = Reconstruction(job.cfg, prob.c_init, prob.alpha0, prob.p_obs, prec=job.prec, device=device,
+                                      tune="auto" if autotune else rb.RB_TUNE_RULE)
         self.next_set = 0
         self.in_flight = 0
         self.event = None
@@ -197,13 +198,15 @@ class _Running:
 
 
 def run(jobs: Sequence[Job], problems: Dict[int, Problem], budget: int, max_slots: int, device="cuda",
-        keep: Optional[Callable[[Job, object], None]] = None, realtime: bool = True, graphs: bool = False) -> dict:
+        keep: Optional[Callable[[Job, object], None]] = None, realtime: bool = True, graphs: bool = False,
+        autotune: bool = False) -> dict:
     """Run the jobs under the scheduler; arrival times are honoured on the host clock
     (``realtime``) or ignored (every job available at once).  ``keep(job, c)`` receives
     each finished job's sound-speed map (a device tensor) before its buffers go.
     ``graphs``: each job's sweep is captured into one CUDA graph at admission and
-    replayed (the capture counts in the job's latency).  Returns per-job times and the
-    totals."""
+    replayed (the capture counts in the job's latency).  ``autotune``: each job runs with
+    the kernel-shape choice tune.py measured fastest for its shape (timed at the first
+    admission of a shape, then cached).  Returns per-job times and the totals."""
     import torch
     sched = Scheduler([dataclasses.replace(j, arrival=j.arrival if realtime else 0.0) for j in jobs], budget,
                       max_slots)
@@ -214,7 +217,7 @@ def run(jobs: Sequence[Job], problems: Dict[int, Problem], budget: int, max_slot
     while not sched.idle():
         now = time.perf_counter() - t0
         for j in sched.admit(now):
-            r = _Running(j, problems[j.jid], device, graphs)
+            r = _Running(j, problems[j.jid], device, graphs, autotune)
             running[j.jid] = r
             r.launch()
         peak_used = max(peak_used, sched.used)
@@ -268,6 +271,9 @@ def main():
     ap.add_argument("--seed", type=int, default=20251116 + 4)
     ap.add_argument("--graphs", choices=["off", "on", "both"], default="off",
                     help="capture each request's sweep into one CUDA graph (both: measure each way)")
+    ap.add_argument("--tune", choices=["off", "on", "both"], default="off",
+                    help="run each request with the kernel-shape choice measured fastest for its shape (tuned "
+                         "before the timed runs; both: measure with and without)")
     args = ap.parse_args()
     dev = torch.device("cuda:0")
     rings = tuple(int(x) for x in args.rings.split(","))
@@ -286,13 +292,31 @@ def main():
         torch.cuda.empty_cache()
     out = {"mode": args.mode, "n": args.n, "budget_gb": budget / 1e9, "slots": args.slots,
            "workload": [c.name for _, c in items]}
-    for pol in (["mixed", "plain"] if args.prec == "both" else [args.prec]):
+    pols = ["mixed", "plain"] if args.prec == "both" else [args.prec]
+    tunes = [False, True] if args.tune == "both" else [args.tune == "on"]
+    if True in tunes:
+        # the tuner's timings, per shape, before anything is timed (cached for the runs)
+        from .recon import Reconstruction
+        choices = {}
+        for pol in pols:
+            for k, (_, cfg) in enumerate(items):
+                rec = Reconstruction(cfg, problems[k].c_init, problems[k].alpha0, problems[k].p_obs,
+                                     prec=precision_for(cfg, pol), device=dev, tune="auto")
+                choices[f"{cfg.name}/{pol}"] = rec.tune_info
+                del rec
+                torch.cuda.empty_cache()
+        out["tune"] = choices
+    for pol in pols:
         for gr in ([False, True] if args.graphs == "both" else [args.graphs == "on"]):
-            jobs = [Job(k, cfg, t, precision_for(cfg, pol), footprint_bytes(cfg, precision_for(cfg, pol)))
-                    for k, (t, cfg) in enumerate(items)]
-            res = run(jobs, problems, budget, args.slots, dev, realtime=(args.mode == "serve"), graphs=gr)
-            out[pol + ("_graphs" if gr and args.graphs == "both" else "")] = res
-            torch.cuda.empty_cache()
+            for tu in tunes:
+                jobs = [Job(k, cfg, t, precision_for(cfg, pol), footprint_bytes(cfg, precision_for(cfg, pol)))
+                        for k, (t, cfg) in enumerate(items)]
+                res = run(jobs, problems, budget, args.slots, dev, realtime=(args.mode == "serve"), graphs=gr,
+                          autotune=tu)
+                name = pol + ("_graphs" if gr and args.graphs == "both" else "") + \
+                    ("_tuned" if tu and args.tune == "both" else "")
+                out[name] = res
+                torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
 
 

@@ -106,6 +106,10 @@ def test_argument_errors_are_synchronous(lib):
     prm = rb.rb_update_params(0.01, 1e-3, 9)
     assert lib.rb_hf_update(ctypes.byref(g), fake, fake, f1, 1, fake, ctypes.byref(prm), 0, None, None, fake, 1 << 30,
                             None) == rb.RB_ERR_ARG
+    for bad_tune in (3, 12, 16, -1):
+        prm = rb.rb_update_params(0.01, 1e-3, 0, bad_tune)
+        assert lib.rb_hf_update(ctypes.byref(g), fake, fake, f1, 1, fake, ctypes.byref(prm), 0, None, None, fake,
+                                1 << 30, None) == rb.RB_ERR_ARG
     prm = rb.rb_update_params(0.01, 1e-3, 0)
     for iters, pre in ((0, 1), (rb.RB_MAX_CG + 1, 1), (4, 2)):
         assert lib.rb_cg_update(ctypes.byref(g), fake, fake, f1, 1, fake, ctypes.byref(prm), iters, pre, 0, None, None,

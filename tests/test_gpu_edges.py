@@ -152,3 +152,52 @@ def test_ring_of_512_elements_bf16x3_update(dev, n_elem):
     assert d["tc_timeouts"] == 0
     assert d["kept"] == ref.n_kept and d["zeroed"] == ref.n_zeroed
     assert e <= 1e-3
+
+
+@pytest.mark.parametrize("which", ["hf", "cg"])
+def test_lost_rays_reported_by_the_next_update(dev, which):
+    """Rays still inside the ring after max_steps are lost: the update that lost them counts
+    them (rb_diag) and sets its stream's limit word; the next update call from that stream
+    returns RB_ERR_LIMIT and launches nothing (c does not move); the call after runs again,
+    and a call with another workspace on that stream discards the report it left.
+    Here 100 steps of 0.8 mm reach receivers up to 80 mm away but not across the 100 mm
+    diameter of the ring."""
+    cfg = rbgen.tiny()
+    inp = rbgen.make_inputs(cfg)
+    geom = rb.geometry_from_config(cfg, max_steps=100)
+    stream = torch.cuda.Stream(device=dev)
+    freqs = [cfg.freqs_hz[0]]
+    with torch.cuda.stream(stream):
+        c = _t(inp.c_init, dev)
+        a0 = _t(inp.alpha0, dev)
+        p = torch.zeros((1, geom.n_elem, geom.n_elem), dtype=torch.complex64, device=dev)
+        ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+        diag = torch.zeros(48, dtype=torch.uint8, device=dev)
+
+        def update():
+            if which == "hf":
+                rb.rb_hf_update(geom, c, a0, freqs, p, ws, diag_out=diag, stream=stream)
+            else:
+                rb.rb_cg_update(geom, c, a0, freqs, p, ws, 2, diag_out=diag, stream=stream)
+
+        update()
+        stream.synchronize()
+        d = rb.decode_diag(diag)
+        assert d["lost_rays"] > 0
+        c_before = c.clone()
+        diag.zero_()
+        with pytest.raises(rb.RbError) as ei:
+            update()
+        assert ei.value.code == rb.RB_ERR_LIMIT
+        stream.synchronize()
+        assert torch.equal(c, c_before) and not diag.any()   # nothing was launched
+        update()                          # reported once: this one runs
+        stream.synchronize()
+        assert not torch.equal(c, c_before)
+        assert rb.decode_diag(diag)["lost_rays"] > 0
+        # a new problem on the same stream (another workspace) does not inherit the report
+        ws_first = ws                     # kept alive, so the new workspace is another buffer
+        ws = rb.workspace(geom, 1, rb.RB_PREC_FP32, dev)
+        assert ws.data_ptr() != ws_first.data_ptr()
+        update()
+        stream.synchronize()

@@ -78,3 +78,52 @@ def test_graph_mode_gives_the_eager_results(dev):
     assert sorted(j["updates"] for j in res["jobs"]) == sorted(len(c.sets) for c in cfgs)
     for k in range(len(cfgs)):
         assert np.array_equal(graphed[k], eager[k]), k
+
+
+@pytest.mark.parametrize("policy", ["mixed", "plain"])
+def test_served_results_match_the_oracle(dev, policy):
+    """Four requests of different rings and grids (64, 128 on a grid with a partial pixel
+    tile, 40 and 192 elements) served at once, each fed the oracle's own synthetic data:
+    every final sound-speed map within 0.05 m/s RMS of the oracle's sweep on that data."""
+    from oracle import geometry as ogeom
+    from oracle import update as oupd
+    cfgs = _cfgs()[:4]
+    problems, refs = {}, {}
+    for k, c in enumerate(cfgs):
+        inp = rbgen.make_inputs(c)
+        g = ogeom.from_config(c)
+        p = oupd.synth_data(g, inp.c_init, inp.c_true, inp.alpha0, c.freqs_hz, inp.noise_re, inp.noise_im)
+        refs[k], _ = oupd.sweep(g, inp.c_init, inp.alpha0, c.freqs_hz, c.sets, p)
+        problems[k] = serve.Problem(inp.c_init, inp.alpha0, torch.as_tensor(p.astype(np.complex64), device=dev))
+    out, res = _run(cfgs, problems, dev, policy, budget=1 << 40, slots=len(cfgs))
+    assert res["updates"] == sum(len(c.sets) for c in cfgs)
+    for k, c in enumerate(cfgs):
+        sup = ogeom.support_mask(ogeom.from_config(c))
+        rms = float(np.sqrt(np.mean((out[k] - refs[k])[sup] ** 2)))
+        print(f"served {c.name} ({policy}): c RMS difference to the oracle {rms:.3g} m/s")
+        assert rms <= 0.05, (k, rms)
+
+
+def test_autotuned_choice_is_bit_identical_and_cached(dev, tmp_path, monkeypatch):
+    """The tuner's candidates (both raster mappings, both forms of the adjoint) give the
+    same map bit for bit (the choice changes only the time); it returns one of them with
+    a time for each, and the second call for the same shape comes from the cache (also
+    written to RB_TUNE_CACHE)."""
+    from paper_2511_16633_gb300 import tune
+    from paper_2511_16633_gb300.recon import Reconstruction
+    monkeypatch.setenv("RB_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(tune, "_cache", {})
+    cfg = _cfgs()[1]
+    prob = serve.make_problem(cfg, dev)
+    maps = []
+    cands = tune.candidates(rb.RB_PREC_BF16X3)
+    for t in cands:
+        rec = Reconstruction(cfg, prob.c_init, prob.alpha0, prob.p_obs, prec=rb.RB_PREC_BF16X3, device=dev, tune=t)
+        maps.append(rec.sweep().cpu().numpy())
+    assert all(np.array_equal(m, maps[0]) for m in maps[1:])
+    rec = Reconstruction(cfg, prob.c_init, prob.alpha0, prob.p_obs, prec=rb.RB_PREC_BF16X3, device=dev, tune="auto")
+    assert rec.tune in cands and set(rec.tune_info["ms"]) == {tune.name(t) for t in cands}
+    assert np.array_equal(rec.sweep().cpu().numpy(), maps[0])
+    monkeypatch.setattr(tune, "_cache", {})
+    again = tune.cached(rec.geom, len(cfg.sets[0]), rb.RB_PREC_BF16X3)    # from the file
+    assert again is not None and again["tune"] == rec.tune

@@ -19,7 +19,17 @@ tube width J = |Q| passes through zero, is ill-conditioned: Q agrees to ~1e-6 of
 scale between FP32 and FP64, which is a percent of J there.  Those few entries carry
 most of the difference (at 512^2, set 3: the largest 1 % of pixels hold 77 % of its
 norm, 3.5e-3 relative), so such sets are held to 2e-2 (1e-2 on the step scale and
-||dc||), and the whole sweep to the 0.05 m/s bound.
+||dc||).
+
+The independent sweeps are held to the 0.05 m/s bound while the media they pass
+through leave at most 0.1 % of the rays past a caustic (the whole sweep at 256^2, the
+first three sets at 512^2).  Beyond that the map from c to the update is not
+continuous: where fans fold, a first-arrival winner flips between triangles of
+different sheets of the fan under any perturbation of c, and its Green's function
+changes by O(1) there.  A 0.001 m/s difference between the two sweeps after set 2 at
+512^2 grows to 0.12 m/s after set 3 (the same update from the same c differs by only
+0.02 m/s) and 1.1 m/s after set 4, on either path; those values are reported, not
+held to the bound.
 """
 import math
 
@@ -111,9 +121,15 @@ def test_sweep_per_set_against_the_oracle(dev, name, prec):
           f"kept diff, sweep c RMS diff [m/s], rays past a caustic")
     for r in rows:
         print(f"  {r[0]}  {r[1]:.3g}  {r[2]:+.2g}  {r[3]:+.2g}  {r[4]:+d}  {r[5]:.3g}  {r[6]}")
+    n_rays = g.n_elem * g.n_rays
+    smooth = True     # every medium so far leaves at most 0.1 % of the rays past a caustic
     for (j, e, ra, rn, dk, crms, ncau) in rows:
         bar, bar_s = (1e-3, 1e-3) if ncau == 0 else (2e-2, 1e-2)
         assert e <= bar, (j, e, ncau)
         assert abs(ra) <= bar_s and abs(rn) <= bar_s, (j, ra, rn)
         assert abs(dk) <= 1e-3 * sets[j]["kept"]
-    assert rows[-1][5] <= 0.05, rows[-1][5]
+        smooth = smooth and ncau <= 1e-3 * n_rays
+        if smooth:
+            assert crms <= 0.05, (j, crms)
+    if name == "breast256":
+        assert smooth     # the whole sweep is held to the bound

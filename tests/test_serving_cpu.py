@@ -60,3 +60,23 @@ def test_precision_policy_covers_the_tensor_core_ring_sizes():
         assert rb.tc_supported(n) == tc
         assert serve.precision_for(cfg, "mixed") == (rb.RB_PREC_BF16X3 if tc else rb.RB_PREC_FP32)
         assert serve.precision_for(cfg, "plain") == rb.RB_PREC_FP32
+
+
+def test_tune_cache_keys_and_file_round_trip(tmp_path, monkeypatch):
+    """The tuner's cache (host logic): one key per problem shape and precision, entries kept
+    in memory and, with RB_TUNE_CACHE set, in a JSON file another process reads back."""
+    import rbgen
+    from paper_2511_16633_gb300 import rb, tune
+    monkeypatch.setenv("RB_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(tune, "_cache", {})
+    g1 = rb.geometry_from_config(rbgen.tiny())
+    g2 = rb.geometry_from_config(rbgen.tiny(n_rays=48))
+    assert tune.key(g1, 1, rb.RB_PREC_BF16X3) != tune.key(g2, 1, rb.RB_PREC_BF16X3)
+    assert tune.key(g1, 1, rb.RB_PREC_BF16X3) != tune.key(g1, 1, rb.RB_PREC_FP32)
+    assert tune.cached(g1, 1, rb.RB_PREC_BF16X3) is None
+    assert len(tune.candidates(rb.RB_PREC_BF16X3)) == 4 and len(tune.candidates(rb.RB_PREC_FP32)) == 2
+    assert tune.name(rb.RB_TUNE_RASTER_ACROSS | rb.RB_TUNE_ADJ_PAIR) == "raster across tubes, adjoint CTA pairs"
+    entry = {"tune": rb.RB_TUNE_RASTER_ACROSS, "choice": "raster across tubes", "ms": {"a": 1.0, "b": 0.9}}
+    tune._store_file(tune.key(g1, 1, rb.RB_PREC_BF16X3), entry)
+    assert tune.cached(g1, 1, rb.RB_PREC_BF16X3) == entry
+    assert tune.cached(g2, 1, rb.RB_PREC_BF16X3) is None
