@@ -193,8 +193,7 @@ def run_ours(args):
             return rb.RB_TUNE_RULE
         if prec not in tuned:
             from paper_2511_16633_gb300.tune import tune_update
-            s0 = cfg.sets[0]
-            tuned[prec] = tune_update(geom, c0, a0, [cfg.freqs_hz[i] for i in s0], p_obs[s0[0]:s0[-1] + 1], prec)
+            tuned[prec] = tune_update(geom, c0, a0, list(cfg.freqs_hz), p_obs, prec, reps=2, sets=cfg.sets)
             torch.cuda.empty_cache()
         return tuned[prec][0]
 

@@ -75,7 +75,8 @@ class Reconstruction:
                  step_mode=rb.RB_STEP_EXACT, device="cuda", cg_iters=0, cg_precond=True, tune=rb.RB_TUNE_RULE):
         """cg_iters > 0 solves each set's linear equation by that many CG iterations
         (rb_cg_update) instead of the one-step update.  tune: an rb_update_params.tune value,
-        or "auto" to time the choices on the first set (tune.py; cached per problem shape)."""
+        or "auto" to time the choices on this problem's sweep (tune.py; cached per problem
+        shape)."""
         import torch
         self.cfg = cfg
         self.geom = rb.geometry_from_config(cfg)
@@ -94,9 +95,8 @@ class Reconstruction:
         self.tune_info = None
         if tune == "auto":
             from .tune import tune_update
-            s = cfg.sets[0]
-            tune, self.tune_info = tune_update(self.geom, self.c, self.alpha0, [cfg.freqs_hz[i] for i in s],
-                                               self.p_obs[s[0]:s[-1] + 1], prec)
+            tune, self.tune_info = tune_update(self.geom, self.c, self.alpha0, list(cfg.freqs_hz), self.p_obs, prec,
+                                               reps=2, sets=cfg.sets)
         self.tune = int(tune)
 
     def update(self, j: int, stream=None):

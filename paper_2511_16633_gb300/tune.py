@@ -6,11 +6,12 @@ how much the medium bends them; the library's rule picks by tube width alone.  T
 tensor-core adjoint runs either on one CTA per pixel tile or on CTA pairs sharing each
 MMA (cta_group::2), which halves the shared-memory traffic of the S operand per CTA.
 The choices do not change the results, so only their time differs, and that is
-measured here: for one problem, ``tune_update`` times a frequency-set update per candidate on
-the caller's own data (a warm-up update, then ``reps`` timed ones, each from a scratch
-copy of c, with CUDA events on a private stream), keeps the fastest and caches it per
-key (ring, grid, pitch, fan, frequencies per set, precision) in memory and, when the
-environment variable RB_TUNE_CACHE names a JSON file, in that file across processes.
+measured here: for one problem, ``tune_update`` times the updates per candidate on
+the caller's own data (a warm-up run, then ``reps`` timed ones, each from a scratch
+copy of c, with CUDA events on a private stream; a whole sweep over the problem's
+frequency sets when they are given), keeps the fastest and caches it per key (ring,
+grid, pitch, fan, frequencies per set, precision) in memory and, when the environment
+variable RB_TUNE_CACHE names a JSON file, in that file across processes.
 """
 from __future__ import annotations
 
@@ -82,18 +83,24 @@ def cached(geom, n_freq: int, prec: int) -> Optional[dict]:
     return _cache.get(k)
 
 
-def tune_update(geom, c, alpha0, freqs, p_obs, prec, reps: int = 3, device=None) -> Tuple[int, dict]:
-    """The fastest ``tune`` value for one rb_hf_update of this problem, and the timings
-    (ms per candidate, median of ``reps``).  c is not modified; the result is cached."""
+def tune_update(geom, c, alpha0, freqs, p_obs, prec, reps: int = 3, device=None, sets=None) -> Tuple[int, dict]:
+    """The fastest ``tune`` value for this problem, and the timings (ms per candidate,
+    median of ``reps``).  Without ``sets`` one rb_hf_update of the frequencies ``freqs``
+    (data p_obs[len(freqs)]) is timed; with ``sets`` (index lists into ``freqs``, data
+    p_obs[len(freqs)]) the whole sweep over them is, from c each time, because the
+    medium the later sets see (rougher, with bent tubes) changes which choice is faster.
+    c is not modified; the result is cached."""
     import torch
-    hit = cached(geom, len(freqs), prec)
+    nf = max(len(s) for s in sets) if sets else len(freqs)
+    hit = cached(geom, nf, prec)
     if hit is not None:
         return int(hit["tune"]), hit
     dev = c.device if device is None else device
     stream = torch.cuda.Stream(device=dev)
+    plan = [list(s) for s in sets] if sets else [list(range(len(freqs)))]
     times = {}
     with torch.cuda.stream(stream):
-        ws = rb.workspace(geom, len(freqs), prec, dev)
+        ws = rb.workspace(geom, nf, prec, dev)
         cs = torch.empty_like(c)
         for cand in candidates(prec):
             ms = []
@@ -101,17 +108,20 @@ def tune_update(geom, c, alpha0, freqs, p_obs, prec, reps: int = 3, device=None)
                 cs.copy_(c)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                rb.rb_hf_update(geom, cs, alpha0, freqs, p_obs, ws, prec=prec, stream=stream, tune=cand)
+                for s in plan:
+                    rb.rb_hf_update(geom, cs, alpha0, [freqs[i] for i in s], p_obs[s[0]:s[-1] + 1], ws, prec=prec,
+                                    stream=stream, tune=cand)
                 e1.record(stream)
                 e1.synchronize()
                 if r > 0:
-                    ms.append(e0.elapsed_time(e1))
+                    ms.append(e0.elapsed_time(e1) / len(plan))
             ms.sort()
             times[name(cand)] = ms[len(ms) // 2]
         del ws, cs
     best = min(candidates(prec), key=lambda t: times[name(t)])
-    entry = {"tune": int(best), "choice": name(best), "ms": times}
-    k = key(geom, len(freqs), prec)
+    entry = {"tune": int(best), "choice": name(best), "ms_per_update": times,
+             "timed": "sweep of %d sets" % len(plan) if sets else "one update"}
+    k = key(geom, nf, prec)
     _cache[k] = entry
     _store_file(k, entry)
     return int(best), entry

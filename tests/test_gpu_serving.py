@@ -122,7 +122,7 @@ def test_autotuned_choice_is_bit_identical_and_cached(dev, tmp_path, monkeypatch
         maps.append(rec.sweep().cpu().numpy())
     assert all(np.array_equal(m, maps[0]) for m in maps[1:])
     rec = Reconstruction(cfg, prob.c_init, prob.alpha0, prob.p_obs, prec=rb.RB_PREC_BF16X3, device=dev, tune="auto")
-    assert rec.tune in cands and set(rec.tune_info["ms"]) == {tune.name(t) for t in cands}
+    assert rec.tune in cands and set(rec.tune_info["ms_per_update"]) == {tune.name(t) for t in cands}
     assert np.array_equal(rec.sweep().cpu().numpy(), maps[0])
     monkeypatch.setattr(tune, "_cache", {})
     again = tune.cached(rec.geom, len(cfg.sets[0]), rb.RB_PREC_BF16X3)    # from the file

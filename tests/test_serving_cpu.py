@@ -76,7 +76,7 @@ def test_tune_cache_keys_and_file_round_trip(tmp_path, monkeypatch):
     assert tune.cached(g1, 1, rb.RB_PREC_BF16X3) is None
     assert len(tune.candidates(rb.RB_PREC_BF16X3)) == 4 and len(tune.candidates(rb.RB_PREC_FP32)) == 2
     assert tune.name(rb.RB_TUNE_RASTER_ACROSS | rb.RB_TUNE_ADJ_PAIR) == "raster across tubes, adjoint CTA pairs"
-    entry = {"tune": rb.RB_TUNE_RASTER_ACROSS, "choice": "raster across tubes", "ms": {"a": 1.0, "b": 0.9}}
+    entry = {"tune": rb.RB_TUNE_RASTER_ACROSS, "choice": "raster across tubes", "ms_per_update": {"a": 1.0, "b": 0.9}}
     tune._store_file(tune.key(g1, 1, rb.RB_PREC_BF16X3), entry)
     assert tune.cached(g1, 1, rb.RB_PREC_BF16X3) == entry
     assert tune.cached(g2, 1, rb.RB_PREC_BF16X3) is None
