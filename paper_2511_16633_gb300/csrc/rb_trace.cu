@@ -319,12 +319,16 @@ __device__ __forceinline__ void put_vtx(Vtx* dst, const Vtx& v) {
 
 // One thread per ray: RK4 from the element to the ring, the end record, and (when
 // verts is set) every vertex into the vertex stream for the rasteriser.
+constexpr int TRACE_GR = 8;   // rays of one fan side by side in a warp (measured: 1, 2, 4, 8, 16)
 __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restrict__ cells, rb_ray_end* __restrict__ ends,
                                                rb_rays S, int write_samples, Vtx* __restrict__ verts,
                                                uint32_t* __restrict__ counters) {
+    // a warp takes TRACE_GR neighbouring rays of 32 / TRACE_GR fans: rays of alike take-off
+    // angles (so alike lengths: the lanes finish together) that share field cells
     const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (u >= (long long)G.n_elem * G.n_rays) return;
-    const int t = (int)(u / G.n_rays), i = (int)(u % G.n_rays);
+    const long long qg = u / ((long long)TRACE_GR * G.n_elem), rg = u % ((long long)TRACE_GR * G.n_elem);
+    const int t = (int)(rg / TRACE_GR), i = (int)(qg * TRACE_GR + rg % TRACE_GR);
+    if (i >= G.n_rays) return;
     const bool valid = true, owner = true;
     const bool put = verts != nullptr;
 
@@ -745,7 +749,8 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
         cudaError_t e = cudaMemsetAsync(K, 0xff, (size_t)G.n_elem * G.npix * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    const long long rays = (long long)G.n_elem * G.n_rays;
+    // threads: every fan's rays padded to a multiple of TRACE_GR (the padding returns at once)
+    const long long rays = (long long)G.n_elem * ((G.n_rays + TRACE_GR - 1) / TRACE_GR) * TRACE_GR;
     k_trace<<<(int)((rays + 127) / 128), 128, 0, s>>>(G, cells, ends, S, ws, V, counters);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && traced) e = cudaEventRecord(traced, s);   // the end records are complete
