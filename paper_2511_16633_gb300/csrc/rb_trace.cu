@@ -222,7 +222,7 @@ __device__ __forceinline__ void key_min(unsigned long long* dst, uint64_t key) {
 // the pixel index: they are evaluated at the row's first pixel and then stepped
 // by their exact per-pixel increments (a few ulps of drift over a box).
 __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, const Vtx& A1, const Vtx& B0, const Vtx& B1,
-                                            uint32_t base, unsigned long long* __restrict__ tab,
+                                            uint32_t base, uint32_t fl, unsigned long long* __restrict__ tab,
                                             const short2* __restrict__ supp) {
     // edge vectors first: most quads are about one pixel, and a box with no pixel centre
     // ends here before the areas and their reciprocals are formed
@@ -286,7 +286,7 @@ __device__ __forceinline__ void raster_quad(const GeoDev& G, const Vtx& A0, cons
                 const float tr1 = fmaf(wb1, tb1, fmaf(wc1, tc1, A0.t));
                 const bool use1 = in1 && (!in0 || tr1 < tr0);
                 const uint32_t id = use1 ? base + 1u : base;
-                key_min(tab + o, ((uint64_t)f2key(use1 ? tr1 : tr0) << 32) | ((uint64_t)id << 8));
+                key_min(tab + o, ((uint64_t)f2key(use1 ? tr1 : tr0) << 32) | ((uint64_t)id << 8) | fl);
             }
             wb0 += db0;
             wc0 += dc0;
@@ -521,6 +521,13 @@ constexpr int KB = 8;   // quads per thread of the tube-major mapping
 #define RASTER_ALONG_K_MIN_PX 4.0   // tube width (pixels, across the ring) from which warps run along the tubes
 #endif
 
+// Low bits of a quad's key: bit 0 when ray i has ended before step k (its vertices
+// there repeat its last one), bit 1 the same for ray i + 1.  The resolve pass reads
+// the rays' ends only for such quads.
+__device__ __forceinline__ uint32_t clamp_flags(int k, int la, int lb) {
+    return (uint32_t)(k > la) | ((uint32_t)(k > lb) << 1);
+}
+
 // Columns [lo, hi] of row iy inside the support disc (2 ix - (nx - 1))^2 +
 // (2 iy - (ny - 1))^2 <= r2max, exact in integers; lo > hi for an empty row.
 __device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
@@ -565,8 +572,8 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
             const Vtx B0 = get_vtx(verts + vidx(G, t, min(k - 1, lb), i + 1));
             const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
             const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
-            raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, keys + (size_t)t * G.npix,
-                        s_supp);
+            raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, clamp_flags(k, la, lb),
+                        keys + (size_t)t * G.npix, s_supp);
         }
     } else {
         const int nkb = (G.max_steps + KB - 1) / KB;
@@ -586,7 +593,8 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
             for (int k = k0; k <= k1; ++k) {
                 const Vtx A1 = get_vtx(verts + vidx(G, t, min(k, la), i));
                 const Vtx B1 = get_vtx(verts + vidx(G, t, min(k, lb), i + 1));
-                raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, tab, s_supp);
+                raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, clamp_flags(k, la, lb), tab,
+                            s_supp);
                 A0 = A1;
                 B0 = B1;
             }
@@ -610,7 +618,12 @@ __device__ __forceinline__ bool resolve_entry(const GeoDev& G, const Vtx* __rest
     udivmod(id >> 1, KQ, kq_magic, qi, qk1);
     // ids come from the rasteriser (i + 1 < n_rays, 1 <= k1 <= max_steps); clamped all the same
     const int i = min((int)qi, G.n_rays - 2), k1 = min((int)qk1 + 1, G.max_steps);
-    const int la = last_vertex(G, ends, t, i), lb = last_vertex(G, ends, t, i + 1);
+    // the rays' last vertices matter only where the rasteriser flagged a clamp
+    int la = G.max_steps, lb = G.max_steps;
+    if (kv.x & 3u) {
+        la = last_vertex(G, ends, t, i);
+        lb = last_vertex(G, ends, t, i + 1);
+    }
     // the winning triangle only: T0 = (A0, B0, B1), T1 = (A0, B1, A1); edge vectors,
     // doubled area (rounded reciprocal) and weights as in bary
     const Vtx A0 = get_vtx(verts + vidx(G, t, min(k1 - 1, la), i));
@@ -668,11 +681,13 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
 
 // Mixed path: the resolve pass fused with the synthesis of the operand images, so the
 // per-(element, pixel) record never goes to memory.  CTA (tile of RB_TP pixels,
-// element block of 16): thread (p, half) resolves elements 16 eb + 8 half + k (k < 8)
-// at pixel p of the tile, keeps their synthesis records in registers, and writes for
-// every frequency of the set the Green's functions of Eqs. 4-5 into rows
-// 4 eb + 2 half + {0, 1} of the pixel's core row in both bf16 planes (the same values
-// as the separate record and image passes: the same record, the same formulas).
+// element block of 16): thread (p, half) loads the keys of elements 16 eb + 8 half + k
+// (k < 8) at pixel p of the tile, then, four elements at a time, resolves them, keeps
+// their synthesis records in registers and writes for every frequency of the set the
+// Green's functions of Eqs. 4-5 into row 4 eb + 2 half + kg of the pixel's core row in
+// both bf16 planes (the same values as the separate record and image passes: the same
+// record, the same formulas).  Four records at a time keep the kernel at 64 registers,
+// four CTAs per SM, to hide the latency of the vertex gathers.
 __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __restrict__ verts,
                                                         const rb_ray_end* __restrict__ ends,
                                                         const unsigned long long* __restrict__ keys,
@@ -684,41 +699,39 @@ __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __r
     const int p = (int)threadIdx.x & (RB_TP - 1), half = (int)threadIdx.x >> 7;
     const int pix = tile * RB_TP + p;
     const int e0 = 16 * eb + 8 * half;
-    float4 sr[8];
     uint32_t holes = 0;
-    if (pix < G.npix) {
-        const int iy = pix / G.nx, ix = pix - iy * G.nx;
-        const DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
-        const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
-        const long long jx = 2LL * ix - (G.nx - 1), jy = 2LL * iy - (G.ny - 1);
-        const bool in_support = jx * jx + jy * jy <= G.r2max;
-        const float c_px = __ldg(c + pix);
-        unsigned long long key[8];
+    const bool live = pix < G.npix;
+    const int iy = live ? pix / G.nx : 0, ix = live ? pix - iy * G.nx : 0;
+    const DF X = df_pixel_coord(ix, G.cxg, G.h_hi, G.h_lo);
+    const DF Y = df_pixel_coord(iy, G.cyg, G.h_hi, G.h_lo);
+    const long long jx = 2LL * ix - (G.nx - 1), jy = 2LL * iy - (G.ny - 1);
+    const bool in_support = live && jx * jx + jy * jy <= G.r2max;
+    const float c_px = live ? __ldg(c + pix) : 0.f;
+    unsigned long long key[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) key[k] = keys[(size_t)(e0 + k) * G.npix + pix];
+    for (int k = 0; k < 8; ++k) key[k] = live ? keys[(size_t)(e0 + k) * G.npix + pix] : ~0ull;
+    // two groups of four elements: one image row (16 bytes per plane) each
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+    for (int kg = 0; kg < 2; ++kg) {
+        float4 sr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = e0 + 4 * kg + q;
             rb_cell rec;
-            if (!resolve_entry(G, verts, ends, key[k], e0 + k, X, Y, kq_magic, rec)) {
-                sr[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!resolve_entry(G, verts, ends, key[4 * kg + q], e, X, Y, kq_magic, rec)) {
+                sr[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (in_support) ++holes;
                 continue;
             }
             DF ex, ey;
-            elem_pos(G, e0 + k, ex, ey);
-            sr[k] = synth_record(rec, c_px, pixel_elem_dist(G, ix, iy, ex, ey), G.inv_cref, G.inv_cref_lo, G.j_floor);
+            elem_pos(G, e, ex, ey);
+            sr[q] = synth_record(rec, c_px, pixel_elem_dist(G, ix, iy, ex, ey), G.inv_cref, G.inv_cref_lo, G.j_floor);
         }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sr[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int fw = 0; fw < F.n; ++fw) {
-        __nv_bfloat16* plane = aimg + (size_t)fw * a_stride + (size_t)tile * 2 * rcn * 1024;
-#pragma unroll
-        for (int kg = 0; kg < 2; ++kg) {
+        for (int fw = 0; fw < F.n; ++fw) {
+            __nv_bfloat16* plane = aimg + (size_t)fw * a_stride + (size_t)tile * 2 * rcn * 1024;
             float2 g[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) g[q] = green_srec(sr[4 * kg + q], F.f[fw]);
+            for (int q = 0; q < 4; ++q) g[q] = green_srec(sr[q], F.f[fw]);
             aimg_put4(plane, rcn, 4 * eb + 2 * half + kg, p, g);
         }
     }
