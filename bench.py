@@ -191,6 +191,8 @@ def run_ours(args):
         # the kernel-shape choice measured fastest on this problem (tune.py), before any timing
         if args.tune == "off":
             return rb.RB_TUNE_RULE
+        if args.tune not in ("on", "off"):
+            return int(args.tune)    # a fixed kernel-shape code (rb_update_params.tune)
         if prec not in tuned:
             from paper_2511_16633_gb300.tune import tune_update
             tuned[prec] = tune_update(geom, c0, a0, list(cfg.freqs_hz), p_obs, prec, reps=2, sets=cfg.sets)
@@ -387,6 +389,8 @@ def run_ours(args):
     }
     if tuned:
         line["tune"] = {("bf16x3" if p == rb.RB_PREC_BF16X3 else "fp32"): v[1] for p, v in tuned.items()}
+    elif args.tune not in ("on", "off"):
+        line["tune"] = {"fixed": int(args.tune)}
     if cg is not None:
         line["cg_variant"] = cg
     if other in runs:
@@ -495,9 +499,11 @@ def main():
     ap.add_argument("--cpu-pix-baseline", type=int, default=160000,
                     help="cpu_baseline of the GPU arm's line: pixels sampled (all fans, all 4 frequencies)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tune", choices=["on", "off"], default="on",
-                    help="run with the kernel-shape choice the tuner measures fastest on this problem (tuned before "
-                         "the warm-up; off: the library's rule)")
+    ap.add_argument("--tune", default="on",
+                    help="on: run with the kernel-shape choice the tuner measures fastest on this problem (tuned "
+                         "before the warm-up); off: the library's rule; an integer: that kernel-shape code "
+                         "(rb_update_params.tune: 1 raster along tubes, 2 across; + 4 adjoint CTA pairs, + 8 one CTA "
+                         "per tile)")
     ap.add_argument("--cg-iters", type=int, default=12,
                     help="also time the CG variant of the update with this many iterations (0: skip)")
     args = ap.parse_args()

@@ -291,7 +291,7 @@ rb_status gradient_stages(const GeoDev& G, const FreqSet& F, const Ws& W, float*
     // operand images of the set itself
     RB_CU(launch_trace(G, cells, ends, nullptr, W.at<void>(W.L.gkeys), tc ? nullptr : tables, W.at<void>(W.L.verts), c,
                        cnt, s, ss->fork, ss->keys, tc ? &F : nullptr, tc ? W.at<void>(W.L.aimg) : nullptr,
-                       params->tune & 3));
+                       params->tune & 3, W.at<uint32_t>(W.L.fanlen)));
     // side branch 2 (needs the end records only): links, residuals, weights, B images
     RB_CU(cudaStreamWaitEvent(s2, ss->fork, 0));
     RB_CU(mark2(RB_STAGE_LINK, 0));
@@ -346,6 +346,7 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->verts = o; o = align256(o + rb_verts_bytes(g->n_elem, g->n_rays, g->max_steps));
     L->gkeys = o; o = align256(o + ne * npix * 8);
     L->ends = o; o = align256(o + ne * (size_t)g->n_rays * sizeof(rb_ray_end));
+    L->fanlen = o; o = align256(o + ne * 4);
     L->pray = o; o = align256(o + nf * ne * ne * 8);
     L->linked = o; o = align256(o + ne * ne);
     L->wts = o; o = align256(o + nf * ne * ne);
@@ -436,7 +437,8 @@ rb_status rb_green_grid(const rb_geometry* geom, const float* c, const float* al
     RB_CU(launch_elem_positions(G, exy, s));
     RB_CU(launch_fields(G, c, alpha0, W.at<float4>(W.L.cells), s));
     RB_CU(launch_trace(G, W.at<float4>(W.L.cells), W.at<rb_ray_end>(W.L.ends), nullptr, W.at<void>(W.L.gkeys), tables,
-                       W.at<void>(W.L.verts), nullptr, cnt, s));
+                       W.at<void>(W.L.verts), nullptr, cnt, s, nullptr, nullptr, nullptr, nullptr, 0,
+                       W.at<uint32_t>(W.L.fanlen)));
     if (g_out) RB_CU(launch_green_out(G, tables, c, F, (float2*)g_out, s));
     return RB_OK;
 }

@@ -244,6 +244,7 @@ struct WsLayout {
     size_t verts;      // [n_elem][max_steps + 1][n_rays] ray vertices, 32 B each (gridding)
     size_t gkeys;      // [n_elem][npix] u64 first-arrival keys (gridding)
     size_t ends;       // [n_elem][n_rays] rb_ray_end
+    size_t fanlen;     // [n_elem] u32: vertices of each fan's longest ray (gridding)
     size_t counters;   // 64 uint32 + 64 double scalars
     size_t pray;       // [n_freq][n_elem][n_elem] float2 (ray data, then residual)
     size_t linked;     // [n_elem][n_elem] u8
@@ -312,7 +313,8 @@ cudaError_t launch_fields(const GeoDev& G, const float* c, const float* alpha0, 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, uint32_t* counters,
                          cudaStream_t s, cudaEvent_t traced = nullptr, cudaEvent_t keys_ready = nullptr,
-                         const FreqSet* F = nullptr, void* images = nullptr, int raster_mode = 0);
+                         const FreqSet* F = nullptr, void* images = nullptr, int raster_mode = 0,
+                         uint32_t* fan_len = nullptr);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);

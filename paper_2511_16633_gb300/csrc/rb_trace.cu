@@ -322,7 +322,7 @@ __device__ __forceinline__ void put_vtx(Vtx* dst, const Vtx& v) {
 constexpr int TRACE_GR = 8;   // rays of one fan side by side in a warp (measured: 1, 2, 4, 8, 16)
 __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restrict__ cells, rb_ray_end* __restrict__ ends,
                                                rb_rays S, int write_samples, Vtx* __restrict__ verts,
-                                               uint32_t* __restrict__ counters) {
+                                               uint32_t* __restrict__ counters, uint32_t* __restrict__ fan_len) {
     // a warp takes TRACE_GR neighbouring rays of 32 / TRACE_GR fans: rays of alike take-off
     // angles (so alike lengths: the lanes finish together) that share field cells
     const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                     e.kappa = ek;
                     e.n_vert = k + 1;
                     ends[(size_t)t * G.n_rays + i] = e;
+                    if (fan_len) atomicMax(fan_len + t, (uint32_t)(k + 1));
                 }
             } else {
                 if (k >= 2 && signbit(nq) != signbit(q)) ++kap;
@@ -469,6 +470,7 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                         e.n_vert = -1;
                         ends[(size_t)t * G.n_rays + i] = e;
                         atomicAdd(counters + CNT_LOST, 1u);
+                        if (fan_len) atomicMax(fan_len + t, (uint32_t)(G.max_steps + 1));
                     }
                 }
             }
@@ -528,6 +530,13 @@ __device__ __forceinline__ uint32_t clamp_flags(int k, int la, int lb) {
     return (uint32_t)(k > la) | ((uint32_t)(k > lb) << 1);
 }
 
+// The last quad index any tube of fan t reaches: its longest ray's last vertex (the
+// tracer's per-fan maximum of the vertex counts), at most max_steps.
+__device__ __forceinline__ int fan_last_quad(const GeoDev& G, const uint32_t* __restrict__ fan_len, int t) {
+    const uint32_t nv = __ldg(fan_len + t);
+    return nv == 0u ? 0 : (int)min(nv - 1u, (uint32_t)G.max_steps);
+}
+
 // Columns [lo, hi] of row iy inside the support disc (2 ix - (nx - 1))^2 +
 // (2 iy - (ny - 1))^2 <= r2max, exact in integers; lo > hi for an empty row.
 __device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
@@ -549,18 +558,19 @@ __device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
 template <bool ALONG_K>
 __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict__ verts,
                                                 const rb_ray_end* __restrict__ ends, unsigned long long* __restrict__ keys,
-                                                uint32_t nt_magic) {
+                                                const uint32_t* __restrict__ fan_len, uint32_t nt_magic) {
     extern __shared__ short2 s_supp[];   // [ny]
     for (int iy = threadIdx.x; iy < G.ny; iy += blockDim.x) s_supp[iy] = support_row(G, iy);
     __syncthreads();
     const int NT = G.n_rays - 1;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
     if (ALONG_K) {
-        const int nkc = (G.max_steps + KW - 1) / KW;
-        const int per_fan = nkc * NT;   // warp items per fan, < 2^31 (the triangle ids fit 24 bits)
         const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-        // fans t = blockIdx.y + j gridDim.y; within a fan, warp item = kc NT + i
-        for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y)
+        // fans t = blockIdx.y + j gridDim.y; within a fan, warp item = kc NT + i, up to the
+        // fan's longest ray (quads k <= its last vertex)
+        for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y) {
+        const int kmax = fan_last_quad(G, fan_len, t);
+        const int per_fan = ((kmax + KW - 1) / KW) * NT;   // < 2^31 (the triangle ids fit 24 bits)
         for (int item = blockIdx.x * wpb + wib; item < per_fan; item += gridDim.x * wpb) {
             uint32_t ukc, ui;
             udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukc, ui);
@@ -575,11 +585,13 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
             raster_quad(G, A0, A1, B0, B1, ((uint32_t)i * KQ + (uint32_t)(k - 1)) * 2u, clamp_flags(k, la, lb),
                         keys + (size_t)t * G.npix, s_supp);
         }
+        }
     } else {
-        const int nkb = (G.max_steps + KB - 1) / KB;
-        const int per_fan = nkb * NT;
-        // fans t = blockIdx.y + j gridDim.y; within a fan, thread item = kb NT + i
-        for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y)
+        // fans t = blockIdx.y + j gridDim.y; within a fan, thread item = kb NT + i, up to the
+        // fan's longest ray
+        for (int t = blockIdx.y; t < G.n_elem; t += gridDim.y) {
+        const int kmax = fan_last_quad(G, fan_len, t);
+        const int per_fan = ((kmax + KB - 1) / KB) * NT;
         for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < per_fan; item += gridDim.x * blockDim.x) {
             uint32_t ukb, ui;
             udivmod((uint32_t)item, (uint32_t)NT, nt_magic, ukb, ui);
@@ -598,6 +610,7 @@ __global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict_
                 A0 = A1;
                 B0 = B1;
             }
+        }
         }
     }
 }
@@ -744,7 +757,7 @@ __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __r
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, uint32_t* counters,
                          cudaStream_t s, cudaEvent_t traced, cudaEvent_t keys_ready, const FreqSet* F, void* images,
-                         int raster_mode) {
+                         int raster_mode, uint32_t* fan_len) {
     rb_rays S{};
     int ws = 0;
     if (samples && samples->vx) {
@@ -754,6 +767,7 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     // vertices are stored whenever a buffer is given; gridding needs them and the keys
     const bool grid = keys != nullptr;
     Vtx* V = (Vtx*)verts;
+    if (grid && !fan_len) return cudaErrorInvalidValue;
     const bool fused = images != nullptr;
     if (fused && (!F || F->n < 1 || !c || (G.n_elem % 16) != 0)) return cudaErrorInvalidValue;
     if (grid && (!V || (!tables && !fused))) return cudaErrorInvalidValue;
@@ -762,9 +776,13 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
         cudaError_t e = cudaMemsetAsync(K, 0xff, (size_t)G.n_elem * G.npix * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
+    if (grid) {
+        cudaError_t e = cudaMemsetAsync(fan_len, 0, (size_t)G.n_elem * sizeof(uint32_t), s);
+        if (e != cudaSuccess) return e;
+    }
     // threads: every fan's rays padded to a multiple of TRACE_GR (the padding returns at once)
     const long long rays = (long long)G.n_elem * ((G.n_rays + TRACE_GR - 1) / TRACE_GR) * TRACE_GR;
-    k_trace<<<(int)((rays + 127) / 128), 128, 0, s>>>(G, cells, ends, S, ws, V, counters);
+    k_trace<<<(int)((rays + 127) / 128), 128, 0, s>>>(G, cells, ends, S, ws, V, counters, grid ? fan_len : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && traced) e = cudaEventRecord(traced, s);   // the end records are complete
     if (e != cudaSuccess || !grid) return e;
@@ -780,9 +798,9 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     const size_t ssm = (size_t)G.ny * sizeof(short2);
     const bool along = raster_mode == 1 || (raster_mode == 0 && tube_px >= RASTER_ALONG_K_MIN_PX);
     if (along)
-        k_raster<true><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, ntm);
+        k_raster<true><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, fan_len, ntm);
     else
-        k_raster<false><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, ntm);
+        k_raster<false><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, fan_len, ntm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
