@@ -72,7 +72,7 @@ __global__ void k_prep_b(int n, const float2* __restrict__ R, const uint8_t* __r
 struct TcArgs {
     GeoDev G;
     FreqSet F;
-    const __nv_bfloat16* aimg; // [n_freq][tiles][hi|lo][2n / 8 rows][1024] A image (k_synth_images)
+    const __nv_bfloat16* aimg; // [n_freq][tiles][hi|lo][2n / 8 rows][1024] A image (layout: aimg_put4)
     size_t aimg_stride;        // bf16 elements per frequency
     const __nv_bfloat16* bu;   // [n_freq][image]
     const __nv_bfloat16* bw;   // [n_freq][image]
@@ -110,7 +110,7 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
 }
 
 // Producer work of one U slice (8 elements, K' = 16) for thread (p, h), h < 4: the
-// A slice in shared memory (two rows of the A image, see k_synth_images) holds, at
+// A slice in shared memory (two rows of the A image, layout of aimg_put4) holds, at
 // K' positions 4h .. 4h + 3 of row p, the bf16
 // hi / lo parts of (Re G, -Im G) of elements r0 + 2h + j (j < 2).  Their sums give
 // G to ~2^-17 relative for the epilogue (gs), and |G|^2 (hi / lo) goes to the V
@@ -1067,7 +1067,7 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
 // columns r' = 2r + {0, 1} of B = conj(G) give D = A B^T (2n x 2n, symmetric) =
 // the real form of conj(d), from which
 //   Re d = D[2e][2r] - D[2e+1][2r+1],  Im d = -(D[2e][2r+1] + D[2e+1][2r]).
-// Both operands come from the adjoint's A image (k_synth_images), read MN-major:
+// Both operands come from the adjoint's A image (layout of aimg_put4), read MN-major:
 // a core matrix there is 8 pixels (K) x 8 consecutive r' (16 bytes each), and a
 // 16-pixel K slice of all r' rows is one 2-D TMA box per plane.  CTA (i, s):
 // 128-row block i of D over pixel split s, the needed column blocks in TMEM;
