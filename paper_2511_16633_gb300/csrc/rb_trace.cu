@@ -790,7 +790,12 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         nsm = 148;
-    const int ry = G.n_elem < 16 ? G.n_elem : 16;
+    // fans in flight (grid rows): up to 128, fewer where their keys would pass 256 MB, at
+    // least 16 (measured on a 256-element ring, 512^2 pixels: 16 fans 1.27 ms, 64 1.23,
+    // 128 1.22, 256 1.26)
+    int ry = 128;
+    while (ry > 16 && (size_t)ry * G.npix * sizeof(unsigned long long) > ((size_t)256 << 20)) ry >>= 1;
+    if (ry > G.n_elem) ry = G.n_elem;
     // tube width in pixels where the fan is widest (across the ring): the ray spacing
     // 2 R pi / n_rays over h
     const double tube_px = 2.0 * G.R_d * RB_PI_D / (double)G.n_rays / G.h_d;
