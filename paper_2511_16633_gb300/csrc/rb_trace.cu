@@ -694,13 +694,15 @@ __global__ void __launch_bounds__(256) k_resolve(GeoDev G, const Vtx* __restrict
 
 // Mixed path: the resolve pass fused with the synthesis of the operand images, so the
 // per-(element, pixel) record never goes to memory.  CTA (tile of RB_TP pixels,
-// element block of 16): thread (p, half) loads the keys of elements 16 eb + 8 half + k
-// (k < 8) at pixel p of the tile, then, four elements at a time, resolves them, keeps
-// their synthesis records in registers and writes for every frequency of the set the
-// Green's functions of Eqs. 4-5 into row 4 eb + 2 half + kg of the pixel's core row in
-// both bf16 planes (the same values as the separate record and image passes: the same
-// record, the same formulas).  Four records at a time keep the kernel at 64 registers,
-// four CTAs per SM, to hide the latency of the vertex gathers.
+// element block of 16), element block major: CTAs side by side take neighbouring tiles
+// of the same 16 fans, whose vertex gathers then meet in L2.  Thread (p, half) loads
+// the keys of elements 16 eb + 8 half + k (k < 8) at pixel p of the tile, then, four
+// elements at a time, resolves them, keeps their synthesis records in registers and
+// writes for every frequency of the set the Green's functions of Eqs. 4-5 into row
+// 4 eb + 2 half + kg of the pixel's core row in both bf16 planes (the same values as
+// the separate record and image passes: the same record, the same formulas).  Four
+// records at a time keep the kernel at 64 registers, four CTAs per SM, to hide the
+// latency of the vertex gathers.
 __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __restrict__ verts,
                                                         const rb_ray_end* __restrict__ ends,
                                                         const unsigned long long* __restrict__ keys,
@@ -708,7 +710,8 @@ __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __r
                                                         __nv_bfloat16* __restrict__ aimg, size_t a_stride,
                                                         uint32_t* __restrict__ counters, uint32_t kq_magic) {
     const int n = G.n_elem, rcn = 2 * n / 8, neb = n / 16;
-    const int tile = (int)blockIdx.x / neb, eb = (int)blockIdx.x % neb;
+    const int ntiles = (G.npix + RB_TP - 1) / RB_TP;
+    const int tile = (int)blockIdx.x % ntiles, eb = (int)blockIdx.x / ntiles;
     const int p = (int)threadIdx.x & (RB_TP - 1), half = (int)threadIdx.x >> 7;
     const int pix = tile * RB_TP + p;
     const int e0 = 16 * eb + 8 * half;
