@@ -147,6 +147,7 @@ struct SideStream {
     cudaStream_t caller = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t start = nullptr, keys = nullptr, fork = nullptr, join = nullptr;
+    cudaEvent_t fwd[2] = {nullptr, nullptr}, red[2] = {nullptr, nullptr};   // forward / its reduce, by parity
     uint32_t* lim_host = nullptr;   // null when host-mapped memory is unavailable
     uint32_t* lim_dev = nullptr;
     const void* last_ws = nullptr;  // workspace of the stream's last update
@@ -199,11 +200,11 @@ cudaError_t side_stream(cudaStream_t caller, SideStream** out) {
     SideStream n;
     n.dev = dev;
     n.caller = caller;
-    cudaEvent_t* evs[4] = {&n.start, &n.keys, &n.fork, &n.join};
+    cudaEvent_t* evs[8] = {&n.start, &n.keys, &n.fork, &n.join, &n.fwd[0], &n.fwd[1], &n.red[0], &n.red[1]};
     cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
     if ((e = cudaThreadExchangeStreamCaptureMode(&mode)) != cudaSuccess) return e;
     e = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
     if (e == cudaSuccess) {
         n.lim_dev = limit_word_dev(g_side_n);
         if (n.lim_dev) {
@@ -213,7 +214,7 @@ cudaError_t side_stream(cudaStream_t caller, SideStream** out) {
     }
     cudaThreadExchangeStreamCaptureMode(&mode);
     if (e != cudaSuccess) {
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 8; ++k)
             if (*evs[k]) cudaEventDestroy(*evs[k]);
         if (n.s) cudaStreamDestroy(n.s);
         return e;
@@ -360,7 +361,8 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->tcimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_b_images_bytes(g->n_elem) : 0));
     // exact G per persistent CTA, then its |G|^2 A slices (bf16 hi and lo)
     L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * (8 + 4) : 0));
-    L->tcfwd = o; o = align256(o + (tcp ? tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS) : 0));
+    // two of them on the update path: one frequency's reduce runs beside the next one's forward
+    L->tcfwd = o; o = align256(o + (tcp ? 2 * align256(tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS)) : 0));
     L->aimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_aimage_elems(g->n_elem, (int)npix) * 2 : 0));
     L->cgv = o; o = align256(o + 4 * npix * 4);
     L->tof = o; o = align256(o + tof_ws_bytes(g->n_elem, g->n_rays, (int)npix));
@@ -581,11 +583,23 @@ rb_status rb_hf_update(const rb_geometry* geom, float* c_inout, const float* alp
     RB_CU(mark(RB_STAGE_DIRECTION, 1));
     RB_CU(mark(RB_STAGE_FORWARD, 0));
     if (params->step_mode == RB_STEP_EXACT) {
+        SideStream* ss = nullptr;
+        if (prec == RB_PREC_BF16X3) {
+            std::lock_guard<std::mutex> lock(g_side_mutex);
+            RB_CU(side_stream(s, &ss));
+        }
+        const size_t half = align256(tc_forward_partial_bytes(G.n_elem, RB_TC_MAX_CTAS));
         for (int w = 0; w < n_freq; ++w) {
             if (prec == RB_PREC_BF16X3) {
-                RB_CU(launch_forward_tc(G, W.at<char>(W.L.aimg) + (size_t)w * tc_aimage_elems(G.n_elem, G.npix) * 2,
-                                        F.f[w], pdir, W.at<float>(W.L.tcfwd), tc_ctas(), nullptr,
-                                        wts + (size_t)w * ne2, part + (size_t)w * 256, cnt, s));
+                // frequency w's reduce runs on the side stream beside frequency w + 1's forward;
+                // the forward of w + 2 reuses w's partial buffer once w's reduce is done
+                if (w >= 2) RB_CU(cudaStreamWaitEvent(s, ss->red[w & 1], 0));
+                RB_CU(launch_forward_tc_overlap(G, W.at<char>(W.L.aimg) + (size_t)w * tc_aimage_elems(G.n_elem, G.npix) * 2,
+                                                F.f[w], pdir, (float*)(W.at<char>(W.L.tcfwd) + (w & 1) * half), tc_ctas(),
+                                                nullptr, wts + (size_t)w * ne2, part + (size_t)w * 256, cnt, s, ss->s,
+                                                ss->fwd[w & 1], ss->red[w & 1]));
+                if (w == n_freq - 1) RB_CU(cudaStreamWaitEvent(s, ss->red[w & 1], 0));   // the last reduce (the
+                                                                                          // others precede it)
             } else {
                 RB_CU(launch_forward_simt(G, tables, c_inout, F.f[w], pdir, fwd, nch, s));
                 RB_CU(launch_forward_reduce(G, F.f[w], fwd, nch, nullptr, wts + (size_t)w * ne2,

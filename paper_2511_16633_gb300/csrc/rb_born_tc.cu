@@ -1423,9 +1423,11 @@ size_t tc_forward_partial_bytes(int n_elem, int n_ctas) {
     return (size_t)(n_ctas + FMAXP) * 128 * (2 * (size_t)n_elem) * sizeof(float);
 }
 
-cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F, const float* m, float* partial,
-                              int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
-                              cudaStream_t s) {
+namespace {
+
+// The forward kernel of one frequency on s; its arguments (which the reduce takes too) in *out.
+cudaError_t forward_tc_kernel(const GeoDev& G, const void* aimg, const FreqC& F, const float* m, float* partial,
+                              int n_ctas, uint32_t* counters, cudaStream_t s, FwdArgs* out) {
     if (!tc_adjoint_supported(G.n_elem) || !aimg) return cudaErrorInvalidValue;
     const FwdArgs A = make_fwd_args(G, F, m, partial, n_ctas, counters);
     // the A image of this frequency as a 2-D tensor: rows of 8 r' x 128 pixels (1024 bf16),
@@ -1452,8 +1454,32 @@ cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F,
         if (e != cudaSuccess) return e;
         k_forward_tc<false><<<A.cta0[A.n_pairs], NTHR_F, sm, s>>>(A, tmap, tmap16);
     }
-    e = cudaGetLastError();
+    *out = A;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F, const float* m, float* partial,
+                              int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
+                              cudaStream_t s) {
+    FwdArgs A;
+    cudaError_t e = forward_tc_kernel(G, aimg, F, m, partial, n_ctas, counters, s, &A);
     if (e != cudaSuccess) return e;
     k_forward_tc_reduce<<<256, 256, 0, s>>>(A, d_out, w, den_part);
     return cudaGetLastError();
+}
+
+cudaError_t launch_forward_tc_overlap(const GeoDev& G, const void* aimg, const FreqC& F, const float* m,
+                                      float* partial, int n_ctas, float2* d_out, const uint8_t* w, double* den_part,
+                                      uint32_t* counters, cudaStream_t s, cudaStream_t r, cudaEvent_t fwd_done,
+                                      cudaEvent_t red_done) {
+    FwdArgs A;
+    cudaError_t e = forward_tc_kernel(G, aimg, F, m, partial, n_ctas, counters, s, &A);
+    if (e == cudaSuccess) e = cudaEventRecord(fwd_done, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(r, fwd_done, 0);
+    if (e != cudaSuccess) return e;
+    k_forward_tc_reduce<<<256, 256, 0, r>>>(A, d_out, w, den_part);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? cudaEventRecord(red_done, r) : e;
 }

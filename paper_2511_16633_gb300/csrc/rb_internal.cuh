@@ -343,6 +343,13 @@ size_t tc_forward_partial_bytes(int n_elem, int n_ctas);
 cudaError_t launch_forward_tc(const GeoDev& G, const void* aimg, const FreqC& F, const float* m, float* partial,
                               int n_ctas, float2* d_out, const uint8_t* w, double* den_part, uint32_t* counters,
                               cudaStream_t s);
+// The same with the split sum on stream r: the forward kernel on s, then (through
+// fwd_done) its reduce on r, which records red_done when done, so the next frequency's
+// forward on s can run beside it (its partial buffer must be another one).
+cudaError_t launch_forward_tc_overlap(const GeoDev& G, const void* aimg, const FreqC& F, const float* m,
+                                      float* partial, int n_ctas, float2* d_out, const uint8_t* w, double* den_part,
+                                      uint32_t* counters, cudaStream_t s, cudaStream_t r, cudaEvent_t fwd_done,
+                                      cudaEvent_t red_done);
 // A images of the adjoint (and optionally the forward's G images) from the synthesis records
 size_t tc_aimage_elems(int n_elem, int npix);
 // operand images of F from the caller's tables (the single-operator entry points)
