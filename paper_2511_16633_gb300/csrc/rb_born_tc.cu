@@ -109,6 +109,33 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+// |G|^2 of elements e .. e + 7 (e a multiple of 8) at pixel p, hi and lo planes, from the
+// tile's V A slices (written by consume_u; K = 32 slices in the chunk_offset layout, so
+// the 8 values of a plane are 16 contiguous bytes): half the bytes of reading G back.
+__device__ __forceinline__ void g2_load(const __nv_bfloat16* vimg, int e, uint32_t p, uint4 (&q)[2]) {
+    const __nv_bfloat16* vs = vimg + (size_t)(e >> 5) * (2 * TP * 32);
+    const uint32_t vo = tc::chunk_offset(p, (uint32_t)(e & 31)) / 2;
+    q[0] = *(const uint4*)(vs + vo);
+    q[1] = *(const uint4*)(vs + TP * 32 + vo);
+}
+
+// hh += sum_i |G_i|^2 V_i over a chunk of 8 elements: V from TMEM (8 columns at taddr),
+// |G|^2 = hi + lo (the values the V MMAs used).
+__device__ __forceinline__ void h_chunk(uint32_t taddr, const uint4 (&q)[2], float& hh) {
+    float v[8];
+    tc::tmem_ld8(taddr, v);
+    const uint32_t wh[4] = {q[0].x, q[0].y, q[0].z, q[0].w}, wl[4] = {q[1].x, q[1].y, q[1].z, q[1].w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float g0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wh[i] & 0xffffu))) +
+                         __bfloat162float(__ushort_as_bfloat16((unsigned short)(wl[i] & 0xffffu)));
+        const float g1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(wh[i] >> 16))) +
+                         __bfloat162float(__ushort_as_bfloat16((unsigned short)(wl[i] >> 16)));
+        hh = fmaf(g0, v[2 * i], hh);
+        hh = fmaf(g1, v[2 * i + 1], hh);
+    }
+}
+
 // Producer work of one U slice (8 elements, K' = 16) for thread (p, h), h < 4: the
 // A slice in shared memory (two rows of the A image, layout of aimg_put4) holds, at
 // K' positions 4h .. 4h + 3 of row p, the bf16
@@ -534,21 +561,16 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 // stage barriers, which keeps every stage's phases in step with its uses ----
                 for (int j = 0; j < nV; ++j) slice([&](const unsigned char*, const unsigned char*) {});
                 // ---- V epilogue (same chunks, |G|^2 against V in columns e) ----
-                if (nch > 0) gload(0, ga);
+                uint4 qa[2], qb[2];
+                if (nch > 0) g2_load(vimg, eb0 + ce0(0), p, qa);
                 acc_wait();
                 float hh = 0.f;
                 if (!err) {
-                    auto hchunk = [&](int k, const float2 (&g)[8]) {
-                        float v[8];
-                        tc::tmem_ld8(tmem + lane_off + (uint32_t)ce0(k), v);
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) hh = fmaf(g[i].x * g[i].x + g[i].y * g[i].y, v[i], hh);
-                    };
                     for (int k = 0; k < nch; k += 2) {
-                        gload(k + 1, gb);
-                        hchunk(k, ga);
-                        if (k + 2 < nch) gload(k + 2, ga);
-                        hchunk(k + 1, gb);
+                        g2_load(vimg, eb0 + ce0(k + 1), p, qb);
+                        h_chunk(tmem + lane_off + (uint32_t)ce0(k), qa, hh);
+                        if (k + 2 < nch) g2_load(vimg, eb0 + ce0(k + 2), p, qa);
+                        h_chunk(tmem + lane_off + (uint32_t)ce0(k + 1), qb, hh);
                     }
                 }
                 acc_release();
@@ -922,21 +944,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHR_A, 1) k_adjoint
                 }
                 // V slices: the producers only pass the stage barriers (as in the single-CTA kernel)
                 for (int j = 0; j < nV; ++j) slice([&](const unsigned char*, const unsigned char*) {});
-                if (nch > 0) gload(0, ga);
+                uint4 qa[2], qb[2];
+                if (nch > 0) g2_load(vimg, eb0 + ce0(0), p, qa);
                 acc_wait();
                 float hh = 0.f;
                 if (!err) {
-                    auto hchunk = [&](int k, const float2 (&g)[8]) {
-                        float v[8];
-                        tc::tmem_ld8(tmem + lane_off + (uint32_t)ce0(k), v);
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) hh = fmaf(g[i].x * g[i].x + g[i].y * g[i].y, v[i], hh);
-                    };
                     for (int k = 0; k < nch; k += 2) {
-                        gload(k + 1, gb);
-                        hchunk(k, ga);
-                        if (k + 2 < nch) gload(k + 2, ga);
-                        hchunk(k + 1, gb);
+                        g2_load(vimg, eb0 + ce0(k + 1), p, qb);
+                        h_chunk(tmem + lane_off + (uint32_t)ce0(k), qa, hh);
+                        if (k + 2 < nch) g2_load(vimg, eb0 + ce0(k + 2), p, qa);
+                        h_chunk(tmem + lane_off + (uint32_t)ce0(k + 1), qb, hh);
                     }
                 }
                 arrive_issuer(r_acc_empty);
