@@ -365,7 +365,6 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
     }
     if (put) put_vtx(verts + vidx(G, t, 0, i), cur);
     const float ds = G.ds, a2 = 0.5f * G.ds, ds6 = G.ds * (1.0f / 6.0f);
-    float pfi = -1.f, pfj = -1.f;   // cell of the last touch
 
     for (int k = 1; k <= G.max_steps; ++k) {
         if (!alive) break;
@@ -379,20 +378,6 @@ __global__ void __launch_bounds__(128) k_trace(GeoDev G, const float4* __restric
                 ray_sincos(tha, &Sa, &Ca);
             }
             const float dth = (thh - tha) + thl;
-            {
-                // touch the field cell one step ahead (a load whose value is never used, so
-                // the warp does not wait for it): its record is in L1 when the stages get there
-                const float lx = (xh + xl) + ds * Ca, ly = (yh + yl) + ds * Sa;
-                const float u = fminf(fmaxf(fmaf(lx, G.inv_h, G.cxg), 0.f), G.fxmax);
-                const float v = fminf(fmaxf(fmaf(ly, G.inv_h, G.cyg), 0.f), G.fymax);
-                const float fi = fminf(floorf(u), G.fxmax - 1.f), fj = fminf(floorf(v), G.fymax - 1.f);
-                if (fi != pfi || fj != pfj) {
-                    pfi = fi;
-                    pfj = fj;
-                    const float4* pc = cells + ((size_t)(int)fj * (size_t)(G.nx - 1) + (size_t)(int)fi) * 8;
-                    asm volatile("{ .reg .f32 t; ld.global.nc.f32 t, [%0]; }" ::"l"(pc));
-                }
-            }
             const Deriv z{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const Deriv k1 = eval_stage(G, cells, cc, xh, xl, yh, yl, Ca, Sa, tha, dth, q, p, 0.f, z);
             const Deriv k2 = eval_stage(G, cells, cc, xh, xl, yh, yl, Ca, Sa, tha, dth, q, p, a2, k1);
@@ -709,7 +694,7 @@ __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __r
                                                         const float* __restrict__ c, FreqSet F,
                                                         __nv_bfloat16* __restrict__ aimg, size_t a_stride,
                                                         uint32_t* __restrict__ counters, uint32_t kq_magic) {
-    const int n = G.n_elem, rcn = 2 * n / 8, neb = n / 16;
+    const int n = G.n_elem, rcn = 2 * n / 8;
     const int ntiles = (G.npix + RB_TP - 1) / RB_TP;
     const int tile = (int)blockIdx.x % ntiles, eb = (int)blockIdx.x / ntiles;
     const int p = (int)threadIdx.x & (RB_TP - 1), half = (int)threadIdx.x >> 7;
