@@ -540,8 +540,13 @@ __device__ __forceinline__ short2 support_row(const GeoDev& G, int iy) {
 // Otherwise a thread takes 8 consecutive quads of one tube and a warp 32 neighbouring
 // tubes at the same steps -- for fans finer than the grid, whose quads mostly cover at
 // most one pixel, where the vertex loads (contiguous across tubes) set the pace.
+// Threads per CTA: 128 along the tubes (smaller blocks leave room sooner for the update's
+// linking kernels beside the rasteriser), 256 across them.
 template <bool ALONG_K>
-__global__ void __launch_bounds__(256) k_raster(GeoDev G, const Vtx* __restrict__ verts,
+constexpr int raster_threads() { return ALONG_K ? 128 : 256; }
+
+template <bool ALONG_K>
+__global__ void __launch_bounds__(raster_threads<ALONG_K>()) k_raster(GeoDev G, const Vtx* __restrict__ verts,
                                                 const rb_ray_end* __restrict__ ends, unsigned long long* __restrict__ keys,
                                                 const uint32_t* __restrict__ fan_len, uint32_t nt_magic) {
     extern __shared__ short2 s_supp[];   // [ny]
@@ -791,9 +796,9 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
     const size_t ssm = (size_t)G.ny * sizeof(short2);
     const bool along = raster_mode == 1 || (raster_mode == 0 && tube_px >= RASTER_ALONG_K_MIN_PX);
     if (along)
-        k_raster<true><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, fan_len, ntm);
+        k_raster<true><<<dim3(nsm * 16 * (256 / raster_threads<true>()) / ry, ry), raster_threads<true>(), ssm, s>>>(G, V, ends, K, fan_len, ntm);
     else
-        k_raster<false><<<dim3(nsm * 16 / ry, ry), 256, ssm, s>>>(G, V, ends, K, fan_len, ntm);
+        k_raster<false><<<dim3(nsm * 16 * (256 / raster_threads<false>()) / ry, ry), raster_threads<false>(), ssm, s>>>(G, V, ends, K, fan_len, ntm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint32_t KQ = (uint32_t)(G.max_steps + 1);
