@@ -305,9 +305,9 @@ def run_ours(args):
               "ms_per_update": o["ms_per_step"], "stage_ms": o["stage_ms"],
               "time_vs_one_step": o["ms_per_step"] / R["ms_per_step"],
               # the gradient stages, 4 CG start kernels, per iteration a forward (+ reduce) and a
-              # B-image prep (mixed path) per frequency, one partial sum, the adjoint and 3 vector
-              # kernels, then 3 apply/norm kernels
-              "gpu_launches_per_update": (18 + nf + args.cg_iters * (3 * nf + 5) if head == "bf16x3"
+              # B-image prep (mixed path) per frequency, one partial sum, the adjoint (+ its sum over
+              # the set's frequencies on the mixed path) and 3 vector kernels, then 3 apply/norm kernels
+              "gpu_launches_per_update": (19 + nf + args.cg_iters * (3 * nf + 6) if head == "bf16x3"
                                           else 18 + args.cg_iters * (2 * nf + 5))}
     peaks, peak_src = _peaks()
     work = algorithmic_work(cfg, nf)
@@ -382,9 +382,9 @@ def run_ours(args):
         "clocks": R["clocks"], "e2e": R["e2e"],
         # launches per update: positions, fields, trace/raster/resolve (the resolve pass writes
         # the operand images on the mixed path), link, residual keys and the three selection
-        # passes, adjoint (+ one B-image prep per frequency on the mixed path), 4 direction
-        # kernels, forward + reduce per frequency, 4 apply/norm kernels
-        "gpu_launches": (19 + 3 * nf) * args.steps if tc else (19 + 2 * nf) * args.steps,
+        # passes, adjoint (+ one B-image prep per frequency and the sum over the set's frequencies
+        # on the mixed path), 4 direction kernels, forward + reduce per frequency, 4 apply/norm kernels
+        "gpu_launches": (20 + 3 * nf) * args.steps if tc else (19 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
     if tuned:

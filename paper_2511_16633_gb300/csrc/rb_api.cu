@@ -359,8 +359,9 @@ size_t rb_ws_layout(const rb_geometry* g, int n_freq, rb_precision prec, WsLayou
     L->part = o; o = align256(o + (size_t)(RB_MAX_FREQ + 2) * 256 * 8);
     L->fwd = o; o = align256(o + (tcp ? 0 : (size_t)rb_fwd_chunks_for((int)npix) * ne * ne * 8));
     L->tcimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_b_images_bytes(g->n_elem) : 0));
-    // exact G per persistent CTA, then its |G|^2 A slices (bf16 hi and lo)
-    L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * (8 + 4) : 0));
+    // exact G per persistent CTA, then its |G|^2 A slices (bf16 hi and lo), then (Re g, H)
+    // of each frequency of the set for the adjoint's sums over the set
+    L->gscr = o; o = align256(o + (tcp ? (size_t)RB_TC_MAX_CTAS * ne * 128 * (8 + 4) + nf * npix * 8 : 0));
     // two of them on the update path: one frequency's reduce runs beside the next one's forward
     L->tcfwd = o; o = align256(o + (tcp ? 2 * align256(tc_forward_partial_bytes(g->n_elem, RB_TC_MAX_CTAS)) : 0));
     L->aimg = o; o = align256(o + (tcp ? (size_t)n_freq * tc_aimage_elems(g->n_elem, (int)npix) * 2 : 0));

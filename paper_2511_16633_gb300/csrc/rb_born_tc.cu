@@ -83,6 +83,7 @@ struct TcArgs {
     float* h_out;              // [n_freq][npix] or null
     float* gsum;               // [npix] or null (sum over w of Re g)
     float* hsum;               // [npix] or null
+    float2* fpart;             // [n_freq][npix] (Re g, H) of each frequency for k_adjoint_sums, or null
     uint32_t* counters;
     int n_tiles;
     uint32_t tmem_cols;
@@ -273,17 +274,19 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
     tc::fence_after();
     const uint32_t tmem = s_tmem;
     __nv_bfloat16* vimg = A.vimg + (size_t)blockIdx.x * (size_t)(n / 32) * (2 * TP * 32);
-    const int my_tiles = (int)blockIdx.x < A.n_tiles ? (A.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int n_items = A.n_tiles * A.F.n;
+    const int my_items = (int)blockIdx.x < n_items ? (n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // slices of this CTA (a few thousand: 32-bit counters, stage and phase advanced
     // incrementally, no divisions in the loops)
-    const int total = my_tiles * A.F.n * npass * per;
+    const int total = my_items * npass * per;
     const size_t img_u = (size_t)n2 * 16, img_w = (size_t)n * 32;  // bf16 per hi (or lo) / W image slice
     auto stage = [&](int s) { return smem + (size_t)s * ST_BYTES; };
 
     if (warp == NPROD / 32 + 1) {
         // ------------------------------ loader ------------------------------
         if (lane == 0) {
-            int ql = 0, s = 0, j = 0, fw = 0, pass = 0, tile = blockIdx.x;
+            int ql = 0, s = 0, j = 0, pass = 0, item = blockIdx.x;
+            int tile = item / A.F.n, fw = item - tile * A.F.n;
             uint32_t ph = 0, vrp = 0;
             bool err = false;
             // the operand image streams through L2 once per launch: first out, so that it does
@@ -357,7 +360,9 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                     j = 0;
                     if (++pass == npass) {
                         pass = 0;
-                        if (++fw == A.F.n) { fw = 0; tile += gridDim.x; }
+                        item += gridDim.x;
+                        tile = item / A.F.n;
+                        fw = item - tile * A.F.n;
                     }
                 }
             }
@@ -471,11 +476,12 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
             __syncwarp();
             if (lane == 0 && !err) tc::mbar_arrive(tc::smem_u32(&s_acc_empty));
         };
-        for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
+        // items (tile, frequency), item = tile F.n + fw, dealt to the CTAs in turn
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            const int tile = item / A.F.n, fw = item - (item / A.F.n) * A.F.n;
             const int px = tile * TP + (int)p;
             const bool valid = px < G.npix;
-            float acc_g = 0.f, acc_h = 0.f;
-            for (int fw = 0; fw < A.F.n; ++fw) {
+            {
                 const FreqC fc = A.F.f[fw];
                 float fg_r = 0.f, fg_i = 0.f, fh = 0.f;   // this frequency's g and H, summed over the passes
                 for (int pass = 0; pass < npass; ++pass) {
@@ -580,18 +586,14 @@ __global__ void __launch_bounds__(NTHR_A, 1) k_adjoint_tc(TcArgs A) {
                 if (h == 0) fh += (hh + s_red[2][0][p] + s_red[2][1][p] + s_red[2][2][p]) * fc.w4;
                 }   // passes
                 if (err) break;
-                if (h == 0) {
-                    if (valid && A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(fg_r, fg_i);
-                    if (valid && A.h_out) A.h_out[(size_t)fw * G.npix + px] = fh;
-                    acc_g += fg_r;
-                    acc_h += fh;
+                if (h == 0 && valid) {
+                    if (A.g_out) A.g_out[(size_t)fw * G.npix + px] = make_float2(fg_r, fg_i);
+                    if (A.h_out) A.h_out[(size_t)fw * G.npix + px] = fh;
+                    // this frequency's Re g and H for the sums over the set (k_adjoint_sums)
+                    if (A.fpart) A.fpart[(size_t)fw * G.npix + px] = make_float2(fg_r, fh);
                 }
             }
             if (err) break;
-            if (valid && h == 0) {
-                if (A.gsum) A.gsum[px] = acc_g;
-                if (A.hsum) A.hsum[px] = acc_h;
-            }
         }
     }
     tc::fence_before();
@@ -1018,6 +1020,24 @@ cudaError_t launch_tables_images(const GeoDev& G, const rb_cell* tables, const f
     return cudaGetLastError();
 }
 
+namespace {
+// gsum = sum over the set's frequencies of Re g, hsum of H, added in frequency order (the
+// order a CTA taking all frequencies of its tile in turn would use).
+__global__ void k_adjoint_sums(const float2* __restrict__ fpart, int n_freq, int npix, float* __restrict__ gsum,
+                               float* __restrict__ hsum) {
+    for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < npix; px += gridDim.x * blockDim.x) {
+        float g = 0.f, h = 0.f;
+        for (int fw = 0; fw < n_freq; ++fw) {
+            const float2 v = fpart[(size_t)fw * npix + px];
+            g += v.x;
+            h += v.y;
+        }
+        if (gsum) gsum[px] = g;
+        if (hsum) hsum[px] = h;
+    }
+}
+}  // namespace
+
 cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& F, const void* images, float2* gscr,
                               int n_ctas, float2* g_out, float* h_out, float* gsum, float* hsum, uint32_t* counters,
                               cudaStream_t s, int variant) {
@@ -1038,6 +1058,7 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
     A.h_out = h_out;
     A.gsum = gsum;
     A.hsum = hsum;
+    A.fpart = nullptr;
     A.counters = counters;
     A.n_tiles = (G.npix + TP - 1) / TP;
     A.n_e = n < 256 ? n : 256;
@@ -1064,8 +1085,13 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
         }
         return cudaGetLastError();
     }
+    // the CTAs take (tile, frequency) items in turn, so the sums over the set go through
+    // the per-frequency buffer that follows the per-CTA scratch in the workspace
+    if (gsum || hsum)
+        A.fpart = (float2*)(A.vimg + (size_t)RB_TC_MAX_CTAS * n * 256);
     const int sm = NST * (int)ST_BYTES;
-    const int grid = n_ctas < A.n_tiles ? n_ctas : A.n_tiles;
+    const int n_items = A.n_tiles * F.n;
+    const int grid = n_ctas < n_items ? n_ctas : n_items;
     if (A.npass == 1) {
         e = cudaFuncSetAttribute(k_adjoint_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return e;
@@ -1075,6 +1101,9 @@ cudaError_t launch_adjoint_tc(const GeoDev& G, const void* aimg, const FreqSet& 
         if (e != cudaSuccess) return e;
         k_adjoint_tc<true><<<grid, NTHR_A, sm, s>>>(A);
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !A.fpart) return e;
+    k_adjoint_sums<<<(G.npix + 255) / 256, 256, 0, s>>>(A.fpart, F.n, G.npix, gsum, hsum);
     return cudaGetLastError();
 }
 

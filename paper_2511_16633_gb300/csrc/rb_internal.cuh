@@ -257,7 +257,8 @@ struct WsLayout {
     size_t part;       // reduction partials: [n_part] double
     size_t fwd;        // forward partial sums: [n_chunks][n_elem][n_elem] float2
     size_t tcimg;      // tensor-core path: bf16 B-operand images, [n_freq][image]
-    size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2
+    size_t gscr;       // tensor-core path: exact G per persistent CTA, [RB_TC_MAX_CTAS][n_elem][128] float2,
+                       // the |G|^2 slices, then (Re g, H) per frequency [n_freq][npix] float2
     size_t tcfwd;      // tensor-core path: partial D blocks of the forward
     size_t aimg;       // tensor-core path: A operand images of the adjoint, [n_freq][...] bf16
     size_t cgv;        // CG variant: x, r, p, q vectors, [4][npix] float
