@@ -127,8 +127,9 @@ ADJ_ISSUE_RATIO = 2.8
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_adjoint_tc launch on breast512 from
 # one ncu capture (--metrics, one pass) of the kernel as it stands in ADJ_TRAFFIC_SOURCE;
 # set to None whenever the kernel changes until it is captured again.
-ADJ_TRAFFIC_BYTES = None
-ADJ_TRAFFIC_SOURCE = None
+ADJ_TRAFFIC_BYTES = 2157880064 + 1073678080
+ADJ_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one k_adjoint_tc launch on "
+                      "breast512, kernel as of commit e24a358 (profiles/launches_breast512_bf16x3.md)")
 
 
 def rays_grid_bytes(cfg, n_vertices):
