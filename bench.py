@@ -207,11 +207,6 @@ def run_ours(args):
         c = c0.clone()
         dc = torch.empty_like(c)
         diag = torch.zeros(48, dtype=torch.uint8, device=dev)
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)]
-        for e in evs:
-            e.record(stream)
-        ev_arr = rb.stage_event_array(evs)
-
         def step(k, events=None):
             j = k % nsets
             # the one-step update sweeps the sets from c_init; the CG variant starts every
@@ -233,6 +228,13 @@ def run_ours(args):
         stage_ms = np.zeros(nst)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+        # stage events of their own for every timed step, so the steps are queued back to back
+        # (no synchronisation between them) and the stage times are read after the last
+        step_evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)] for _ in range(n_steps)]
+        for es in step_evs:
+            for e in es:
+                e.record(stream)
+        step_arrs = [rb.stage_event_array(es) for es in step_evs]
         clocks = ClockSampler(local) if with_clocks else None
         if world > 1:
             torch.distributed.barrier()
@@ -240,13 +242,12 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k in range(n_steps):
             starts[k].record(stream)
-            step(args.warmup + k, ev_arr)
+            step(args.warmup + k, step_arrs[k])
             ends[k].record(stream)
-            # the stage events are reused every step: read them after this step completes
-            ends[k].synchronize()
-            for s_ in range(nst):
-                stage_ms[s_] += evs[2 * s_].elapsed_time(evs[2 * s_ + 1])
         torch.cuda.synchronize()
+        for k in range(n_steps):
+            for s_ in range(nst):
+                stage_ms[s_] += step_evs[k][2 * s_].elapsed_time(step_evs[k][2 * s_ + 1])
         if world > 1:
             torch.distributed.barrier()
         wall = time.perf_counter() - t0
