@@ -308,8 +308,8 @@ def run_ours(args):
               # the gradient stages, 4 CG start kernels, per iteration a forward (+ reduce) and a
               # B-image prep (mixed path) per frequency, one partial sum, the adjoint (+ its sum over
               # the set's frequencies on the mixed path) and 3 vector kernels, then 3 apply/norm kernels
-              "gpu_launches_per_update": (19 + nf + args.cg_iters * (3 * nf + 6) if head == "bf16x3"
-                                          else 18 + args.cg_iters * (2 * nf + 5))}
+              "gpu_launches_per_update": (20 + nf + args.cg_iters * (3 * nf + 6) if head == "bf16x3"
+                                          else 19 + args.cg_iters * (2 * nf + 5))}
     peaks, peak_src = _peaks()
     work = algorithmic_work(cfg, nf)
     st = R["stage_ms"]
@@ -381,11 +381,11 @@ def run_ours(args):
         "roofline": roof, "roofline_contractions": {"adjoint": roof_adj, "forward": roof_fwd},
         "roofline_images": roof_img, "roofline_rays_grid": roof_rg,
         "clocks": R["clocks"], "e2e": R["e2e"],
-        # launches per update: positions, fields, trace/raster/resolve (the resolve pass writes
+        # launches per update: positions, fields, keys reset, trace/raster/resolve (the resolve pass writes
         # the operand images on the mixed path), link, residual keys and the three selection
         # passes, adjoint (+ one B-image prep per frequency and the sum over the set's frequencies
         # on the mixed path), 4 direction kernels, forward + reduce per frequency, 4 apply/norm kernels
-        "gpu_launches": (20 + 3 * nf) * args.steps if tc else (19 + 2 * nf) * args.steps,
+        "gpu_launches": (21 + 3 * nf) * args.steps if tc else (20 + 2 * nf) * args.steps,
         "diag_last": {k: R["diag"][k] for k in ("dc_norm", "alpha", "lost_rays", "holes", "kept", "zeroed")},
     }
     if tuned:

@@ -316,6 +316,9 @@ cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends,
                          cudaStream_t s, cudaEvent_t traced = nullptr, cudaEvent_t keys_ready = nullptr,
                          const FreqSet* F = nullptr, void* images = nullptr, int raster_mode = 0,
                          uint32_t* fan_len = nullptr);
+// Resets the first-arrival keys (n_elem * npix u64) to all ones, on s, with a fill
+// narrow enough to run beside the tracer (for the keys_ready form of launch_trace).
+cudaError_t launch_keys_reset(const GeoDev& G, void* keys, cudaStream_t s);
 size_t rb_verts_bytes(int n_elem, int n_rays, int max_steps);
 cudaError_t launch_green_out(const GeoDev& G, const rb_cell* tables, const float* c, const FreqSet& F,
                              float2* g_out, cudaStream_t s);

@@ -745,7 +745,26 @@ __global__ void __launch_bounds__(256) k_resolve_images(GeoDev G, const Vtx* __r
     if ((threadIdx.x & 31) == 0 && holes) atomicAdd(counters + CNT_HOLES, holes);
 }
 
+// All-ones fill of the first-arrival keys with one CTA per SM, grid-stride, 16-byte
+// stores.  Run on a side stream beside the tracer: a CTA this small co-resides with the
+// tracer's CTAs instead of taking their slots, as a full-width fill does.
+__global__ void __launch_bounds__(256) k_keys_reset(uint4* K, size_t n16) {
+    const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+        K[i] = ones;
+}
+
 }  // namespace
+
+cudaError_t launch_keys_reset(const GeoDev& G, void* keys, cudaStream_t s) {
+    const size_t bytes = (size_t)G.n_elem * G.npix * sizeof(unsigned long long);
+    if (((uintptr_t)keys & 15) || (bytes & 15)) return cudaMemsetAsync(keys, 0xff, bytes, s);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm = 148;
+    k_keys_reset<<<nsm, 256, 0, s>>>((uint4*)keys, bytes / 16);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_trace(const GeoDev& G, const float4* cells, rb_ray_end* ends, const rb_rays* samples,
                          void* keys, rb_cell* tables, void* verts, const float* c, uint32_t* counters,
