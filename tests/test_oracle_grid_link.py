@@ -5,6 +5,8 @@
   J equal to the distance within the same kind of bound.
 * Caustic medium: the first-arrival winner at sampled pixels equals a brute
   force over every triangle of the fan (no bounding boxes, no early exits).
+* The sampled-pixel tables and Green's functions (the oracle of the full-size GPU
+  tests) equal the full ones at the listed pixels, bit for bit.
 * Linking: exact reciprocity p[e,r] = p[r,e] in a homogeneous medium (the
   fan geometry is mirror-symmetric), the linked traveltime equal to the chord
   time, and in a heterogeneous medium a reciprocity error that falls as the
@@ -23,7 +25,7 @@ import numpy as np
 import pytest
 
 import rbgen
-from oracle import geometry, grid, link, rays
+from oracle import geometry, green, grid, link, rays
 from oracle.rays import VQ, VT, VX, VY
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "acquisition.json")
@@ -106,6 +108,28 @@ def test_first_arrival_matches_brute_force_in_caustic_medium():
     assert multi == 2
 
 
+def test_sampled_pixel_tables_and_green_equal_the_full_ones():
+    """grid_pixels and green(..., pix) (the sampled forms the full-size GPU tests use as
+    their oracle) select from the full first-arrival tables exactly: same winner, Q, L,
+    kappa, triangle and hole flag at every listed pixel, in the listed order."""
+    cfg = rbgen.tiny()
+    g = geometry.from_config(cfg)
+    X, Y = geometry.pixel_centres(g)
+    c = 1480.0 - 300.0 * np.exp(-((X - 0.004) ** 2 + (Y + 0.003) ** 2) / (2 * 0.008 ** 2))
+    al = np.zeros_like(c)
+    full = grid.grid(g, c, al)
+    npix = g.nx * g.ny
+    rng = np.random.default_rng(11)
+    pix = np.concatenate([[npix - 1, 0], rng.choice(npix, 97, replace=False), [npix // 2, npix // 2]])
+    part = grid.grid_pixels(g, c, al, pix)
+    assert part.n_lost == full.n_lost
+    for name in ("t_res", "q", "l", "kappa", "tri", "hit"):
+        assert np.array_equal(getattr(part, name), getattr(full, name)[:, pix]), name
+    assert part.hit.any() and not part.hit.all()   # support and outside both sampled
+    f = cfg.freqs_hz[0]
+    assert np.array_equal(green.green(g, part, c, f, pix=pix), green.green(g, full, c, f)[:, pix])
+
+
 def test_link_reciprocity_homogeneous_exact():
     cfg = rbgen.tiny()
     g = geometry.from_config(cfg)
@@ -165,7 +189,6 @@ def test_ray_data_in_water_is_the_hankel_green_function(f):
     falls by exp(-K_a alpha0 f^y r) along the chord."""
     from scipy.special import hankel1
 
-    from oracle import green
     cfg = rbgen.tiny(n_rays=256)
     g = geometry.from_config(cfg)
     c = np.full((g.ny, g.nx), g.c_ref)
