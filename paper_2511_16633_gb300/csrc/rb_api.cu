@@ -129,9 +129,11 @@ int tc_ctas() {
         if ((x) != cudaSuccess) return RB_ERR_CUDA; \
     } while (0)
 
-// A side stream per (device, caller stream) for the work of an update that does not wait
-// for the gridding (linking, residuals, data weights, B images), forked after the ray
-// trace and joined before the adjoint, so that updates issued on different streams (the
+// A side stream per (device, caller stream) for the work of an update that need not sit
+// on the caller's stream: the first-arrival keys reset beside the ray trace, the work
+// that does not wait for the gridding (linking, residuals, data weights, B images),
+// forked after the trace and joined before the adjoint, and each frequency's forward
+// reduce beside the next forward; so that updates issued on different streams (the
 // requests of a server) do not queue behind one another's side work.  Created on first
 // use and kept for the process (at most kMaxSide; beyond that, callers share the entries
 // of their device, which stays correct and only serialises their side work); the mutex
